@@ -1,0 +1,190 @@
+/*
+ * rwpc.h -- C ABI of the GB300 random-walk preconditioner library (librwpc.so).
+ *
+ * Method: H. Qian, S. S. Sapatnekar, "Stochastic Preconditioning for Iterative
+ * Linear Equation Solvers".  For an R-matrix A (symmetric M-matrix, irreducibly
+ * diagonally dominant, Sec. 1) the library runs the random-walk game of Sec. 2.1
+ * (transition -A_ij/A_ii, absorption at the diagonal excess, Eq. map) with rows
+ * 0..k-1 as homes for walks started at row k (Sec. 2.2.1), counts per start row
+ * the journey record of Sec. 3.1 (walks M, end counts H, returns J), and turns
+ * it into an incomplete factor with the one-step-exact estimator of Sec. 5.2
+ * (Eqs. newy, newz) and a post-processing threshold drop (footnote of Sec. 4).
+ * The factor is applied inside preconditioned conjugate gradients (Algorithm 1).
+ *
+ * Factor convention.  Indices are 0-based and in A's own order.  The library
+ * returns Y (unit lower triangular; only the strict lower part is stored, CSR,
+ * columns ascending) and D (diagonal) with  A ~= Y^T diag(D) Y.  In the paper's
+ * notation this is L_rev(A) = rev(Y)^T and D_rev(A) = rev(D) (Eqs. y and d): the
+ * paper's reversal is a relabelling only, so no data is reordered.
+ *
+ * Lifetime.  A factor allocates and frees through its context: destroy every
+ * factor of a context before the context itself.
+ *
+ * Memory.  Every pointer inside rw_csr and every d_* argument is a DEVICE
+ * pointer owned by the caller, on the device current when the context was made.
+ * Factor storage and scratch are allocated by the library through the
+ * context's allocator (cudaMallocAsync on the context stream by default) and
+ * released by rw_factor_destroy / at the end of the call.  Host pointers are
+ * marked h_*.
+ *
+ * Streams.  All device work of a call is enqueued on the context's stream.
+ * Calls return after synchronising that stream whenever they return host data
+ * (status, counts); device outputs are complete when the call returns.
+ *
+ * Errors.  Every entry point returns an rw_status (0 = RW_OK, negative =
+ * error); no exception crosses the ABI.  rw_last_error() gives a message for
+ * the last failing call of the calling thread.
+ */
+#ifndef RWPC_H
+#define RWPC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RW_OK = 0,
+    RW_ERR_ARG = -1,            /* bad argument (null pointer, size, budget < 1, ...) */
+    RW_ERR_NOT_RMATRIX = -2,    /* A is not in the required R-matrix form (see rw_csr) */
+    RW_ERR_WALK_CAP = -3,       /* a walk reached rw_options.max_steps hops */
+    RW_ERR_ALLOC = -4,          /* the allocator failed */
+    RW_ERR_NO_CONVERGENCE = -5, /* PCG reached max_iter (tol > 0) */
+    RW_ERR_BREAKDOWN = -6,      /* PCG found p.Ap <= 0 */
+    RW_ERR_CUDA = -7,           /* a CUDA runtime call failed */
+    RW_ERR_TIMEOUT = -8,        /* a bounded device-side wait gave up */
+    RW_ERR_CAPACITY = -9        /* a per-row budget exceeds the merge capacity */
+} rw_status;
+
+typedef enum { RW_FP64 = 0, RW_FP32_MIXED = 1 } rw_precision;
+
+/* Square CSR matrix on the device.  Requirements (checked, RW_ERR_NOT_RMATRIX):
+ * row_ptr[0] = 0, non-decreasing, row_ptr[n] = nnz; columns strictly
+ * ascending within a row and in [0, n); the diagonal is stored and positive;
+ * every stored off-diagonal is strictly negative (no explicit zeros); every
+ * row is diagonally dominant: A_ii + sum_{j != i} A_ij >= -1e-12 A_ii.
+ * Symmetry and irreducibility are the caller's promise (not checked: a
+ * component without ground makes walks run to the step cap, RW_ERR_WALK_CAP). */
+typedef struct {
+    int32_t n;
+    int64_t nnz;
+    const int32_t* row_ptr; /* [n+1] */
+    const int32_t* col;     /* [nnz] */
+    const double* val;      /* [nnz] */
+} rw_csr;
+
+/* Optional allocator, e.g. a framework's caching allocator.  alloc returns a
+ * device pointer aligned to 256 bytes or NULL; free releases it.  The stream
+ * is the context stream (cudaStream_t passed as void*). */
+typedef void* (*rw_alloc_fn)(void* user, size_t bytes, void* stream);
+typedef void (*rw_free_fn)(void* user, void* ptr, size_t bytes, void* stream);
+
+typedef struct {
+    uint64_t max_steps;      /* walk step cap (default 1 << 24) */
+    int32_t keep_records;    /* 1: keep the per-walk records in the factor (default 0) */
+    int32_t record_lengths;  /* 1: records hold walk lengths instead of returns (default 0) */
+    int32_t store_fp32;      /* 1: also keep FP32 copies of Y, Y^T and D (default 1) */
+    int32_t refine_every;    /* FP32 PCG: true-residual replacement period (default 50) */
+    int32_t walk_blocks_per_sm; /* 0 = from the occupancy calculator */
+    int32_t timing;          /* 1: record per-phase device times (default 1) */
+} rw_options;
+
+typedef struct rw_context rw_context;
+typedef struct rw_factor rw_factor;
+
+/* Read-only view of a factor.  All arrays are device pointers owned by the
+ * factor (valid until rw_factor_destroy). */
+typedef struct {
+    int32_t n;
+    int64_t nnz;               /* stored entries of Y (strict lower) */
+    const int64_t* y_row_ptr;  /* [n+1] */
+    const int32_t* y_col;      /* [nnz], ascending, < row */
+    const double* y_val;       /* [nnz] */
+    const double* d;           /* [n] */
+    const int64_t* yt_row_ptr; /* Y^T in CSR: row i holds (k, Y_ki), k > i, ascending */
+    const int32_t* yt_col;
+    const double* yt_val;
+    const float* y_val32;      /* FP32 copies (NULL unless store_fp32) */
+    const float* yt_val32;
+    const float* d32;
+    const uint32_t* walks;     /* [n] M'_k: walks from row k (0 for exact rows) */
+    const uint64_t* visits;    /* [n] J'_k: visits to k by walks from k, start included */
+    const uint32_t* ground;    /* [n] G'_k: walks from k absorbed at ground */
+    const int32_t* walk_rows;  /* [n_walk_rows] rows that ran walks, ascending */
+    const int64_t* walk_base;  /* [n_walk_rows+1] first record of each walk row */
+    const int32_t* records;    /* [2*total_walks] (end, returns|length) or NULL; end -1 = ground */
+    int32_t n_walk_rows;
+    int64_t total_walks;
+    uint64_t total_hops;       /* sum of walk lengths (hops), first step included */
+    int32_t fwd_levels;        /* depth of the DAG of Y z = v */
+    int32_t bwd_levels;        /* depth of the DAG of Y^T w = r */
+    float phase_ms[8];         /* tables, walk, merge, emit, transpose, levels, fp32, total */
+} rw_factor_desc;
+
+typedef struct {
+    int32_t iterations;        /* max over right-hand sides */
+    double rel_residual;       /* max over right-hand sides of ||b - A x|| / ||b|| (true) */
+    float solve_ms;            /* device time of the solve */
+} rw_pcg_stats;
+
+/* Fill *opt with the defaults listed in rw_options. */
+void rw_options_default(rw_options* opt);
+
+/* Create a context on the current device.  stream: cudaStream_t (NULL = the
+ * legacy default stream).  alloc/free: both NULL for cudaMallocAsync /
+ * cudaFreeAsync on the stream.  opt may be NULL (defaults). */
+rw_status rw_context_create(rw_context** out, void* stream, rw_alloc_fn alloc, rw_free_fn free_fn,
+                            void* user, const rw_options* opt);
+void rw_context_destroy(rw_context* ctx);
+
+/* Precondition step of Algorithm 1 with a uniform budget: walks_per_row walks
+ * from every row that has an upper neighbour (rows without one are exact and
+ * use no walks, Sec. 5.2).  Draw s of walk w from row k is word (s mod 4) of
+ * Philox-4x32-10 with counter (s/4, w, k, tag) and key (lo32(seed), hi32(seed)),
+ * tag = (matrix_index << 2), matrix_index = 0 here.  Entries with
+ * |Y_ki| < drop_tol are dropped (drop_tol >= 0; 0 keeps every entry).
+ * On success *out receives a new factor (rw_factor_destroy releases it). */
+rw_status rw_build_factor(rw_context* ctx, const rw_csr* A, uint32_t walks_per_row, uint64_t seed,
+                          double drop_tol, rw_factor** out);
+
+/* Same with per-row budgets: d_budget[k] walks from row k (device, [n]; read
+ * only for rows with an upper neighbour, each of which needs >= 1). */
+rw_status rw_build_factor_budget(rw_context* ctx, const rw_csr* A, const uint32_t* d_budget,
+                                 uint64_t seed, double drop_tol, rw_factor** out);
+
+rw_status rw_factor_view(const rw_factor* F, rw_factor_desc* desc);
+void rw_factor_destroy(rw_factor* F);
+
+/* Solve step of Algorithm 1: PCG with M = Y^T diag(D) Y for nrhs right-hand
+ * sides at once (1 <= nrhs <= 16).  d_b, d_x: node-major [n, nrhs] FP64
+ * (entry i of right-hand side r at i*nrhs + r).  x starts at 0.  Each
+ * right-hand side stops when its true residual ||b - A x||_2 < tol ||b||_2
+ * (the tolerance of the paper's Sec. 6); tol = 0 runs exactly max_iter
+ * iterations.  prec = RW_FP32_MIXED: FP32 vectors, SpMV, factor and triangular
+ * solves; FP64 dot products, alpha/beta and x, and the residual replaced by an
+ * FP64 b - A x every refine_every iterations.  Returns RW_ERR_NO_CONVERGENCE
+ * (x still written) if some right-hand side did not reach tol in max_iter.
+ * h_iters/h_relres (host, [nrhs], may be NULL) receive per right-hand side
+ * iterations and true relative residuals. */
+rw_status pcg_solve(rw_context* ctx, const rw_csr* A, const rw_factor* F, const double* d_b,
+                    double* d_x, int32_t nrhs, double tol, int32_t max_iter, rw_precision prec,
+                    rw_pcg_stats* stats, int32_t* h_iters, double* h_relres);
+
+/* z = (Y^T diag(D) Y)^-1 r for nrhs node-major right-hand sides (FP64): the
+ * preconditioner application inside pcg_solve (backward solve with Y^T,
+ * scaling by 1/D, forward solve with Y). */
+rw_status rw_precond_apply(rw_context* ctx, const rw_factor* F, const double* d_r, double* d_z,
+                           int32_t nrhs);
+
+/* y = A x for nrhs node-major vectors (FP64). */
+rw_status rw_spmv(rw_context* ctx, const rw_csr* A, const double* d_x, double* d_y, int32_t nrhs);
+
+const char* rw_status_string(rw_status s);
+const char* rw_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RWPC_H */

@@ -90,6 +90,8 @@ def _load():
                             ctypes.c_double, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                             i32p, f64p]
     lib.orc_pcg.restype = ctypes.c_int
+    lib.orc_precond_apply.argtypes = [ctypes.c_int32, i64p, i32p, f64p, f64p, f64p, f64p]
+    lib.orc_precond_apply.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -211,6 +213,26 @@ def reuse_trace(seq, nlabels):
     if m < 0:
         raise OracleError(m, "reuse trace")
     return dM, dJ, list(zip(hs[:m].tolist(), he[:m].tolist()))
+
+
+def precond_apply(F, r):
+    """z = (Y^T diag(D) Y)^-1 r for one vector (FP64)."""
+    lib = _load()
+    n = len(F["D"])
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    z = np.zeros(n)
+    yrp = np.ascontiguousarray(F["rowptr"], dtype=np.int64)
+    ycol = np.ascontiguousarray(F["col"], dtype=np.int32)
+    yval = np.ascontiguousarray(F["val"], dtype=np.float64)
+    if ycol.size == 0:
+        ycol, yval = np.zeros(1, np.int32), np.zeros(1)
+    D = np.ascontiguousarray(F["D"], dtype=np.float64)
+    rc = lib.orc_precond_apply(n, _ptr(yrp, ctypes.c_int64), _ptr(ycol, ctypes.c_int32),
+                               _ptr(yval, ctypes.c_double), _ptr(D, ctypes.c_double),
+                               _ptr(r, ctypes.c_double), _ptr(z, ctypes.c_double))
+    if rc:
+        raise OracleError(rc, "oracle precond")
+    return z
 
 
 def pcg(A, F, b, tol, max_iter, mixed=False, refine_every=50):

@@ -727,6 +727,15 @@ done:
     return rc;
 }
 
+int orc_precond_apply(int32_t n, const int64_t* Yrp, const int32_t* Ycol, const double* Yval,
+                      const double* D, const double* r, double* z) {
+    double* w = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    if (!w) return -4;
+    precond64(n, Yrp, Ycol, Yval, D, r, w, z);
+    free(w);
+    return 0;
+}
+
 int orc_pcg(int32_t n, const int32_t* Arp, const int32_t* Acol, const double* Aval,
             const int64_t* Yrp, const int32_t* Ycol, const double* Yval, const double* D,
             const double* b, double* x, double tol, int32_t max_iter, int32_t mixed,

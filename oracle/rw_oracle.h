@@ -72,6 +72,11 @@ void orc_factor_free(orc_factor* f);
 int32_t orc_reuse_trace(const int32_t* seq, int32_t len, int32_t nlabels,
                         int64_t* dM, int64_t* dJ, int32_t* hs, int32_t* he, int32_t cap);
 
+/* z = (Y^T diag(D) Y)^-1 r in FP64: backward substitution with Y^T, scaling by
+ * 1/D, forward substitution with Y (the preconditioner of Algorithm 1). */
+int orc_precond_apply(int32_t n, const int64_t* Yrp, const int32_t* Ycol, const double* Yval,
+                      const double* D, const double* r, double* z);
+
 /*
  * Preconditioned conjugate gradients with M = Y^T D Y (Algorithm 1, "solve").
  * One right-hand side.  mixed=0: FP64 throughout.  mixed=1: FP32 vectors, SpMV,

@@ -1,0 +1,356 @@
+"""Random-walk incomplete LDL^T preconditioner and PCG on GB300 (sm_103a).
+
+Python binding of ``librwpc.so``: argument marshalling only.  Every step of the
+factor construction and of the solve runs in the library's CUDA kernels; PyTorch
+provides device memory (the tensors passed in and out) and streams.  There is no
+CPU fallback: if the library is not built, ``load()`` raises.
+
+The functions carry the C ABI's names (see ``include/rwpc.h``):
+``rw_context_create``, ``rw_build_factor``, ``rw_build_factor_budget``,
+``rw_factor_view``, ``rw_factor_destroy``, ``pcg_solve``, ``rw_precond_apply``,
+``rw_spmv``, ``rw_status_string``, ``rw_last_error``.
+
+Method: Qian & Sapatnekar, "Stochastic Preconditioning for Iterative Linear
+Equation Solvers" -- walk game of Sec. 2.1, journey record of Sec. 3.1,
+one-step-exact estimator of Sec. 5.2, PCG of Algorithm 1.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import weakref
+
+from . import _build
+
+__all__ = [
+    "load", "RwError", "CSR", "Context", "Factor", "rw_options_default", "rw_context_create",
+    "rw_context_destroy", "rw_build_factor", "rw_build_factor_budget", "rw_factor_view",
+    "rw_factor_destroy", "pcg_solve", "rw_precond_apply", "rw_spmv", "rw_status_string",
+    "rw_last_error", "RW_FP64", "RW_FP32_MIXED",
+]
+
+RW_FP64 = 0
+RW_FP32_MIXED = 1
+RW_OK = 0
+STATUS = {0: "RW_OK", -1: "RW_ERR_ARG", -2: "RW_ERR_NOT_RMATRIX", -3: "RW_ERR_WALK_CAP",
+          -4: "RW_ERR_ALLOC", -5: "RW_ERR_NO_CONVERGENCE", -6: "RW_ERR_BREAKDOWN",
+          -7: "RW_ERR_CUDA", -8: "RW_ERR_TIMEOUT", -9: "RW_ERR_CAPACITY"}
+
+_c_void_p = ctypes.c_void_p
+_i32, _i64, _u32, _u64, _f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double
+
+
+class rw_csr_t(ctypes.Structure):
+    _fields_ = [("n", _i32), ("nnz", _i64), ("row_ptr", _c_void_p), ("col", _c_void_p),
+                ("val", _c_void_p)]
+
+
+class rw_options_t(ctypes.Structure):
+    _fields_ = [("max_steps", _u64), ("keep_records", _i32), ("record_lengths", _i32),
+                ("store_fp32", _i32), ("refine_every", _i32), ("walk_blocks_per_sm", _i32),
+                ("timing", _i32)]
+
+
+class rw_factor_desc_t(ctypes.Structure):
+    _fields_ = [("n", _i32), ("nnz", _i64), ("y_row_ptr", _c_void_p), ("y_col", _c_void_p),
+                ("y_val", _c_void_p), ("d", _c_void_p), ("yt_row_ptr", _c_void_p),
+                ("yt_col", _c_void_p), ("yt_val", _c_void_p), ("y_val32", _c_void_p),
+                ("yt_val32", _c_void_p), ("d32", _c_void_p), ("walks", _c_void_p),
+                ("visits", _c_void_p), ("ground", _c_void_p), ("walk_rows", _c_void_p),
+                ("walk_base", _c_void_p), ("records", _c_void_p), ("n_walk_rows", _i32),
+                ("total_walks", _i64), ("total_hops", _u64), ("fwd_levels", _i32),
+                ("bwd_levels", _i32), ("phase_ms", ctypes.c_float * 8)]
+
+
+class rw_pcg_stats_t(ctypes.Structure):
+    _fields_ = [("iterations", _i32), ("rel_residual", _f64), ("solve_ms", ctypes.c_float)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(_c_void_p, _c_void_p, ctypes.c_size_t, _c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, _c_void_p, _c_void_p, ctypes.c_size_t, _c_void_p)
+
+_lib = None
+
+
+class RwError(RuntimeError):
+    def __init__(self, code, where):
+        msg = rw_last_error() if _lib is not None else ""
+        super().__init__(f"{where}: {STATUS.get(code, code)} ({code}): {msg}")
+        self.code = code
+
+
+def load():
+    """Load librwpc.so (built by ``_build.build()``); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"CUDA library not built ({_build.LIB}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(_build.LIB)
+    P = ctypes.POINTER
+    lib.rw_options_default.argtypes = [P(rw_options_t)]
+    lib.rw_options_default.restype = None
+    lib.rw_context_create.argtypes = [P(_c_void_p), _c_void_p, ALLOC_FN, FREE_FN, _c_void_p,
+                                      P(rw_options_t)]
+    lib.rw_context_create.restype = ctypes.c_int
+    lib.rw_context_destroy.argtypes = [_c_void_p]
+    lib.rw_context_destroy.restype = None
+    lib.rw_build_factor.argtypes = [_c_void_p, P(rw_csr_t), _u32, _u64, _f64, P(_c_void_p)]
+    lib.rw_build_factor.restype = ctypes.c_int
+    lib.rw_build_factor_budget.argtypes = [_c_void_p, P(rw_csr_t), _c_void_p, _u64, _f64,
+                                           P(_c_void_p)]
+    lib.rw_build_factor_budget.restype = ctypes.c_int
+    lib.rw_factor_view.argtypes = [_c_void_p, P(rw_factor_desc_t)]
+    lib.rw_factor_view.restype = ctypes.c_int
+    lib.rw_factor_destroy.argtypes = [_c_void_p]
+    lib.rw_factor_destroy.restype = None
+    lib.pcg_solve.argtypes = [_c_void_p, P(rw_csr_t), _c_void_p, _c_void_p, _c_void_p, _i32, _f64,
+                              _i32, ctypes.c_int, P(rw_pcg_stats_t), _c_void_p, _c_void_p]
+    lib.pcg_solve.restype = ctypes.c_int
+    lib.rw_precond_apply.argtypes = [_c_void_p, _c_void_p, _c_void_p, _c_void_p, _i32]
+    lib.rw_precond_apply.restype = ctypes.c_int
+    lib.rw_spmv.argtypes = [_c_void_p, P(rw_csr_t), _c_void_p, _c_void_p, _i32]
+    lib.rw_spmv.restype = ctypes.c_int
+    lib.rw_status_string.argtypes = [ctypes.c_int]
+    lib.rw_status_string.restype = ctypes.c_char_p
+    lib.rw_last_error.argtypes = []
+    lib.rw_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(rc, where):
+    if rc != RW_OK:
+        raise RwError(rc, where)
+
+
+def rw_status_string(code):
+    return load().rw_status_string(code).decode()
+
+
+def rw_last_error():
+    return load().rw_last_error().decode()
+
+
+def rw_options_default(**overrides):
+    o = rw_options_t()
+    load().rw_options_default(ctypes.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+# ---------------------------------------------------------------------------
+# Device CSR held by torch tensors
+# ---------------------------------------------------------------------------
+
+class CSR:
+    """Square CSR on the GPU: rowptr/col int32, val float64 (torch tensors)."""
+
+    def __init__(self, rowptr, col, val):
+        import torch
+        for t, dt in ((rowptr, torch.int32), (col, torch.int32), (val, torch.float64)):
+            if t.dtype != dt or not t.is_cuda or not t.is_contiguous():
+                raise ValueError("CSR wants contiguous CUDA tensors int32/int32/float64")
+        self.rowptr, self.col, self.val = rowptr, col, val
+        self.n = rowptr.numel() - 1
+        self.nnz = col.numel()
+        self._c = rw_csr_t(self.n, self.nnz, rowptr.data_ptr(), col.data_ptr(), val.data_ptr())
+
+    @classmethod
+    def from_host(cls, A, device="cuda"):
+        import torch
+        return cls(torch.as_tensor(A.rowptr, dtype=torch.int32).to(device).contiguous(),
+                   torch.as_tensor(A.col, dtype=torch.int32).to(device).contiguous(),
+                   torch.as_tensor(A.val, dtype=torch.float64).to(device).contiguous())
+
+    @property
+    def c(self):
+        return self._c
+
+
+class _DevArray:
+    def __init__(self, ptr, n, typestr):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False),
+                                         "version": 3, "strides": None}
+
+
+def _dev_tensor(ptr, n, typestr):
+    import torch
+    dt = {"<i4": torch.int32, "<i8": torch.int64, "<u4": torch.int32, "<u8": torch.int64,
+          "<f8": torch.float64, "<f4": torch.float32}[typestr]
+    if not ptr or n == 0:
+        return torch.empty(0, dtype=dt, device="cuda")
+    t = torch.as_tensor(_DevArray(ptr, n, typestr), device="cuda")
+    return t.view(dt) if t.dtype != dt else t
+
+
+# ---------------------------------------------------------------------------
+# Context and factor handles
+# ---------------------------------------------------------------------------
+
+class Context:
+    """A library context bound to the current device and a CUDA stream.
+
+    stream: a torch.cuda.Stream (default: the current stream).  With
+    torch_allocator=True the library allocates its storage through PyTorch's
+    caching allocator; otherwise through cudaMallocAsync on the stream.
+    """
+
+    def __init__(self, stream=None, options=None, torch_allocator=False):
+        import torch
+        lib = load()
+        self.stream = stream or torch.cuda.current_stream()
+        self.options = options or rw_options_default()
+        self._keep = []
+        self._factors = weakref.WeakSet()  # factors free through the context: close them first
+        if torch_allocator:
+            dev = torch.cuda.current_device()
+
+            def _alloc(user, size, stream_ptr):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(size), dev, int(stream_ptr or 0))
+                except Exception:
+                    return None
+
+            def _free(user, ptr, size, stream_ptr):
+                torch.cuda.caching_allocator_delete(ptr)
+
+            af, ff = ALLOC_FN(_alloc), FREE_FN(_free)
+            self._keep += [af, ff]
+        else:
+            af, ff = ALLOC_FN(), FREE_FN()
+        h = _c_void_p()
+        _check(lib.rw_context_create(ctypes.byref(h), _c_void_p(self.stream.cuda_stream), af, ff,
+                                     None, ctypes.byref(self.options)), "rw_context_create")
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            for f in list(self._factors):
+                f.destroy()
+            load().rw_context_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Factor:
+    """Handle to a factor built on the GPU: A ~= Y^T diag(D) Y."""
+
+    def __init__(self, ctx, handle):
+        self.ctx = ctx
+        self.handle = handle
+        ctx._factors.add(self)
+        self.desc = rw_factor_view(self)
+
+    def tensors(self):
+        """Zero-copy torch views of the factor's device arrays (valid while the
+        factor lives)."""
+        d = self.desc
+        n, nnz = d.n, d.nnz
+        out = {
+            "y_row_ptr": _dev_tensor(d.y_row_ptr, n + 1, "<i8"),
+            "y_col": _dev_tensor(d.y_col, nnz, "<i4"),
+            "y_val": _dev_tensor(d.y_val, nnz, "<f8"),
+            "d": _dev_tensor(d.d, n, "<f8"),
+            "yt_row_ptr": _dev_tensor(d.yt_row_ptr, n + 1, "<i8"),
+            "yt_col": _dev_tensor(d.yt_col, nnz, "<i4"),
+            "yt_val": _dev_tensor(d.yt_val, nnz, "<f8"),
+            "walks": _dev_tensor(d.walks, n, "<u4"),
+            "visits": _dev_tensor(d.visits, n, "<u8"),
+            "ground": _dev_tensor(d.ground, n, "<u4"),
+        }
+        if d.y_val32:
+            out["y_val32"] = _dev_tensor(d.y_val32, nnz, "<f4")
+            out["yt_val32"] = _dev_tensor(d.yt_val32, nnz, "<f4")
+            out["d32"] = _dev_tensor(d.d32, n, "<f4")
+        if d.records:
+            out["records"] = _dev_tensor(d.records, 2 * d.total_walks, "<i4")
+            out["walk_rows"] = _dev_tensor(d.walk_rows, d.n_walk_rows, "<i4")
+            out["walk_base"] = _dev_tensor(d.walk_base, d.n_walk_rows + 1, "<i8")
+        return out
+
+    def destroy(self):
+        if self.handle and self.ctx.handle:
+            rw_factor_destroy(self)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+# C ABI entry points (same names)
+# ---------------------------------------------------------------------------
+
+def rw_context_create(stream=None, options=None, torch_allocator=False):
+    return Context(stream, options, torch_allocator)
+
+
+def rw_context_destroy(ctx):
+    ctx.close()
+
+
+def rw_build_factor(ctx, A, walks_per_row, seed, drop_tol):
+    h = _c_void_p()
+    _check(load().rw_build_factor(ctx.handle, ctypes.byref(A.c), int(walks_per_row), int(seed),
+                                  float(drop_tol), ctypes.byref(h)), "rw_build_factor")
+    return Factor(ctx, h)
+
+
+def rw_build_factor_budget(ctx, A, budget, seed, drop_tol):
+    """budget: CUDA int32/uint32 tensor [n] of walks per row."""
+    h = _c_void_p()
+    _check(load().rw_build_factor_budget(ctx.handle, ctypes.byref(A.c), _c_void_p(budget.data_ptr()),
+                                         int(seed), float(drop_tol), ctypes.byref(h)),
+           "rw_build_factor_budget")
+    return Factor(ctx, h)
+
+
+def rw_factor_view(F):
+    d = rw_factor_desc_t()
+    _check(load().rw_factor_view(F.handle, ctypes.byref(d)), "rw_factor_view")
+    return d
+
+
+def rw_factor_destroy(F):
+    load().rw_factor_destroy(F.handle)
+    F.handle = None
+
+
+def pcg_solve(ctx, A, F, b, x, tol, max_iter, prec=RW_FP64):
+    """b, x: CUDA float64 tensors [n] or [n, nrhs] (node-major).  Returns
+    (status, stats, iterations per rhs, true relative residual per rhs);
+    raises on errors other than RW_ERR_NO_CONVERGENCE."""
+    import numpy as np
+    nrhs = 1 if b.dim() == 1 else b.shape[1]
+    st = rw_pcg_stats_t()
+    its = np.zeros(nrhs, np.int32)
+    rel = np.zeros(nrhs, np.float64)
+    rc = load().pcg_solve(ctx.handle, ctypes.byref(A.c), F.handle, _c_void_p(b.data_ptr()),
+                          _c_void_p(x.data_ptr()), nrhs, float(tol), int(max_iter), int(prec),
+                          ctypes.byref(st), its.ctypes.data_as(_c_void_p),
+                          rel.ctypes.data_as(_c_void_p))
+    if rc not in (RW_OK, -5):
+        raise RwError(rc, "pcg_solve")
+    return rc, st, its, rel
+
+
+def rw_precond_apply(ctx, F, r, z):
+    nrhs = 1 if r.dim() == 1 else r.shape[1]
+    _check(load().rw_precond_apply(ctx.handle, F.handle, _c_void_p(r.data_ptr()),
+                                   _c_void_p(z.data_ptr()), nrhs), "rw_precond_apply")
+
+
+def rw_spmv(ctx, A, x, y):
+    nrhs = 1 if x.dim() == 1 else x.shape[1]
+    _check(load().rw_spmv(ctx.handle, ctypes.byref(A.c), _c_void_p(x.data_ptr()),
+                          _c_void_p(y.data_ptr()), nrhs), "rw_spmv")

@@ -1,0 +1,481 @@
+// rw_api.cu -- C ABI of librwpc: contexts, factor construction (Algorithm 1,
+// "Precondition") and the PCG solve (Algorithm 1, "solve").
+#include <climits>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "rw_internal.h"
+
+namespace rw {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+rw_status check_cuda(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return RW_OK;
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    if (e == cudaErrorMemoryAllocation) return RW_ERR_ALLOC;
+    return RW_ERR_CUDA;
+}
+
+rw_status check_launch(const char* what) { return check_cuda(cudaGetLastError(), what); }
+
+rw_status reset_status(rw_context* ctx) {
+    DevStatus init{};
+    init.bad_row = UINT_MAX;
+    *ctx->h_status = init;
+    return check_cuda(cudaMemcpyAsync(ctx->d_status, ctx->h_status, sizeof(DevStatus),
+                                      cudaMemcpyHostToDevice, ctx->stream),
+                      "status reset");
+}
+
+rw_status read_status(rw_context* ctx, const char* what) {
+    rw_status rc = check_cuda(cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(DevStatus),
+                                              cudaMemcpyDeviceToHost, ctx->stream),
+                              what);
+    if (rc) return rc;
+    if ((rc = check_cuda(cudaStreamSynchronize(ctx->stream), what))) return rc;
+    const DevStatus& st = *ctx->h_status;
+    if (st.bad_row != UINT_MAX) {
+        set_error("%s: row %u is not in R-matrix form (sorted columns, positive diagonal, "
+                  "negative off-diagonals, diagonal dominance)",
+                  what, st.bad_row - 1u);
+        return RW_ERR_NOT_RMATRIX;
+    }
+    if (st.bad_budget) {
+        set_error("%s: %u rows with an upper neighbour have a zero walk budget", what,
+                  st.bad_budget);
+        return RW_ERR_ARG;
+    }
+    if (st.walk_cap) {
+        set_error("%s: %u walks reached the step cap (is every component grounded?)", what,
+                  st.walk_cap);
+        return RW_ERR_WALK_CAP;
+    }
+    if (st.capacity) {
+        set_error("%s: %u rows exceed the merge capacity (walks + lower neighbours > 12288)",
+                  what, st.capacity);
+        return RW_ERR_CAPACITY;
+    }
+    if (st.timeout) {
+        set_error("%s: %u device-side waits gave up", what, st.timeout);
+        return RW_ERR_TIMEOUT;
+    }
+    return RW_OK;
+}
+
+void* Pool::get(size_t bytes) {
+    bytes = (bytes + 255) & ~(size_t)255;
+    void* p = nullptr;
+    if (ctx->alloc) {
+        p = ctx->alloc(ctx->user, bytes, (void*)ctx->stream);
+        if (!p) set_error("allocator returned NULL for %zu bytes", bytes);
+    } else {
+        cudaError_t e = cudaMallocAsync(&p, bytes, ctx->stream);
+        if (e != cudaSuccess) {
+            set_error("cudaMallocAsync(%zu): %s", bytes, cudaGetErrorString(e));
+            p = nullptr;
+        }
+    }
+    if (p) bufs.push_back({p, bytes});
+    return p;
+}
+
+void Pool::release(void* p) {
+    for (size_t i = 0; i < bufs.size(); ++i)
+        if (bufs[i].p == p) {
+            if (ctx->free_fn) ctx->free_fn(ctx->user, p, bufs[i].bytes, (void*)ctx->stream);
+            else cudaFreeAsync(p, ctx->stream);
+            bufs.erase(bufs.begin() + (long)i);
+            return;
+        }
+}
+
+void Pool::release_all() {
+    if (!ctx) return;
+    for (size_t i = bufs.size(); i-- > 0;) {
+        if (ctx->free_fn) ctx->free_fn(ctx->user, bufs[i].p, bufs[i].bytes, (void*)ctx->stream);
+        else cudaFreeAsync(bufs[i].p, ctx->stream);
+    }
+    bufs.clear();
+}
+
+static rw_status check_csr(const rw_csr* A) {
+    if (!A) {
+        set_error("matrix is NULL");
+        return RW_ERR_ARG;
+    }
+    if (A->n < 0 || A->nnz < A->n || A->nnz >= ((int64_t)1 << 31)) {
+        set_error("matrix sizes out of range (n=%d, nnz=%lld)", A->n, (long long)A->nnz);
+        return A->nnz < A->n ? RW_ERR_NOT_RMATRIX : RW_ERR_ARG;
+    }
+    if (A->n > 0 && (!A->row_ptr || !A->col || !A->val)) {
+        set_error("matrix arrays are NULL");
+        return RW_ERR_ARG;
+    }
+    return RW_OK;
+}
+
+}  // namespace rw
+
+using namespace rw;
+
+extern "C" {
+
+void rw_options_default(rw_options* opt) {
+    if (!opt) return;
+    memset(opt, 0, sizeof(*opt));
+    opt->max_steps = 1ull << 24;
+    opt->keep_records = 0;
+    opt->record_lengths = 0;
+    opt->store_fp32 = 1;
+    opt->refine_every = 50;
+    opt->walk_blocks_per_sm = 0;
+    opt->timing = 1;
+}
+
+const char* rw_status_string(rw_status s) {
+    switch (s) {
+        case RW_OK: return "ok";
+        case RW_ERR_ARG: return "invalid argument";
+        case RW_ERR_NOT_RMATRIX: return "matrix is not an R-matrix in the required form";
+        case RW_ERR_WALK_CAP: return "a walk reached the step cap";
+        case RW_ERR_ALLOC: return "allocation failed";
+        case RW_ERR_NO_CONVERGENCE: return "PCG did not converge";
+        case RW_ERR_BREAKDOWN: return "PCG breakdown";
+        case RW_ERR_CUDA: return "CUDA error";
+        case RW_ERR_TIMEOUT: return "device-side wait timed out";
+        case RW_ERR_CAPACITY: return "per-row budget exceeds the merge capacity";
+    }
+    return "unknown status";
+}
+
+const char* rw_last_error(void) { return g_err; }
+
+rw_status rw_context_create(rw_context** out, void* stream, rw_alloc_fn alloc, rw_free_fn free_fn,
+                            void* user, const rw_options* opt) {
+    if (!out || ((alloc == nullptr) != (free_fn == nullptr))) {
+        set_error("rw_context_create: bad arguments");
+        return RW_ERR_ARG;
+    }
+    *out = nullptr;
+    rw_context* c = new (std::nothrow) rw_context();
+    if (!c) return RW_ERR_ALLOC;
+    c->stream = static_cast<cudaStream_t>(stream);
+    c->alloc = alloc;
+    c->free_fn = free_fn;
+    c->user = user;
+    if (opt) c->opt = *opt;
+    else rw_options_default(&c->opt);
+    if (c->opt.max_steps < 1) c->opt.max_steps = 1ull << 24;
+    rw_status rc;
+    if ((rc = check_cuda(cudaGetDevice(&c->device), "cudaGetDevice")) ||
+        (rc = check_cuda(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount,
+                                                c->device),
+                         "device attribute")) ||
+        (rc = check_cuda(cudaMalloc(&c->d_status, sizeof(DevStatus)), "cudaMalloc status")) ||
+        (rc = check_cuda(cudaMallocHost(&c->h_status, sizeof(DevStatus)), "cudaMallocHost")) ||
+        (rc = check_cuda(cudaMallocHost(&c->h_small, 4096), "cudaMallocHost"))) {
+        rw_context_destroy(c);
+        return rc;
+    }
+    for (auto& e : c->ev) {
+        if ((rc = check_cuda(cudaEventCreate(&e), "cudaEventCreate"))) {
+            rw_context_destroy(c);
+            return rc;
+        }
+    }
+    if (!alloc) {
+        // keep freed stream-ordered allocations cached in the device pool
+        cudaMemPool_t mp;
+        if (cudaDeviceGetDefaultMemPool(&mp, c->device) == cudaSuccess) {
+            uint64_t thr = UINT64_MAX;
+            cudaMemPoolSetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+    }
+    *out = c;
+    return RW_OK;
+}
+
+void rw_context_destroy(rw_context* ctx) {
+    if (!ctx) return;
+    if (ctx->stream || true) cudaStreamSynchronize(ctx->stream);
+    for (auto& e : ctx->ev)
+        if (e) cudaEventDestroy(e);
+    if (ctx->d_status) cudaFree(ctx->d_status);
+    if (ctx->h_status) cudaFreeHost(ctx->h_status);
+    if (ctx->h_small) cudaFreeHost(ctx->h_small);
+    delete ctx;
+}
+
+static rw_status build_factor_impl(rw_context* ctx, const rw_csr* A, uint32_t uniform,
+                                   const uint32_t* d_budget, uint64_t seed, double drop_tol,
+                                   rw_factor** out) {
+    if (!ctx || !out) {
+        set_error("rw_build_factor: NULL context or output");
+        return RW_ERR_ARG;
+    }
+    *out = nullptr;
+    rw_status rc = check_csr(A);
+    if (rc) return rc;
+    if (!(drop_tol >= 0.0) || !(drop_tol < 1e300)) {
+        set_error("drop_tol must be finite and >= 0");
+        return RW_ERR_ARG;
+    }
+    if (!d_budget && uniform < 1) {
+        set_error("walks_per_row must be >= 1");
+        return RW_ERR_ARG;
+    }
+    cudaStream_t s = ctx->stream;
+    const bool timing = ctx->opt.timing != 0;
+    rw_factor* F = new (std::nothrow) rw_factor(ctx);
+    if (!F) return RW_ERR_ALLOC;
+    Pool scratch(ctx);
+    const int32_t n = A->n;
+    rw_factor_desc& d = F->desc;
+    memset(&d, 0, sizeof(d));
+    d.n = n;
+    Tables T;
+    WalkSpace ws;
+    FactorOut fo;
+    float ms_walk = 0.f, ms_merge = 0.f, ms_emit = 0.f;
+    int2* rec = nullptr;
+    unsigned long long* d_hops = nullptr;
+    int64_t* yt_rp = nullptr;
+    int32_t* yt_col = nullptr;
+    double* yt_val = nullptr;
+    if ((rc = reset_status(ctx))) goto fail;
+    if (timing) cudaEventRecord(ctx->ev[10], s);
+    if ((rc = build_tables(ctx, A, T, scratch))) goto fail;
+    if ((rc = build_walk_space(ctx, T, uniform, d_budget, ws, ctx->opt.keep_records ? F->pool : scratch)))
+        goto fail;
+    if (timing) cudaEventRecord(ctx->ev[11], s);
+    rec = alloc_n<int2>(ctx->opt.keep_records ? F->pool : scratch, ws.total);
+    d_hops = alloc_n<unsigned long long>(scratch, 1);
+    if (!rec || !d_hops) {
+        rc = RW_ERR_ALLOC;
+        goto fail;
+    }
+    {
+        WalkLaunch wl;
+        wl.seed = seed;
+        wl.matrix_index = 0;
+        wl.tag = 0;
+        wl.max_steps = ctx->opt.max_steps;
+        wl.record_lengths = ctx->opt.record_lengths;
+        if ((rc = run_walks(ctx, T, ws, wl, rec, d_hops, scratch, timing ? &ms_walk : nullptr)))
+            goto fail;
+        if ((rc = read_status(ctx, "walks"))) goto fail;  // no merge of stopped walks
+    }
+    if ((rc = emit_factor(ctx, A, T, ws, rec, drop_tol, fo, F->pool, scratch,
+                          timing ? &ms_merge : nullptr, timing ? &ms_emit : nullptr)))
+        goto fail;
+    yt_rp = alloc_n<int64_t>(F->pool, n + 1);
+    yt_col = alloc_n<int32_t>(F->pool, fo.nnz);
+    yt_val = alloc_n<double>(F->pool, fo.nnz);
+    if (!yt_rp || !yt_col || !yt_val) {
+        rc = RW_ERR_ALLOC;
+        goto fail;
+    }
+    if ((rc = transpose_factor(ctx, n, fo, yt_rp, yt_col, yt_val, scratch))) goto fail;
+    if (timing) cudaEventRecord(ctx->ev[12], s);
+    F->fwd_order = alloc_n<int32_t>(F->pool, n);
+    F->bwd_order = alloc_n<int32_t>(F->pool, n);
+    if (!F->fwd_order || !F->bwd_order) {
+        rc = RW_ERR_ALLOC;
+        goto fail;
+    }
+    if ((rc = compute_levels(ctx, n, fo.y_rp, fo.y_col, false, F->fwd_order, &d.fwd_levels, scratch)))
+        goto fail;
+    if ((rc = compute_levels(ctx, n, yt_rp, yt_col, true, F->bwd_order, &d.bwd_levels, scratch)))
+        goto fail;
+    if (timing) cudaEventRecord(ctx->ev[13], s);
+    if (ctx->opt.store_fp32) {
+        float* y32 = alloc_n<float>(F->pool, fo.nnz);
+        float* yt32 = alloc_n<float>(F->pool, fo.nnz);
+        float* d32 = alloc_n<float>(F->pool, n);
+        if (!y32 || !yt32 || !d32) {
+            rc = RW_ERR_ALLOC;
+            goto fail;
+        }
+        launch_to_fp32(fo.y_val, y32, fo.nnz, s, ctx->num_sms);
+        launch_to_fp32(yt_val, yt32, fo.nnz, s, ctx->num_sms);
+        launch_to_fp32(fo.d, d32, n, s, ctx->num_sms);
+        if ((rc = check_launch("fp32 copies"))) goto fail;
+        d.y_val32 = y32;
+        d.yt_val32 = yt32;
+        d.d32 = d32;
+    }
+    if (timing) cudaEventRecord(ctx->ev[14], s);
+    {
+        unsigned long long* hh = static_cast<unsigned long long*>(ctx->h_small);
+        if ((rc = check_cuda(cudaMemcpyAsync(hh, d_hops, 8, cudaMemcpyDeviceToHost, s), "copy")))
+            goto fail;
+        if ((rc = read_status(ctx, "factor build"))) goto fail;
+        d.total_hops = hh[0];
+    }
+    d.nnz = fo.nnz;
+    d.y_row_ptr = fo.y_rp;
+    d.y_col = fo.y_col;
+    d.y_val = fo.y_val;
+    d.d = fo.d;
+    d.yt_row_ptr = yt_rp;
+    d.yt_col = yt_col;
+    d.yt_val = yt_val;
+    d.walks = fo.M;
+    d.visits = fo.J;
+    d.ground = fo.G;
+    d.n_walk_rows = T.n_walk_rows;
+    d.total_walks = ws.total;
+    if (ctx->opt.keep_records) {
+        d.records = reinterpret_cast<const int32_t*>(rec);
+        d.walk_base = ws.wbase;
+        int32_t* wr = alloc_n<int32_t>(F->pool, T.n_walk_rows);
+        if (!wr) {
+            rc = RW_ERR_ALLOC;
+            goto fail;
+        }
+        if (T.n_walk_rows > 0 &&
+            (rc = check_cuda(cudaMemcpyAsync(wr, T.walk_rows, sizeof(int32_t) * (size_t)T.n_walk_rows,
+                                             cudaMemcpyDeviceToDevice, s),
+                             "copy")))
+            goto fail;
+        d.walk_rows = wr;
+    }
+    if (timing) {
+        float t_tab = 0.f, t_tr = 0.f, t_lev = 0.f, t_fp = 0.f, t_all = 0.f;
+        cudaEventSynchronize(ctx->ev[14]);
+        cudaEventElapsedTime(&t_tab, ctx->ev[10], ctx->ev[11]);
+        cudaEventElapsedTime(&t_lev, ctx->ev[12], ctx->ev[13]);
+        cudaEventElapsedTime(&t_fp, ctx->ev[13], ctx->ev[14]);
+        cudaEventElapsedTime(&t_all, ctx->ev[10], ctx->ev[14]);
+        float t_to_tr = 0.f;
+        cudaEventElapsedTime(&t_to_tr, ctx->ev[11], ctx->ev[12]);
+        t_tr = t_to_tr - ms_walk - ms_merge - ms_emit;
+        d.phase_ms[0] = t_tab;
+        d.phase_ms[1] = ms_walk;
+        d.phase_ms[2] = ms_merge;
+        d.phase_ms[3] = ms_emit;
+        d.phase_ms[4] = t_tr;
+        d.phase_ms[5] = t_lev;
+        d.phase_ms[6] = t_fp;
+        d.phase_ms[7] = t_all;
+    }
+    scratch.release_all();
+    if ((rc = check_cuda(cudaStreamSynchronize(s), "sync"))) goto fail;
+    *out = F;
+    return RW_OK;
+fail:
+    scratch.release_all();
+    cudaStreamSynchronize(s);
+    delete F;
+    return rc;
+}
+
+rw_status rw_build_factor(rw_context* ctx, const rw_csr* A, uint32_t walks_per_row, uint64_t seed,
+                          double drop_tol, rw_factor** out) {
+    return build_factor_impl(ctx, A, walks_per_row, nullptr, seed, drop_tol, out);
+}
+
+rw_status rw_build_factor_budget(rw_context* ctx, const rw_csr* A, const uint32_t* d_budget,
+                                 uint64_t seed, double drop_tol, rw_factor** out) {
+    if (!d_budget && A && A->n > 0) {
+        set_error("rw_build_factor_budget: budget is NULL");
+        return RW_ERR_ARG;
+    }
+    return build_factor_impl(ctx, A, 0u, d_budget, seed, drop_tol, out);
+}
+
+rw_status rw_factor_view(const rw_factor* F, rw_factor_desc* desc) {
+    if (!F || !desc) {
+        set_error("rw_factor_view: NULL argument");
+        return RW_ERR_ARG;
+    }
+    *desc = F->desc;
+    return RW_OK;
+}
+
+void rw_factor_destroy(rw_factor* F) {
+    if (!F) return;
+    cudaStreamSynchronize(F->ctx->stream);
+    delete F;
+}
+
+static FactorView view_of(const rw_factor* F) {
+    const rw_factor_desc& d = F->desc;
+    FactorView v;
+    v.n = d.n;
+    v.nnz = d.nnz;
+    v.y_rp = d.y_row_ptr;
+    v.y_col = d.y_col;
+    v.y_val = d.y_val;
+    v.y_val32 = d.y_val32;
+    v.yt_rp = d.yt_row_ptr;
+    v.yt_col = d.yt_col;
+    v.yt_val = d.yt_val;
+    v.yt_val32 = d.yt_val32;
+    v.d = d.d;
+    v.d32 = d.d32;
+    v.fwd_order = F->fwd_order;
+    v.bwd_order = F->bwd_order;
+    return v;
+}
+
+rw_status pcg_solve(rw_context* ctx, const rw_csr* A, const rw_factor* F, const double* d_b,
+                    double* d_x, int32_t nrhs, double tol, int32_t max_iter, rw_precision prec,
+                    rw_pcg_stats* stats, int32_t* h_iters, double* h_relres) {
+    if (!ctx || !F || !d_b || !d_x) {
+        set_error("pcg_solve: NULL argument");
+        return RW_ERR_ARG;
+    }
+    rw_status rc = check_csr(A);
+    if (rc) return rc;
+    if (A->n != F->desc.n || nrhs < 1 || nrhs > 16 || max_iter < 0 || !(tol >= 0.0) ||
+        (prec != RW_FP64 && prec != RW_FP32_MIXED)) {
+        set_error("pcg_solve: bad arguments (n=%d vs factor %d, nrhs=%d, max_iter=%d)", A->n,
+                  F->desc.n, nrhs, max_iter);
+        return RW_ERR_ARG;
+    }
+    if (stats) memset(stats, 0, sizeof(*stats));
+    if (A->n == 0) return RW_OK;
+    if ((rc = reset_status(ctx))) return rc;
+    return pcg_run(ctx, A, view_of(F), d_b, d_x, nrhs, tol, max_iter, prec, stats, h_iters, h_relres);
+}
+
+rw_status rw_precond_apply(rw_context* ctx, const rw_factor* F, const double* d_r, double* d_z,
+                           int32_t nrhs) {
+    if (!ctx || !F || !d_r || !d_z || nrhs < 1 || nrhs > 16) {
+        set_error("rw_precond_apply: bad arguments");
+        return RW_ERR_ARG;
+    }
+    if (F->desc.n == 0) return RW_OK;
+    rw_status rc = reset_status(ctx);
+    if (rc) return rc;
+    Pool sc(ctx);
+    rc = precond_fp64(ctx, view_of(F), d_r, d_z, nrhs, sc);
+    sc.release_all();
+    cudaStreamSynchronize(ctx->stream);
+    return rc;
+}
+
+rw_status rw_spmv(rw_context* ctx, const rw_csr* A, const double* d_x, double* d_y, int32_t nrhs) {
+    if (!ctx || !d_x || !d_y || nrhs < 1 || nrhs > 16) {
+        set_error("rw_spmv: bad arguments");
+        return RW_ERR_ARG;
+    }
+    rw_status rc = check_csr(A);
+    if (rc) return rc;
+    if (A->n == 0) return RW_OK;
+    if ((rc = reset_status(ctx))) return rc;
+    if ((rc = spmv_fp64(ctx, A, d_x, d_y, nrhs))) return rc;
+    return read_status(ctx, "spmv");
+}
+
+}  // extern "C"

@@ -1,0 +1,535 @@
+// rw_emit.cu -- journey record -> incomplete factor.
+//
+// For every walk row k the per-walk records are merged into end-point counts
+// H'_ki (warp-level __match_any_sync, then a shared-memory hash table), the
+// union of the end points and the lower neighbours of k is sorted, and the
+// factor row follows the one-step-exact estimator (Sec. 5.2):
+//   a    = S_k / A_kk,  S_k = sum_{j>k} A_kj
+//   Y_ki = A_ki / A_kk + a * (H'_ki / M'_k)          (Eq. newy)
+//   D_kk = A_kk / (1 + a * (1 - J'_k / M'_k))        (Eq. newz with Eq. d: D = 1/Z)
+// each operation rounded once, in this order.  Entries with |Y_ki| < drop_tol
+// are dropped (post-processing drop, footnote of Sec. 4).  Rows without an
+// upper neighbour are exact: Y_ki = A_ki / A_kk, D_kk = A_kk.
+#include "rw_internal.h"
+
+namespace rw {
+
+constexpr uint32_t kNbrFlag = 0x80000000u;
+constexpr uint32_t kCountMask = 0x7FFFFFFFu;
+constexpr int kLog2SmallHash = 10;              // 1024 slots per warp
+constexpr int kSmallCap = 768;                  // distinct keys a warp table accepts
+constexpr int kLog2BigHash = 14;                // 16384 slots per block
+constexpr int kBigCap = 12288;
+
+struct MergeParams {
+    const int32_t* __restrict__ rp;
+    const int32_t* __restrict__ col;
+    const double* __restrict__ val;
+    const int32_t* __restrict__ dpos;
+    const int4* __restrict__ wrow;
+    const int64_t* __restrict__ wbase;
+    const int64_t* __restrict__ tbase;
+    const int2* __restrict__ rec;
+    const double* __restrict__ S;
+    const double* __restrict__ diag;
+    double drop_tol;
+    int32_t nw;
+    int32_t* tcol;
+    double* tval;
+    int64_t* ycnt;
+    double* D;
+    uint32_t* M;
+    uint64_t* J;
+    uint32_t* G;
+    int32_t* big_rows;
+    int32_t* n_big;
+    DevStatus* st;
+};
+
+template <int TEAM>
+__device__ __forceinline__ void team_sync() {
+    if (TEAM == 32) __syncwarp();
+    else __syncthreads();
+}
+
+template <int TEAM>
+__device__ __forceinline__ int team_rank() {
+    return TEAM == 32 ? (int)lane_id() : (int)threadIdx.x;
+}
+
+// Exclusive count of `f` over the team in thread order; total in *total.
+template <int TEAM>
+__device__ __forceinline__ int team_prefix(bool f, int* total, int* wsm) {
+    const unsigned b = __ballot_sync(kFull, f);
+    const int in_warp = __popc(b & lanemask_lt());
+    if (TEAM == 32) {
+        *total = __popc(b);
+        return in_warp;
+    }
+    const int warp = threadIdx.x >> 5;
+    if (lane_id() == 0) wsm[warp] = __popc(b);
+    __syncthreads();
+    int pre = 0, tot = 0;
+#pragma unroll
+    for (int i = 0; i < TEAM / 32; ++i) {
+        const int c = wsm[i];
+        pre += (i < warp) ? c : 0;
+        tot += c;
+    }
+    __syncthreads();
+    *total = tot;
+    return pre + in_warp;
+}
+
+template <int TEAM, typename T>
+__device__ __forceinline__ T team_sum(T v, T* sm) {
+    v = warp_sum(v);
+    if (TEAM == 32) return v;
+    if (threadIdx.x == 0) *sm = T(0);
+    __syncthreads();
+    if (lane_id() == 0) atomicAdd(sm, v);
+    __syncthreads();
+    const T r = *sm;
+    __syncthreads();
+    return r;
+}
+
+template <int LOG2HC>
+__device__ __forceinline__ void hash_insert(int* keys, uint32_t* vals, int key, uint32_t add,
+                                            bool flag) {
+    constexpr uint32_t mask = (1u << LOG2HC) - 1u;
+    uint32_t h = ((uint32_t)key * 2654435761u) >> (32 - LOG2HC);
+    for (;;) {
+        const int prev = atomicCAS(&keys[h], -1, key);
+        if (prev == -1 || prev == key) {
+            if (flag) atomicOr(&vals[h], kNbrFlag);
+            else atomicAdd(&vals[h], add);
+            return;
+        }
+        h = (h + 1u) & mask;
+    }
+}
+
+// Bitonic sort of keys[0..P) (with vals) ascending, P a power of two.
+template <int TEAM>
+__device__ void team_bitonic(int* keys, uint32_t* vals, int P) {
+    const int t = team_rank<TEAM>();
+    for (int size = 2; size <= P; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = t; i < (P >> 1); i += TEAM) {
+                const int lo = 2 * i - (i & (stride - 1));
+                const int hi = lo + stride;
+                const bool asc = (lo & size) == 0;
+                const int a = keys[lo], b = keys[hi];
+                if ((a > b) == asc) {
+                    keys[lo] = b;
+                    keys[hi] = a;
+                    const uint32_t va = vals[lo];
+                    vals[lo] = vals[hi];
+                    vals[hi] = va;
+                }
+            }
+            team_sync<TEAM>();
+        }
+    }
+}
+
+// Merge the records of walk row r and write its kept entries (ascending
+// columns) to the row's slot of the temporary area.
+template <int TEAM, int LOG2HC>
+__device__ void merge_row(const MergeParams& P, int32_t r, int* keys, uint32_t* vals, int* wsm,
+                          unsigned long long* sm64) {
+    constexpr int HC = 1 << LOG2HC;
+    const int t = team_rank<TEAM>();
+    const int4 info = P.wrow[r];
+    const int32_t k = info.x;
+    const int64_t b0 = P.wbase[r], b1 = P.wbase[r + 1];
+    const int32_t rs = P.rp[k], dp = P.dpos[k];
+
+    for (int i = t; i < HC; i += TEAM) {
+        keys[i] = -1;
+        vals[i] = 0u;
+    }
+    team_sync<TEAM>();
+    for (int32_t p = rs + t; p < dp; p += TEAM) hash_insert<LOG2HC>(keys, vals, P.col[p], 0u, true);
+
+    unsigned long long jsum = 0;
+    unsigned gsum = 0, csum = 0;
+    for (int64_t base = b0; base < b1; base += TEAM) {
+        const int64_t idx = base + t;
+        const bool valid = idx < b1;
+        int2 rc = make_int2(-3, 0);
+        if (valid) rc = P.rec[idx];
+        if (valid) {
+            jsum += (unsigned)rc.y;
+            gsum += rc.x == -1;
+            csum += (rc.x < -1 || rc.x >= k);  // step cap (or a record that is not an end node)
+        }
+        const bool ep = valid && rc.x >= 0 && rc.x < k;
+        const unsigned em = __ballot_sync(kFull, ep);
+        if (ep) {
+            const unsigned g = __match_any_sync(em, rc.x);
+            if ((int)lane_id() == __ffs(g) - 1) hash_insert<LOG2HC>(keys, vals, rc.x, __popc(g), false);
+        }
+    }
+    team_sync<TEAM>();
+
+    // move the occupied slots to the front, in slot order
+    int u = 0;
+    for (int base = 0; base < HC; base += TEAM) {
+        const int key = keys[base + t];
+        const uint32_t v = vals[base + t];
+        const bool occ = key != -1;
+        int tot;
+        const int pos = team_prefix<TEAM>(occ, &tot, wsm);
+        team_sync<TEAM>();
+        if (occ) {
+            keys[u + pos] = key;
+            vals[u + pos] = v;
+        }
+        u += tot;
+        team_sync<TEAM>();
+    }
+    int Pw = 1;
+    while (Pw < u) Pw <<= 1;
+    for (int i = u + t; i < Pw; i += TEAM) {
+        keys[i] = 0x7FFFFFFF;
+        vals[i] = 0u;
+    }
+    team_sync<TEAM>();
+    team_bitonic<TEAM>(keys, vals, Pw);
+
+    const double akk = P.diag[k];
+    const double a = __ddiv_rn(P.S[k], akk);
+    const double Mk = (double)(b1 - b0);
+    const int64_t tb = P.tbase[r];
+    int kept = 0;
+    for (int base = 0; base < u; base += TEAM) {
+        const int s = base + t;
+        bool keep = false;
+        int key = 0;
+        double y = 0.0;
+        if (s < u) {
+            key = keys[s];
+            const uint32_t v = vals[s];
+            double d = 0.0;
+            if (v & kNbrFlag) {
+                int lo = rs, hi = dp - 1;  // binary search of the column among the lower entries
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (P.col[mid] < key) lo = mid + 1;
+                    else hi = mid;
+                }
+                d = __ddiv_rn(P.val[lo], akk);
+            }
+            const double ratio = __ddiv_rn((double)(v & kCountMask), Mk);
+            y = __dadd_rn(d, __dmul_rn(a, ratio));
+            keep = fabs(y) >= P.drop_tol;
+        }
+        int tot;
+        const int pos = team_prefix<TEAM>(keep, &tot, wsm);
+        if (keep) {
+            P.tcol[tb + kept + pos] = key;
+            P.tval[tb + kept + pos] = y;
+        }
+        kept += tot;
+    }
+    jsum = team_sum<TEAM, unsigned long long>(jsum, sm64);
+    const unsigned long long g_all = team_sum<TEAM, unsigned long long>(gsum, sm64);
+    const unsigned long long c_all = team_sum<TEAM, unsigned long long>(csum, sm64);
+    if (t == 0) {
+        const uint64_t Jk = (uint64_t)(b1 - b0) + jsum;
+        const double q = __ddiv_rn((double)Jk, Mk);
+        P.D[k] = __ddiv_rn(akk, __dadd_rn(1.0, __dmul_rn(a, __dadd_rn(1.0, -q))));
+        P.M[k] = (uint32_t)(b1 - b0);
+        P.J[k] = Jk;
+        P.G[k] = (uint32_t)g_all;
+        P.ycnt[k] = kept;
+        if (c_all) atomicAdd(&P.st->walk_cap, (unsigned)c_all);
+    }
+    team_sync<TEAM>();
+}
+
+constexpr int kMergeWarps = 8;
+
+__global__ void __launch_bounds__(32 * kMergeWarps) k_merge_small(const MergeParams P) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int HC = 1 << kLog2SmallHash;
+    const int warp = threadIdx.x >> 5;
+    int* keys = reinterpret_cast<int*>(smem) + warp * HC;
+    uint32_t* vals = reinterpret_cast<uint32_t*>(smem + kMergeWarps * HC * sizeof(int)) + warp * HC;
+    const int32_t gw = blockIdx.x * kMergeWarps + warp;
+    const int32_t nwarps = gridDim.x * kMergeWarps;
+    for (int32_t r = gw; r < P.nw; r += nwarps) {
+        const int64_t m = P.wbase[r + 1] - P.wbase[r];
+        const int4 info = P.wrow[r];
+        if (m + info.w > kSmallCap) {
+            if (lane_id() == 0) P.big_rows[atomicAdd(P.n_big, 1)] = r;
+            continue;
+        }
+        merge_row<32, kLog2SmallHash>(P, r, keys, vals, nullptr, nullptr);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_merge_big(const MergeParams P, int32_t nbig) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int HC = 1 << kLog2BigHash;
+    int* keys = reinterpret_cast<int*>(smem);
+    uint32_t* vals = reinterpret_cast<uint32_t*>(smem + HC * sizeof(int));
+    __shared__ int wsm[8];
+    __shared__ unsigned long long sm64;
+    for (int32_t i = blockIdx.x; i < nbig; i += gridDim.x) {
+        const int32_t r = P.big_rows[i];
+        const int64_t m = P.wbase[r + 1] - P.wbase[r];
+        const int4 info = P.wrow[r];
+        if (m + info.w > kBigCap) {
+            if (threadIdx.x == 0) atomicAdd(&P.st->capacity, 1u);
+            continue;
+        }
+        merge_row<256, kLog2BigHash>(P, r, keys, vals, wsm, &sm64);
+    }
+}
+
+// Temporary slot capacity per walk row: walks + lower neighbours.
+__global__ void k_slot_sizes(int32_t nw, const int4* __restrict__ wrow,
+                             const int64_t* __restrict__ wbase, int64_t* cap) {
+    for (int32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < nw; r += gridDim.x * blockDim.x)
+        cap[r] = wbase[r + 1] - wbase[r] + wrow[r].w;
+}
+
+// Exact rows (no upper neighbour, Sec. 5.2): count pass and fill pass.
+__global__ void k_exact_rows(int32_t n, const uint32_t* __restrict__ wflag,
+                             const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                             const double* __restrict__ val, const int32_t* __restrict__ dpos,
+                             double drop_tol, int64_t* ycnt, double* D, uint32_t* M, uint64_t* J,
+                             uint32_t* G, const int64_t* y_rp, int32_t* y_col, double* y_val) {
+    for (int32_t l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x) {
+        if (wflag[l + 1] != wflag[l]) continue;
+        const int32_t s = rp[l], dp = dpos[l];
+        const double dg = val[dp];
+        if (!y_rp) {
+            int64_t c = 0;
+            for (int32_t p = s; p < dp; ++p) c += fabs(__ddiv_rn(val[p], dg)) >= drop_tol;
+            ycnt[l] = c;
+            D[l] = dg;
+            M[l] = 0u;
+            J[l] = 0u;
+            G[l] = 0u;
+        } else {
+            int64_t o = y_rp[l];
+            for (int32_t p = s; p < dp; ++p) {
+                const double y = __ddiv_rn(val[p], dg);
+                if (fabs(y) >= drop_tol) {
+                    y_col[o] = col[p];
+                    y_val[o] = y;
+                    ++o;
+                }
+            }
+        }
+    }
+}
+
+// Copy each walk row's kept entries from its slot to the final CSR.
+__global__ void k_copy_rows(int32_t nw, const int4* __restrict__ wrow,
+                            const int64_t* __restrict__ tbase, const int32_t* __restrict__ tcol,
+                            const double* __restrict__ tval, const int64_t* __restrict__ y_rp,
+                            int32_t* y_col, double* y_val) {
+    const int32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int32_t r = gw; r < nw; r += nwarps) {
+        const int32_t k = wrow[r].x;
+        const int64_t o = y_rp[k], c = y_rp[k + 1] - o, tb = tbase[r];
+        for (int64_t i = lane_id(); i < c; i += 32) {
+            y_col[o + i] = tcol[tb + i];
+            y_val[o + i] = tval[tb + i];
+        }
+    }
+}
+
+rw_status emit_factor(rw_context* ctx, const rw_csr* A, const Tables& T, const WalkSpace& ws,
+                      const int2* rec, double drop_tol, FactorOut& fo, Pool& pool, Pool& scratch,
+                      float* ms_merge, float* ms_emit) {
+    cudaStream_t s = ctx->stream;
+    const int32_t n = A->n, nw = T.n_walk_rows;
+    rw_status rc;
+    fo.y_rp = alloc_n<int64_t>(pool, n + 1);
+    fo.d = alloc_n<double>(pool, n);
+    fo.M = alloc_n<uint32_t>(pool, n);
+    fo.J = alloc_n<uint64_t>(pool, n);
+    fo.G = alloc_n<uint32_t>(pool, n);
+    int64_t* tbase = alloc_n<int64_t>(scratch, nw + 1);
+    int32_t* big_rows = alloc_n<int32_t>(scratch, nw);
+    int32_t* n_big = alloc_n<int32_t>(scratch, 1);
+    if (!fo.y_rp || !fo.d || !fo.M || !fo.J || !fo.G || !tbase || !big_rows || !n_big)
+        return RW_ERR_ALLOC;
+    const int blocks = grid_for(std::max(n, nw), 256, ctx->num_sms * 8);
+    if (nw > 0) {
+        k_slot_sizes<<<blocks, 256, 0, s>>>(nw, T.wrow, ws.wbase, tbase);
+        if ((rc = check_launch("slot sizes"))) return rc;
+    }
+    if ((rc = check_cuda(scan_i64(tbase, tbase, nw, s, scratch), "scan"))) return rc;
+    int64_t* h64 = static_cast<int64_t*>(ctx->h_small);
+    if ((rc = check_cuda(cudaMemcpyAsync(h64, tbase + nw, 8, cudaMemcpyDeviceToHost, s), "copy")))
+        return rc;
+    if ((rc = check_cuda(cudaStreamSynchronize(s), "sync"))) return rc;
+    const int64_t tslots = h64[0];
+    int32_t* tcol = alloc_n<int32_t>(scratch, tslots);
+    double* tval = alloc_n<double>(scratch, tslots);
+    if (!tcol || !tval) return RW_ERR_ALLOC;
+    if ((rc = check_cuda(cudaMemsetAsync(n_big, 0, sizeof(int32_t), s), "memset"))) return rc;
+
+    MergeParams P;
+    P.rp = A->row_ptr;
+    P.col = A->col;
+    P.val = A->val;
+    P.dpos = T.diag_pos;
+    P.wrow = T.wrow;
+    P.wbase = ws.wbase;
+    P.tbase = tbase;
+    P.rec = rec;
+    P.S = T.S;
+    P.diag = T.diag;
+    P.drop_tol = drop_tol;
+    P.nw = nw;
+    P.tcol = tcol;
+    P.tval = tval;
+    P.ycnt = fo.y_rp;
+    P.D = fo.d;
+    P.M = fo.M;
+    P.J = fo.J;
+    P.G = fo.G;
+    P.big_rows = big_rows;
+    P.n_big = n_big;
+    P.st = ctx->d_status;
+
+    if (ms_merge) cudaEventRecord(ctx->ev[2], s);
+    if (nw > 0) {
+        const size_t sm_small = (size_t)kMergeWarps * (1 << kLog2SmallHash) * 8;
+        static bool attr_small = false;
+        if (!attr_small) {
+            if ((rc = check_cuda(cudaFuncSetAttribute(k_merge_small,
+                                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                      (int)sm_small),
+                                 "smem attribute")))
+                return rc;
+            attr_small = true;
+        }
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_merge_small, 32 * kMergeWarps,
+                                                      sm_small);
+        if (per_sm < 1) per_sm = 1;
+        const int mblocks = grid_for(nw, kMergeWarps, ctx->num_sms * per_sm);
+        k_merge_small<<<mblocks, 32 * kMergeWarps, sm_small, s>>>(P);
+        if ((rc = check_launch("merge (warp tables)"))) return rc;
+        int32_t* h32 = static_cast<int32_t*>(ctx->h_small);
+        if ((rc = check_cuda(cudaMemcpyAsync(h32, n_big, 4, cudaMemcpyDeviceToHost, s), "copy")))
+            return rc;
+        if ((rc = check_cuda(cudaStreamSynchronize(s), "sync"))) return rc;
+        const int32_t nbig = h32[0];
+        if (nbig > 0) {
+            const size_t sm_big = (size_t)(1 << kLog2BigHash) * 8;
+            static bool attr_big = false;
+            if (!attr_big) {
+                if ((rc = check_cuda(cudaFuncSetAttribute(k_merge_big,
+                                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                          (int)sm_big),
+                                     "smem attribute")))
+                    return rc;
+                attr_big = true;
+            }
+            k_merge_big<<<grid_for(nbig, 1, ctx->num_sms), 256, sm_big, s>>>(P, nbig);
+            if ((rc = check_launch("merge (block tables)"))) return rc;
+        }
+    }
+    k_exact_rows<<<blocks, 256, 0, s>>>(n, T.walk_flag, A->row_ptr, A->col, A->val, T.diag_pos,
+                                        drop_tol, fo.y_rp, fo.d, fo.M, fo.J, fo.G, nullptr, nullptr,
+                                        nullptr);
+    if ((rc = check_launch("exact rows"))) return rc;
+    if (ms_merge) cudaEventRecord(ctx->ev[3], s);
+    if ((rc = check_cuda(scan_i64(fo.y_rp, fo.y_rp, n, s, scratch), "scan"))) return rc;
+    if ((rc = check_cuda(cudaMemcpyAsync(h64, fo.y_rp + n, 8, cudaMemcpyDeviceToHost, s), "copy")))
+        return rc;
+    if ((rc = read_status(ctx, "merge"))) return rc;
+    fo.nnz = h64[0];
+    fo.y_col = alloc_n<int32_t>(pool, fo.nnz);
+    fo.y_val = alloc_n<double>(pool, fo.nnz);
+    if (!fo.y_col || !fo.y_val) return RW_ERR_ALLOC;
+    if (nw > 0) {
+        k_copy_rows<<<grid_for((int64_t)nw * 32, 256, ctx->num_sms * 8), 256, 0, s>>>(
+            nw, T.wrow, tbase, tcol, tval, fo.y_rp, fo.y_col, fo.y_val);
+        if ((rc = check_launch("copy rows"))) return rc;
+    }
+    k_exact_rows<<<blocks, 256, 0, s>>>(n, T.walk_flag, A->row_ptr, A->col, A->val, T.diag_pos,
+                                        drop_tol, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                        fo.y_rp, fo.y_col, fo.y_val);
+    if ((rc = check_launch("exact rows fill"))) return rc;
+    if (ms_merge || ms_emit) {
+        cudaEventRecord(ctx->ev[4], s);
+        cudaEventSynchronize(ctx->ev[4]);
+        if (ms_merge) cudaEventElapsedTime(ms_merge, ctx->ev[2], ctx->ev[3]);
+        if (ms_emit) cudaEventElapsedTime(ms_emit, ctx->ev[3], ctx->ev[4]);
+    }
+    return RW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Transpose: Y^T in CSR, each row's columns ascending.
+// ---------------------------------------------------------------------------
+__global__ void k_col_counts(int32_t n, const int64_t* __restrict__ rp,
+                             const int32_t* __restrict__ col, uint32_t* cnt) {
+    for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+        for (int64_t p = rp[k]; p < rp[k + 1]; ++p) atomicAdd(&cnt[col[p]], 1u);
+}
+
+__global__ void k_scatter_t(int32_t n, const int64_t* __restrict__ rp,
+                            const int32_t* __restrict__ col, const double* __restrict__ val,
+                            const int64_t* __restrict__ trp, uint32_t* fill, int32_t* tcol,
+                            double* tval) {
+    for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+        for (int64_t p = rp[k]; p < rp[k + 1]; ++p) {
+            const int32_t i = col[p];
+            const int64_t o = trp[i] + atomicAdd(&fill[i], 1u);
+            tcol[o] = k;
+            tval[o] = val[p];
+        }
+}
+
+__global__ void k_sort_rows(int32_t n, const int64_t* __restrict__ rp, int32_t* col, double* val) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int64_t s = rp[i], e = rp[i + 1];
+        for (int64_t p = s + 1; p < e; ++p) {
+            const int32_t c = col[p];
+            const double v = val[p];
+            int64_t q = p - 1;
+            while (q >= s && col[q] > c) {
+                col[q + 1] = col[q];
+                val[q + 1] = val[q];
+                --q;
+            }
+            col[q + 1] = c;
+            val[q + 1] = v;
+        }
+    }
+}
+
+rw_status transpose_factor(rw_context* ctx, int32_t n, const FactorOut& fo, int64_t* yt_rp,
+                           int32_t* yt_col, double* yt_val, Pool& scratch) {
+    cudaStream_t s = ctx->stream;
+    uint32_t* cnt = alloc_n<uint32_t>(scratch, n + 1);
+    if (!cnt) return RW_ERR_ALLOC;
+    rw_status rc;
+    if ((rc = check_cuda(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * (size_t)(n + 1), s), "memset")))
+        return rc;
+    const int blocks = grid_for(n, 256, ctx->num_sms * 8);
+    k_col_counts<<<blocks, 256, 0, s>>>(n, fo.y_rp, fo.y_col, cnt);
+    if ((rc = check_launch("transpose counts"))) return rc;
+    if ((rc = check_cuda(scan_u32_to_i64(cnt, yt_rp, n, s, scratch), "scan"))) return rc;
+    if ((rc = check_cuda(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * (size_t)(n + 1), s), "memset")))
+        return rc;
+    k_scatter_t<<<blocks, 256, 0, s>>>(n, fo.y_rp, fo.y_col, fo.y_val, yt_rp, cnt, yt_col, yt_val);
+    if ((rc = check_launch("transpose scatter"))) return rc;
+    k_sort_rows<<<blocks, 256, 0, s>>>(n, yt_rp, yt_col, yt_val);
+    return check_launch("transpose sort");
+}
+
+}  // namespace rw

@@ -1,0 +1,184 @@
+// rw_internal.h -- host-side structures shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "rw_common.cuh"
+#include "rwpc.h"
+
+struct rw_context {
+    cudaStream_t stream = nullptr;
+    rw_alloc_fn alloc = nullptr;
+    rw_free_fn free_fn = nullptr;
+    void* user = nullptr;
+    rw_options opt{};
+    int device = 0;
+    int num_sms = 0;
+    rw::DevStatus* d_status = nullptr;  // device copy
+    rw::DevStatus* h_status = nullptr;  // pinned host copy
+    void* h_small = nullptr;            // pinned host scratch (256 bytes)
+    cudaEvent_t ev[16] = {};
+};
+
+namespace rw {
+
+void set_error(const char* fmt, ...);
+
+// Device allocations made through the context's allocator.
+struct Pool {
+    rw_context* ctx = nullptr;
+    struct Buf {
+        void* p;
+        size_t bytes;
+    };
+    std::vector<Buf> bufs;
+    explicit Pool(rw_context* c = nullptr) : ctx(c) {}
+    void* get(size_t bytes);   // nullptr on failure (error message set)
+    void release(void* p);     // free one allocation now
+    void release_all();
+    ~Pool() { release_all(); }
+    Pool(const Pool&) = delete;
+    Pool& operator=(const Pool&) = delete;
+};
+
+template <typename T>
+inline T* alloc_n(Pool& pool, int64_t n) {
+    return static_cast<T*>(pool.get(sizeof(T) * (size_t)(n > 0 ? n : 1)));
+}
+
+// Exclusive prefix sum of n values; out has n + 1 entries (out[n] = total).
+// Works for in == out.  tmp: scratch from the pool.
+cudaError_t scan_u32(const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t s, Pool& pool);
+cudaError_t scan_u32_to_i64(const uint32_t* in, int64_t* out, int64_t n, cudaStream_t s,
+                            Pool& pool);
+cudaError_t scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s, Pool& pool);
+
+inline int grid_for(int64_t work, int block, int max_blocks) {
+    int64_t g = (work + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > max_blocks) g = max_blocks;
+    return (int)g;
+}
+
+// ---- build path (rw_tables.cu, rw_walk.cu, rw_emit.cu, rw_levels.cu) -------
+
+// Walk tables of one matrix, in the layout read by the walk kernel.
+//  thr:  per node a block of 8*blk32 uint32 words: [deg, t_0 .. t_{deg-1}, pad]
+//  nxt:  same indexing: nxt[w] = {column of threshold word w, block offset of that column}
+//  fthr: per walk row a block [updeg, lowdeg, ft_0 .. ft_{updeg-1}, pad]
+// Block offsets are in units of 8 words (32 bytes): every block starts on a
+// DRAM sector boundary.  Padding thresholds are 0xFFFFFFFF.
+struct Tables {
+    int32_t n = 0;
+    uint32_t* thr = nullptr;
+    uint2* nxt = nullptr;
+    uint32_t* fthr = nullptr;
+    uint32_t* toff8 = nullptr;    // [n+1]
+    uint32_t* foff8 = nullptr;    // [n+1]
+    int32_t* deg = nullptr;       // [n] off-diagonal count
+    int32_t* lowdeg = nullptr;    // [n] entries with column < row
+    double* S = nullptr;          // [n] sum_{j>k} A_kj
+    double* diag = nullptr;       // [n] A_kk
+    int32_t* diag_pos = nullptr;  // [n] CSR position of the diagonal
+    uint32_t* walk_flag = nullptr;    // [n+1] scanned into the walk-row index
+    int32_t n_walk_rows = 0;
+    int4* wrow = nullptr;         // [n_walk_rows] {k, foff8_k, toff8_k, lowdeg_k}
+    int32_t* walk_rows = nullptr; // [n_walk_rows] k ascending
+    uint64_t table_words = 0, first_words = 0;
+};
+
+rw_status build_tables(rw_context* ctx, const rw_csr* A, Tables& T, Pool& pool);
+
+// Per-walk-row budgets and the walk index space.
+struct WalkSpace {
+    int64_t total = 0;            // total walks
+    int64_t* wbase = nullptr;     // [n_walk_rows + 1]
+    int32_t* chunk_row = nullptr; // [nchunks]
+    int64_t nchunks = 0;
+};
+constexpr int kWalkChunk = 32;
+
+rw_status build_walk_space(rw_context* ctx, const Tables& T, uint32_t uniform,
+                           const uint32_t* d_budget, WalkSpace& ws, Pool& pool);
+
+struct WalkLaunch {
+    uint64_t seed = 0;
+    uint32_t matrix_index = 0;
+    uint32_t tag = 0;
+    uint64_t max_steps = 1ull << 24;
+    int record_lengths = 0;
+};
+
+rw_status run_walks(rw_context* ctx, const Tables& T, const WalkSpace& ws, const WalkLaunch& wl,
+                    int2* rec, unsigned long long* d_hops, Pool& pool, float* ms);
+
+// Merge + emission: per-walk records -> Y (CSR), D, counters.
+struct FactorOut {
+    int64_t nnz = 0;
+    int64_t* y_rp = nullptr;
+    int32_t* y_col = nullptr;
+    double* y_val = nullptr;
+    double* d = nullptr;
+    uint32_t* M = nullptr;
+    uint64_t* J = nullptr;
+    uint32_t* G = nullptr;
+};
+
+rw_status emit_factor(rw_context* ctx, const rw_csr* A, const Tables& T, const WalkSpace& ws,
+                      const int2* rec, double drop_tol, FactorOut& fo, Pool& pool,
+                      Pool& scratch, float* ms_merge, float* ms_emit);
+
+rw_status transpose_factor(rw_context* ctx, int32_t n, const FactorOut& fo, int64_t* yt_rp,
+                           int32_t* yt_col, double* yt_val, Pool& scratch);
+
+// Level orders for the two triangular solves: rows sorted by level.
+rw_status compute_levels(rw_context* ctx, int32_t n, const int64_t* rp, const int32_t* col,
+                         bool descending, int32_t* order, int32_t* depth, Pool& scratch);
+
+// ---- solve path (rw_solve.cu) ----------------------------------------------
+
+struct FactorView {
+    int32_t n;
+    int64_t nnz;
+    const int64_t* y_rp;
+    const int32_t* y_col;
+    const double* y_val;
+    const float* y_val32;
+    const int64_t* yt_rp;
+    const int32_t* yt_col;
+    const double* yt_val;
+    const float* yt_val32;
+    const double* d;
+    const float* d32;
+    const int32_t* fwd_order;
+    const int32_t* bwd_order;
+};
+
+void launch_to_fp32(const double* in, float* out, int64_t cnt, cudaStream_t s, int num_sms);
+rw_status spmv_fp64(rw_context* ctx, const rw_csr* A, const double* x, double* y, int nrhs);
+rw_status precond_fp64(rw_context* ctx, const FactorView& F, const double* r, double* z,
+                       int nrhs, Pool& scratch);
+rw_status pcg_run(rw_context* ctx, const rw_csr* A, const FactorView& F, const double* b,
+                  double* x, int nrhs, double tol, int max_iter, rw_precision prec,
+                  rw_pcg_stats* stats, int32_t* h_iters, double* h_relres);
+
+// Launch-and-check helper: returns RW_ERR_CUDA with a message on failure.
+rw_status check_cuda(cudaError_t e, const char* what);
+rw_status check_launch(const char* what);
+rw_status read_status(rw_context* ctx, const char* what);  // syncs, maps device flags
+rw_status reset_status(rw_context* ctx);
+
+}  // namespace rw
+
+struct rw_factor {
+    rw_context* ctx = nullptr;
+    rw::Pool pool;
+    rw_factor_desc desc{};
+    int32_t* fwd_order = nullptr;
+    int32_t* bwd_order = nullptr;
+    explicit rw_factor(rw_context* c) : ctx(c), pool(c) {}
+};

@@ -1,0 +1,595 @@
+// rw_solve.cu -- the solve step of Algorithm 1: PCG with M = Y^T diag(D) Y.
+//
+//   z = M^-1 r:  Y^T w = r (backward), v = w / D, Y z = v (forward).
+//
+// Vectors are node-major [n, nrhs], so one node's right-hand sides share a
+// DRAM sector and every gather serves all of them.  The triangular solves are
+// sync-free: rows are visited in level order by a co-resident grid, each
+// row's warp waits (bounded) until the values it depends on have left the
+// "pending" state, computes its row and publishes it with one relaxed store.
+// Scalars (alpha, beta, norms) stay on the device; the host reads one small
+// status record per iteration.
+#include <algorithm>
+#include <cmath>
+
+#include "rw_internal.h"
+
+namespace rw {
+
+constexpr int kDotParts = 1024;  // blocks of the dot-product producing kernels
+
+// ---------------------------------------------------------------------------
+// SpMV: y = A x for node-major vectors.  GS lanes per row, each lane keeps one
+// accumulator per right-hand side.  Optionally accumulates per-block partial
+// dot products x.y (per right-hand side) for the PCG step.
+// ---------------------------------------------------------------------------
+template <typename TA, typename TV, int NR, int GS>
+__global__ void __launch_bounds__(256) k_spmv(int32_t n, const int32_t* __restrict__ rp,
+                                              const int32_t* __restrict__ col,
+                                              const TA* __restrict__ val, const TV* __restrict__ x,
+                                              TV* __restrict__ y, int nrhs, double* part) {
+    __shared__ double sdot[NR];
+    if (part && threadIdx.x < NR) sdot[threadIdx.x] = 0.0;
+    if (part) __syncthreads();
+    const int g = (int)(lane_id() % GS);
+    const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / GS;
+    const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / GS;
+    double mydot[NR];
+#pragma unroll
+    for (int j = 0; j < NR; ++j) mydot[j] = 0.0;
+    for (int64_t row = grp; row < n; row += ngrp) {
+        TV acc[NR];
+#pragma unroll
+        for (int j = 0; j < NR; ++j) acc[j] = TV(0);
+        const int32_t s = rp[row], e = rp[row + 1];
+        for (int32_t p = s + g; p < e; p += GS) {
+            const int32_t c = col[p];
+            const TV a = (TV)val[p];
+#pragma unroll
+            for (int j = 0; j < NR; ++j)
+                if (j < nrhs) acc[j] += a * x[(size_t)c * nrhs + j];
+        }
+#pragma unroll
+        for (int j = 0; j < NR; ++j)
+#pragma unroll
+            for (int o = GS / 2; o > 0; o >>= 1) acc[j] += __shfl_xor_sync(kFull, acc[j], o, GS);
+        if (g == 0) {
+#pragma unroll
+            for (int j = 0; j < NR; ++j)
+                if (j < nrhs) {
+                    y[(size_t)row * nrhs + j] = acc[j];
+                    if (part) mydot[j] += (double)x[(size_t)row * nrhs + j] * (double)acc[j];
+                }
+        }
+    }
+    if (part) {
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+            double v = warp_sum(mydot[j]);
+            if (lane_id() == 0 && j < nrhs) atomicAdd(&sdot[j], v);
+        }
+        __syncthreads();
+        if (threadIdx.x < NR) part[(size_t)blockIdx.x * 16 + threadIdx.x] = sdot[threadIdx.x];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Sync-free triangular solve over a strict triangular CSR in level order:
+//   x_row = rhs_row / scale_row - sum_p val_p * x_{col_p}
+// (scale = D for the forward solve, none for the backward solve).  x must be
+// filled with the pending marker beforehand.  Co-resident grid (cooperative
+// launch); warp w handles positions w, w + NW, ... of the order.
+// ---------------------------------------------------------------------------
+template <typename T, int NR>
+__global__ void __launch_bounds__(256) k_trisolve(int32_t n, const int32_t* __restrict__ order,
+                                                  const int64_t* __restrict__ rp,
+                                                  const int32_t* __restrict__ col,
+                                                  const T* __restrict__ val,
+                                                  const T* __restrict__ rhs,
+                                                  const T* __restrict__ scale, T* x, int nrhs,
+                                                  DevStatus* st) {
+    constexpr int G = 32 / NR;
+    const int lane = (int)lane_id();
+    const int j = lane % NR;
+    const int eg = lane / NR;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const bool jok = j < nrhs;
+    for (int64_t pos = gw; pos < n; pos += nw) {
+        const int32_t row = order[pos];
+        const int64_t s = rp[row], e = rp[row + 1];
+        T b = T(0);
+        if (eg == 0 && jok) {
+            b = rhs[(size_t)row * nrhs + j];
+            if (scale) b = b / scale[row];
+        }
+        T acc = T(0);
+        for (int64_t p = s + eg; p < e; p += G) {
+            const int32_t c = col[p];
+            const T yv = val[p];
+            if (jok) {
+                const T* src = x + (size_t)c * nrhs + j;
+                T v = ld_relaxed(src);
+                unsigned spins = 0;
+                while (is_pending(v)) {
+                    if (wait_gives_up(spins, &st->timeout)) {
+                        v = T(0);
+                        break;
+                    }
+                    v = ld_relaxed(src);
+                }
+                acc += yv * v;
+            }
+        }
+#pragma unroll
+        for (int o = NR; o < 32; o <<= 1) acc += __shfl_xor_sync(kFull, acc, o);
+        if (eg == 0 && jok) st_relaxed(x + (size_t)row * nrhs + j, b - acc);
+    }
+}
+
+template <typename T>
+__global__ void k_fill_pending(T* x, int64_t cnt) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+         i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = pending_value(T(0));
+}
+
+// ---------------------------------------------------------------------------
+// PCG vector kernels and device scalars.
+// ---------------------------------------------------------------------------
+struct PcgScalars {
+    double bnorm2[16];
+    double rho[16];
+    double pq[16];
+    double alpha[16];
+    double rr[16];
+    double tt[16];
+    double beta[16];
+    int active[16];
+    int check[16];
+    int iters[16];
+    int broke;
+    int any_active;
+    int any_check;
+    int pad;
+};
+
+// Deterministic reduction of per-block partials: part[b * NR + j].
+__device__ double reduce_parts(const double* part, int nparts, int j) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nparts; b += blockDim.x) s += part[(size_t)b * 16 + j];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    const double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+enum ScalarOp { kOpBnorm = 0, kOpRho0, kOpAlpha, kOpResid, kOpTrue, kOpBeta, kOpReport };
+
+// One block of 256 threads.  part: [kDotParts][16].
+__global__ void __launch_bounds__(256) k_scalars(PcgScalars* S, const double* part, int nparts,
+                                                 int nrhs, int op, double tol, int it) {
+    for (int j = 0; j < nrhs; ++j) {
+        const double v = reduce_parts(part, nparts, j);
+        if (threadIdx.x != 0) continue;
+        switch (op) {
+            case kOpBnorm:
+                S->bnorm2[j] = v;
+                S->active[j] = v > 0.0;
+                S->iters[j] = 0;
+                break;
+            case kOpRho0:
+                S->rho[j] = v;
+                break;
+            case kOpAlpha:
+                S->pq[j] = v;
+                if (S->active[j]) {
+                    if (!(v > 0.0)) {
+                        S->broke = 1;
+                        S->active[j] = 0;
+                        S->alpha[j] = 0.0;
+                    } else {
+                        S->alpha[j] = S->rho[j] / v;
+                    }
+                } else {
+                    S->alpha[j] = 0.0;
+                }
+                break;
+            case kOpResid:
+                S->rr[j] = v;
+                S->check[j] = S->active[j] && (sqrt(v) < tol * sqrt(S->bnorm2[j]));
+                break;
+            case kOpTrue:
+                S->tt[j] = v;
+                if (S->check[j] && sqrt(v) < tol * sqrt(S->bnorm2[j])) {
+                    S->active[j] = 0;
+                    S->iters[j] = it;
+                }
+                break;
+            case kOpBeta:
+                S->beta[j] = S->active[j] ? v / S->rho[j] : 0.0;
+                S->rho[j] = v;
+                break;
+            case kOpReport:
+                S->tt[j] = v;
+                break;
+        }
+    }
+    if (threadIdx.x == 0) {
+        int a = 0, c = 0;
+        for (int j = 0; j < nrhs; ++j) {
+            a |= S->active[j];
+            c |= S->check[j];
+        }
+        S->any_active = a;
+        S->any_check = c;
+        if (op == kOpTrue)
+            for (int j = 0; j < nrhs; ++j) S->check[j] = 0;
+    }
+}
+
+// Block-level partial sums of a.b per right-hand side into part[blockIdx][j].
+template <typename TA, typename TB>
+__device__ void block_dot_parts(const TA* a, const TB* b, int64_t n, int nrhs, double* part) {
+    __shared__ double sd[16];
+    if (threadIdx.x < 16) sd[threadIdx.x] = 0.0;
+    __syncthreads();
+    const int64_t total = n * nrhs;
+    double acc[16];
+    for (int j = 0; j < 16; ++j) acc[j] = 0.0;
+    // thread handles whole nodes so that each accumulator belongs to one rhs
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        for (int j = 0; j < nrhs; ++j)
+            acc[j] += (double)a[i * nrhs + j] * (double)b[i * nrhs + j];
+    (void)total;
+    for (int j = 0; j < nrhs; ++j) {
+        const double v = warp_sum(acc[j]);
+        if (lane_id() == 0) atomicAdd(&sd[j], v);
+    }
+    __syncthreads();
+    if (threadIdx.x < 16) part[(size_t)blockIdx.x * 16 + threadIdx.x] = sd[threadIdx.x];
+}
+
+template <typename TA, typename TB>
+__global__ void __launch_bounds__(256) k_dot(const TA* a, const TB* b, int64_t n, int nrhs,
+                                             double* part) {
+    block_dot_parts(a, b, n, nrhs, part);
+}
+
+// x += alpha p (x FP64), r -= alpha q; partial r.r; marks w and z pending.
+template <typename T>
+__global__ void __launch_bounds__(256) k_update_xr(int64_t n, int nrhs, const PcgScalars* S,
+                                                   double* x, T* r, const T* p, const T* q, T* w,
+                                                   T* z, double* part) {
+    __shared__ double al[16];
+    if (threadIdx.x < 16) al[threadIdx.x] = threadIdx.x < (unsigned)nrhs ? S->alpha[threadIdx.x] : 0.0;
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        for (int j = 0; j < nrhs; ++j) {
+            const size_t o = (size_t)i * nrhs + j;
+            const double a = al[j];
+            if (a != 0.0) {
+                x[o] += a * (double)p[o];
+                r[o] = (T)((double)r[o] - a * (double)q[o]);
+            }
+            w[o] = pending_value(T(0));
+            z[o] = pending_value(T(0));
+        }
+    __syncthreads();
+    block_dot_parts(r, r, n, nrhs, part);
+}
+
+// p = z + beta p
+template <typename T>
+__global__ void __launch_bounds__(256) k_update_p(int64_t n, int nrhs, const PcgScalars* S,
+                                                  const T* z, T* p) {
+    __shared__ double be[16];
+    if (threadIdx.x < 16) be[threadIdx.x] = threadIdx.x < (unsigned)nrhs ? S->beta[threadIdx.x] : 0.0;
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        for (int j = 0; j < nrhs; ++j) {
+            const size_t o = (size_t)i * nrhs + j;
+            p[o] = (T)((double)z[o] + be[j] * (double)p[o]);
+        }
+}
+
+// t = b - A x in FP64 (true residual), optionally stored to r (residual
+// replacement) in T; partial t.t.
+template <typename T>
+__global__ void __launch_bounds__(256) k_true_resid(int32_t n, const int32_t* __restrict__ rp,
+                                                    const int32_t* __restrict__ col,
+                                                    const double* __restrict__ val,
+                                                    const double* __restrict__ b,
+                                                    const double* __restrict__ x, int nrhs,
+                                                    T* r_out, double* part) {
+    __shared__ double sd[16];
+    if (threadIdx.x < 16) sd[threadIdx.x] = 0.0;
+    __syncthreads();
+    double acc2[16];
+    for (int j = 0; j < 16; ++j) acc2[j] = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t s = rp[i], e = rp[i + 1];
+        for (int j = 0; j < nrhs; ++j) {
+            double ax = 0.0;
+            for (int32_t p = s; p < e; ++p) ax += val[p] * x[(size_t)col[p] * nrhs + j];
+            const double t = b[(size_t)i * nrhs + j] - ax;
+            if (r_out) r_out[(size_t)i * nrhs + j] = (T)t;
+            acc2[j] += t * t;
+        }
+    }
+    for (int j = 0; j < nrhs; ++j) {
+        const double v = warp_sum(acc2[j]);
+        if (lane_id() == 0) atomicAdd(&sd[j], v);
+    }
+    __syncthreads();
+    if (threadIdx.x < 16) part[(size_t)blockIdx.x * 16 + threadIdx.x] = sd[threadIdx.x];
+}
+
+template <typename Tin, typename Tout>
+__global__ void k_convert(const Tin* in, Tout* out, int64_t cnt) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (Tout)in[i];
+}
+
+__global__ void k_check_finite(const double* v, int64_t cnt, DevStatus* st) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (!isfinite(v[i])) atomicAdd(&st->pad[0], 1u);
+}
+
+// ---------------------------------------------------------------------------
+// Host-side dispatch
+// ---------------------------------------------------------------------------
+static int pow2_at_least(int v) {
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+template <typename TA, typename TV, int NR>
+static void launch_spmv_nr(int32_t n, const int32_t* rp, const int32_t* col, const TA* val,
+                           const TV* x, TV* y, int nrhs, double* part, int blocks, cudaStream_t s) {
+    k_spmv<TA, TV, NR, 8><<<blocks, 256, 0, s>>>(n, rp, col, val, x, y, nrhs, part);
+}
+
+template <typename TA, typename TV>
+static rw_status launch_spmv(rw_context* ctx, int32_t n, const int32_t* rp, const int32_t* col,
+                             const TA* val, const TV* x, TV* y, int nrhs, double* part) {
+    cudaStream_t s = ctx->stream;
+    const int nr = pow2_at_least(nrhs);
+    const int blocks = part ? kDotParts : grid_for((int64_t)n * 8, 256, ctx->num_sms * 16);
+    switch (nr) {
+        case 1: launch_spmv_nr<TA, TV, 1>(n, rp, col, val, x, y, nrhs, part, blocks, s); break;
+        case 2: launch_spmv_nr<TA, TV, 2>(n, rp, col, val, x, y, nrhs, part, blocks, s); break;
+        case 4: launch_spmv_nr<TA, TV, 4>(n, rp, col, val, x, y, nrhs, part, blocks, s); break;
+        case 8: launch_spmv_nr<TA, TV, 8>(n, rp, col, val, x, y, nrhs, part, blocks, s); break;
+        default: launch_spmv_nr<TA, TV, 16>(n, rp, col, val, x, y, nrhs, part, blocks, s); break;
+    }
+    return check_launch("spmv");
+}
+
+template <typename T, int NR>
+static rw_status launch_trisolve_nr(rw_context* ctx, int32_t n, const int32_t* order,
+                                    const int64_t* rp, const int32_t* col, const T* val,
+                                    const T* rhs, const T* scale, T* x, int nrhs) {
+    auto fn = k_trisolve<T, NR>;
+    static int per_sm = -1;
+    if (per_sm < 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0);
+        if (per_sm < 1) per_sm = 1;
+    }
+    int64_t blocks = (int64_t)per_sm * ctx->num_sms;
+    const int64_t need = ((int64_t)n + 7) / 8;  // 8 warps per block, one row per warp at a time
+    if (blocks > need) blocks = need;
+    if (blocks < 1) blocks = 1;
+    DevStatus* st = ctx->d_status;
+    void* args[] = {(void*)&n, (void*)&order, (void*)&rp, (void*)&col, (void*)&val, (void*)&rhs,
+                    (void*)&scale, (void*)&x, (void*)&nrhs, (void*)&st};
+    return check_cuda(cudaLaunchCooperativeKernel((const void*)fn, dim3((unsigned)blocks), dim3(256),
+                                                  args, 0, ctx->stream),
+                      "triangular solve launch");
+}
+
+template <typename T>
+static rw_status launch_trisolve(rw_context* ctx, int32_t n, const int32_t* order,
+                                 const int64_t* rp, const int32_t* col, const T* val, const T* rhs,
+                                 const T* scale, T* x, int nrhs) {
+    switch (pow2_at_least(nrhs)) {
+        case 1: return launch_trisolve_nr<T, 1>(ctx, n, order, rp, col, val, rhs, scale, x, nrhs);
+        case 2: return launch_trisolve_nr<T, 2>(ctx, n, order, rp, col, val, rhs, scale, x, nrhs);
+        case 4: return launch_trisolve_nr<T, 4>(ctx, n, order, rp, col, val, rhs, scale, x, nrhs);
+        case 8: return launch_trisolve_nr<T, 8>(ctx, n, order, rp, col, val, rhs, scale, x, nrhs);
+        default: return launch_trisolve_nr<T, 16>(ctx, n, order, rp, col, val, rhs, scale, x, nrhs);
+    }
+}
+
+template <typename T>
+static rw_status fill_pending(rw_context* ctx, T* x, int64_t cnt) {
+    k_fill_pending<T><<<grid_for(cnt, 256, ctx->num_sms * 8), 256, 0, ctx->stream>>>(x, cnt);
+    return check_launch("fill");
+}
+
+// z = Y^-1 D^-1 Y^-T r; w: scratch [n, nrhs]; w and z must be pending.
+template <typename T>
+static rw_status precond_t(rw_context* ctx, const FactorView& F, const T* yv, const T* ytv,
+                           const T* d, const T* r, T* w, T* z, int nrhs) {
+    rw_status rc = launch_trisolve<T>(ctx, F.n, F.bwd_order, F.yt_rp, F.yt_col, ytv, r, nullptr, w,
+                                      nrhs);
+    if (rc) return rc;
+    return launch_trisolve<T>(ctx, F.n, F.fwd_order, F.y_rp, F.y_col, yv, w, d, z, nrhs);
+}
+
+void launch_to_fp32(const double* in, float* out, int64_t cnt, cudaStream_t s, int num_sms) {
+    k_convert<double, float><<<grid_for(cnt, 256, num_sms * 8), 256, 0, s>>>(in, out, cnt);
+}
+
+rw_status spmv_fp64(rw_context* ctx, const rw_csr* A, const double* x, double* y, int nrhs) {
+    return launch_spmv<double, double>(ctx, A->n, A->row_ptr, A->col, A->val, x, y, nrhs, nullptr);
+}
+
+rw_status precond_fp64(rw_context* ctx, const FactorView& F, const double* r, double* z,
+                       int nrhs, Pool& scratch) {
+    const int64_t cnt = (int64_t)F.n * nrhs;
+    double* w = alloc_n<double>(scratch, cnt);
+    if (!w) return RW_ERR_ALLOC;
+    rw_status rc;
+    if ((rc = fill_pending(ctx, w, cnt))) return rc;
+    if ((rc = fill_pending(ctx, z, cnt))) return rc;
+    if ((rc = precond_t<double>(ctx, F, F.y_val, F.yt_val, F.d, r, w, z, nrhs))) return rc;
+    return read_status(ctx, "preconditioner");
+}
+
+template <typename T>
+static rw_status pcg_t(rw_context* ctx, const rw_csr* A, const FactorView& F, const double* b,
+                       double* x, int nrhs, double tol, int max_iter, rw_pcg_stats* stats,
+                       int32_t* h_iters, double* h_relres, Pool& sc, const T* Aval, const T* yv,
+                       const T* ytv, const T* dv, bool mixed) {
+    cudaStream_t s = ctx->stream;
+    const int32_t n = A->n;
+    const int64_t cnt = (int64_t)n * nrhs;
+    T* r = alloc_n<T>(sc, cnt);
+    T* z = alloc_n<T>(sc, cnt);
+    T* p = alloc_n<T>(sc, cnt);
+    T* q = alloc_n<T>(sc, cnt);
+    T* w = alloc_n<T>(sc, cnt);
+    double* part = alloc_n<double>(sc, (int64_t)kDotParts * 16);
+    PcgScalars* S = alloc_n<PcgScalars>(sc, 1);
+    if (!r || !z || !p || !q || !w || !part || !S) return RW_ERR_ALLOC;
+    PcgScalars* hS = static_cast<PcgScalars*>(ctx->h_small);
+    const int vb = grid_for(n, 256, kDotParts);
+    rw_status rc;
+    if ((rc = check_cuda(cudaMemsetAsync(S, 0, sizeof(PcgScalars), s), "memset"))) return rc;
+    if ((rc = check_cuda(cudaMemsetAsync(x, 0, sizeof(double) * (size_t)cnt, s), "memset"))) return rc;
+    if ((rc = check_cuda(cudaMemsetAsync(part, 0, sizeof(double) * kDotParts * 16, s), "memset")))
+        return rc;
+    k_check_finite<<<vb, 256, 0, s>>>(b, cnt, ctx->d_status);
+    k_convert<double, T><<<vb, 256, 0, s>>>(b, r, cnt);
+    k_dot<double, double><<<vb, 256, 0, s>>>(b, b, n, nrhs, part);
+    k_scalars<<<1, 256, 0, s>>>(S, part, vb, nrhs, kOpBnorm, tol, 0);
+    if ((rc = check_launch("pcg init"))) return rc;
+    if ((rc = fill_pending(ctx, w, cnt))) return rc;
+    if ((rc = fill_pending(ctx, z, cnt))) return rc;
+    if ((rc = precond_t<T>(ctx, F, yv, ytv, dv, r, w, z, nrhs))) return rc;
+    k_dot<T, T><<<vb, 256, 0, s>>>(r, z, n, nrhs, part);
+    k_scalars<<<1, 256, 0, s>>>(S, part, vb, nrhs, kOpRho0, tol, 0);
+    k_convert<T, T><<<vb, 256, 0, s>>>(z, p, cnt);
+    if ((rc = check_launch("pcg start"))) return rc;
+    if ((rc = check_cuda(cudaMemcpyAsync(hS, S, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s), "copy")))
+        return rc;
+    if ((rc = read_status(ctx, "pcg start"))) return rc;
+    if (ctx->d_status && static_cast<rw::DevStatus*>(ctx->h_status)->pad[0]) {
+        set_error("pcg: right-hand side holds a non-finite value");
+        return RW_ERR_ARG;
+    }
+    int done_iters = 0;
+    const int refine = ctx->opt.refine_every > 0 ? ctx->opt.refine_every : 50;
+    bool any_active = hS->any_active != 0;
+    for (int it = 1; it <= max_iter && any_active; ++it) {
+        done_iters = it;
+        if ((rc = launch_spmv<T, T>(ctx, n, A->row_ptr, A->col, Aval, p, q, nrhs, part))) return rc;
+        k_scalars<<<1, 256, 0, s>>>(S, part, kDotParts, nrhs, kOpAlpha, tol, it);
+        k_update_xr<T><<<vb, 256, 0, s>>>(n, nrhs, S, x, r, p, q, w, z, part);
+        if (mixed && it % refine == 0)
+            k_true_resid<T><<<vb, 256, 0, s>>>(n, A->row_ptr, A->col, A->val, b, x, nrhs, r, part);
+        k_scalars<<<1, 256, 0, s>>>(S, part, vb, nrhs, kOpResid, tol, it);
+        if ((rc = check_launch("pcg step"))) return rc;
+        if ((rc = check_cuda(cudaMemcpyAsync(hS, S, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s),
+                             "copy")))
+            return rc;
+        if ((rc = check_cuda(cudaStreamSynchronize(s), "sync"))) return rc;
+        if (hS->any_check) {
+            k_true_resid<T><<<vb, 256, 0, s>>>(n, A->row_ptr, A->col, A->val, b, x, nrhs, nullptr,
+                                               part);
+            k_scalars<<<1, 256, 0, s>>>(S, part, vb, nrhs, kOpTrue, tol, it);
+            if ((rc = check_launch("pcg true residual"))) return rc;
+            if ((rc = check_cuda(cudaMemcpyAsync(hS, S, sizeof(PcgScalars), cudaMemcpyDeviceToHost,
+                                                 s),
+                                 "copy")))
+                return rc;
+            if ((rc = check_cuda(cudaStreamSynchronize(s), "sync"))) return rc;
+            if (!hS->any_active) break;
+        }
+        if (hS->broke) break;
+        if ((rc = precond_t<T>(ctx, F, yv, ytv, dv, r, w, z, nrhs))) return rc;
+        k_dot<T, T><<<vb, 256, 0, s>>>(r, z, n, nrhs, part);
+        k_scalars<<<1, 256, 0, s>>>(S, part, vb, nrhs, kOpBeta, tol, it);
+        k_update_p<T><<<vb, 256, 0, s>>>(n, nrhs, S, z, p);
+        if ((rc = check_launch("pcg direction"))) return rc;
+    }
+    // final true residuals for the report
+    k_true_resid<T><<<vb, 256, 0, s>>>(n, A->row_ptr, A->col, A->val, b, x, nrhs, nullptr, part);
+    k_scalars<<<1, 256, 0, s>>>(S, part, vb, nrhs, kOpReport, tol, done_iters);
+    if ((rc = check_launch("pcg report"))) return rc;
+    if ((rc = check_cuda(cudaMemcpyAsync(hS, S, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s), "copy")))
+        return rc;
+    if ((rc = read_status(ctx, "pcg"))) return rc;
+    int maxit = 0;
+    double maxrel = 0.0;
+    bool conv_all = true;
+    for (int j = 0; j < nrhs; ++j) {
+        const int itj = hS->active[j] ? done_iters : hS->iters[j];
+        if (hS->active[j]) conv_all = false;
+        const double rel = hS->bnorm2[j] > 0.0 ? std::sqrt(hS->tt[j] / hS->bnorm2[j]) : 0.0;
+        maxit = std::max(maxit, itj);
+        maxrel = std::max(maxrel, rel);
+        if (h_iters) h_iters[j] = itj;
+        if (h_relres) h_relres[j] = rel;
+    }
+    if (stats) {
+        stats->iterations = maxit;
+        stats->rel_residual = maxrel;
+    }
+    if (hS->broke) {
+        set_error("pcg breakdown: p.Ap <= 0");
+        return RW_ERR_BREAKDOWN;
+    }
+    if (tol > 0.0 && !conv_all) {
+        set_error("pcg did not reach the tolerance in %d iterations", max_iter);
+        return RW_ERR_NO_CONVERGENCE;
+    }
+    return RW_OK;
+}
+
+rw_status pcg_run(rw_context* ctx, const rw_csr* A, const FactorView& F, const double* b,
+                  double* x, int nrhs, double tol, int max_iter, rw_precision prec,
+                  rw_pcg_stats* stats, int32_t* h_iters, double* h_relres) {
+    Pool sc(ctx);
+    cudaStream_t s = ctx->stream;
+    rw_status rc;
+    if (ctx->opt.timing) cudaEventRecord(ctx->ev[8], s);
+    if (prec == RW_FP32_MIXED) {
+        if (!F.y_val32 || !F.yt_val32 || !F.d32) {
+            set_error("pcg: FP32 mode needs a factor built with store_fp32 = 1");
+            return RW_ERR_ARG;
+        }
+        float* a32 = alloc_n<float>(sc, A->nnz);
+        if (!a32) return RW_ERR_ALLOC;
+        k_convert<double, float><<<grid_for(A->nnz, 256, ctx->num_sms * 8), 256, 0, s>>>(
+            A->val, a32, A->nnz);
+        if ((rc = check_launch("convert A"))) return rc;
+        rc = pcg_t<float>(ctx, A, F, b, x, nrhs, tol, max_iter, stats, h_iters, h_relres, sc, a32,
+                          F.y_val32, F.yt_val32, F.d32, true);
+    } else {
+        rc = pcg_t<double>(ctx, A, F, b, x, nrhs, tol, max_iter, stats, h_iters, h_relres, sc,
+                           A->val, F.y_val, F.yt_val, F.d, false);
+    }
+    if (ctx->opt.timing && stats) {
+        cudaEventRecord(ctx->ev[9], s);
+        cudaEventSynchronize(ctx->ev[9]);
+        cudaEventElapsedTime(&stats->solve_ms, ctx->ev[8], ctx->ev[9]);
+    }
+    return rc;
+}
+
+}  // namespace rw

@@ -1,0 +1,329 @@
+// rw_tables.cu -- prefix sums, matrix validation and the walk tables.
+//
+// The walk tables encode the transition probabilities of the walk game
+// (Sec. 2.1, Eq. map) as integer thresholds of cumulative probabilities, and
+// the first step of each walk over the upper neighbours only (Sec. 5.2).
+#include <climits>
+#include <cstdarg>
+#include <cstdio>
+
+#include "rw_internal.h"
+
+namespace rw {
+
+// ---------------------------------------------------------------------------
+// Exclusive prefix sum: tiles of 2048 values (256 threads x 8 consecutive
+// values per thread), tile totals scanned recursively.
+// ---------------------------------------------------------------------------
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+template <typename T>
+__device__ T block_exclusive_scan(T v, T* total) {
+    __shared__ T warp_tot[kScanThreads / 32];
+    const unsigned lane = lane_id(), warp = threadIdx.x >> 5;
+    T incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T y = __shfl_up_sync(kFull, incl, o);
+        if ((int)lane >= o) incl += y;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        T t = (lane < kScanThreads / 32) ? warp_tot[lane] : T(0);
+        T ti = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            T y = __shfl_up_sync(kFull, ti, o);
+            if ((int)lane >= o) ti += y;
+        }
+        if (lane < kScanThreads / 32) warp_tot[lane] = ti - t;
+        if (lane == kScanThreads / 32 - 1) *total = ti;
+    }
+    __syncthreads();
+    T r = warp_tot[warp] + incl - v;
+    __syncthreads();
+    return r;
+}
+
+template <typename Tin, typename Tout>
+__global__ void __launch_bounds__(kScanThreads) k_tile_sums(const Tin* in, int64_t n, Tout* sums) {
+    __shared__ Tout tot;
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    Tout acc = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i)
+        if (base + i < n) acc += (Tout)in[base + i];
+    block_exclusive_scan<Tout>(acc, &tot);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+template <typename Tin, typename Tout>
+__global__ void __launch_bounds__(kScanThreads)
+    k_tile_scan(const Tin* in, int64_t n, const Tout* tile_off, Tout* out) {
+    __shared__ Tout tot;
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    Tout v[kScanItems];
+    Tout acc = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        v[i] = (base + i < n) ? (Tout)in[base + i] : Tout(0);
+        acc += v[i];
+    }
+    Tout pre = block_exclusive_scan<Tout>(acc, &tot);
+    if (tile_off) pre += tile_off[blockIdx.x];
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        if (base + i < n) {
+            out[base + i] = pre;
+            if (base + i == n - 1) out[n] = pre + v[i];
+        }
+        pre += v[i];
+    }
+}
+
+template <typename Tout>
+__global__ void k_set_zero(Tout* p) { *p = 0; }
+
+template <typename Tin, typename Tout>
+static cudaError_t scan_impl(const Tin* in, Tout* out, int64_t n, cudaStream_t s, Pool& pool) {
+    if (n <= 0) {
+        k_set_zero<Tout><<<1, 1, 0, s>>>(out);
+        return cudaGetLastError();
+    }
+    const int64_t tiles = (n + kScanTile - 1) / kScanTile;
+    if (tiles == 1) {
+        k_tile_scan<Tin, Tout><<<1, kScanThreads, 0, s>>>(in, n, nullptr, out);
+        return cudaGetLastError();
+    }
+    Tout* sums = alloc_n<Tout>(pool, tiles + 1);
+    if (!sums) return cudaErrorMemoryAllocation;
+    k_tile_sums<Tin, Tout><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, sums);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = scan_impl<Tout, Tout>(sums, sums, tiles, s, pool);
+    if (e != cudaSuccess) return e;
+    k_tile_scan<Tin, Tout><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, sums, out);
+    return cudaGetLastError();
+}
+
+cudaError_t scan_u32(const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t s, Pool& pool) {
+    return scan_impl<uint32_t, uint32_t>(in, out, n, s, pool);
+}
+cudaError_t scan_u32_to_i64(const uint32_t* in, int64_t* out, int64_t n, cudaStream_t s,
+                            Pool& pool) {
+    return scan_impl<uint32_t, int64_t>(in, out, n, s, pool);
+}
+cudaError_t scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s, Pool& pool) {
+    return scan_impl<int64_t, int64_t>(in, out, n, s, pool);
+}
+
+// ---------------------------------------------------------------------------
+// Validation and per-row sizes.  One thread per row.
+// ---------------------------------------------------------------------------
+__global__ void k_row_info(int32_t n, int64_t nnz, const int32_t* __restrict__ rp,
+                           const int32_t* __restrict__ col, const double* __restrict__ val,
+                           int32_t* deg, int32_t* lowdeg, int32_t* dpos, uint32_t* blk_full,
+                           uint32_t* blk_first, uint32_t* walk_flag, DevStatus* st) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (rp[0] != 0 || (int64_t)rp[n] != nnz))
+        atomicMin(&st->bad_row, 1u);
+    for (int32_t l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x) {
+        int32_t s = rp[l], e = rp[l + 1];
+        bool ok = e > s && s >= 0 && (int64_t)e <= nnz;
+        if (!ok) e = s;  // do not read outside the arrays
+        int32_t lo = 0, up = 0, prev = -1, dp = -1;
+        double dg = 0.0, sum = 0.0;
+        for (int32_t p = s; p < e; ++p) {
+            const int32_t c = col[p];
+            const double v = val[p];
+            if (c < 0 || c >= n || c <= prev) ok = false;
+            prev = c;
+            if (c == l) {
+                dp = p;
+                dg = v;
+                if (!(v > 0.0) || !isfinite(v)) ok = false;
+            } else {
+                if (!(v < 0.0) || !isfinite(v)) ok = false;
+                sum = __dadd_rn(sum, -v);
+                if (c < l) ++lo; else ++up;
+            }
+        }
+        if (dp < 0) ok = false;
+        if (ok && __dadd_rn(dg, -sum) < __dmul_rn(-1e-12, dg)) ok = false;
+        if (!ok) atomicMin(&st->bad_row, (unsigned)l + 1u);
+        const int32_t d = lo + up;
+        deg[l] = d;
+        lowdeg[l] = lo;
+        dpos[l] = dp;
+        blk_full[l] = (uint32_t)(1 + d + 7) / 8u;
+        blk_first[l] = up > 0 ? (uint32_t)(2 + up + 7) / 8u : 0u;
+        walk_flag[l] = up > 0 ? 1u : 0u;
+    }
+}
+
+// Thresholds and successor entries.  One thread per row; the sums run
+// sequentially over the row in ascending column order, each addition and
+// division rounded once (the same order the sampling rule is defined in).
+__global__ void k_fill_tables(int32_t n, const int32_t* __restrict__ rp,
+                              const int32_t* __restrict__ col, const double* __restrict__ val,
+                              const int32_t* __restrict__ deg, const int32_t* __restrict__ lowdeg,
+                              const int32_t* __restrict__ dpos, const uint32_t* __restrict__ toff8,
+                              const uint32_t* __restrict__ foff8, uint32_t* thr, uint2* nxt,
+                              uint32_t* fthr, double* S, double* diag) {
+    for (int32_t l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x) {
+        const int32_t s = rp[l], e = rp[l + 1], dp = dpos[l], d = deg[l], lo = lowdeg[l];
+        const double dg = val[dp];
+        diag[l] = dg;
+        const uint64_t tb = (uint64_t)toff8[l] * 8u;
+        const uint64_t tend = (uint64_t)toff8[l + 1] * 8u;
+        thr[tb] = (uint32_t)d;
+        nxt[tb] = make_uint2(0u, 0u);
+        double c = 0.0;
+        uint64_t w = tb + 1;
+        for (int32_t p = s; p < e; ++p) {
+            if (p == dp) continue;
+            c = __dadd_rn(c, -val[p]);
+            thr[w] = cumulative_threshold(c, dg);
+            const int32_t j = col[p];
+            nxt[w] = make_uint2((uint32_t)j, toff8[j]);
+            ++w;
+        }
+        for (; w < tend; ++w) {
+            thr[w] = 0xFFFFFFFFu;
+            nxt[w] = make_uint2(0u, 0u);
+        }
+        const int32_t up = d - lo;
+        double cu = 0.0;
+        if (up > 0) {
+            for (int32_t p = dp + 1; p < e; ++p) cu = __dadd_rn(cu, -val[p]);
+            const uint64_t fb = (uint64_t)foff8[l] * 8u;
+            const uint64_t fend = (uint64_t)foff8[l + 1] * 8u;
+            fthr[fb] = (uint32_t)up;
+            fthr[fb + 1] = (uint32_t)lo;
+            double cc = 0.0;
+            uint64_t q = fb + 2;
+            for (int32_t p = dp + 1; p < e; ++p) {
+                cc = __dadd_rn(cc, -val[p]);
+                fthr[q++] = cumulative_threshold(cc, cu);
+            }
+            for (; q < fend; ++q) fthr[q] = 0xFFFFFFFFu;
+        }
+        S[l] = -cu;
+    }
+}
+
+__global__ void k_walk_rows(int32_t n, const uint32_t* __restrict__ widx,
+                            const uint32_t* __restrict__ toff8, const uint32_t* __restrict__ foff8,
+                            const int32_t* __restrict__ lowdeg, int4* wrow, int32_t* walk_rows) {
+    for (int32_t l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x) {
+        const uint32_t r = widx[l];
+        if (widx[l + 1] != r) {
+            wrow[r] = make_int4(l, (int)foff8[l], (int)toff8[l], lowdeg[l]);
+            walk_rows[r] = l;
+        }
+    }
+}
+
+rw_status build_tables(rw_context* ctx, const rw_csr* A, Tables& T, Pool& pool) {
+    const int32_t n = A->n;
+    cudaStream_t s = ctx->stream;
+    T.n = n;
+    T.deg = alloc_n<int32_t>(pool, n);
+    T.lowdeg = alloc_n<int32_t>(pool, n);
+    T.diag_pos = alloc_n<int32_t>(pool, n);
+    T.toff8 = alloc_n<uint32_t>(pool, n + 1);
+    T.foff8 = alloc_n<uint32_t>(pool, n + 1);
+    T.walk_flag = alloc_n<uint32_t>(pool, n + 1);
+    T.S = alloc_n<double>(pool, n);
+    T.diag = alloc_n<double>(pool, n);
+    if (!T.deg || !T.lowdeg || !T.diag_pos || !T.toff8 || !T.foff8 || !T.walk_flag || !T.S ||
+        !T.diag)
+        return RW_ERR_ALLOC;
+    const int blocks = grid_for(n, 256, ctx->num_sms * 8);
+    k_row_info<<<blocks, 256, 0, s>>>(n, A->nnz, A->row_ptr, A->col, A->val, T.deg, T.lowdeg, T.diag_pos,
+                                      T.toff8, T.foff8, T.walk_flag, ctx->d_status);
+    rw_status rc = check_launch("row info");
+    if (rc) return rc;
+    if ((rc = check_cuda(scan_u32(T.toff8, T.toff8, n, s, pool), "scan"))) return rc;
+    if ((rc = check_cuda(scan_u32(T.foff8, T.foff8, n, s, pool), "scan"))) return rc;
+    if ((rc = check_cuda(scan_u32(T.walk_flag, T.walk_flag, n, s, pool), "scan"))) return rc;
+    uint32_t* hs = static_cast<uint32_t*>(ctx->h_small);
+    if ((rc = check_cuda(cudaMemcpyAsync(hs, T.toff8 + n, 4, cudaMemcpyDeviceToHost, s), "copy")))
+        return rc;
+    if ((rc = check_cuda(cudaMemcpyAsync(hs + 1, T.foff8 + n, 4, cudaMemcpyDeviceToHost, s),
+                         "copy")))
+        return rc;
+    if ((rc = check_cuda(cudaMemcpyAsync(hs + 2, T.walk_flag + n, 4, cudaMemcpyDeviceToHost, s),
+                         "copy")))
+        return rc;
+    if ((rc = read_status(ctx, "matrix validation"))) return rc;
+    T.table_words = (uint64_t)hs[0] * 8u;
+    T.first_words = (uint64_t)hs[1] * 8u;
+    T.n_walk_rows = (int32_t)hs[2];
+    T.thr = alloc_n<uint32_t>(pool, (int64_t)T.table_words);
+    T.nxt = alloc_n<uint2>(pool, (int64_t)T.table_words);
+    T.fthr = alloc_n<uint32_t>(pool, (int64_t)T.first_words);
+    T.wrow = alloc_n<int4>(pool, T.n_walk_rows);
+    T.walk_rows = alloc_n<int32_t>(pool, T.n_walk_rows);
+    if (!T.thr || !T.nxt || !T.fthr || !T.wrow || !T.walk_rows) return RW_ERR_ALLOC;
+    k_fill_tables<<<blocks, 256, 0, s>>>(n, A->row_ptr, A->col, A->val, T.deg, T.lowdeg,
+                                         T.diag_pos, T.toff8, T.foff8, T.thr, T.nxt, T.fthr, T.S,
+                                         T.diag);
+    if ((rc = check_launch("fill tables"))) return rc;
+    k_walk_rows<<<blocks, 256, 0, s>>>(n, T.walk_flag, T.toff8, T.foff8, T.lowdeg, T.wrow,
+                                       T.walk_rows);
+    return check_launch("walk rows");
+}
+
+// ---------------------------------------------------------------------------
+// Walk index space: record index = wbase[r] + w for walk w of walk row r.
+// chunk_row[c] = the walk row that holds walk c * kWalkChunk.
+// ---------------------------------------------------------------------------
+__global__ void k_budgets(int32_t nw, const int4* __restrict__ wrow, uint32_t uniform,
+                          const uint32_t* __restrict__ budget, int64_t* out, DevStatus* st) {
+    for (int32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < nw; r += gridDim.x * blockDim.x) {
+        const uint32_t b = budget ? budget[wrow[r].x] : uniform;
+        if (b == 0u) atomicAdd(&st->bad_budget, 1u);
+        out[r] = (int64_t)b;
+    }
+}
+
+__global__ void k_chunk_rows(int32_t nw, const int64_t* __restrict__ wbase, int32_t* chunk_row) {
+    for (int32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < nw; r += gridDim.x * blockDim.x) {
+        const int64_t c0 = (wbase[r] + kWalkChunk - 1) / kWalkChunk;
+        const int64_t c1 = (wbase[r + 1] + kWalkChunk - 1) / kWalkChunk;
+        for (int64_t c = c0; c < c1; ++c) chunk_row[c] = r;
+    }
+}
+
+rw_status build_walk_space(rw_context* ctx, const Tables& T, uint32_t uniform,
+                           const uint32_t* d_budget, WalkSpace& ws, Pool& pool) {
+    cudaStream_t s = ctx->stream;
+    const int32_t nw = T.n_walk_rows;
+    ws.wbase = alloc_n<int64_t>(pool, nw + 1);
+    if (!ws.wbase) return RW_ERR_ALLOC;
+    const int blocks = grid_for(nw, 256, ctx->num_sms * 8);
+    rw_status rc;
+    if (nw > 0) {
+        k_budgets<<<blocks, 256, 0, s>>>(nw, T.wrow, uniform, d_budget, ws.wbase, ctx->d_status);
+        if ((rc = check_launch("budgets"))) return rc;
+    }
+    if ((rc = check_cuda(scan_i64(ws.wbase, ws.wbase, nw, s, pool), "scan"))) return rc;
+    int64_t* hs = static_cast<int64_t*>(ctx->h_small);
+    if ((rc = check_cuda(cudaMemcpyAsync(hs, ws.wbase + nw, 8, cudaMemcpyDeviceToHost, s), "copy")))
+        return rc;
+    if ((rc = read_status(ctx, "walk budgets"))) return rc;
+    ws.total = hs[0];
+    ws.nchunks = (ws.total + kWalkChunk - 1) / kWalkChunk;
+    ws.chunk_row = alloc_n<int32_t>(pool, ws.nchunks);
+    if (!ws.chunk_row) return RW_ERR_ALLOC;
+    if (nw > 0) {
+        k_chunk_rows<<<blocks, 256, 0, s>>>(nw, ws.wbase, ws.chunk_row);
+        if ((rc = check_launch("chunk rows"))) return rc;
+    }
+    return RW_OK;
+}
+
+}  // namespace rw

@@ -1,0 +1,57 @@
+"""The C-ABI library builds, loads without a GPU and exports every function
+that include/rwpc.h declares (no compute calls here)."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "rwpc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"typedef[^;]*;", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*([A-Za-z_][A-Za-z0-9_]*)\s*\(",
+                       src, flags=re.M)
+    return sorted(set(n for n in names if not n.startswith("RW")))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_math_0609672_gb300 import _build
+    return _build.build()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("rw_build_factor", "pcg_solve", "rw_context_create", "rw_factor_view"):
+        assert required in names
+
+
+def test_library_exports_every_declared_function(lib_path):
+    out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True,
+                         text=True, check=True).stdout
+    exported = {l.split()[-1] for l in out.splitlines() if " T " in l}
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+
+
+def test_library_loads_without_gpu(lib_path):
+    import paper_math_0609672_gb300 as P
+    lib = P.load()
+    assert P.rw_status_string(-2).startswith("matrix is not")
+    o = P.rw_options_default()
+    assert o.max_steps == 1 << 24 and o.store_fp32 == 1 and o.refine_every == 50
+
+
+def test_product_path_has_no_cpu_fallback():
+    # the package must not import the oracle anywhere
+    pkg = os.path.join(ROOT, "paper_math_0609672_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt, f
+                assert "rw_oracle" not in txt, f

@@ -1,0 +1,238 @@
+"""GPU factor construction vs the CPU oracle (bit-exact).
+
+Walk records, counters (M', J', G'), hop totals, Y (CSR pattern and FP64
+values) and D must be identical to the oracle's on the same seeded inputs:
+the walk game, keying, sampling rule and the FP64 operation order of
+Eqs. newy/newz are fixed on both sides.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_math_0609672_gb300 as P
+    from paper_math_0609672_gb300 import _build
+    _build.build()
+    return P
+
+
+@pytest.fixture(scope="module")
+def ctx(P):
+    c = P.Context(options=P.rw_options_default(keep_records=1))
+    yield c
+    c.close()
+
+
+def gpu_factor(P, ctx, A, walks, seed, drop, budget=None):
+    import torch
+    dA = P.CSR.from_host(A)
+    if budget is None:
+        F = P.rw_build_factor(ctx, dA, walks, seed, drop)
+    else:
+        F = P.rw_build_factor_budget(ctx, dA, torch.as_tensor(budget.astype(np.int32)).cuda(),
+                                     seed, drop)
+    t = {k: v.cpu().numpy() for k, v in F.tensors().items()}
+    t["total_hops"] = int(F.desc.total_hops)
+    t["fwd_levels"], t["bwd_levels"] = F.desc.fwd_levels, F.desc.bwd_levels
+    t["phase_ms"] = list(F.desc.phase_ms)
+    F.destroy()
+    return t
+
+
+def assert_factor_equal(t, ref, records=True):
+    n = len(ref["D"])
+    assert np.array_equal(t["y_row_ptr"], ref["rowptr"])
+    assert np.array_equal(t["y_col"], ref["col"])
+    assert np.array_equal(t["y_val"].view(np.int64), ref["val"].view(np.int64))
+    assert np.array_equal(t["d"].view(np.int64), ref["D"].view(np.int64))
+    assert np.array_equal(t["walks"].astype(np.uint64), ref["M"])
+    assert np.array_equal(t["visits"].astype(np.uint64), ref["J"])
+    assert np.array_equal(t["ground"].astype(np.uint64), ref["G"])
+    assert t["total_hops"] == int(ref["hops"].sum())
+    if records and "rec_end" in ref:
+        rec = t["records"].reshape(-1, 2)
+        assert np.array_equal(rec[:, 0], ref["rec_end"])
+        assert np.array_equal(rec[:, 1].astype(np.uint32), ref["rec_ret"])
+        assert np.array_equal(t["walk_rows"], ref["walk_rows"])
+
+
+def levels_of(n, rp, col):
+    lev = np.zeros(n, np.int64)
+    for k in range(n):
+        s, e = rp[k], rp[k + 1]
+        if e > s:
+            lev[k] = 1 + lev[col[s:e]].max()
+    return lev
+
+
+def test_c1_bit_exact(P, ctx):
+    cfg = W.make_config(1)
+    A = cfg["A"]
+    t = gpu_factor(P, ctx, A, cfg["walks"], cfg["walk_seed"], cfg["drop_tol"])
+    ref = oracle.build_factor(A, cfg["walks"], cfg["walk_seed"], cfg["drop_tol"], records=True)
+    assert_factor_equal(t, ref)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_random_rmatrices_bit_exact(P, ctx, seed):
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(2, 400))
+    A = W.random_rmatrix(n, rng, p_edge=float(rng.uniform(0.005, 0.2)),
+                         excess_hi=float(rng.uniform(0.001, 0.5)))
+    walks = int(rng.integers(1, 80))
+    drop = [0.0, 1e-3, 2e-2, 0.2][seed]
+    wseed = int(rng.integers(0, 2**63))
+    t = gpu_factor(P, ctx, A, walks, wseed, drop)
+    ref = oracle.build_factor(A, walks, wseed, drop, records=True)
+    assert_factor_equal(t, ref)
+
+
+def test_per_row_budgets_bit_exact(P, ctx):
+    rng = np.random.default_rng(7)
+    A = W.grid3d(9, 9, 9, 27, rng, excess_frac=1e-3)
+    budget = rng.integers(1, 120, size=A.n).astype(np.uint32)
+    t = gpu_factor(P, ctx, A, 0, 99, 1e-3, budget=budget)
+    ref = oracle.build_factor(A, budget, 99, 1e-3, records=True)
+    assert_factor_equal(t, ref)
+
+
+def test_large_row_budgets_use_block_merge(P, ctx):
+    # rows whose walks + lower neighbours exceed the warp table (768) go to the
+    # block-level merge; both paths must agree with the oracle
+    rng = np.random.default_rng(8)
+    A = W.grid2d_5pt(12, 12)
+    budget = np.where(rng.random(A.n) < 0.3, 3000, 40).astype(np.uint32)
+    t = gpu_factor(P, ctx, A, 0, 5, 0.0, budget=budget)
+    ref = oracle.build_factor(A, budget, 5, 0.0, records=True)
+    assert_factor_equal(t, ref)
+
+
+@pytest.mark.parametrize("family", ["grid7", "grid27", "rgg", "longrange"])
+def test_families_bit_exact(P, ctx, family):
+    rng = np.random.default_rng(11)
+    if family == "grid7":
+        A = W.make_config(2, scale=0.25)["A"]      # 16^3, weak grounding
+        walks, drop = 200, 1e-3
+    elif family == "grid27":
+        A = W.make_config(5, scale=0.125)["A"]     # 16^3, degree 26: multi-sector rows
+        walks, drop = 60, 1e-3
+    elif family == "rgg":
+        A = W.rgg(3000, rng)
+        walks, drop = 100, 1e-3
+    else:
+        A = W.make_config(3, scale=0.06)["A"]      # 60^2 + long-range edges
+        walks, drop = 100, 1e-3
+    t = gpu_factor(P, ctx, A, walks, 12345, drop)
+    ref = oracle.build_factor(A, walks, 12345, drop, records=True)
+    assert_factor_equal(t, ref)
+
+
+def test_full_size_c2_sampled_rows(P, ctx):
+    """Workload 2 at full size (n = 262144, 500 walks/row) on the GPU; the
+    oracle recomputes a seeded sample of rows (rows are independent)."""
+    cfg = W.make_config(2)
+    A = cfg["A"]
+    t = gpu_factor(P, ctx, A, cfg["walks"], cfg["walk_seed"], cfg["drop_tol"])
+    rng = np.random.default_rng(2024)
+    rows = np.unique(np.concatenate([rng.choice(A.n, 120, replace=False), [0, 1, A.n - 1]]))
+    ref = oracle.build_factor(A, cfg["walks"], cfg["walk_seed"], cfg["drop_tol"], rows=rows)
+    for k in rows:
+        a, b = t["y_row_ptr"][k], t["y_row_ptr"][k + 1]
+        c, d = ref["rowptr"][k], ref["rowptr"][k + 1]
+        assert np.array_equal(t["y_col"][a:b], ref["col"][c:d]), k
+        assert np.array_equal(t["y_val"][a:b].view(np.int64), ref["val"][c:d].view(np.int64)), k
+        assert t["d"][k].view(np.int64) == ref["D"][k].view(np.int64), k
+        assert t["walks"][k] == ref["M"][k] and t["visits"][k] == ref["J"][k]
+        assert t["ground"][k] == ref["G"][k]
+    # properties that hold at any size
+    n = A.n
+    assert np.all(t["d"] > 0) and np.all(np.diff(t["y_row_ptr"]) >= 0)
+    assert np.all(np.abs(t["y_val"]) >= cfg["drop_tol"])
+    wr = oracle.walk_rows(A)
+    assert np.all(t["walks"][wr] == cfg["walks"])
+    assert t["total_hops"] > 0
+
+
+def test_transpose_and_levels(P, ctx):
+    import scipy.sparse as sp
+    A = W.make_config(2, scale=0.25)["A"]
+    t = gpu_factor(P, ctx, A, 100, 3, 1e-3)
+    n = A.n
+    Y = sp.csr_matrix((t["y_val"], t["y_col"], t["y_row_ptr"]), shape=(n, n))
+    Yt = Y.T.tocsr()
+    Yt.sort_indices()
+    assert np.array_equal(t["yt_row_ptr"], Yt.indptr)
+    assert np.array_equal(t["yt_col"], Yt.indices)
+    assert np.array_equal(t["yt_val"], Yt.data)
+    assert t["fwd_levels"] == levels_of(n, t["y_row_ptr"], t["y_col"]).max() + 1
+    rev = levels_of(n, *(lambda M: (M.indptr, M.indices))(
+        sp.csr_matrix((Yt.data, (n - 1 - np.repeat(np.arange(n), np.diff(Yt.indptr)),
+                                 n - 1 - Yt.indices)), shape=(n, n))))
+    assert t["bwd_levels"] == rev.max() + 1
+    assert np.allclose(t["y_val32"], t["y_val"].astype(np.float32), rtol=0, atol=0)
+
+
+def test_edge_cases(P, ctx):
+    # one node; a diagonal matrix (no walks at all); rows without upper neighbours
+    one = W.assemble(1, np.array([], np.int64), np.array([], np.int64), np.array([]), [2.0])
+    t = gpu_factor(P, ctx, one, 10, 0, 0.0)
+    assert t["d"].tolist() == [2.0] and t["y_col"].size == 0
+    diag = W.assemble(5, np.array([], np.int64), np.array([], np.int64), np.array([]),
+                      np.arange(1.0, 6.0))
+    t = gpu_factor(P, ctx, diag, 7, 0, 0.0)
+    assert t["d"].tolist() == [1, 2, 3, 4, 5] and t["total_hops"] == 0
+    A = W.tridiag(2)
+    t = gpu_factor(P, ctx, A, 1, 0, 0.0)
+    ref = oracle.build_factor(A, 1, 0, 0.0, records=True)
+    assert_factor_equal(t, ref)
+
+
+def test_rejects_bad_inputs(P, ctx):
+    A = W.grid2d_5pt(4, 4)
+    bad = W.CSR(A.n, A.rowptr.copy(), A.col.copy(), A.val.copy())
+    bad.val[1] = 0.5
+    with pytest.raises(P.RwError) as e:
+        gpu_factor(P, ctx, bad, 5, 0, 0.0)
+    assert e.value.code == -2
+    bad = W.CSR(A.n, A.rowptr.copy(), A.col.copy(), A.val.copy())
+    bad.col[[0, 1]] = bad.col[[1, 0]]
+    with pytest.raises(P.RwError) as e:
+        gpu_factor(P, ctx, bad, 5, 0, 0.0)
+    assert e.value.code == -2
+    with pytest.raises(P.RwError) as e:
+        gpu_factor(P, ctx, A, 0, 0, 0.0)
+    assert e.value.code == -1
+    with pytest.raises(P.RwError) as e:
+        gpu_factor(P, ctx, A, 0, 0, 0.0, budget=np.zeros(A.n, np.uint32))
+    assert e.value.code == -1
+    with pytest.raises(P.RwError) as e:
+        gpu_factor(P, ctx, A, 5, 0, -1.0)
+    assert e.value.code == -1
+
+
+def test_step_cap_reported(P):
+    # walks longer than max_steps are stopped and reported; nothing hangs
+    c = P.Context(options=P.rw_options_default(max_steps=3))
+    A = W.make_config(2, scale=0.1)["A"]
+    with pytest.raises(P.RwError) as e:
+        gpu_factor(P, c, A, 5, 0, 0.0)
+    assert e.value.code == -3
+    c.close()
+
+
+def test_torch_allocator_context(P):
+    c = P.Context(torch_allocator=True)
+    A = W.make_config(1)["A"]
+    t = gpu_factor(P, c, A, 20, 4, 1e-3)
+    ref = oracle.build_factor(A, 20, 4, 1e-3)
+    assert np.array_equal(t["y_val"], ref["val"]) and np.array_equal(t["d"], ref["D"])
+    c.close()

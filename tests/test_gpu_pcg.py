@@ -1,0 +1,161 @@
+"""GPU solve path vs the CPU oracle: SpMV, the preconditioner application
+z = (Y^T D Y)^-1 r, and PCG (Algorithm 1) in FP64 (1e-10 relative at an equal
+iteration count) and in FP32 mixed precision (reaches the tolerance; error
+against the FP64 oracle solution reported and bounded)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_math_0609672_gb300 as P
+    from paper_math_0609672_gb300 import _build
+    _build.build()
+    return P
+
+
+@pytest.fixture(scope="module")
+def ctx(P):
+    c = P.Context()
+    yield c
+    c.close()
+
+
+def _dev(a):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def test_spmv_matches_reference(P, ctx):
+    rng = np.random.default_rng(1)
+    A = W.make_config(2, scale=0.25)["A"]
+    x = rng.standard_normal((A.n, 4))
+    y = _dev(np.zeros_like(x))
+    P.rw_spmv(ctx, P.CSR.from_host(A), _dev(x), y)
+    ref = A.to_scipy() @ x
+    assert np.allclose(y.cpu().numpy(), ref, rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("nrhs", [1, 3, 4, 16])
+def test_precond_matches_oracle(P, ctx, nrhs):
+    rng = np.random.default_rng(nrhs)
+    A = W.make_config(2, scale=0.25)["A"]
+    dA = P.CSR.from_host(A)
+    F = P.rw_build_factor(ctx, dA, 100, 7, 1e-3)
+    ref = oracle.build_factor(A, 100, 7, 1e-3)
+    r = rng.standard_normal((A.n, nrhs))
+    z = _dev(np.zeros_like(r))
+    P.rw_precond_apply(ctx, F, _dev(r), z)
+    zg = z.cpu().numpy()
+    for j in range(nrhs):
+        zr = oracle.precond_apply(ref, r[:, j])
+        assert np.linalg.norm(zg[:, j] - zr) / np.linalg.norm(zr) < 1e-12
+    F.destroy()
+
+
+def test_pcg_fp64_equal_iterations_c1(P, ctx):
+    cfg = W.make_config(1)
+    A, b = cfg["A"], cfg["b"]
+    dA = P.CSR.from_host(A)
+    F = P.rw_build_factor(ctx, dA, cfg["walks"], cfg["walk_seed"], cfg["drop_tol"])
+    ref = oracle.build_factor(A, cfg["walks"], cfg["walk_seed"], cfg["drop_tol"])
+    for K in (1, 5, 12):
+        x = _dev(np.zeros_like(b))
+        rc, st, its, rel = P.pcg_solve(ctx, dA, F, _dev(b), x, 0.0, K)
+        xr, itr, rr, rcr = oracle.pcg(A, ref, b[:, 0], 0.0, K)
+        assert its[0] == K == itr
+        xg = x.cpu().numpy()[:, 0]
+        assert np.linalg.norm(xg - xr) / np.linalg.norm(xr) < 1e-10, K
+        assert abs(rel[0] - rr) <= 1e-8 * max(rr, 1e-30) + 1e-15
+    F.destroy()
+
+
+def test_pcg_fp64_converges_like_oracle_c1(P, ctx):
+    cfg = W.make_config(1)
+    A, b = cfg["A"], cfg["b"]
+    dA = P.CSR.from_host(A)
+    F = P.rw_build_factor(ctx, dA, cfg["walks"], cfg["walk_seed"], cfg["drop_tol"])
+    ref = oracle.build_factor(A, cfg["walks"], cfg["walk_seed"], cfg["drop_tol"])
+    x = _dev(np.zeros_like(b))
+    rc, st, its, rel = P.pcg_solve(ctx, dA, F, _dev(b), x, cfg["tol"], 500)
+    xr, itr, rr, rcr = oracle.pcg(A, ref, b[:, 0], cfg["tol"], 500)
+    assert rc == 0 and rcr == 0 and rel[0] < cfg["tol"]
+    assert its[0] == itr
+    xg = x.cpu().numpy()[:, 0]
+    assert np.linalg.norm(xg - xr) / np.linalg.norm(xr) < 1e-10
+    F.destroy()
+
+
+def test_pcg_multi_rhs_c2_scaled(P, ctx):
+    cfg = W.make_config(2, scale=0.25)
+    A, b = cfg["A"], cfg["b"]
+    dA = P.CSR.from_host(A)
+    F = P.rw_build_factor(ctx, dA, cfg["walks"], cfg["walk_seed"], cfg["drop_tol"])
+    ref = oracle.build_factor(A, cfg["walks"], cfg["walk_seed"], cfg["drop_tol"])
+    x = _dev(np.zeros_like(b))
+    rc, st, its, rel = P.pcg_solve(ctx, dA, F, _dev(b), x, cfg["tol"], 500)
+    assert rc == 0 and np.all(rel < cfg["tol"])
+    xg = x.cpu().numpy()
+    true = np.linalg.norm(b - A.to_scipy() @ xg, axis=0) / np.linalg.norm(b, axis=0)
+    assert np.all(true < cfg["tol"])
+    for j in range(b.shape[1]):
+        xr, itr, rr, rcr = oracle.pcg(A, ref, b[:, j], cfg["tol"], 500)
+        assert its[j] == itr
+        assert np.linalg.norm(xg[:, j] - xr) / np.linalg.norm(xr) < 1e-10
+    F.destroy()
+
+
+def test_pcg_fp32_mixed_reaches_tolerance(P, ctx):
+    cfg = W.make_config(3, scale=0.1)          # 100^2 grid + long-range edges
+    A, b = cfg["A"], cfg["b"]
+    dA = P.CSR.from_host(A)
+    F = P.rw_build_factor(ctx, dA, cfg["walks"], cfg["walk_seed"], cfg["drop_tol"])
+    ref = oracle.build_factor(A, cfg["walks"], cfg["walk_seed"], cfg["drop_tol"])
+    x = _dev(np.zeros_like(b))
+    rc, st, its, rel = P.pcg_solve(ctx, dA, F, _dev(b), x, cfg["tol"], 1000, P.RW_FP32_MIXED)
+    assert rc == 0 and rel[0] < cfg["tol"]
+    xg = x.cpu().numpy()[:, 0]
+    true = np.linalg.norm(b[:, 0] - A.to_scipy() @ xg) / np.linalg.norm(b[:, 0])
+    assert true < cfg["tol"]
+    x64, it64, rr64, _ = oracle.pcg(A, ref, b[:, 0], cfg["tol"], 1000)
+    xm, itm, rrm, _ = oracle.pcg(A, ref, b[:, 0], cfg["tol"], 1000, mixed=True)
+    err = np.linalg.norm(xg - x64) / np.linalg.norm(x64)
+    # both reach ||r|| < 1e-6 ||b||; kappa(A) bounds the solution error
+    assert err < 1e-3, err
+    assert abs(int(its[0]) - itm) <= max(2, itm // 5)
+    F.destroy()
+
+
+def test_pcg_zero_rhs_and_nonfinite(P, ctx):
+    A = W.grid2d_5pt(8, 8)
+    dA = P.CSR.from_host(A)
+    F = P.rw_build_factor(ctx, dA, 10, 1, 0.0)
+    b = np.zeros((A.n, 2))
+    b[:, 1] = 1.0
+    x = _dev(np.zeros_like(b))
+    rc, st, its, rel = P.pcg_solve(ctx, dA, F, _dev(b), x, 1e-8, 100)
+    assert rc == 0 and its[0] == 0 and not x.cpu().numpy()[:, 0].any() and rel[1] < 1e-8
+    b[3, 1] = np.nan
+    with pytest.raises(P.RwError) as e:
+        P.pcg_solve(ctx, dA, F, _dev(b), x, 1e-8, 100)
+    assert e.value.code == -1
+    F.destroy()
+
+
+def test_pcg_reports_no_convergence(P, ctx):
+    cfg = W.make_config(1)
+    A, b = cfg["A"], cfg["b"]
+    dA = P.CSR.from_host(A)
+    F = P.rw_build_factor(ctx, dA, 20, 0, 1e-2)
+    x = _dev(np.zeros_like(b))
+    rc, st, its, rel = P.pcg_solve(ctx, dA, F, _dev(b), x, 1e-14, 2)
+    assert rc == -5 and its[0] == 2 and rel[0] > 1e-14
+    F.destroy()

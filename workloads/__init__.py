@@ -223,14 +223,17 @@ def grid2d_longrange(nx, ny, rng, n_long=2, glo=0.01, ghi=1.0, boundary_excess=1
     return assemble(n, ei, ej, g, excess)
 
 
-def rgg(n, rng, mean_degree=8.0, excess_value=1e-2, excess_fraction=0.01):
+def rgg(n, rng, mean_degree=8.0, excess_value=1e-2, excess_fraction=0.01, relative=True):
     """Random geometric graph Laplacian in the unit square.
 
     Points uniform in [0,1]^2, radius r = sqrt(mean_degree / (pi n)),
-    conductance 1/distance.  Excess `excess_value` (absolute) on a random
-    `excess_fraction` of the rows; every connected component without a
-    grounded row gets the excess on its lowest-index node so that the matrix
-    is irreducibly dominant per component and n is unchanged.
+    conductance 1/distance.  Excess on a random `excess_fraction` of the rows:
+    `excess_value` times the row's conductance sum (relative=True), or the
+    absolute value `excess_value` (relative=False; with conductances of order
+    1/r this grounds so weakly that walks from the first rows run for 1e7+
+    hops).  Every connected component without a grounded row gets the excess
+    on its lowest-index node so that the matrix is irreducibly dominant per
+    component and n is unchanged.
     """
     from scipy.spatial import cKDTree
     from scipy.sparse import coo_matrix
@@ -245,16 +248,20 @@ def rgg(n, rng, mean_degree=8.0, excess_value=1e-2, excess_fraction=0.01):
     ei, ej, d = ei[keep], ej[keep], d[keep]
     lo, hi = np.minimum(ei, ej), np.maximum(ei, ej)
     g = 1.0 / d
+    scale = conductance_sums(n, lo, hi, g) if relative else np.ones(n)
+    scale = np.where(scale > 0, scale, 1.0)  # isolated nodes
     excess = np.zeros(n)
     nground = max(1, int(round(excess_fraction * n)))
-    excess[rng.choice(n, size=nground, replace=False)] = excess_value
+    pick = rng.choice(n, size=nground, replace=False)
+    excess[pick] = excess_value * scale[pick]
     adj = coo_matrix((np.ones(lo.size), (lo, hi)), shape=(n, n))
     ncomp, lab = connected_components(adj, directed=False)
     grounded = np.zeros(ncomp, dtype=bool)
     grounded[lab[excess > 0]] = True
     first = np.full(ncomp, n, dtype=np.int64)
     np.minimum.at(first, lab, np.arange(n))
-    excess[first[~grounded]] = excess_value
+    fix = first[~grounded]
+    excess[fix] = excess_value * scale[fix]
     return assemble(n, lo, hi, g, excess)
 
 
