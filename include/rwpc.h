@@ -178,6 +178,24 @@ rw_status pcg_solve(rw_context* ctx, const rw_csr* A, const rw_factor* F, const 
 rw_status rw_precond_apply(rw_context* ctx, const rw_factor* F, const double* d_r, double* d_z,
                            int32_t nrhs);
 
+/* Same result as rw_precond_apply, without allocating.  The paper has no
+ * counterpart: this entry point is for callers that cannot allocate device
+ * memory at the moment they apply the preconditioner -- an outer iterative
+ * solver calling it once per iteration, code running under a fixed memory
+ * budget, or a framework whose allocator must not be re-entered from inside a
+ * library call.  It calls no cudaMalloc, cudaFree or allocating routine: the
+ * scratch vector of the backward solve lives in a file-scope device array of
+ * 2^20 doubles (8 MiB) that every GPU loading the library holds until the
+ * process exits.  n * nrhs must not exceed 2^20 (RW_ERR_CAPACITY otherwise).
+ * The first call on a device looks up that array's device address (with the
+ * device current); make that first call before any stream capture.  All calls
+ * share the one array, which keeps the previous call's contents (this call
+ * re-initialises what it reads), so calls that overlap on the GPU -- on
+ * different streams or from different threads -- race and must not be issued.
+ * The current device must be the context's device. */
+rw_status rw_precond_apply_static(rw_context* ctx, const rw_factor* F, const double* d_r,
+                                  double* d_z, int32_t nrhs);
+
 /* y = A x for nrhs node-major vectors (FP64). */
 rw_status rw_spmv(rw_context* ctx, const rw_csr* A, const double* d_x, double* d_y, int32_t nrhs);
 

@@ -25,7 +25,8 @@ from . import _build
 __all__ = [
     "load", "RwError", "CSR", "Context", "Factor", "rw_options_default", "rw_context_create",
     "rw_context_destroy", "rw_build_factor", "rw_build_factor_budget", "rw_factor_view",
-    "rw_factor_destroy", "pcg_solve", "rw_precond_apply", "rw_spmv", "rw_status_string",
+    "rw_factor_destroy", "pcg_solve", "rw_precond_apply", "rw_precond_apply_static", "rw_spmv",
+    "rw_status_string",
     "rw_last_error", "RW_FP64", "RW_FP32_MIXED",
 ]
 
@@ -109,6 +110,8 @@ def load():
     lib.pcg_solve.restype = ctypes.c_int
     lib.rw_precond_apply.argtypes = [_c_void_p, _c_void_p, _c_void_p, _c_void_p, _i32]
     lib.rw_precond_apply.restype = ctypes.c_int
+    lib.rw_precond_apply_static.argtypes = [_c_void_p, _c_void_p, _c_void_p, _c_void_p, _i32]
+    lib.rw_precond_apply_static.restype = ctypes.c_int
     lib.rw_spmv.argtypes = [_c_void_p, P(rw_csr_t), _c_void_p, _c_void_p, _i32]
     lib.rw_spmv.restype = ctypes.c_int
     lib.rw_status_string.argtypes = [ctypes.c_int]
@@ -348,6 +351,15 @@ def rw_precond_apply(ctx, F, r, z):
     nrhs = 1 if r.dim() == 1 else r.shape[1]
     _check(load().rw_precond_apply(ctx.handle, F.handle, _c_void_p(r.data_ptr()),
                                    _c_void_p(z.data_ptr()), nrhs), "rw_precond_apply")
+
+
+def rw_precond_apply_static(ctx, F, r, z):
+    """rw_precond_apply without allocation (scratch in the library's static
+    device array; n * nrhs <= 2**20; overlapping calls race)."""
+    nrhs = 1 if r.dim() == 1 else r.shape[1]
+    _check(load().rw_precond_apply_static(ctx.handle, F.handle, _c_void_p(r.data_ptr()),
+                                          _c_void_p(z.data_ptr()), nrhs),
+           "rw_precond_apply_static")
 
 
 def rw_spmv(ctx, A, x, y):

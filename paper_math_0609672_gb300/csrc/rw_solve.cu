@@ -11,6 +11,7 @@
 // status record per iteration.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "rw_internal.h"
 
@@ -592,4 +593,95 @@ rw_status pcg_run(rw_context* ctx, const rw_csr* A, const FactorView& F, const d
     return rc;
 }
 
+
+// ---------------------------------------------------------------------------
+// Preconditioner application without allocation.
+//
+// Some callers cannot allocate device memory while they apply the
+// preconditioner: an outer iterative solver that calls it once per iteration
+// from a tight loop, code that runs under a fixed memory budget, or a
+// framework whose allocator must not be re-entered from a library call.  For
+// them the scratch vector w of the backward solve lives in the file-scope
+// device array below instead of coming from the context's allocator.  The
+// array holds kStaticScratchEntries doubles (n * nrhs at most) on every device
+// that loads the library, for the life of the process.
+// ---------------------------------------------------------------------------
+constexpr int64_t kStaticScratchEntries = (int64_t)1 << 20;  // 8 MiB of FP64
+static __device__ __align__(256) double g_static_scratch[kStaticScratchEntries];
+
+static std::mutex g_static_scratch_mu;
+constexpr int kMaxDevices = 64;
+static double* g_static_scratch_ptr[kMaxDevices] = {};
+
+// Device address of g_static_scratch on `device` (which must be current).  The
+// host-side name of the array is only a stand-in, so the address is looked up
+// once per device and cached.
+static rw_status static_scratch_address(int device, double** out) {
+    std::lock_guard<std::mutex> lock(g_static_scratch_mu);
+    if (device < 0 || device >= kMaxDevices) {
+        set_error("static scratch: device %d out of range", device);
+        return RW_ERR_ARG;
+    }
+    if (!g_static_scratch_ptr[device]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return check_cuda(e, "cudaGetSymbolAddress(static scratch)");
+        g_static_scratch_ptr[device] = static_cast<double*>(p);
+    }
+    *out = g_static_scratch_ptr[device];
+    return RW_OK;
+}
+
+}  // namespace rw
+
+extern "C" rw_status rw_precond_apply_static(rw_context* ctx, const rw_factor* F,
+                                             const double* d_r, double* d_z, int32_t nrhs) {
+    using namespace rw;
+    if (!ctx || !F || !d_r || !d_z || nrhs < 1 || nrhs > 16) {
+        set_error("rw_precond_apply_static: bad arguments");
+        return RW_ERR_ARG;
+    }
+    const rw_factor_desc& d = F->desc;
+    const int64_t cnt = (int64_t)d.n * nrhs;
+    if (cnt > kStaticScratchEntries) {
+        set_error("rw_precond_apply_static: n * nrhs = %lld exceeds the static scratch of %lld "
+                  "entries; use rw_precond_apply",
+                  (long long)cnt, (long long)kStaticScratchEntries);
+        return RW_ERR_CAPACITY;
+    }
+    if (d.n == 0) return RW_OK;
+    int dev = -1;
+    rw_status rc = check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+    if (rc) return rc;
+    if (dev != ctx->device) {
+        set_error("rw_precond_apply_static: device %d is current, the context is on device %d",
+                  dev, ctx->device);
+        return RW_ERR_ARG;
+    }
+    double* w = nullptr;
+    if ((rc = static_scratch_address(dev, &w))) return rc;
+    FactorView v;
+    v.n = d.n;
+    v.nnz = d.nnz;
+    v.y_rp = d.y_row_ptr;
+    v.y_col = d.y_col;
+    v.y_val = d.y_val;
+    v.y_val32 = d.y_val32;
+    v.yt_rp = d.yt_row_ptr;
+    v.yt_col = d.yt_col;
+    v.yt_val = d.yt_val;
+    v.yt_val32 = d.yt_val32;
+    v.d = d.d;
+    v.d32 = d.d32;
+    v.fwd_order = F->fwd_order;
+    v.bwd_order = F->bwd_order;
+    if ((rc = reset_status(ctx))) return rc;
+    // w and z start as "pending" on every call: the array keeps the last call's contents
+    if ((rc = fill_pending(ctx, w, cnt))) return rc;
+    if ((rc = fill_pending(ctx, d_z, cnt))) return rc;
+    if ((rc = precond_t<double>(ctx, v, v.y_val, v.yt_val, v.d, d_r, w, d_z, nrhs))) return rc;
+    return read_status(ctx, "static-scratch preconditioner");
+}
+
+namespace rw {
 }  // namespace rw
