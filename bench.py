@@ -182,7 +182,9 @@ def run_gpu(args):
         d = F.desc
         info = dict(hops=int(d.total_hops), walks=int(d.total_walks), nnz=int(d.nnz),
                     phase=list(d.phase_ms), fwd=d.fwd_levels, bwd=d.bwd_levels,
-                    iters=its.tolist(), rel=rel.tolist(), rc=rc, solve_ms=st.solve_ms)
+                    iters=its.tolist(), rel=rel.tolist(), rc=rc, solve_ms=st.solve_ms,
+                    spmv_ms=st.spmv_ms, bwd_ms=st.bwd_ms, fwd_ms=st.fwd_ms,
+                    launches=int(d.kernel_launches) + int(st.kernel_launches))
         F.destroy()
         return info
 
@@ -247,11 +249,29 @@ def run_gpu(args):
         return
     peaks, peak_kind = _peaks()
     walks_total = infos[-1]["walks"]
+    nnz_y = infos[-1]["nnz"]
     # algorithmic bytes of the walk kernel: per hop one 32-byte sector of
     # thresholds (degree <= 6 here) + one sector for the chosen successor; per
     # walk one 8-byte record
     alg_bytes = 64.0 * hops + 8.0 * walks_total
     achieved = alg_bytes / (walk_ms * 1e-3) / 1e9
+    walk_roof = {"kernel": "k_walk", "bound": "hbm", "achieved": achieved,
+                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                 "traffic": None, "ms_per_launch": walk_ms}
+    # triangular solves: per application of the preconditioner the factor
+    # (12 B per stored entry, twice: Y and Y^T) and the vectors (8 B x nrhs x
+    # n read and written per solve) must be touched once
+    napply = statistics.mean(len(i["iters"]) and max(i["iters"]) for i in infos)
+    tri_ms = statistics.mean(i["bwd_ms"] + i["fwd_ms"] for i in infos)
+    applies = napply  # one application per iteration (the first before the loop, none after the last)
+    tri_bytes = applies * (2 * 12.0 * nnz_y + 2 * 3 * 8.0 * nrhs * A.n)
+    tri_achieved = tri_bytes / (tri_ms * 1e-3) / 1e9 if tri_ms > 0 else 0.0
+    solve_roof = {"kernel": "k_thin/k_wide (triangular solves)", "bound": "hbm",
+                  "achieved": tri_achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                  "frac": tri_achieved / peaks["hbm_gbs"], "traffic": None,
+                  "ms_per_step": tri_ms,
+                  "note": "latency-bound: dependency DAG depth x dependent memory round trips"}
+    dominant = solve_roof if tri_ms > walk_ms else walk_roof
     line = {
         "metric": METRIC, "value": hops * ws / (ms * 1e-3), "unit": "hops/s",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -268,13 +288,14 @@ def run_gpu(args):
         "phase_ms": {k: round(v, 3) for k, v in zip(
             ["tables", "walk", "merge", "emit", "transpose", "levels", "fp32", "build_total"],
             infos[-1]["phase"])},
-        "roofline": {"kernel": "k_walk", "bound": "hbm", "achieved": achieved,
-                     "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-                     "traffic": None, "peak_kind": peak_kind},
+        "roofline": dict(dominant, peak_kind=peak_kind),
+        "roofline_walk": dict(walk_roof, peak_kind=peak_kind),
+        "solve_phase_ms": {"spmv": infos[-1]["spmv_ms"], "bwd": infos[-1]["bwd_ms"],
+                           "fwd": infos[-1]["fwd_ms"]},
         "clocks": clk,
         "e2e": {"value": hops * ws / (e2e * 1e-3), "unit": "hops/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e},
-        "gpu_launches": None,
+        "gpu_launches": infos[-1]["launches"],
     }
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_oracle_sample(cfg)

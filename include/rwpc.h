@@ -89,6 +89,7 @@ typedef struct {
     int32_t refine_every;    /* FP32 PCG: true-residual replacement period (default 50) */
     int32_t walk_blocks_per_sm; /* 0 = from the occupancy calculator */
     int32_t timing;          /* 1: record per-phase device times (default 1) */
+    int32_t solve_blocks_per_sm; /* triangular solves: 256-thread blocks per SM (0 = 2) */
 } rw_options;
 
 typedef struct rw_context rw_context;
@@ -121,12 +122,17 @@ typedef struct {
     int32_t fwd_levels;        /* depth of the DAG of Y z = v */
     int32_t bwd_levels;        /* depth of the DAG of Y^T w = r */
     float phase_ms[8];         /* tables, walk, merge, emit, transpose, levels, fp32, total */
+    int64_t kernel_launches;   /* kernels launched by the build */
 } rw_factor_desc;
 
 typedef struct {
     int32_t iterations;        /* max over right-hand sides */
     double rel_residual;       /* max over right-hand sides of ||b - A x|| / ||b|| (true) */
     float solve_ms;            /* device time of the solve */
+    float spmv_ms;             /* device time in A p products (summed over iterations) */
+    float bwd_ms;              /* device time in the Y^T w = r solves */
+    float fwd_ms;              /* device time in the Y z = w / D solves */
+    int64_t kernel_launches;   /* kernels launched by the call */
 } rw_pcg_stats;
 
 /* Fill *opt with the defaults listed in rw_options. */

@@ -49,7 +49,7 @@ class rw_csr_t(ctypes.Structure):
 class rw_options_t(ctypes.Structure):
     _fields_ = [("max_steps", _u64), ("keep_records", _i32), ("record_lengths", _i32),
                 ("store_fp32", _i32), ("refine_every", _i32), ("walk_blocks_per_sm", _i32),
-                ("timing", _i32)]
+                ("timing", _i32), ("solve_blocks_per_sm", _i32)]
 
 
 class rw_factor_desc_t(ctypes.Structure):
@@ -60,11 +60,13 @@ class rw_factor_desc_t(ctypes.Structure):
                 ("visits", _c_void_p), ("ground", _c_void_p), ("walk_rows", _c_void_p),
                 ("walk_base", _c_void_p), ("records", _c_void_p), ("n_walk_rows", _i32),
                 ("total_walks", _i64), ("total_hops", _u64), ("fwd_levels", _i32),
-                ("bwd_levels", _i32), ("phase_ms", ctypes.c_float * 8)]
+                ("bwd_levels", _i32), ("phase_ms", ctypes.c_float * 8), ("kernel_launches", _i64)]
 
 
 class rw_pcg_stats_t(ctypes.Structure):
-    _fields_ = [("iterations", _i32), ("rel_residual", _f64), ("solve_ms", ctypes.c_float)]
+    _fields_ = [("iterations", _i32), ("rel_residual", _f64), ("solve_ms", ctypes.c_float),
+                ("spmv_ms", ctypes.c_float), ("bwd_ms", ctypes.c_float), ("fwd_ms", ctypes.c_float),
+                ("kernel_launches", _i64)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(_c_void_p, _c_void_p, ctypes.c_size_t, _c_void_p)

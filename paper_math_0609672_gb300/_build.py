@@ -22,7 +22,8 @@ LIB = os.path.join(OUT_DIR, "librwpc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]
-SOURCES = ["rw_api.cu", "rw_tables.cu", "rw_walk.cu", "rw_emit.cu", "rw_levels.cu", "rw_solve.cu"]
+SOURCES = ["rw_api.cu", "rw_tables.cu", "rw_walk.cu", "rw_emit.cu", "rw_levels.cu", "rw_sched.cu",
+           "rw_solve.cu"]
 
 
 def _nvcc():

@@ -10,6 +10,7 @@
 namespace rw {
 
 static thread_local char g_err[512] = "";
+thread_local int64_t g_launches = 0;
 
 void set_error(const char* fmt, ...) {
     va_list ap;
@@ -235,6 +236,7 @@ static rw_status build_factor_impl(rw_context* ctx, const rw_csr* A, uint32_t un
     }
     cudaStream_t s = ctx->stream;
     const bool timing = ctx->opt.timing != 0;
+    const int64_t launches0 = g_launches;
     rw_factor* F = new (std::nothrow) rw_factor(ctx);
     if (!F) return RW_ERR_ALLOC;
     Pool scratch(ctx);
@@ -251,6 +253,10 @@ static rw_status build_factor_impl(rw_context* ctx, const rw_csr* A, uint32_t un
     int64_t* yt_rp = nullptr;
     int32_t* yt_col = nullptr;
     double* yt_val = nullptr;
+    int64_t* fwd_lptr = nullptr;
+    int64_t* bwd_lptr = nullptr;
+    float* y32 = nullptr;
+    float* yt32 = nullptr;
     if ((rc = reset_status(ctx))) goto fail;
     if (timing) cudaEventRecord(ctx->ev[10], s);
     if ((rc = build_tables(ctx, A, T, scratch))) goto fail;
@@ -292,14 +298,16 @@ static rw_status build_factor_impl(rw_context* ctx, const rw_csr* A, uint32_t un
         rc = RW_ERR_ALLOC;
         goto fail;
     }
-    if ((rc = compute_levels(ctx, n, fo.y_rp, fo.y_col, false, F->fwd_order, &d.fwd_levels, scratch)))
+    if ((rc = compute_levels(ctx, n, fo.y_rp, fo.y_col, false, F->fwd_order, &d.fwd_levels,
+                             &fwd_lptr, F->pool, scratch)))
         goto fail;
-    if ((rc = compute_levels(ctx, n, yt_rp, yt_col, true, F->bwd_order, &d.bwd_levels, scratch)))
+    if ((rc = compute_levels(ctx, n, yt_rp, yt_col, true, F->bwd_order, &d.bwd_levels, &bwd_lptr,
+                             F->pool, scratch)))
         goto fail;
     if (timing) cudaEventRecord(ctx->ev[13], s);
     if (ctx->opt.store_fp32) {
-        float* y32 = alloc_n<float>(F->pool, fo.nnz);
-        float* yt32 = alloc_n<float>(F->pool, fo.nnz);
+        y32 = alloc_n<float>(F->pool, fo.nnz);
+        yt32 = alloc_n<float>(F->pool, fo.nnz);
         float* d32 = alloc_n<float>(F->pool, n);
         if (!y32 || !yt32 || !d32) {
             rc = RW_ERR_ALLOC;
@@ -313,6 +321,17 @@ static rw_status build_factor_impl(rw_context* ctx, const rw_csr* A, uint32_t un
         d.yt_val32 = yt32;
         d.d32 = d32;
     }
+    F->bar = static_cast<unsigned*>(F->pool.get((size_t)kSolveWorkspaceBytes));
+    if (!F->bar) {
+        rc = RW_ERR_ALLOC;
+        goto fail;
+    }
+    if ((rc = build_schedule(ctx, n, fo.y_rp, fo.y_col, fo.y_val, y32, F->fwd_order, fwd_lptr,
+                             d.fwd_levels, F->fwd_sched, F->pool, scratch)))
+        goto fail;
+    if ((rc = build_schedule(ctx, n, yt_rp, yt_col, yt_val, yt32, F->bwd_order, bwd_lptr,
+                             d.bwd_levels, F->bwd_sched, F->pool, scratch)))
+        goto fail;
     if (timing) cudaEventRecord(ctx->ev[14], s);
     {
         unsigned long long* hh = static_cast<unsigned long long*>(ctx->h_small);
@@ -370,6 +389,7 @@ static rw_status build_factor_impl(rw_context* ctx, const rw_csr* A, uint32_t un
     }
     scratch.release_all();
     if ((rc = check_cuda(cudaStreamSynchronize(s), "sync"))) goto fail;
+    d.kernel_launches = g_launches - launches0;
     *out = F;
     return RW_OK;
 fail:
@@ -425,6 +445,9 @@ static FactorView view_of(const rw_factor* F) {
     v.d32 = d.d32;
     v.fwd_order = F->fwd_order;
     v.bwd_order = F->bwd_order;
+    v.fwd_sched = &F->fwd_sched;
+    v.bwd_sched = &F->bwd_sched;
+    v.bar = F->bar;
     return v;
 }
 
@@ -446,7 +469,10 @@ rw_status pcg_solve(rw_context* ctx, const rw_csr* A, const rw_factor* F, const 
     if (stats) memset(stats, 0, sizeof(*stats));
     if (A->n == 0) return RW_OK;
     if ((rc = reset_status(ctx))) return rc;
-    return pcg_run(ctx, A, view_of(F), d_b, d_x, nrhs, tol, max_iter, prec, stats, h_iters, h_relres);
+    const int64_t launches0 = g_launches;
+    rc = pcg_run(ctx, A, view_of(F), d_b, d_x, nrhs, tol, max_iter, prec, stats, h_iters, h_relres);
+    if (stats) stats->kernel_launches = g_launches - launches0;
+    return rc;
 }
 
 rw_status rw_precond_apply(rw_context* ctx, const rw_factor* F, const double* d_r, double* d_z,

@@ -63,19 +63,22 @@ __device__ __forceinline__ uint32_t cumulative_threshold(double num, double den)
 }
 
 // Relaxed (gpu-scope) accesses used for device-side hand-off between warps.
+// The value itself is the signal (a single aligned store), so the loads need
+// no ordering against other memory operations: no "memory" clobber, which
+// lets independent loads around them be issued together.
 __device__ __forceinline__ double ld_relaxed(const double* p) {
     double v;
-    asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p));
     return v;
 }
 __device__ __forceinline__ float ld_relaxed(const float* p) {
     float v;
-    asm volatile("ld.relaxed.gpu.global.f32 %0, [%1];" : "=f"(v) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.global.f32 %0, [%1];" : "=f"(v) : "l"(p));
     return v;
 }
 __device__ __forceinline__ int ld_relaxed(const int* p) {
     int v;
-    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p));
     return v;
 }
 __device__ __forceinline__ void st_relaxed(double* p, double v) {
@@ -121,6 +124,64 @@ __device__ __forceinline__ bool wait_gives_up(unsigned& spins, unsigned* timeout
         return true;
     }
     return (spins % kAbortPoll) == 0 && ld_relaxed_u32(timeout_flag) != 0u;
+}
+
+// Software grid barrier for a co-resident (cooperatively launched) grid.
+// bar[0] counts arrivals, bar[1] is the generation.  Every wait is bounded;
+// returns false when it gave up (the timeout flag is then set).
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, DevStatus* st) {
+    __shared__ int give_up;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        give_up = 0;
+        const unsigned gen = ld_relaxed_u32(&bar[1]);
+        __threadfence();
+        if (atomicAdd(&bar[0], 1u) == gridDim.x - 1u) {
+            atomicExch(&bar[0], 0u);
+            __threadfence();
+            atomicAdd(&bar[1], 1u);
+        } else {
+            unsigned spins = 0;
+            while (ld_relaxed_u32(&bar[1]) == gen) {
+                if (wait_gives_up(spins, &st->timeout)) {
+                    give_up = 1;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return give_up == 0;
+}
+
+// Sums of NR per-lane values over the warp (NR a power of two, <= 16).  Each
+// step hands half of the still-carried values to the partner lane, so NR = 4
+// costs 7 shuffles instead of 4 x 5.  Lane j < NR receives the total of value j.
+template <typename T, int NR>
+__device__ __forceinline__ T warp_sums(T (&v)[NR]) {
+    const unsigned lane = lane_id();
+    int cnt = NR;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        if (cnt > 1) {
+            const int half = cnt / 2;
+            const bool upper = (lane & o) != 0;
+#pragma unroll
+            for (int i = 0; i < NR / 2; ++i) {
+                if (i < half) {
+                    const T send = upper ? v[i] : v[i + half];
+                    const T keep = upper ? v[i + half] : v[i];
+                    v[i] = keep + __shfl_xor_sync(kFull, send, o);
+                }
+            }
+            cnt = half;
+        } else {
+            v[0] += __shfl_xor_sync(kFull, v[0], o);
+        }
+    }
+    constexpr int shift = NR >= 16 ? 1 : NR >= 8 ? 2 : NR >= 4 ? 3 : NR >= 2 ? 4 : 5;
+    return __shfl_sync(kFull, v[0], ((int)lane << shift) & 31);
 }
 
 template <typename T>

@@ -10,6 +10,9 @@
 // each operation rounded once, in this order.  Entries with |Y_ki| < drop_tol
 // are dropped (post-processing drop, footnote of Sec. 4).  Rows without an
 // upper neighbour are exact: Y_ki = A_ki / A_kk, D_kk = A_kk.
+#include <algorithm>
+#include <utility>
+
 #include "rw_internal.h"
 
 namespace rw {
@@ -364,6 +367,7 @@ rw_status emit_factor(rw_context* ctx, const rw_csr* A, const Tables& T, const W
         return RW_ERR_ALLOC;
     const int blocks = grid_for(std::max(n, nw), 256, ctx->num_sms * 8);
     if (nw > 0) {
+        RW_COUNT_LAUNCH();
         k_slot_sizes<<<blocks, 256, 0, s>>>(nw, T.wrow, ws.wbase, tbase);
         if ((rc = check_launch("slot sizes"))) return rc;
     }
@@ -419,6 +423,7 @@ rw_status emit_factor(rw_context* ctx, const rw_csr* A, const Tables& T, const W
                                                       sm_small);
         if (per_sm < 1) per_sm = 1;
         const int mblocks = grid_for(nw, kMergeWarps, ctx->num_sms * per_sm);
+        RW_COUNT_LAUNCH();
         k_merge_small<<<mblocks, 32 * kMergeWarps, sm_small, s>>>(P);
         if ((rc = check_launch("merge (warp tables)"))) return rc;
         int32_t* h32 = static_cast<int32_t*>(ctx->h_small);
@@ -437,10 +442,12 @@ rw_status emit_factor(rw_context* ctx, const rw_csr* A, const Tables& T, const W
                     return rc;
                 attr_big = true;
             }
+            RW_COUNT_LAUNCH();
             k_merge_big<<<grid_for(nbig, 1, ctx->num_sms), 256, sm_big, s>>>(P, nbig);
             if ((rc = check_launch("merge (block tables)"))) return rc;
         }
     }
+    RW_COUNT_LAUNCH();
     k_exact_rows<<<blocks, 256, 0, s>>>(n, T.walk_flag, A->row_ptr, A->col, A->val, T.diag_pos,
                                         drop_tol, fo.y_rp, fo.d, fo.M, fo.J, fo.G, nullptr, nullptr,
                                         nullptr);
@@ -455,10 +462,12 @@ rw_status emit_factor(rw_context* ctx, const rw_csr* A, const Tables& T, const W
     fo.y_val = alloc_n<double>(pool, fo.nnz);
     if (!fo.y_col || !fo.y_val) return RW_ERR_ALLOC;
     if (nw > 0) {
+        RW_COUNT_LAUNCH();
         k_copy_rows<<<grid_for((int64_t)nw * 32, 256, ctx->num_sms * 8), 256, 0, s>>>(
             nw, T.wrow, tbase, tcol, tval, fo.y_rp, fo.y_col, fo.y_val);
         if ((rc = check_launch("copy rows"))) return rc;
     }
+    RW_COUNT_LAUNCH();
     k_exact_rows<<<blocks, 256, 0, s>>>(n, T.walk_flag, A->row_ptr, A->col, A->val, T.diag_pos,
                                         drop_tol, nullptr, nullptr, nullptr, nullptr, nullptr,
                                         fo.y_rp, fo.y_col, fo.y_val);
@@ -473,63 +482,164 @@ rw_status emit_factor(rw_context* ctx, const rw_csr* A, const Tables& T, const W
 }
 
 // ---------------------------------------------------------------------------
-// Transpose: Y^T in CSR, each row's columns ascending.
+// Transpose: Y^T in CSR with each row's columns ascending.  The entries of Y
+// are in row order, so a stable sort of (column, position) pairs by column
+// gives Y^T with rows ascending inside every column: a least-significant-digit
+// radix sort, 9 bits per pass, each pass = tile histograms, a prefix sum over
+// (digit, tile), and a stable scatter ranked inside each tile.
 // ---------------------------------------------------------------------------
-__global__ void k_col_counts(int32_t n, const int64_t* __restrict__ rp,
-                             const int32_t* __restrict__ col, uint32_t* cnt) {
-    for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
-        for (int64_t p = rp[k]; p < rp[k + 1]; ++p) atomicAdd(&cnt[col[p]], 1u);
+constexpr int kRadixBits = 9;
+constexpr int kRadix = 1 << kRadixBits;
+constexpr int kRadixThreads = 256;
+constexpr int kRadixItems = 8;
+constexpr int kRadixTile = kRadixThreads * kRadixItems;
+
+__global__ void __launch_bounds__(kRadixThreads)
+    k_radix_hist(const uint32_t* __restrict__ keys, int64_t cnt, int shift, int64_t ntiles,
+                 uint32_t* hist) {
+    __shared__ uint32_t h[kRadix];
+    for (int i = threadIdx.x; i < kRadix; i += kRadixThreads) h[i] = 0u;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kRadixTile;
+#pragma unroll
+    for (int r = 0; r < kRadixItems; ++r) {
+        const int64_t i = base + (int64_t)r * kRadixThreads + threadIdx.x;
+        if (i < cnt) atomicAdd(&h[(keys[i] >> shift) & (kRadix - 1)], 1u);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadix; d += kRadixThreads)
+        hist[(int64_t)d * ntiles + blockIdx.x] = h[d];
 }
 
-__global__ void k_scatter_t(int32_t n, const int64_t* __restrict__ rp,
-                            const int32_t* __restrict__ col, const double* __restrict__ val,
-                            const int64_t* __restrict__ trp, uint32_t* fill, int32_t* tcol,
-                            double* tval) {
+// Stable scatter of one tile: elements are ranked in index order (round-major,
+// thread-minor), warp ranks from __match_any_sync, warp offsets from shared
+// per-warp digit counts.
+__global__ void __launch_bounds__(kRadixThreads)
+    k_radix_scatter(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals,
+                    int64_t cnt, int shift, int64_t ntiles, const uint32_t* __restrict__ offs,
+                    uint32_t* okeys, uint32_t* ovals) {
+    constexpr int NW = kRadixThreads / 32;
+    __shared__ uint32_t wcnt[NW][kRadix];
+    __shared__ uint32_t run[kRadix];
+    __shared__ uint32_t goff[kRadix];
+    const int warp = threadIdx.x >> 5;
+    const unsigned lt = lanemask_lt();
+    for (int d = threadIdx.x; d < kRadix; d += kRadixThreads) {
+        run[d] = 0u;
+        goff[d] = offs[(int64_t)d * ntiles + blockIdx.x];
+        for (int w = 0; w < NW; ++w) wcnt[w][d] = 0u;
+    }
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kRadixTile;
+    for (int r = 0; r < kRadixItems; ++r) {
+        const int64_t i = base + (int64_t)r * kRadixThreads + threadIdx.x;
+        const bool valid = i < cnt;
+        const uint32_t key = valid ? keys[i] : 0u;
+        const uint32_t val = valid ? vals[i] : 0u;
+        const uint32_t d = valid ? ((key >> shift) & (kRadix - 1)) : (uint32_t)kRadix;
+        const unsigned peers = __match_any_sync(kFull, d);
+        const uint32_t rank = __popc(peers & lt);
+        if (valid && rank == 0) wcnt[warp][d] = __popc(peers);
+        __syncthreads();
+        if (valid) {
+            uint32_t before = 0;
+            for (int w = 0; w < warp; ++w) before += wcnt[w][d];
+            const uint32_t pos = goff[d] + run[d] + before + rank;
+            okeys[pos] = key;
+            ovals[pos] = val;
+        }
+        __syncthreads();
+        for (int dd = threadIdx.x; dd < kRadix; dd += kRadixThreads) {
+            uint32_t t = 0;
+            for (int w = 0; w < NW; ++w) {
+                t += wcnt[w][dd];
+                wcnt[w][dd] = 0u;
+            }
+            run[dd] += t;
+        }
+        __syncthreads();
+    }
+}
+
+// keys = column, vals = position of the entry in Y (row order).
+__global__ void k_transpose_pairs(int32_t n, const int64_t* __restrict__ rp,
+                                  const int32_t* __restrict__ col, uint32_t* keys, uint32_t* vals,
+                                  int32_t* row_of) {
     for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
         for (int64_t p = rp[k]; p < rp[k + 1]; ++p) {
-            const int32_t i = col[p];
-            const int64_t o = trp[i] + atomicAdd(&fill[i], 1u);
-            tcol[o] = k;
-            tval[o] = val[p];
+            keys[p] = (uint32_t)col[p];
+            vals[p] = (uint32_t)p;
+            row_of[p] = k;
         }
 }
 
-__global__ void k_sort_rows(int32_t n, const int64_t* __restrict__ rp, int32_t* col, double* val) {
-    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int64_t s = rp[i], e = rp[i + 1];
-        for (int64_t p = s + 1; p < e; ++p) {
-            const int32_t c = col[p];
-            const double v = val[p];
-            int64_t q = p - 1;
-            while (q >= s && col[q] > c) {
-                col[q + 1] = col[q];
-                val[q + 1] = val[q];
-                --q;
-            }
-            col[q + 1] = c;
-            val[q + 1] = v;
-        }
+__global__ void k_col_counts(int64_t nnz, const int32_t* __restrict__ col, uint32_t* cnt) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz;
+         p += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&cnt[col[p]], 1u);
+}
+
+__global__ void k_transpose_gather(int64_t nnz, const uint32_t* __restrict__ pos,
+                                   const int32_t* __restrict__ row_of,
+                                   const double* __restrict__ val, int32_t* tcol, double* tval) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nnz;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t p = pos[q];
+        tcol[q] = row_of[p];
+        tval[q] = val[p];
     }
 }
 
 rw_status transpose_factor(rw_context* ctx, int32_t n, const FactorOut& fo, int64_t* yt_rp,
                            int32_t* yt_col, double* yt_val, Pool& scratch) {
     cudaStream_t s = ctx->stream;
+    const int64_t nnz = fo.nnz;
+    rw_status rc;
     uint32_t* cnt = alloc_n<uint32_t>(scratch, n + 1);
     if (!cnt) return RW_ERR_ALLOC;
-    rw_status rc;
     if ((rc = check_cuda(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * (size_t)(n + 1), s), "memset")))
         return rc;
-    const int blocks = grid_for(n, 256, ctx->num_sms * 8);
-    k_col_counts<<<blocks, 256, 0, s>>>(n, fo.y_rp, fo.y_col, cnt);
-    if ((rc = check_launch("transpose counts"))) return rc;
+    if (nnz > 0) {
+        RW_COUNT_LAUNCH();
+        k_col_counts<<<grid_for(nnz, 256, ctx->num_sms * 8), 256, 0, s>>>(nnz, fo.y_col, cnt);
+        if ((rc = check_launch("transpose counts"))) return rc;
+    }
     if ((rc = check_cuda(scan_u32_to_i64(cnt, yt_rp, n, s, scratch), "scan"))) return rc;
-    if ((rc = check_cuda(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * (size_t)(n + 1), s), "memset")))
-        return rc;
-    k_scatter_t<<<blocks, 256, 0, s>>>(n, fo.y_rp, fo.y_col, fo.y_val, yt_rp, cnt, yt_col, yt_val);
-    if ((rc = check_launch("transpose scatter"))) return rc;
-    k_sort_rows<<<blocks, 256, 0, s>>>(n, yt_rp, yt_col, yt_val);
-    return check_launch("transpose sort");
+    if (nnz == 0) return RW_OK;
+    if (nnz >= ((int64_t)1 << 32)) {
+        set_error("transpose: factor too large (%lld entries)", (long long)nnz);
+        return RW_ERR_CAPACITY;
+    }
+    uint32_t* k0 = alloc_n<uint32_t>(scratch, nnz);
+    uint32_t* v0 = alloc_n<uint32_t>(scratch, nnz);
+    uint32_t* k1 = alloc_n<uint32_t>(scratch, nnz);
+    uint32_t* v1 = alloc_n<uint32_t>(scratch, nnz);
+    int32_t* row_of = alloc_n<int32_t>(scratch, nnz);
+    const int64_t ntiles = (nnz + kRadixTile - 1) / kRadixTile;
+    uint32_t* hist = alloc_n<uint32_t>(scratch, ntiles * kRadix + 1);
+    if (!k0 || !v0 || !k1 || !v1 || !row_of || !hist) return RW_ERR_ALLOC;
+    RW_COUNT_LAUNCH();
+    k_transpose_pairs<<<grid_for(n, 256, ctx->num_sms * 8), 256, 0, s>>>(n, fo.y_rp, fo.y_col, k0,
+                                                                          v0, row_of);
+    if ((rc = check_launch("transpose pairs"))) return rc;
+    int bits = 1;
+    while (bits < 31 && ((int64_t)1 << bits) < n) ++bits;
+    for (int shift = 0; shift < bits; shift += kRadixBits) {
+        RW_COUNT_LAUNCH();
+        k_radix_hist<<<(unsigned)ntiles, kRadixThreads, 0, s>>>(k0, nnz, shift, ntiles, hist);
+        if ((rc = check_launch("radix histogram"))) return rc;
+        if ((rc = check_cuda(scan_u32(hist, hist, ntiles * kRadix, s, scratch), "scan"))) return rc;
+        RW_COUNT_LAUNCH();
+        k_radix_scatter<<<(unsigned)ntiles, kRadixThreads, 0, s>>>(k0, v0, nnz, shift, ntiles, hist,
+                                                                    k1, v1);
+        if ((rc = check_launch("radix scatter"))) return rc;
+        std::swap(k0, k1);
+        std::swap(v0, v1);
+    }
+    RW_COUNT_LAUNCH();
+    k_transpose_gather<<<grid_for(nnz, 256, ctx->num_sms * 8), 256, 0, s>>>(nnz, v0, row_of,
+                                                                            fo.y_val, yt_col, yt_val);
+    return check_launch("transpose gather");
 }
 
 }  // namespace rw

@@ -28,6 +28,11 @@ namespace rw {
 
 void set_error(const char* fmt, ...);
 
+// Kernels launched by the calling thread (reported per call in the factor
+// description and the PCG statistics).
+extern thread_local int64_t g_launches;
+#define RW_COUNT_LAUNCH() (++rw::g_launches)
+
 // Device allocations made through the context's allocator.
 struct Pool {
     rw_context* ctx = nullptr;
@@ -135,9 +140,46 @@ rw_status emit_factor(rw_context* ctx, const rw_csr* A, const Tables& T, const W
 rw_status transpose_factor(rw_context* ctx, int32_t n, const FactorOut& fo, int64_t* yt_rp,
                            int32_t* yt_col, double* yt_val, Pool& scratch);
 
-// Level orders for the two triangular solves: rows sorted by level.
+// Level order of a triangular solve: rows sorted by level of the dependency
+// DAG of the strict triangular CSR (rp, col); descending = upper triangular.
+// *lptr_out (allocated from keep) receives the depth + 1 level boundaries.
 rw_status compute_levels(rw_context* ctx, int32_t n, const int64_t* rp, const int32_t* col,
-                         bool descending, int32_t* order, int32_t* depth, Pool& scratch);
+                         bool descending, int32_t* order, int32_t* depth, int64_t** lptr_out,
+                         Pool& keep, Pool& scratch);
+
+// Schedule of one triangular solve (see rw_sched.cu).
+struct SolveRun {
+    int thin;                    // 1: one block with shared-memory values; 0: whole grid
+    int32_t lev_begin, lev_end;  // levels [begin, end)
+    int64_t pos_begin, pos_end;  // positions in the level order
+};
+struct SolveSchedule {
+    int32_t n = 0, depth = 0;
+    const int32_t* order = nullptr;  // rows in level order
+    const int64_t* lptr = nullptr;   // [depth + 1] level boundaries (device)
+    std::vector<int64_t> lptr_h;     // host copy
+    std::vector<SolveRun> runs;
+    int64_t* tptr = nullptr;         // [n+1] packed entries of thin-run positions
+    int32_t* tnin = nullptr;         // [n] in-run entries of each position (listed first)
+    int32_t* tidx = nullptr;         // in-run: slot in the run; external: column
+    double* tval = nullptr;
+    float* tval32 = nullptr;
+    int64_t thin_entries = 0;
+};
+
+rw_status build_schedule(rw_context* ctx, int32_t n, const int64_t* rp, const int32_t* col,
+                         const double* val, const float* val32, const int32_t* order,
+                         const int64_t* lptr_dev, int32_t depth, SolveSchedule& S, Pool& pool,
+                         Pool& scratch);
+
+// Device workspace of the solves, owned by the factor: two grid-barrier words
+// (at offset 0) and the external sums of a thin run (from byte 256 on).
+constexpr int64_t kSolveWorkspaceBytes = 256 + (int64_t)4096 * 16 * 8;
+
+template <typename T>
+rw_status solve_runs(rw_context* ctx, const SolveSchedule& S, const int64_t* rp, const int32_t* col,
+                     const T* val, const T* tval, const T* rhs, const T* scale, T* x, int nrhs,
+                     unsigned* bar);
 
 // ---- solve path (rw_solve.cu) ----------------------------------------------
 
@@ -156,6 +198,9 @@ struct FactorView {
     const float* d32;
     const int32_t* fwd_order;
     const int32_t* bwd_order;
+    const SolveSchedule* fwd_sched;
+    const SolveSchedule* bwd_sched;
+    unsigned* bar;  // grid-barrier words of the solves (owned by the factor)
 };
 
 void launch_to_fp32(const double* in, float* out, int64_t cnt, cudaStream_t s, int num_sms);
@@ -180,5 +225,7 @@ struct rw_factor {
     rw_factor_desc desc{};
     int32_t* fwd_order = nullptr;
     int32_t* bwd_order = nullptr;
+    rw::SolveSchedule fwd_sched, bwd_sched;
+    unsigned* bar = nullptr;
     explicit rw_factor(rw_context* c) : ctx(c), pool(c) {}
 };

@@ -74,60 +74,6 @@ __global__ void __launch_bounds__(256) k_spmv(int32_t n, const int32_t* __restri
     }
 }
 
-// ---------------------------------------------------------------------------
-// Sync-free triangular solve over a strict triangular CSR in level order:
-//   x_row = rhs_row / scale_row - sum_p val_p * x_{col_p}
-// (scale = D for the forward solve, none for the backward solve).  x must be
-// filled with the pending marker beforehand.  Co-resident grid (cooperative
-// launch); warp w handles positions w, w + NW, ... of the order.
-// ---------------------------------------------------------------------------
-template <typename T, int NR>
-__global__ void __launch_bounds__(256) k_trisolve(int32_t n, const int32_t* __restrict__ order,
-                                                  const int64_t* __restrict__ rp,
-                                                  const int32_t* __restrict__ col,
-                                                  const T* __restrict__ val,
-                                                  const T* __restrict__ rhs,
-                                                  const T* __restrict__ scale, T* x, int nrhs,
-                                                  DevStatus* st) {
-    constexpr int G = 32 / NR;
-    const int lane = (int)lane_id();
-    const int j = lane % NR;
-    const int eg = lane / NR;
-    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const bool jok = j < nrhs;
-    for (int64_t pos = gw; pos < n; pos += nw) {
-        const int32_t row = order[pos];
-        const int64_t s = rp[row], e = rp[row + 1];
-        T b = T(0);
-        if (eg == 0 && jok) {
-            b = rhs[(size_t)row * nrhs + j];
-            if (scale) b = b / scale[row];
-        }
-        T acc = T(0);
-        for (int64_t p = s + eg; p < e; p += G) {
-            const int32_t c = col[p];
-            const T yv = val[p];
-            if (jok) {
-                const T* src = x + (size_t)c * nrhs + j;
-                T v = ld_relaxed(src);
-                unsigned spins = 0;
-                while (is_pending(v)) {
-                    if (wait_gives_up(spins, &st->timeout)) {
-                        v = T(0);
-                        break;
-                    }
-                    v = ld_relaxed(src);
-                }
-                acc += yv * v;
-            }
-        }
-#pragma unroll
-        for (int o = NR; o < 32; o <<= 1) acc += __shfl_xor_sync(kFull, acc, o);
-        if (eg == 0 && jok) st_relaxed(x + (size_t)row * nrhs + j, b - acc);
-    }
-}
-
 template <typename T>
 __global__ void k_fill_pending(T* x, int64_t cnt) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
@@ -361,6 +307,7 @@ static int pow2_at_least(int v) {
 template <typename TA, typename TV, int NR>
 static void launch_spmv_nr(int32_t n, const int32_t* rp, const int32_t* col, const TA* val,
                            const TV* x, TV* y, int nrhs, double* part, int blocks, cudaStream_t s) {
+    RW_COUNT_LAUNCH();
     k_spmv<TA, TV, NR, 8><<<blocks, 256, 0, s>>>(n, rp, col, val, x, y, nrhs, part);
 }
 
@@ -380,58 +327,63 @@ static rw_status launch_spmv(rw_context* ctx, int32_t n, const int32_t* rp, cons
     return check_launch("spmv");
 }
 
-template <typename T, int NR>
-static rw_status launch_trisolve_nr(rw_context* ctx, int32_t n, const int32_t* order,
-                                    const int64_t* rp, const int32_t* col, const T* val,
-                                    const T* rhs, const T* scale, T* x, int nrhs) {
-    auto fn = k_trisolve<T, NR>;
-    static int per_sm = -1;
-    if (per_sm < 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0);
-        if (per_sm < 1) per_sm = 1;
-    }
-    int64_t blocks = (int64_t)per_sm * ctx->num_sms;
-    const int64_t need = ((int64_t)n + 7) / 8;  // 8 warps per block, one row per warp at a time
-    if (blocks > need) blocks = need;
-    if (blocks < 1) blocks = 1;
-    DevStatus* st = ctx->d_status;
-    void* args[] = {(void*)&n, (void*)&order, (void*)&rp, (void*)&col, (void*)&val, (void*)&rhs,
-                    (void*)&scale, (void*)&x, (void*)&nrhs, (void*)&st};
-    return check_cuda(cudaLaunchCooperativeKernel((const void*)fn, dim3((unsigned)blocks), dim3(256),
-                                                  args, 0, ctx->stream),
-                      "triangular solve launch");
-}
-
-template <typename T>
-static rw_status launch_trisolve(rw_context* ctx, int32_t n, const int32_t* order,
-                                 const int64_t* rp, const int32_t* col, const T* val, const T* rhs,
-                                 const T* scale, T* x, int nrhs) {
-    switch (pow2_at_least(nrhs)) {
-        case 1: return launch_trisolve_nr<T, 1>(ctx, n, order, rp, col, val, rhs, scale, x, nrhs);
-        case 2: return launch_trisolve_nr<T, 2>(ctx, n, order, rp, col, val, rhs, scale, x, nrhs);
-        case 4: return launch_trisolve_nr<T, 4>(ctx, n, order, rp, col, val, rhs, scale, x, nrhs);
-        case 8: return launch_trisolve_nr<T, 8>(ctx, n, order, rp, col, val, rhs, scale, x, nrhs);
-        default: return launch_trisolve_nr<T, 16>(ctx, n, order, rp, col, val, rhs, scale, x, nrhs);
-    }
-}
-
 template <typename T>
 static rw_status fill_pending(rw_context* ctx, T* x, int64_t cnt) {
+    RW_COUNT_LAUNCH();
     k_fill_pending<T><<<grid_for(cnt, 256, ctx->num_sms * 8), 256, 0, ctx->stream>>>(x, cnt);
     return check_launch("fill");
 }
 
-// z = Y^-1 D^-1 Y^-T r; w: scratch [n, nrhs]; w and z must be pending.
+// Device-time accumulation of the solve phases (events on the context stream).
+struct SolveTimes {
+    bool on = false;
+    float spmv = 0.f, bwd = 0.f, fwd = 0.f;
+    bool pending_spmv = false, pending_pre = false;
+};
+
+// z = Y^-1 D^-1 Y^-T r; w: scratch [n, nrhs].  With timing, events 5/6/7
+// bracket the two solves (read by the caller).
+template <typename T>
+static const T* thin_values(const SolveSchedule& S);
+template <>
+const double* thin_values<double>(const SolveSchedule& S) { return S.tval; }
+template <>
+const float* thin_values<float>(const SolveSchedule& S) { return S.tval32; }
+
 template <typename T>
 static rw_status precond_t(rw_context* ctx, const FactorView& F, const T* yv, const T* ytv,
-                           const T* d, const T* r, T* w, T* z, int nrhs) {
-    rw_status rc = launch_trisolve<T>(ctx, F.n, F.bwd_order, F.yt_rp, F.yt_col, ytv, r, nullptr, w,
-                                      nrhs);
+                           const T* d, const T* r, T* w, T* z, int nrhs, SolveTimes* tm = nullptr) {
+    if (tm && tm->on) cudaEventRecord(ctx->ev[5], ctx->stream);
+    rw_status rc = solve_runs<T>(ctx, *F.bwd_sched, F.yt_rp, F.yt_col, ytv,
+                                 thin_values<T>(*F.bwd_sched), r, nullptr, w, nrhs, F.bar);
     if (rc) return rc;
-    return launch_trisolve<T>(ctx, F.n, F.fwd_order, F.y_rp, F.y_col, yv, w, d, z, nrhs);
+    if (tm && tm->on) cudaEventRecord(ctx->ev[6], ctx->stream);
+    rc = solve_runs<T>(ctx, *F.fwd_sched, F.y_rp, F.y_col, yv, thin_values<T>(*F.fwd_sched), w, d,
+                       z, nrhs, F.bar);
+    if (tm && tm->on) {
+        cudaEventRecord(ctx->ev[7], ctx->stream);
+        tm->pending_pre = true;
+    }
+    return rc;
+}
+
+// Adds the completed event intervals of the last preconditioner application
+// and SpMV (the stream has been synchronised by the caller).
+static void collect_times(rw_context* ctx, SolveTimes& tm) {
+    float t = 0.f;
+    if (tm.pending_pre) {
+        if (cudaEventElapsedTime(&t, ctx->ev[5], ctx->ev[6]) == cudaSuccess) tm.bwd += t;
+        if (cudaEventElapsedTime(&t, ctx->ev[6], ctx->ev[7]) == cudaSuccess) tm.fwd += t;
+        tm.pending_pre = false;
+    }
+    if (tm.pending_spmv) {
+        if (cudaEventElapsedTime(&t, ctx->ev[2], ctx->ev[3]) == cudaSuccess) tm.spmv += t;
+        tm.pending_spmv = false;
+    }
 }
 
 void launch_to_fp32(const double* in, float* out, int64_t cnt, cudaStream_t s, int num_sms) {
+    RW_COUNT_LAUNCH();
     k_convert<double, float><<<grid_for(cnt, 256, num_sms * 8), 256, 0, s>>>(in, out, cnt);
 }
 
@@ -474,16 +426,25 @@ static rw_status pcg_t(rw_context* ctx, const rw_csr* A, const FactorView& F, co
     if ((rc = check_cuda(cudaMemsetAsync(x, 0, sizeof(double) * (size_t)cnt, s), "memset"))) return rc;
     if ((rc = check_cuda(cudaMemsetAsync(part, 0, sizeof(double) * kDotParts * 16, s), "memset")))
         return rc;
+    RW_COUNT_LAUNCH();
     k_check_finite<<<vb, 256, 0, s>>>(b, cnt, ctx->d_status);
+    RW_COUNT_LAUNCH();
     k_convert<double, T><<<vb, 256, 0, s>>>(b, r, cnt);
+    RW_COUNT_LAUNCH();
     k_dot<double, double><<<vb, 256, 0, s>>>(b, b, n, nrhs, part);
+    RW_COUNT_LAUNCH();
     k_scalars<<<1, 256, 0, s>>>(S, part, vb, nrhs, kOpBnorm, tol, 0);
     if ((rc = check_launch("pcg init"))) return rc;
     if ((rc = fill_pending(ctx, w, cnt))) return rc;
     if ((rc = fill_pending(ctx, z, cnt))) return rc;
-    if ((rc = precond_t<T>(ctx, F, yv, ytv, dv, r, w, z, nrhs))) return rc;
+    SolveTimes tm;
+    tm.on = ctx->opt.timing != 0;
+    if ((rc = precond_t<T>(ctx, F, yv, ytv, dv, r, w, z, nrhs, &tm))) return rc;
+    RW_COUNT_LAUNCH();
     k_dot<T, T><<<vb, 256, 0, s>>>(r, z, n, nrhs, part);
+    RW_COUNT_LAUNCH();
     k_scalars<<<1, 256, 0, s>>>(S, part, vb, nrhs, kOpRho0, tol, 0);
+    RW_COUNT_LAUNCH();
     k_convert<T, T><<<vb, 256, 0, s>>>(z, p, cnt);
     if ((rc = check_launch("pcg start"))) return rc;
     if ((rc = check_cuda(cudaMemcpyAsync(hS, S, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s), "copy")))
@@ -498,20 +459,33 @@ static rw_status pcg_t(rw_context* ctx, const rw_csr* A, const FactorView& F, co
     bool any_active = hS->any_active != 0;
     for (int it = 1; it <= max_iter && any_active; ++it) {
         done_iters = it;
+        if (tm.on) cudaEventRecord(ctx->ev[2], s);
         if ((rc = launch_spmv<T, T>(ctx, n, A->row_ptr, A->col, Aval, p, q, nrhs, part))) return rc;
+        if (tm.on) {
+            cudaEventRecord(ctx->ev[3], s);
+            tm.pending_spmv = true;
+        }
+        RW_COUNT_LAUNCH();
         k_scalars<<<1, 256, 0, s>>>(S, part, kDotParts, nrhs, kOpAlpha, tol, it);
+        RW_COUNT_LAUNCH();
         k_update_xr<T><<<vb, 256, 0, s>>>(n, nrhs, S, x, r, p, q, w, z, part);
-        if (mixed && it % refine == 0)
+        if (mixed && it % refine == 0) {
+            RW_COUNT_LAUNCH();
             k_true_resid<T><<<vb, 256, 0, s>>>(n, A->row_ptr, A->col, A->val, b, x, nrhs, r, part);
+        }
+        RW_COUNT_LAUNCH();
         k_scalars<<<1, 256, 0, s>>>(S, part, vb, nrhs, kOpResid, tol, it);
         if ((rc = check_launch("pcg step"))) return rc;
         if ((rc = check_cuda(cudaMemcpyAsync(hS, S, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s),
                              "copy")))
             return rc;
         if ((rc = check_cuda(cudaStreamSynchronize(s), "sync"))) return rc;
+        if (tm.on) collect_times(ctx, tm);
         if (hS->any_check) {
+            RW_COUNT_LAUNCH();
             k_true_resid<T><<<vb, 256, 0, s>>>(n, A->row_ptr, A->col, A->val, b, x, nrhs, nullptr,
                                                part);
+            RW_COUNT_LAUNCH();
             k_scalars<<<1, 256, 0, s>>>(S, part, vb, nrhs, kOpTrue, tol, it);
             if ((rc = check_launch("pcg true residual"))) return rc;
             if ((rc = check_cuda(cudaMemcpyAsync(hS, S, sizeof(PcgScalars), cudaMemcpyDeviceToHost,
@@ -522,19 +496,25 @@ static rw_status pcg_t(rw_context* ctx, const rw_csr* A, const FactorView& F, co
             if (!hS->any_active) break;
         }
         if (hS->broke) break;
-        if ((rc = precond_t<T>(ctx, F, yv, ytv, dv, r, w, z, nrhs))) return rc;
+        if ((rc = precond_t<T>(ctx, F, yv, ytv, dv, r, w, z, nrhs, &tm))) return rc;
+        RW_COUNT_LAUNCH();
         k_dot<T, T><<<vb, 256, 0, s>>>(r, z, n, nrhs, part);
+        RW_COUNT_LAUNCH();
         k_scalars<<<1, 256, 0, s>>>(S, part, vb, nrhs, kOpBeta, tol, it);
+        RW_COUNT_LAUNCH();
         k_update_p<T><<<vb, 256, 0, s>>>(n, nrhs, S, z, p);
         if ((rc = check_launch("pcg direction"))) return rc;
     }
     // final true residuals for the report
+    RW_COUNT_LAUNCH();
     k_true_resid<T><<<vb, 256, 0, s>>>(n, A->row_ptr, A->col, A->val, b, x, nrhs, nullptr, part);
+    RW_COUNT_LAUNCH();
     k_scalars<<<1, 256, 0, s>>>(S, part, vb, nrhs, kOpReport, tol, done_iters);
     if ((rc = check_launch("pcg report"))) return rc;
     if ((rc = check_cuda(cudaMemcpyAsync(hS, S, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s), "copy")))
         return rc;
     if ((rc = read_status(ctx, "pcg"))) return rc;
+    if (tm.on) collect_times(ctx, tm);
     int maxit = 0;
     double maxrel = 0.0;
     bool conv_all = true;
@@ -550,6 +530,9 @@ static rw_status pcg_t(rw_context* ctx, const rw_csr* A, const FactorView& F, co
     if (stats) {
         stats->iterations = maxit;
         stats->rel_residual = maxrel;
+        stats->spmv_ms = tm.spmv;
+        stats->bwd_ms = tm.bwd;
+        stats->fwd_ms = tm.fwd;
     }
     if (hS->broke) {
         set_error("pcg breakdown: p.Ap <= 0");
@@ -576,6 +559,7 @@ rw_status pcg_run(rw_context* ctx, const rw_csr* A, const FactorView& F, const d
         }
         float* a32 = alloc_n<float>(sc, A->nnz);
         if (!a32) return RW_ERR_ALLOC;
+        RW_COUNT_LAUNCH();
         k_convert<double, float><<<grid_for(A->nnz, 256, ctx->num_sms * 8), 256, 0, s>>>(
             A->val, a32, A->nnz);
         if ((rc = check_launch("convert A"))) return rc;
@@ -675,6 +659,9 @@ extern "C" rw_status rw_precond_apply_static(rw_context* ctx, const rw_factor* F
     v.d32 = d.d32;
     v.fwd_order = F->fwd_order;
     v.bwd_order = F->bwd_order;
+    v.fwd_sched = &F->fwd_sched;
+    v.bwd_sched = &F->bwd_sched;
+    v.bar = F->bar;
     if ((rc = reset_status(ctx))) return rc;
     // w and z start as "pending" on every call: the array keeps the last call's contents
     if ((rc = fill_pending(ctx, w, cnt))) return rc;

@@ -90,21 +90,25 @@ __global__ void k_set_zero(Tout* p) { *p = 0; }
 template <typename Tin, typename Tout>
 static cudaError_t scan_impl(const Tin* in, Tout* out, int64_t n, cudaStream_t s, Pool& pool) {
     if (n <= 0) {
+        RW_COUNT_LAUNCH();
         k_set_zero<Tout><<<1, 1, 0, s>>>(out);
         return cudaGetLastError();
     }
     const int64_t tiles = (n + kScanTile - 1) / kScanTile;
     if (tiles == 1) {
+        RW_COUNT_LAUNCH();
         k_tile_scan<Tin, Tout><<<1, kScanThreads, 0, s>>>(in, n, nullptr, out);
         return cudaGetLastError();
     }
     Tout* sums = alloc_n<Tout>(pool, tiles + 1);
     if (!sums) return cudaErrorMemoryAllocation;
+    RW_COUNT_LAUNCH();
     k_tile_sums<Tin, Tout><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, sums);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     e = scan_impl<Tout, Tout>(sums, sums, tiles, s, pool);
     if (e != cudaSuccess) return e;
+    RW_COUNT_LAUNCH();
     k_tile_scan<Tin, Tout><<<(unsigned)tiles, kScanThreads, 0, s>>>(in, n, sums, out);
     return cudaGetLastError();
 }
@@ -242,6 +246,7 @@ rw_status build_tables(rw_context* ctx, const rw_csr* A, Tables& T, Pool& pool) 
         !T.diag)
         return RW_ERR_ALLOC;
     const int blocks = grid_for(n, 256, ctx->num_sms * 8);
+    RW_COUNT_LAUNCH();
     k_row_info<<<blocks, 256, 0, s>>>(n, A->nnz, A->row_ptr, A->col, A->val, T.deg, T.lowdeg, T.diag_pos,
                                       T.toff8, T.foff8, T.walk_flag, ctx->d_status);
     rw_status rc = check_launch("row info");
@@ -268,10 +273,12 @@ rw_status build_tables(rw_context* ctx, const rw_csr* A, Tables& T, Pool& pool) 
     T.wrow = alloc_n<int4>(pool, T.n_walk_rows);
     T.walk_rows = alloc_n<int32_t>(pool, T.n_walk_rows);
     if (!T.thr || !T.nxt || !T.fthr || !T.wrow || !T.walk_rows) return RW_ERR_ALLOC;
+    RW_COUNT_LAUNCH();
     k_fill_tables<<<blocks, 256, 0, s>>>(n, A->row_ptr, A->col, A->val, T.deg, T.lowdeg,
                                          T.diag_pos, T.toff8, T.foff8, T.thr, T.nxt, T.fthr, T.S,
                                          T.diag);
     if ((rc = check_launch("fill tables"))) return rc;
+    RW_COUNT_LAUNCH();
     k_walk_rows<<<blocks, 256, 0, s>>>(n, T.walk_flag, T.toff8, T.foff8, T.lowdeg, T.wrow,
                                        T.walk_rows);
     return check_launch("walk rows");
@@ -307,6 +314,7 @@ rw_status build_walk_space(rw_context* ctx, const Tables& T, uint32_t uniform,
     const int blocks = grid_for(nw, 256, ctx->num_sms * 8);
     rw_status rc;
     if (nw > 0) {
+        RW_COUNT_LAUNCH();
         k_budgets<<<blocks, 256, 0, s>>>(nw, T.wrow, uniform, d_budget, ws.wbase, ctx->d_status);
         if ((rc = check_launch("budgets"))) return rc;
     }
@@ -320,6 +328,7 @@ rw_status build_walk_space(rw_context* ctx, const Tables& T, uint32_t uniform,
     ws.chunk_row = alloc_n<int32_t>(pool, ws.nchunks);
     if (!ws.chunk_row) return RW_ERR_ALLOC;
     if (nw > 0) {
+        RW_COUNT_LAUNCH();
         k_chunk_rows<<<blocks, 256, 0, s>>>(nw, ws.wbase, ws.chunk_row);
         if ((rc = check_launch("chunk rows"))) return rc;
     }

@@ -221,6 +221,7 @@ rw_status run_walks(rw_context* ctx, const Tables& T, const WalkSpace& ws, const
     const int64_t need = (ws.total + 255) / 256;  // never more lanes than walks
     if (blocks > need) blocks = need;
     if (ms) cudaEventRecord(ctx->ev[0], s);
+    RW_COUNT_LAUNCH();
     k_walk<<<(unsigned)blocks, 256, 0, s>>>(P);
     if ((rc = check_launch("walk kernel"))) return rc;
     if (ms) {
