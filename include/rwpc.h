@@ -160,6 +160,18 @@ rw_status rw_build_factor(rw_context* ctx, const rw_csr* A, uint32_t walks_per_r
 rw_status rw_build_factor_budget(rw_context* ctx, const rw_csr* A, const uint32_t* d_budget,
                                  uint64_t seed, double drop_tol, rw_factor** out);
 
+/* Batched precondition step: factors of nmat matrices (As: host array of
+ * device CSRs) whose walks all run in ONE persistent kernel launch, with work
+ * stealing across rows of all matrices.  Matrix m draws with tag (m << 2) and
+ * key seeds[m] (host array), so its factor equals rw_build_factor with matrix
+ * index m.  d_budgets: host array of nmat device budget pointers (an entry or
+ * the whole array may be NULL: uniform walks_per_row).  outs[m] receive the
+ * factors (each released by rw_factor_destroy).  Per-walk records are not
+ * kept for batched builds.  On error no factor is returned. */
+rw_status rw_build_factor_batched(rw_context* ctx, int32_t nmat, const rw_csr* As,
+                                  const uint32_t* const* d_budgets, uint32_t walks_per_row,
+                                  const uint64_t* seeds, double drop_tol, rw_factor** outs);
+
 rw_status rw_factor_view(const rw_factor* F, rw_factor_desc* desc);
 void rw_factor_destroy(rw_factor* F);
 
@@ -177,6 +189,17 @@ void rw_factor_destroy(rw_factor* F);
 rw_status pcg_solve(rw_context* ctx, const rw_csr* A, const rw_factor* F, const double* d_b,
                     double* d_x, int32_t nrhs, double tol, int32_t max_iter, rw_precision prec,
                     rw_pcg_stats* stats, int32_t* h_iters, double* h_relres);
+
+/* pcg_solve for nmat matrices (host arrays of matrices, factors, and device
+ * right-hand-side / solution pointers), each with nrhs node-major right-hand
+ * sides.  stats: host [nmat] (may be NULL); h_iters/h_relres: host
+ * [nmat * nrhs] (may be NULL).  Returns RW_ERR_NO_CONVERGENCE if any right-hand
+ * side missed tol, the first other error otherwise. */
+rw_status pcg_solve_batched(rw_context* ctx, int32_t nmat, const rw_csr* As,
+                            const rw_factor* const* Fs, const double* const* d_b,
+                            double* const* d_x, int32_t nrhs, double tol, int32_t max_iter,
+                            rw_precision prec, rw_pcg_stats* stats, int32_t* h_iters,
+                            double* h_relres);
 
 /* z = (Y^T diag(D) Y)^-1 r for nrhs node-major right-hand sides (FP64): the
  * preconditioner application inside pcg_solve (backward solve with Y^T,

@@ -24,6 +24,7 @@ from . import _build
 
 __all__ = [
     "load", "RwError", "CSR", "Context", "Factor", "rw_options_default", "rw_context_create",
+    "rw_build_factor_batched", "pcg_solve_batched",
     "rw_context_destroy", "rw_build_factor", "rw_build_factor_budget", "rw_factor_view",
     "rw_factor_destroy", "pcg_solve", "rw_precond_apply", "rw_precond_apply_static", "rw_spmv",
     "rw_status_string",
@@ -103,6 +104,9 @@ def load():
     lib.rw_build_factor_budget.argtypes = [_c_void_p, P(rw_csr_t), _c_void_p, _u64, _f64,
                                            P(_c_void_p)]
     lib.rw_build_factor_budget.restype = ctypes.c_int
+    lib.rw_build_factor_batched.argtypes = [_c_void_p, _i32, P(rw_csr_t), P(_c_void_p), _u32,
+                                            P(_u64), _f64, P(_c_void_p)]
+    lib.rw_build_factor_batched.restype = ctypes.c_int
     lib.rw_factor_view.argtypes = [_c_void_p, P(rw_factor_desc_t)]
     lib.rw_factor_view.restype = ctypes.c_int
     lib.rw_factor_destroy.argtypes = [_c_void_p]
@@ -110,6 +114,10 @@ def load():
     lib.pcg_solve.argtypes = [_c_void_p, P(rw_csr_t), _c_void_p, _c_void_p, _c_void_p, _i32, _f64,
                               _i32, ctypes.c_int, P(rw_pcg_stats_t), _c_void_p, _c_void_p]
     lib.pcg_solve.restype = ctypes.c_int
+    lib.pcg_solve_batched.argtypes = [_c_void_p, _i32, P(rw_csr_t), P(_c_void_p), P(_c_void_p),
+                                      P(_c_void_p), _i32, _f64, _i32, ctypes.c_int,
+                                      P(rw_pcg_stats_t), _c_void_p, _c_void_p]
+    lib.pcg_solve_batched.restype = ctypes.c_int
     lib.rw_precond_apply.argtypes = [_c_void_p, _c_void_p, _c_void_p, _c_void_p, _i32]
     lib.rw_precond_apply.restype = ctypes.c_int
     lib.rw_precond_apply_static.argtypes = [_c_void_p, _c_void_p, _c_void_p, _c_void_p, _i32]
@@ -320,6 +328,22 @@ def rw_build_factor_budget(ctx, A, budget, seed, drop_tol):
     return Factor(ctx, h)
 
 
+def rw_build_factor_batched(ctx, As, walks_per_row, seeds, drop_tol, budgets=None):
+    """Factors of several matrices whose walks run in one launch; matrix m
+    draws with matrix index m.  budgets: None or a list of CUDA budget tensors
+    (entries may be None).  Returns a list of Factor."""
+    nmat = len(As)
+    arr = (rw_csr_t * nmat)(*[A.c for A in As])
+    sd = (_u64 * nmat)(*[int(x) for x in seeds])
+    outs = (_c_void_p * nmat)()
+    bud = None
+    if budgets is not None:
+        bud = (_c_void_p * nmat)(*[(b.data_ptr() if b is not None else None) for b in budgets])
+    _check(load().rw_build_factor_batched(ctx.handle, nmat, arr, bud, int(walks_per_row), sd,
+                                          float(drop_tol), outs), "rw_build_factor_batched")
+    return [Factor(ctx, _c_void_p(outs[m])) for m in range(nmat)]
+
+
 def rw_factor_view(F):
     d = rw_factor_desc_t()
     _check(load().rw_factor_view(F.handle, ctypes.byref(d)), "rw_factor_view")
@@ -347,6 +371,27 @@ def pcg_solve(ctx, A, F, b, x, tol, max_iter, prec=RW_FP64):
     if rc not in (RW_OK, -5):
         raise RwError(rc, "pcg_solve")
     return rc, st, its, rel
+
+
+def pcg_solve_batched(ctx, As, Fs, bs, xs, tol, max_iter, prec=RW_FP64):
+    """pcg_solve over several matrices; bs/xs: lists of CUDA tensors [n_m, nrhs].
+    Returns (status, stats list, iterations [nmat, nrhs], relres [nmat, nrhs])."""
+    import numpy as np
+    nmat = len(As)
+    nrhs = 1 if bs[0].dim() == 1 else bs[0].shape[1]
+    arr = (rw_csr_t * nmat)(*[A.c for A in As])
+    fh = (_c_void_p * nmat)(*[F.handle.value if hasattr(F.handle, "value") else F.handle for F in Fs])
+    bp = (_c_void_p * nmat)(*[b.data_ptr() for b in bs])
+    xp = (_c_void_p * nmat)(*[x.data_ptr() for x in xs])
+    st = (rw_pcg_stats_t * nmat)()
+    its = np.zeros((nmat, nrhs), np.int32)
+    rel = np.zeros((nmat, nrhs), np.float64)
+    rc = load().pcg_solve_batched(ctx.handle, nmat, arr, fh, bp, xp, nrhs, float(tol), int(max_iter),
+                                  int(prec), st, its.ctypes.data_as(_c_void_p),
+                                  rel.ctypes.data_as(_c_void_p))
+    if rc not in (RW_OK, -5):
+        raise RwError(rc, "pcg_solve_batched")
+    return rc, list(st), its, rel
 
 
 def rw_precond_apply(ctx, F, r, z):

@@ -5,6 +5,8 @@
 #include <cstdio>
 #include <cstring>
 
+#include <vector>
+
 #include "rw_internal.h"
 
 namespace rw {
@@ -216,130 +218,82 @@ void rw_context_destroy(rw_context* ctx) {
     delete ctx;
 }
 
-static rw_status build_factor_impl(rw_context* ctx, const rw_csr* A, uint32_t uniform,
-                                   const uint32_t* d_budget, uint64_t seed, double drop_tol,
-                                   rw_factor** out) {
-    if (!ctx || !out) {
-        set_error("rw_build_factor: NULL context or output");
-        return RW_ERR_ARG;
-    }
-    *out = nullptr;
-    rw_status rc = check_csr(A);
-    if (rc) return rc;
-    if (!(drop_tol >= 0.0) || !(drop_tol < 1e300)) {
-        set_error("drop_tol must be finite and >= 0");
-        return RW_ERR_ARG;
-    }
-    if (!d_budget && uniform < 1) {
-        set_error("walks_per_row must be >= 1");
-        return RW_ERR_ARG;
-    }
-    cudaStream_t s = ctx->stream;
-    const bool timing = ctx->opt.timing != 0;
-    const int64_t launches0 = g_launches;
-    rw_factor* F = new (std::nothrow) rw_factor(ctx);
-    if (!F) return RW_ERR_ALLOC;
-    Pool scratch(ctx);
-    const int32_t n = A->n;
-    rw_factor_desc& d = F->desc;
-    memset(&d, 0, sizeof(d));
-    d.n = n;
+// One matrix of a (possibly batched) factor build.
+struct MatBuild {
+    const rw_csr* A = nullptr;
+    const uint32_t* budget = nullptr;  // device [n] or NULL (uniform)
+    uint64_t seed = 0;
+    uint32_t matrix_index = 0;
+    rw_factor* F = nullptr;
     Tables T;
     WalkSpace ws;
+    int64_t rec_base = 0;   // first record of this matrix in the batch
+    int64_t row_base = 0;   // first walk row of this matrix in the batch
+    int64_t launches = 0;
+};
+
+// The rest of the build of one matrix after the walks: merge and emission,
+// transpose, levels, FP32 copies, solve schedules, description.
+static rw_status finish_factor(rw_context* ctx, MatBuild& mb, const int2* rec, bool rec_owned,
+                               double drop_tol, uint64_t hops, float ms_walk, Pool& scratch) {
+    cudaStream_t s = ctx->stream;
+    const bool timing = ctx->opt.timing != 0;
+    rw_factor* F = mb.F;
+    rw_factor_desc& d = F->desc;
+    const rw_csr* A = mb.A;
+    const int32_t n = A->n;
     FactorOut fo;
-    float ms_walk = 0.f, ms_merge = 0.f, ms_emit = 0.f;
-    int2* rec = nullptr;
-    unsigned long long* d_hops = nullptr;
-    int64_t* yt_rp = nullptr;
-    int32_t* yt_col = nullptr;
-    double* yt_val = nullptr;
+    float ms_merge = 0.f, ms_emit = 0.f;
     int64_t* fwd_lptr = nullptr;
     int64_t* bwd_lptr = nullptr;
     float* y32 = nullptr;
     float* yt32 = nullptr;
-    if ((rc = reset_status(ctx))) goto fail;
-    if (timing) cudaEventRecord(ctx->ev[10], s);
-    if ((rc = build_tables(ctx, A, T, scratch))) goto fail;
-    if ((rc = build_walk_space(ctx, T, uniform, d_budget, ws, ctx->opt.keep_records ? F->pool : scratch)))
-        goto fail;
+    rw_status rc;
+    const int64_t launches0 = g_launches;
     if (timing) cudaEventRecord(ctx->ev[11], s);
-    rec = alloc_n<int2>(ctx->opt.keep_records ? F->pool : scratch, ws.total);
-    d_hops = alloc_n<unsigned long long>(scratch, 1);
-    if (!rec || !d_hops) {
-        rc = RW_ERR_ALLOC;
-        goto fail;
-    }
-    {
-        WalkLaunch wl;
-        wl.seed = seed;
-        wl.matrix_index = 0;
-        wl.tag = 0;
-        wl.max_steps = ctx->opt.max_steps;
-        wl.record_lengths = ctx->opt.record_lengths;
-        if ((rc = run_walks(ctx, T, ws, wl, rec, d_hops, scratch, timing ? &ms_walk : nullptr)))
-            goto fail;
-        if ((rc = read_status(ctx, "walks"))) goto fail;  // no merge of stopped walks
-    }
-    if ((rc = emit_factor(ctx, A, T, ws, rec, drop_tol, fo, F->pool, scratch,
+    if ((rc = emit_factor(ctx, A, mb.T, mb.ws, rec, drop_tol, fo, F->pool, scratch,
                           timing ? &ms_merge : nullptr, timing ? &ms_emit : nullptr)))
-        goto fail;
-    yt_rp = alloc_n<int64_t>(F->pool, n + 1);
-    yt_col = alloc_n<int32_t>(F->pool, fo.nnz);
-    yt_val = alloc_n<double>(F->pool, fo.nnz);
-    if (!yt_rp || !yt_col || !yt_val) {
-        rc = RW_ERR_ALLOC;
-        goto fail;
-    }
-    if ((rc = transpose_factor(ctx, n, fo, yt_rp, yt_col, yt_val, scratch))) goto fail;
+        return rc;
+    int64_t* yt_rp = alloc_n<int64_t>(F->pool, n + 1);
+    int32_t* yt_col = alloc_n<int32_t>(F->pool, fo.nnz);
+    double* yt_val = alloc_n<double>(F->pool, fo.nnz);
+    if (!yt_rp || !yt_col || !yt_val) return RW_ERR_ALLOC;
+    if ((rc = transpose_factor(ctx, n, fo, yt_rp, yt_col, yt_val, scratch))) return rc;
     if (timing) cudaEventRecord(ctx->ev[12], s);
     F->fwd_order = alloc_n<int32_t>(F->pool, n);
     F->bwd_order = alloc_n<int32_t>(F->pool, n);
-    if (!F->fwd_order || !F->bwd_order) {
-        rc = RW_ERR_ALLOC;
-        goto fail;
-    }
+    if (!F->fwd_order || !F->bwd_order) return RW_ERR_ALLOC;
     if ((rc = compute_levels(ctx, n, fo.y_rp, fo.y_col, false, F->fwd_order, &d.fwd_levels,
                              &fwd_lptr, F->pool, scratch)))
-        goto fail;
+        return rc;
     if ((rc = compute_levels(ctx, n, yt_rp, yt_col, true, F->bwd_order, &d.bwd_levels, &bwd_lptr,
                              F->pool, scratch)))
-        goto fail;
+        return rc;
     if (timing) cudaEventRecord(ctx->ev[13], s);
     if (ctx->opt.store_fp32) {
         y32 = alloc_n<float>(F->pool, fo.nnz);
         yt32 = alloc_n<float>(F->pool, fo.nnz);
         float* d32 = alloc_n<float>(F->pool, n);
-        if (!y32 || !yt32 || !d32) {
-            rc = RW_ERR_ALLOC;
-            goto fail;
-        }
+        if (!y32 || !yt32 || !d32) return RW_ERR_ALLOC;
         launch_to_fp32(fo.y_val, y32, fo.nnz, s, ctx->num_sms);
         launch_to_fp32(yt_val, yt32, fo.nnz, s, ctx->num_sms);
         launch_to_fp32(fo.d, d32, n, s, ctx->num_sms);
-        if ((rc = check_launch("fp32 copies"))) goto fail;
+        if ((rc = check_launch("fp32 copies"))) return rc;
         d.y_val32 = y32;
         d.yt_val32 = yt32;
         d.d32 = d32;
     }
     F->bar = static_cast<unsigned*>(F->pool.get((size_t)kSolveWorkspaceBytes));
-    if (!F->bar) {
-        rc = RW_ERR_ALLOC;
-        goto fail;
-    }
+    if (!F->bar) return RW_ERR_ALLOC;
     if ((rc = build_schedule(ctx, n, fo.y_rp, fo.y_col, fo.y_val, y32, F->fwd_order, fwd_lptr,
                              d.fwd_levels, F->fwd_sched, F->pool, scratch)))
-        goto fail;
+        return rc;
     if ((rc = build_schedule(ctx, n, yt_rp, yt_col, yt_val, yt32, F->bwd_order, bwd_lptr,
                              d.bwd_levels, F->bwd_sched, F->pool, scratch)))
-        goto fail;
+        return rc;
     if (timing) cudaEventRecord(ctx->ev[14], s);
-    {
-        unsigned long long* hh = static_cast<unsigned long long*>(ctx->h_small);
-        if ((rc = check_cuda(cudaMemcpyAsync(hh, d_hops, 8, cudaMemcpyDeviceToHost, s), "copy")))
-            goto fail;
-        if ((rc = read_status(ctx, "factor build"))) goto fail;
-        d.total_hops = hh[0];
-    }
+    if ((rc = read_status(ctx, "factor build"))) return rc;
+    d.total_hops = hops;
     d.nnz = fo.nnz;
     d.y_row_ptr = fo.y_rp;
     d.y_col = fo.y_col;
@@ -351,52 +305,220 @@ static rw_status build_factor_impl(rw_context* ctx, const rw_csr* A, uint32_t un
     d.walks = fo.M;
     d.visits = fo.J;
     d.ground = fo.G;
-    d.n_walk_rows = T.n_walk_rows;
-    d.total_walks = ws.total;
-    if (ctx->opt.keep_records) {
+    d.n_walk_rows = mb.T.n_walk_rows;
+    d.total_walks = mb.ws.total;
+    if (ctx->opt.keep_records && rec_owned) {
         d.records = reinterpret_cast<const int32_t*>(rec);
-        d.walk_base = ws.wbase;
-        int32_t* wr = alloc_n<int32_t>(F->pool, T.n_walk_rows);
-        if (!wr) {
-            rc = RW_ERR_ALLOC;
-            goto fail;
-        }
-        if (T.n_walk_rows > 0 &&
-            (rc = check_cuda(cudaMemcpyAsync(wr, T.walk_rows, sizeof(int32_t) * (size_t)T.n_walk_rows,
+        d.walk_base = mb.ws.wbase;
+        int32_t* wr = alloc_n<int32_t>(F->pool, mb.T.n_walk_rows);
+        if (!wr) return RW_ERR_ALLOC;
+        if (mb.T.n_walk_rows > 0 &&
+            (rc = check_cuda(cudaMemcpyAsync(wr, mb.T.walk_rows,
+                                             sizeof(int32_t) * (size_t)mb.T.n_walk_rows,
                                              cudaMemcpyDeviceToDevice, s),
                              "copy")))
-            goto fail;
+            return rc;
         d.walk_rows = wr;
     }
     if (timing) {
-        float t_tab = 0.f, t_tr = 0.f, t_lev = 0.f, t_fp = 0.f, t_all = 0.f;
+        float t_tr = 0.f, t_lev = 0.f, t_fp = 0.f, t_fin = 0.f;
         cudaEventSynchronize(ctx->ev[14]);
-        cudaEventElapsedTime(&t_tab, ctx->ev[10], ctx->ev[11]);
+        cudaEventElapsedTime(&t_tr, ctx->ev[11], ctx->ev[12]);
         cudaEventElapsedTime(&t_lev, ctx->ev[12], ctx->ev[13]);
         cudaEventElapsedTime(&t_fp, ctx->ev[13], ctx->ev[14]);
-        cudaEventElapsedTime(&t_all, ctx->ev[10], ctx->ev[14]);
-        float t_to_tr = 0.f;
-        cudaEventElapsedTime(&t_to_tr, ctx->ev[11], ctx->ev[12]);
-        t_tr = t_to_tr - ms_walk - ms_merge - ms_emit;
-        d.phase_ms[0] = t_tab;
+        cudaEventElapsedTime(&t_fin, ctx->ev[11], ctx->ev[14]);
         d.phase_ms[1] = ms_walk;
         d.phase_ms[2] = ms_merge;
         d.phase_ms[3] = ms_emit;
-        d.phase_ms[4] = t_tr;
+        d.phase_ms[4] = t_tr - ms_merge - ms_emit;
         d.phase_ms[5] = t_lev;
         d.phase_ms[6] = t_fp;
-        d.phase_ms[7] = t_all;
+        d.phase_ms[7] = d.phase_ms[0] + ms_walk + t_fin;
+    }
+    mb.launches += g_launches - launches0;
+    return RW_OK;
+}
+
+__global__ void k_concat_walk_rows(int32_t nw, const int4* __restrict__ wrow,
+                                   const int64_t* __restrict__ wbase, int64_t rec_base, int32_t m,
+                                   int4* wrow_all, int64_t* wbase_all, int32_t* wmat_all) {
+    for (int32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < nw; r += gridDim.x * blockDim.x) {
+        wrow_all[r] = wrow[r];
+        wbase_all[r] = wbase[r] + rec_base;
+        wmat_all[r] = m;
+    }
+}
+
+__global__ void k_set_i64(int64_t* p, int64_t v) { *p = v; }
+
+// Build factors of one or more matrices; the walks of all of them run in one
+// persistent launch (work stealing across matrices).
+static rw_status build_factors(rw_context* ctx, std::vector<MatBuild>& mbs, uint32_t uniform,
+                               double drop_tol) {
+    cudaStream_t s = ctx->stream;
+    const bool timing = ctx->opt.timing != 0;
+    const int nmat = (int)mbs.size();
+    rw_status rc = RW_OK;
+    Pool scratch(ctx);
+    int2* rec = nullptr;
+    unsigned long long* d_hops = nullptr;
+    float ms_walk = 0.f;
+    WalkBatch wb;
+    std::vector<MatWalk> hmats(nmat);
+    if ((rc = reset_status(ctx))) return rc;
+    for (auto& mb : mbs) {
+        mb.F = new (std::nothrow) rw_factor(ctx);
+        if (!mb.F) {
+            rc = RW_ERR_ALLOC;
+            goto fail;
+        }
+        memset(&mb.F->desc, 0, sizeof(mb.F->desc));
+        mb.F->desc.n = mb.A->n;
+    }
+    // tables and walk spaces
+    {
+        int64_t total = 0, rows = 0;
+        for (int m = 0; m < nmat; ++m) {
+            MatBuild& mb = mbs[m];
+            const int64_t launches0 = g_launches;
+            if (timing) cudaEventRecord(ctx->ev[10], s);
+            Pool& keep = ctx->opt.keep_records ? mb.F->pool : scratch;
+            if ((rc = build_tables(ctx, mb.A, mb.T, scratch))) goto fail;
+            if ((rc = build_walk_space(ctx, mb.T, uniform, mb.budget, mb.ws, keep))) goto fail;
+            if (timing) {
+                cudaEventRecord(ctx->ev[11], s);
+                cudaEventSynchronize(ctx->ev[11]);
+                cudaEventElapsedTime(&mb.F->desc.phase_ms[0], ctx->ev[10], ctx->ev[11]);
+            }
+            mb.rec_base = total;
+            mb.row_base = rows;
+            total += mb.ws.total;
+            rows += mb.T.n_walk_rows;
+            hmats[m] = mat_walk(mb.T, mb.seed, mb.matrix_index, 0);
+            mb.launches += g_launches - launches0;
+        }
+        wb.nmat = nmat;
+        wb.total = total;
+        if (nmat == 1) {
+            wb.m0 = hmats[0];
+            wb.wrow = mbs[0].T.wrow;
+            wb.wbase = mbs[0].ws.wbase;
+            wb.chunk_row = mbs[0].ws.chunk_row;
+        } else {
+            int4* wrow_all = alloc_n<int4>(scratch, rows);
+            int64_t* wbase_all = alloc_n<int64_t>(scratch, rows + 1);
+            int32_t* wmat_all = alloc_n<int32_t>(scratch, rows);
+            MatWalk* dmats = alloc_n<MatWalk>(scratch, nmat);
+            const int64_t nchunks = (total + kWalkChunk - 1) / kWalkChunk;
+            int32_t* chunk_row = alloc_n<int32_t>(scratch, nchunks);
+            if (!wrow_all || !wbase_all || !wmat_all || !dmats || !chunk_row) {
+                rc = RW_ERR_ALLOC;
+                goto fail;
+            }
+            for (int m = 0; m < nmat; ++m) {
+                const MatBuild& mb = mbs[m];
+                if (mb.T.n_walk_rows == 0) continue;
+                RW_COUNT_LAUNCH();
+                k_concat_walk_rows<<<grid_for(mb.T.n_walk_rows, 256, ctx->num_sms * 4), 256, 0, s>>>(
+                    mb.T.n_walk_rows, mb.T.wrow, mb.ws.wbase, mb.rec_base, m,
+                    wrow_all + mb.row_base, wbase_all + mb.row_base, wmat_all + mb.row_base);
+            }
+            RW_COUNT_LAUNCH();
+            k_set_i64<<<1, 1, 0, s>>>(wbase_all + rows, total);
+            if ((rc = check_launch("batch walk rows"))) goto fail;
+            if ((rc = check_cuda(cudaMemcpyAsync(dmats, hmats.data(), sizeof(MatWalk) * nmat,
+                                                 cudaMemcpyHostToDevice, s),
+                                 "copy")))
+                goto fail;
+            if ((rc = build_chunk_rows(ctx, (int32_t)rows, wbase_all, chunk_row))) goto fail;
+            wb.mats = dmats;
+            wb.wmat = wmat_all;
+            wb.wrow = wrow_all;
+            wb.wbase = wbase_all;
+            wb.chunk_row = chunk_row;
+        }
+    }
+    // walks of all matrices
+    {
+        const bool keep_rec = ctx->opt.keep_records && nmat == 1;
+        rec = alloc_n<int2>(keep_rec ? mbs[0].F->pool : scratch, wb.total);
+        d_hops = alloc_n<unsigned long long>(scratch, nmat);
+        if (!rec || !d_hops) {
+            rc = RW_ERR_ALLOC;
+            goto fail;
+        }
+        WalkLaunch wl;
+        wl.max_steps = ctx->opt.max_steps;
+        wl.record_lengths = ctx->opt.record_lengths;
+        const int64_t launches0 = g_launches;
+        if ((rc = run_walks(ctx, wb, wl, rec, d_hops, scratch, timing ? &ms_walk : nullptr)))
+            goto fail;
+        if ((rc = read_status(ctx, "walks"))) goto fail;  // no merge of stopped walks
+        mbs[0].launches += g_launches - launches0;
+    }
+    {
+        std::vector<unsigned long long> hops(nmat);
+        if ((rc = check_cuda(cudaMemcpy(hops.data(), d_hops, sizeof(unsigned long long) * nmat,
+                                        cudaMemcpyDeviceToHost),
+                             "copy")))
+            goto fail;
+        for (int m = 0; m < nmat; ++m) {
+            MatBuild& mb = mbs[m];
+            if ((rc = finish_factor(ctx, mb, rec + mb.rec_base, nmat == 1, drop_tol, hops[m],
+                                    ms_walk, scratch)))
+                goto fail;
+            mb.F->desc.kernel_launches = mb.launches;
+        }
     }
     scratch.release_all();
     if ((rc = check_cuda(cudaStreamSynchronize(s), "sync"))) goto fail;
-    d.kernel_launches = g_launches - launches0;
-    *out = F;
     return RW_OK;
 fail:
     scratch.release_all();
     cudaStreamSynchronize(s);
-    delete F;
+    for (auto& mb : mbs) {
+        delete mb.F;
+        mb.F = nullptr;
+    }
     return rc;
+}
+
+static rw_status check_build_args(rw_context* ctx, const rw_csr* A, double drop_tol) {
+    if (!ctx) {
+        set_error("factor build: NULL context");
+        return RW_ERR_ARG;
+    }
+    rw_status rc = check_csr(A);
+    if (rc) return rc;
+    if (!(drop_tol >= 0.0) || !(drop_tol < 1e300)) {
+        set_error("drop_tol must be finite and >= 0");
+        return RW_ERR_ARG;
+    }
+    return RW_OK;
+}
+
+static rw_status build_factor_impl(rw_context* ctx, const rw_csr* A, uint32_t uniform,
+                                   const uint32_t* d_budget, uint64_t seed, double drop_tol,
+                                   rw_factor** out) {
+    if (!out) {
+        set_error("rw_build_factor: NULL output");
+        return RW_ERR_ARG;
+    }
+    *out = nullptr;
+    rw_status rc = check_build_args(ctx, A, drop_tol);
+    if (rc) return rc;
+    if (!d_budget && uniform < 1) {
+        set_error("walks_per_row must be >= 1");
+        return RW_ERR_ARG;
+    }
+    std::vector<MatBuild> mbs(1);
+    mbs[0].A = A;
+    mbs[0].budget = d_budget;
+    mbs[0].seed = seed;
+    mbs[0].matrix_index = 0;
+    if ((rc = build_factors(ctx, mbs, uniform, drop_tol))) return rc;
+    *out = mbs[0].F;
+    return RW_OK;
 }
 
 rw_status rw_build_factor(rw_context* ctx, const rw_csr* A, uint32_t walks_per_row, uint64_t seed,
@@ -411,6 +533,34 @@ rw_status rw_build_factor_budget(rw_context* ctx, const rw_csr* A, const uint32_
         return RW_ERR_ARG;
     }
     return build_factor_impl(ctx, A, 0u, d_budget, seed, drop_tol, out);
+}
+
+rw_status rw_build_factor_batched(rw_context* ctx, int32_t nmat, const rw_csr* As,
+                                  const uint32_t* const* d_budgets, uint32_t walks_per_row,
+                                  const uint64_t* seeds, double drop_tol, rw_factor** outs) {
+    if (!ctx || nmat < 1 || !As || !seeds || !outs) {
+        set_error("rw_build_factor_batched: bad arguments");
+        return RW_ERR_ARG;
+    }
+    for (int32_t m = 0; m < nmat; ++m) outs[m] = nullptr;
+    std::vector<MatBuild> mbs(nmat);
+    for (int32_t m = 0; m < nmat; ++m) {
+        rw_status rc = check_build_args(ctx, &As[m], drop_tol);
+        if (rc) return rc;
+        const uint32_t* bud = d_budgets ? d_budgets[m] : nullptr;
+        if (!bud && walks_per_row < 1) {
+            set_error("walks_per_row must be >= 1 for matrices without a budget");
+            return RW_ERR_ARG;
+        }
+        mbs[m].A = &As[m];
+        mbs[m].budget = bud;
+        mbs[m].seed = seeds[m];
+        mbs[m].matrix_index = (uint32_t)m;
+    }
+    rw_status rc = build_factors(ctx, mbs, walks_per_row, drop_tol);
+    if (rc) return rc;
+    for (int32_t m = 0; m < nmat; ++m) outs[m] = mbs[m].F;
+    return RW_OK;
 }
 
 rw_status rw_factor_view(const rw_factor* F, rw_factor_desc* desc) {
@@ -473,6 +623,29 @@ rw_status pcg_solve(rw_context* ctx, const rw_csr* A, const rw_factor* F, const 
     rc = pcg_run(ctx, A, view_of(F), d_b, d_x, nrhs, tol, max_iter, prec, stats, h_iters, h_relres);
     if (stats) stats->kernel_launches = g_launches - launches0;
     return rc;
+}
+
+rw_status pcg_solve_batched(rw_context* ctx, int32_t nmat, const rw_csr* As,
+                            const rw_factor* const* Fs, const double* const* d_b,
+                            double* const* d_x, int32_t nrhs, double tol, int32_t max_iter,
+                            rw_precision prec, rw_pcg_stats* stats, int32_t* h_iters,
+                            double* h_relres) {
+    if (!ctx || nmat < 1 || !As || !Fs || !d_b || !d_x) {
+        set_error("pcg_solve_batched: bad arguments");
+        return RW_ERR_ARG;
+    }
+    rw_status worst = RW_OK;
+    for (int32_t m = 0; m < nmat; ++m) {
+        rw_pcg_stats st{};
+        rw_status rc = pcg_solve(ctx, &As[m], Fs[m], d_b[m], d_x[m], nrhs, tol, max_iter, prec, &st,
+                                 h_iters ? h_iters + (size_t)m * nrhs : nullptr,
+                                 h_relres ? h_relres + (size_t)m * nrhs : nullptr);
+        if (stats) stats[m] = st;
+        if (rc != RW_OK && rc != RW_ERR_NO_CONVERGENCE) return rc;
+        if (rc == RW_ERR_NO_CONVERGENCE) worst = rc;
+    }
+    if (worst) set_error("pcg_solve_batched: some right-hand sides did not converge");
+    return worst;
 }
 
 rw_status rw_precond_apply(rw_context* ctx, const rw_factor* F, const double* d_r, double* d_z,

@@ -109,17 +109,42 @@ constexpr int kWalkChunk = 32;
 
 rw_status build_walk_space(rw_context* ctx, const Tables& T, uint32_t uniform,
                            const uint32_t* d_budget, WalkSpace& ws, Pool& pool);
+// chunk_row[c] = the walk row holding walk c * kWalkChunk (wbase: [nw+1]).
+rw_status build_chunk_rows(rw_context* ctx, int32_t nw, const int64_t* wbase, int32_t* chunk_row);
 
 struct WalkLaunch {
-    uint64_t seed = 0;
-    uint32_t matrix_index = 0;
-    uint32_t tag = 0;
     uint64_t max_steps = 1ull << 24;
     int record_lengths = 0;
 };
 
-rw_status run_walks(rw_context* ctx, const Tables& T, const WalkSpace& ws, const WalkLaunch& wl,
-                    int2* rec, unsigned long long* d_hops, Pool& pool, float* ms);
+// Tables, key and tag of one matrix as the walk kernel reads them.  The tag
+// is (matrix_index << 2) | kind (kind 0: factor walks, 1: pilot walks).
+struct MatWalk {
+    const uint32_t* thr;
+    const uint2* nxt;
+    const uint32_t* fthr;
+    uint32_t key0, key1, tag, pad;
+};
+
+// The walk index space of one launch (one matrix, or several concatenated).
+struct WalkBatch {
+    int nmat = 1;
+    MatWalk m0{};                  // the single matrix (nmat == 1)
+    const MatWalk* mats = nullptr; // [nmat] device (nmat > 1)
+    const int32_t* wmat = nullptr; // [walk rows] matrix of each walk row (nmat > 1)
+    const int4* wrow = nullptr;
+    const int64_t* wbase = nullptr;
+    const int32_t* chunk_row = nullptr;
+    int64_t total = 0;
+};
+
+inline MatWalk mat_walk(const Tables& T, uint64_t seed, uint32_t matrix_index, uint32_t kind) {
+    return MatWalk{T.thr, T.nxt, T.fthr, (uint32_t)seed, (uint32_t)(seed >> 32),
+                   (matrix_index << 2) | (kind & 3u), 0u};
+}
+
+rw_status run_walks(rw_context* ctx, const WalkBatch& wb, const WalkLaunch& wl, int2* rec,
+                    unsigned long long* d_hops, Pool& pool, float* ms);
 
 // Merge + emission: per-walk records -> Y (CSR), D, counters.
 struct FactorOut {

@@ -305,6 +305,13 @@ __global__ void k_chunk_rows(int32_t nw, const int64_t* __restrict__ wbase, int3
     }
 }
 
+rw_status build_chunk_rows(rw_context* ctx, int32_t nw, const int64_t* wbase, int32_t* chunk_row) {
+    if (nw <= 0) return RW_OK;
+    RW_COUNT_LAUNCH();
+    k_chunk_rows<<<grid_for(nw, 256, ctx->num_sms * 8), 256, 0, ctx->stream>>>(nw, wbase, chunk_row);
+    return check_launch("chunk rows");
+}
+
 rw_status build_walk_space(rw_context* ctx, const Tables& T, uint32_t uniform,
                            const uint32_t* d_budget, WalkSpace& ws, Pool& pool) {
     cudaStream_t s = ctx->stream;

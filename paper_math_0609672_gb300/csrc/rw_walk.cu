@@ -22,9 +22,8 @@
 namespace rw {
 
 struct WalkParams {
-    const uint32_t* __restrict__ thr;
-    const uint2* __restrict__ nxt;
-    const uint32_t* __restrict__ fthr;
+    const MatWalk* __restrict__ mats;   // per matrix: tables, key, tag
+    const int32_t* __restrict__ wmat;   // matrix of each walk row (batched launches)
     const int4* __restrict__ wrow;
     const int64_t* __restrict__ wbase;
     const int32_t* __restrict__ chunk_row;
@@ -33,9 +32,9 @@ struct WalkParams {
     int2* rec;
     unsigned long long* hops;
     DevStatus* st;
-    uint32_t key0, key1, tag;
     uint64_t max_steps;
     int record_lengths;
+    MatWalk m0;                         // the matrix of a single-matrix launch
 };
 
 // Number of thresholds t <= u among the 8 words of a block (padding words are
@@ -50,6 +49,7 @@ __device__ __forceinline__ uint4 ld_nc4(const uint32_t* p) {
     return __ldg(reinterpret_cast<const uint4*>(p));
 }
 
+template <bool MULTI>
 __global__ void __launch_bounds__(256) k_walk(const WalkParams P) {
     const unsigned lane = lane_id();
     const unsigned lt = lanemask_lt();
@@ -61,9 +61,14 @@ __global__ void __launch_bounds__(256) k_walk(const WalkParams P) {
     bool active = false;
     int64_t widx = 0;
     uint32_t k = 0, w = 0, coff = 0, ret = 0;
+    // the walking lane's matrix (fixed for a single-matrix launch)
+    const uint32_t* thr = P.m0.thr;
+    const uint2* nxt = P.m0.nxt;
+    uint32_t key0 = P.m0.key0, key1 = P.m0.key1, tag = P.m0.tag;
     uint64_t h = 0;
     Philox4 rnd{0u, 0u, 0u, 0u};
     unsigned long long my_hops = 0;
+    int32_t my_m = 0;  // matrix whose hops my_hops holds
 
     for (;;) {
         // ---- refill idle lanes from the warp's pool of walk indices ----
@@ -92,12 +97,28 @@ __global__ void __launch_bounds__(256) k_walk(const WalkParams P) {
                 widx = pool_next + rank;
                 while (P.wbase[r + 1] <= widx) ++r;
                 const int4 info = P.wrow[r];
+                const uint32_t* fthr = P.m0.fthr;
+                if (MULTI) {
+                    const int32_t m = P.wmat[r];
+                    if (m != my_m) {
+                        if (my_hops) atomicAdd(P.hops + my_m, my_hops);
+                        my_hops = 0;
+                        my_m = m;
+                    }
+                    const MatWalk& mw = P.mats[m];
+                    thr = mw.thr;
+                    nxt = mw.nxt;
+                    fthr = mw.fthr;
+                    key0 = mw.key0;
+                    key1 = mw.key1;
+                    tag = mw.tag;
+                }
                 k = (uint32_t)info.x;
                 w = (uint32_t)(widx - P.wbase[r]);
-                rnd = philox4x32_10(0u, w, k, P.tag, P.key0, P.key1);
+                rnd = philox4x32_10(0u, w, k, tag, key0, key1);
                 const uint32_t u = rnd.v0;
                 // first step: least m with u < ft_m among the upper neighbours, else the last
-                const uint32_t* fb = P.fthr + (size_t)info.y * 8u;
+                const uint32_t* fb = fthr + (size_t)info.y * 8u;
                 const uint4 a = ld_nc4(fb), b = ld_nc4(fb + 4);
                 const uint32_t up = a.x;
                 uint32_t m = (uint32_t)(a.z <= u) + (uint32_t)(a.w <= u) + (uint32_t)(b.x <= u) +
@@ -111,7 +132,7 @@ __global__ void __launch_bounds__(256) k_walk(const WalkParams P) {
                     }
                 }
                 if (m > up - 1u) m = up - 1u;
-                const uint2 e = __ldg(P.nxt + (size_t)info.z * 8u + 1u + (uint32_t)info.w + m);
+                const uint2 e = __ldg(nxt + (size_t)info.z * 8u + 1u + (uint32_t)info.w + m);
                 coff = e.y;
                 h = 1;
                 ret = 0;
@@ -136,11 +157,11 @@ __global__ void __launch_bounds__(256) k_walk(const WalkParams P) {
                 if (h >= P.max_steps) atomicAdd(&P.st->walk_cap, 1u);
             } else {
                 const uint32_t sidx = (uint32_t)h;
-                if ((sidx & 3u) == 0u) rnd = philox4x32_10(sidx >> 2, w, k, P.tag, P.key0, P.key1);
+                if ((sidx & 3u) == 0u) rnd = philox4x32_10(sidx >> 2, w, k, tag, key0, key1);
                 const uint32_t q = sidx & 3u;
                 const uint32_t u = q == 0u ? rnd.v0 : q == 1u ? rnd.v1 : q == 2u ? rnd.v2 : rnd.v3;
                 ++h;
-                const uint32_t* blk = P.thr + (size_t)coff * 8u;
+                const uint32_t* blk = thr + (size_t)coff * 8u;
                 const uint4 a = ld_nc4(blk), b = ld_nc4(blk + 4);
                 const uint32_t deg = a.x;
                 uint32_t m = (uint32_t)(a.y <= u) + (uint32_t)(a.z <= u) + (uint32_t)(a.w <= u) +
@@ -158,7 +179,7 @@ __global__ void __launch_bounds__(256) k_walk(const WalkParams P) {
                     end = -1;  // ground
                     done = true;
                 } else {
-                    const uint2 e = __ldg(P.nxt + (size_t)coff * 8u + 1u + m);
+                    const uint2 e = __ldg(nxt + (size_t)coff * 8u + 1u + m);
                     if (e.x < k) {
                         end = (int32_t)e.x;  // home
                         done = true;
@@ -175,54 +196,59 @@ __global__ void __launch_bounds__(256) k_walk(const WalkParams P) {
             }
         }
     }
-    my_hops = warp_sum(my_hops);
-    if (lane == 0 && my_hops) atomicAdd(P.hops, my_hops);
+    if (MULTI) {
+        if (my_hops) atomicAdd(P.hops + my_m, my_hops);
+    } else {
+        my_hops = warp_sum(my_hops);
+        if (lane == 0 && my_hops) atomicAdd(P.hops, my_hops);
+    }
 }
 
-rw_status run_walks(rw_context* ctx, const Tables& T, const WalkSpace& ws, const WalkLaunch& wl,
-                    int2* rec, unsigned long long* d_hops, Pool& pool, float* ms) {
+rw_status run_walks(rw_context* ctx, const WalkBatch& wb, const WalkLaunch& wl, int2* rec,
+                    unsigned long long* d_hops, Pool& pool, float* ms) {
     cudaStream_t s = ctx->stream;
     unsigned long long* cursor = alloc_n<unsigned long long>(pool, 1);
     if (!cursor) return RW_ERR_ALLOC;
     rw_status rc;
     if ((rc = check_cuda(cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), s), "memset")))
         return rc;
-    if ((rc = check_cuda(cudaMemsetAsync(d_hops, 0, sizeof(unsigned long long), s), "memset")))
+    if ((rc = check_cuda(cudaMemsetAsync(d_hops, 0, sizeof(unsigned long long) * wb.nmat, s),
+                         "memset")))
         return rc;
-    if (ws.total == 0) {
+    if (wb.total == 0) {
         if (ms) *ms = 0.f;
         return RW_OK;
     }
-    WalkParams P;
-    P.thr = T.thr;
-    P.nxt = T.nxt;
-    P.fthr = T.fthr;
-    P.wrow = T.wrow;
-    P.wbase = ws.wbase;
-    P.chunk_row = ws.chunk_row;
-    P.total = ws.total;
+    const bool multi = wb.nmat > 1;
+    WalkParams P{};
+    P.mats = wb.mats;
+    P.wmat = wb.wmat;
+    P.wrow = wb.wrow;
+    P.wbase = wb.wbase;
+    P.chunk_row = wb.chunk_row;
+    P.total = wb.total;
     P.cursor = cursor;
     P.rec = rec;
     P.hops = d_hops;
     P.st = ctx->d_status;
-    P.key0 = (uint32_t)wl.seed;
-    P.key1 = (uint32_t)(wl.seed >> 32);
-    P.tag = (wl.matrix_index << 2) | (wl.tag & 3u);
     P.max_steps = wl.max_steps;
     P.record_lengths = wl.record_lengths;
+    P.m0 = wb.m0;
     int per_sm = ctx->opt.walk_blocks_per_sm;
     if (per_sm <= 0) {
-        if ((rc = check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk, 256, 0),
+        if ((rc = check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                 &per_sm, multi ? k_walk<true> : k_walk<false>, 256, 0),
                              "occupancy")))
             return rc;
         if (per_sm < 1) per_sm = 1;
     }
     int64_t blocks = (int64_t)per_sm * ctx->num_sms;
-    const int64_t need = (ws.total + 255) / 256;  // never more lanes than walks
+    const int64_t need = (wb.total + 255) / 256;  // never more lanes than walks
     if (blocks > need) blocks = need;
     if (ms) cudaEventRecord(ctx->ev[0], s);
     RW_COUNT_LAUNCH();
-    k_walk<<<(unsigned)blocks, 256, 0, s>>>(P);
+    if (multi) k_walk<true><<<(unsigned)blocks, 256, 0, s>>>(P);
+    else k_walk<false><<<(unsigned)blocks, 256, 0, s>>>(P);
     if ((rc = check_launch("walk kernel"))) return rc;
     if (ms) {
         cudaEventRecord(ctx->ev[1], s);

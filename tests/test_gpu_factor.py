@@ -236,3 +236,25 @@ def test_torch_allocator_context(P):
     ref = oracle.build_factor(A, 20, 4, 1e-3)
     assert np.array_equal(t["y_val"], ref["val"]) and np.array_equal(t["d"], ref["D"])
     c.close()
+
+
+def test_batched_build_matches_per_matrix_oracle(P, ctx):
+    """One walk launch over several matrices of uneven size and family; matrix
+    m draws with matrix index m and must equal the oracle with that index."""
+    import torch
+    rng = np.random.default_rng(31)
+    mats = [W.rgg(int(n), rng) for n in (300, 1700, 40, 5000)]
+    mats.append(W.make_config(2, scale=0.2)["A"])
+    mats.append(W.tridiag(2))
+    seeds = [int(x) for x in rng.integers(0, 2**62, size=len(mats))]
+    dAs = [P.CSR.from_host(A) for A in mats]
+    budgets = [None] * len(mats)
+    budgets[1] = torch.as_tensor(rng.integers(1, 60, size=mats[1].n).astype(np.int32)).cuda()
+    Fs = P.rw_build_factor_batched(ctx, dAs, 37, seeds, 1e-3, budgets=budgets)
+    for m, (A, F) in enumerate(zip(mats, Fs)):
+        t = {k: v.cpu().numpy() for k, v in F.tensors().items()}
+        t["total_hops"] = int(F.desc.total_hops)
+        walks = np.asarray(budgets[m].cpu().numpy(), np.uint32) if budgets[m] is not None else 37
+        ref = oracle.build_factor(A, walks, seeds[m], 1e-3, matrix_index=m)
+        assert_factor_equal(t, ref, records=False)
+        F.destroy()

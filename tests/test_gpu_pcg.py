@@ -159,3 +159,26 @@ def test_pcg_reports_no_convergence(P, ctx):
     rc, st, its, rel = P.pcg_solve(ctx, dA, F, _dev(b), x, 1e-14, 2)
     assert rc == -5 and its[0] == 2 and rel[0] > 1e-14
     F.destroy()
+
+
+def test_batched_pcg_matches_single(P, ctx):
+    """Batched factor build + batched PCG on matrices of uneven size: each
+    solution equals the oracle PCG on the oracle factor with that matrix index."""
+    rng = np.random.default_rng(9)
+    mats = [W.rgg(int(n), rng) for n in (500, 2500, 1200)]
+    seeds = [11, 22, 33]
+    dAs = [P.CSR.from_host(A) for A in mats]
+    Fs = P.rw_build_factor_batched(ctx, dAs, 60, seeds, 1e-3)
+    bs = [rng.standard_normal((A.n, 3)) for A in mats]
+    xs = [_dev(np.zeros_like(b)) for b in bs]
+    rc, st, its, rel = P.pcg_solve_batched(ctx, dAs, Fs, [_dev(b) for b in bs], xs, 1e-8, 500)
+    assert rc == 0 and np.all(rel < 1e-8)
+    for m, A in enumerate(mats):
+        ref = oracle.build_factor(A, 60, seeds[m], 1e-3, matrix_index=m)
+        xg = xs[m].cpu().numpy()
+        for j in range(3):
+            xr, itr, rr, _ = oracle.pcg(A, ref, bs[m][:, j], 1e-8, 500)
+            assert its[m, j] == itr
+            assert np.linalg.norm(xg[:, j] - xr) / np.linalg.norm(xr) < 1e-10
+    for F in Fs:
+        F.destroy()
