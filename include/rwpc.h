@@ -228,6 +228,96 @@ rw_status rw_precond_apply_static(rw_context* ctx, const rw_factor* F, const dou
 /* y = A x for nrhs node-major vectors (FP64). */
 rw_status rw_spmv(rw_context* ctx, const rw_csr* A, const double* d_x, double* d_y, int32_t nrhs);
 
+/* ---- Learned walk budget ------------------------------------------------
+ * Sec. 5.1 chooses M_k per row so that the mean walk length Xi'_k of the M_k
+ * walks from row k is within a relative margin Delta of its expectation at
+ * confidence alpha (Eq. lengthdelta), i.e. M*_k = (z_alpha sigma_k /
+ * (Delta Xi'_k))^2, with a lower bound on M_k.  Here a small network predicts
+ * log((sigma_k / Xi'_k)^2) from per-row graph features (trained on pilot-walk
+ * statistics), and the normaliser turns the predicted relative needs into
+ * integer budgets with a requested mean and minimum, i.e. it fixes
+ * (z_alpha / Delta)^2 from the walk count one is willing to spend.          */
+
+#define RW_NUM_FEATURES 12
+#define RW_FEATURE_STRIDE 16   /* floats per feature row; entries 12..15 are 0 */
+#define RW_MLP_PARAMS 5313     /* 64*16 + 64 + 64*64 + 64 + 64 + 1 */
+
+typedef struct rw_mlp rw_mlp;
+
+/* Per-row graph features into d_feat [n][RW_FEATURE_STRIDE] (FP32, computed
+ * in FP64): 0 log(1+degree), 1 upper/degree, 2 lower/degree, 3 excess/A_kk,
+ * 4 -S_k/A_kk (S_k: sum of the row's upper entries), 5 entropy of the
+ * transition probabilities -A_kj/(sum of the row's off-diagonal weights),
+ * 6 largest weight / weight sum, 7 k/(n-1), 8 mean over neighbours c of
+ * (row sum of c)/A_cc, 9 log(1 + mean neighbour degree), 10 log(1 + sum over
+ * upper neighbours c of the entries of row c with column > k), 11 log A_kk.
+ * A must be an R-matrix in rw_csr form (not re-validated here). */
+rw_status rw_row_features(rw_context* ctx, const rw_csr* A, float* d_feat);
+
+/* Pilot walks: pilot_walks (>= 2) walks from every walk row under the walk
+ * kind 1 (Philox counter word 3 = 1; rw_build_factor uses kind 0), and per row
+ * the mean Xi'_k and sample standard deviation sigma_k of the walk lengths
+ * (hops), the label log((sigma_k/Xi'_k)^2 + 1e-6) and has_k = 1 (rows without
+ * walks: all four 0).  Outputs are device arrays [n].  Errors as for
+ * rw_build_factor (RW_ERR_NOT_RMATRIX, RW_ERR_WALK_CAP, ...). */
+rw_status rw_pilot_stats(rw_context* ctx, const rw_csr* A, uint32_t pilot_walks, uint64_t seed,
+                         float* d_mean, float* d_sd, float* d_label, float* d_has);
+
+/* The network 12 -> 64 -> 64 -> 1 (ReLU): x = bf16((f - mu) * inv_sd),
+ * h1 = bf16(relu(W1 x + b1)), h2 = relu(W2 h1 + b2), y = w3.h2 + b3; W1 and W2
+ * are used in BF16 with FP32 accumulation (tensor cores), the master copy is
+ * FP32.  Parameter vector layout (RW_MLP_PARAMS floats): W1 [64][16]
+ * (output-major; columns 12..15 ignored), b1 [64], W2 [64][64] (output-major),
+ * b2 [64], w3 [64], b3.  Standardisation vector (32 floats): mu [16],
+ * inv_sd [16].  rw_mlp_create draws He-uniform weights from seed (zero biases,
+ * mu = 0, inv_sd = 1).  The model lives on the context's device; destroy it
+ * before the context. */
+rw_status rw_mlp_create(rw_context* ctx, uint64_t seed, rw_mlp** out);
+void rw_mlp_destroy(rw_mlp* M);
+/* Host copies: h_params/h_norm receive the current values (if not NULL),
+ * after h_set_params/h_set_norm (if not NULL) were installed; setting the
+ * parameters resets the Adam state. */
+rw_status rw_mlp_params(rw_mlp* M, float* h_params, float* h_norm, const float* h_set_params,
+                        const float* h_set_norm);
+/* d_out[r] = y of feature row r, r < nrows (d_feat as rw_row_features). */
+rw_status rw_mlp_predict(rw_context* ctx, const rw_mlp* M, const float* d_feat, int64_t nrows,
+                         float* d_out);
+/* Gradient (h_grad [RW_MLP_PARAMS], host) of the loss (1/B) sum_r (y_r -
+ * label_r)^2 over the B = nrows feature rows listed in d_rows (device uint32
+ * indices into d_feat/d_label), and the loss (h_loss, optional).  The backward
+ * pass rounds dL/dh2 to BF16 for the product with W2 (tensor cores); weight
+ * gradients accumulate in FP32 in a fixed order (deterministic). */
+rw_status rw_mlp_gradient(rw_context* ctx, rw_mlp* M, const float* d_feat, const float* d_label,
+                          const uint32_t* d_rows, int64_t nrows, float* h_grad, float* h_loss);
+/* Adam training (beta 0.9/0.999, eps 1e-8, learning rate lr) on the rows with
+ * d_mask[r] > 0, for `epochs` passes of floor(rows/batch) mini-batches in a
+ * seeded shuffled order.  set_norm != 0 first sets mu/inv_sd to the masked
+ * rows' feature means and inverse standard deviations.  h_epoch_loss
+ * (optional, [epochs]) receives each epoch's mean squared error. */
+rw_status rw_mlp_train(rw_context* ctx, rw_mlp* M, const float* d_feat, const float* d_label,
+                       const float* d_mask, int64_t nrows, int32_t epochs, int32_t batch, float lr,
+                       uint64_t seed, int32_t set_norm, float* h_epoch_loss);
+
+/* Integer walk budgets from relative needs w_k >= 0 (device [n]): over the
+ * walk rows (rows with an upper neighbour; the others get 0), with
+ * T = floor(mean_budget * walk_rows + 1/2):
+ *   quota q_k(s) = min(min(T, 2^31), max(min_budget, s w_k)),
+ *   V_k = round-half-even(q_k 2^20) (fixed point), s found by a fixed doubling
+ *   and bisection search for the largest sum_k V_k(s) not above T 2^20;
+ *   budget_k = floor(V_k 2^-20) + R / walk_rows + [rank_k < R mod walk_rows],
+ *   R = T - sum floor, ranks by fractional part descending then k ascending
+ *   (largest-remainder apportionment).
+ * The budgets sum to T exactly and each is at least min_budget.  Every step is
+ * exact arithmetic, so the result is reproducible bit for bit.  Errors:
+ * RW_ERR_ARG for min_budget < 1, mean_budget < min_budget or > 2^31, T > 2^40,
+ * or a negative, infinite or NaN weight on a walk row. */
+rw_status rw_budget_normalize(rw_context* ctx, const rw_csr* A, const float* d_weight,
+                              double mean_budget, uint32_t min_budget, uint32_t* d_budget);
+/* Features -> network -> w_k = exp(y_k) (FP32, y clamped to [-60, 60]) ->
+ * rw_budget_normalize.  d_budget [n] feeds rw_build_factor_budget. */
+rw_status rw_budget_predict(rw_context* ctx, const rw_csr* A, const rw_mlp* M, double mean_budget,
+                            uint32_t min_budget, uint32_t* d_budget);
+
 const char* rw_status_string(rw_status s);
 const char* rw_last_error(void);
 

@@ -29,7 +29,14 @@ __all__ = [
     "rw_factor_destroy", "pcg_solve", "rw_precond_apply", "rw_precond_apply_static", "rw_spmv",
     "rw_status_string",
     "rw_last_error", "RW_FP64", "RW_FP32_MIXED",
+    "Mlp", "rw_row_features", "rw_pilot_stats", "rw_mlp_create", "rw_mlp_predict",
+    "rw_mlp_gradient", "rw_mlp_train", "rw_budget_normalize", "rw_budget_predict",
+    "RW_NUM_FEATURES", "RW_FEATURE_STRIDE", "RW_MLP_PARAMS",
 ]
+
+RW_NUM_FEATURES = 12
+RW_FEATURE_STRIDE = 16
+RW_MLP_PARAMS = 5313
 
 RW_FP64 = 0
 RW_FP32_MIXED = 1
@@ -128,6 +135,23 @@ def load():
     lib.rw_status_string.restype = ctypes.c_char_p
     lib.rw_last_error.argtypes = []
     lib.rw_last_error.restype = ctypes.c_char_p
+    vp = _c_void_p
+    sigs = {
+        "rw_row_features": [vp, P(rw_csr_t), vp],
+        "rw_pilot_stats": [vp, P(rw_csr_t), _u32, _u64, vp, vp, vp, vp],
+        "rw_mlp_create": [vp, _u64, P(vp)],
+        "rw_mlp_params": [vp, vp, vp, vp, vp],
+        "rw_mlp_predict": [vp, vp, vp, ctypes.c_int64, vp],
+        "rw_mlp_gradient": [vp, vp, vp, vp, vp, ctypes.c_int64, vp, vp],
+        "rw_mlp_train": [vp, vp, vp, vp, vp, ctypes.c_int64, _i32, _i32, ctypes.c_float, _u64, _i32, vp],
+        "rw_budget_normalize": [vp, P(rw_csr_t), vp, _f64, _u32, vp],
+        "rw_budget_predict": [vp, P(rw_csr_t), vp, _f64, _u32, vp],
+    }
+    for name, args in sigs.items():
+        getattr(lib, name).argtypes = args
+        getattr(lib, name).restype = ctypes.c_int
+    lib.rw_mlp_destroy.argtypes = [vp]
+    lib.rw_mlp_destroy.restype = None
     _lib = lib
     return lib
 
@@ -217,6 +241,7 @@ class Context:
         self.options = options or rw_options_default()
         self._keep = []
         self._factors = weakref.WeakSet()  # factors free through the context: close them first
+        self._mlps = weakref.WeakSet()
         if torch_allocator:
             dev = torch.cuda.current_device()
 
@@ -242,6 +267,8 @@ class Context:
         if self.handle:
             for f in list(self._factors):
                 f.destroy()
+            for m in list(self._mlps):
+                m.destroy()
             load().rw_context_destroy(self.handle)
             self.handle = None
 
@@ -413,3 +440,117 @@ def rw_spmv(ctx, A, x, y):
     nrhs = 1 if x.dim() == 1 else x.shape[1]
     _check(load().rw_spmv(ctx.handle, ctypes.byref(A.c), _c_void_p(x.data_ptr()),
                           _c_void_p(y.data_ptr()), nrhs), "rw_spmv")
+
+
+# ---------------------------------------------------------------------------
+# Learned walk budget
+# ---------------------------------------------------------------------------
+
+def _ptr(t):
+    return _c_void_p(t.data_ptr())
+
+
+class Mlp:
+    """Handle to the budget network (12 -> 64 -> 64 -> 1) on the context's device."""
+
+    def __init__(self, ctx, seed=0):
+        self.ctx = ctx
+        h = _c_void_p()
+        _check(load().rw_mlp_create(ctx.handle, int(seed), ctypes.byref(h)), "rw_mlp_create")
+        self.handle = h
+        ctx._mlps.add(self)
+
+    def params(self):
+        """(parameter vector, standardisation vector) as numpy float32 arrays."""
+        import numpy as np
+        p = np.zeros(RW_MLP_PARAMS, np.float32)
+        nrm = np.zeros(2 * RW_FEATURE_STRIDE, np.float32)
+        _check(load().rw_mlp_params(self.handle, p.ctypes.data_as(_c_void_p),
+                                    nrm.ctypes.data_as(_c_void_p), None, None), "rw_mlp_params")
+        return p, nrm
+
+    def set_params(self, params=None, norm=None):
+        import numpy as np
+        p = None if params is None else np.ascontiguousarray(params, np.float32)
+        nrm = None if norm is None else np.ascontiguousarray(norm, np.float32)
+        assert p is None or p.size == RW_MLP_PARAMS
+        assert nrm is None or nrm.size == 2 * RW_FEATURE_STRIDE
+        _check(load().rw_mlp_params(self.handle, None, None,
+                                    None if p is None else p.ctypes.data_as(_c_void_p),
+                                    None if nrm is None else nrm.ctypes.data_as(_c_void_p)),
+               "rw_mlp_params")
+
+    def save(self, path):
+        import numpy as np
+        p, nrm = self.params()
+        np.savez(path, params=p, norm=nrm)
+
+    def load_file(self, path):
+        import numpy as np
+        z = np.load(path)
+        self.set_params(z["params"], z["norm"])
+
+    def destroy(self):
+        if self.handle and self.ctx.handle:
+            load().rw_mlp_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def rw_mlp_create(ctx, seed=0):
+    return Mlp(ctx, seed)
+
+
+def rw_row_features(ctx, A, feat):
+    """feat: CUDA float32 tensor [n, RW_FEATURE_STRIDE]."""
+    _check(load().rw_row_features(ctx.handle, ctypes.byref(A.c), _ptr(feat)), "rw_row_features")
+
+
+def rw_pilot_stats(ctx, A, pilot_walks, seed, mean, sd, label, has):
+    """mean, sd, label, has: CUDA float32 tensors [n]."""
+    _check(load().rw_pilot_stats(ctx.handle, ctypes.byref(A.c), int(pilot_walks), int(seed),
+                                 _ptr(mean), _ptr(sd), _ptr(label), _ptr(has)), "rw_pilot_stats")
+
+
+def rw_mlp_predict(ctx, M, feat, out):
+    _check(load().rw_mlp_predict(ctx.handle, M.handle, _ptr(feat), int(out.numel()), _ptr(out)),
+           "rw_mlp_predict")
+
+
+def rw_mlp_gradient(ctx, M, feat, label, rows):
+    """Gradient (numpy float32 [RW_MLP_PARAMS]) and mean squared error over the
+    rows listed in the CUDA int32/uint32 tensor `rows`."""
+    import numpy as np
+    g = np.zeros(RW_MLP_PARAMS, np.float32)
+    loss = ctypes.c_float()
+    _check(load().rw_mlp_gradient(ctx.handle, M.handle, _ptr(feat), _ptr(label), _ptr(rows),
+                                  int(rows.numel()), g.ctypes.data_as(_c_void_p), ctypes.byref(loss)),
+           "rw_mlp_gradient")
+    return g, loss.value
+
+
+def rw_mlp_train(ctx, M, feat, label, mask, epochs, batch, lr, seed=0, set_norm=True):
+    """Adam training on the rows with mask > 0.  Returns the per-epoch mean
+    squared error (numpy float32 [epochs])."""
+    import numpy as np
+    losses = np.zeros(max(1, epochs), np.float32)
+    _check(load().rw_mlp_train(ctx.handle, M.handle, _ptr(feat), _ptr(label), _ptr(mask),
+                               int(label.numel()), int(epochs), int(batch), float(lr), int(seed),
+                               1 if set_norm else 0, losses.ctypes.data_as(_c_void_p)), "rw_mlp_train")
+    return losses[:epochs]
+
+
+def rw_budget_normalize(ctx, A, weight, mean_budget, min_budget, budget):
+    """weight: CUDA float32 [n]; budget: CUDA int32/uint32 [n] (output)."""
+    _check(load().rw_budget_normalize(ctx.handle, ctypes.byref(A.c), _ptr(weight), float(mean_budget),
+                                      int(min_budget), _ptr(budget)), "rw_budget_normalize")
+
+
+def rw_budget_predict(ctx, A, M, mean_budget, min_budget, budget):
+    _check(load().rw_budget_predict(ctx.handle, ctypes.byref(A.c), M.handle, float(mean_budget),
+                                    int(min_budget), _ptr(budget)), "rw_budget_predict")

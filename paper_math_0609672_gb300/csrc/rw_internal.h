@@ -26,6 +26,10 @@ struct rw_context {
 
 namespace rw {
 
+constexpr int kFeatures = RW_NUM_FEATURES;
+constexpr int kFeatStride = RW_FEATURE_STRIDE;
+constexpr int kMlpParams = RW_MLP_PARAMS;
+
 void set_error(const char* fmt, ...);
 
 // Kernels launched by the calling thread (reported per call in the factor
