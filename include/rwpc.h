@@ -55,7 +55,7 @@ typedef enum {
     RW_ERR_BREAKDOWN = -6,      /* PCG found p.Ap <= 0 */
     RW_ERR_CUDA = -7,           /* a CUDA runtime call failed */
     RW_ERR_TIMEOUT = -8,        /* a bounded device-side wait gave up */
-    RW_ERR_CAPACITY = -9        /* a per-row budget exceeds the merge capacity */
+    RW_ERR_CAPACITY = -9        /* a row has more than 2^29 possible end points (merge table limit) */
 } rw_status;
 
 typedef enum { RW_FP64 = 0, RW_FP32_MIXED = 1 } rw_precision;

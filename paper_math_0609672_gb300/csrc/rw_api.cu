@@ -63,7 +63,7 @@ rw_status read_status(rw_context* ctx, const char* what) {
         return RW_ERR_WALK_CAP;
     }
     if (st.capacity) {
-        set_error("%s: %u rows exceed the merge capacity (walks + lower neighbours > 12288)",
+        set_error("%s: %u rows exceed the merge capacity",
                   what, st.capacity);
         return RW_ERR_CAPACITY;
     }
@@ -155,7 +155,7 @@ const char* rw_status_string(rw_status s) {
         case RW_ERR_BREAKDOWN: return "PCG breakdown";
         case RW_ERR_CUDA: return "CUDA error";
         case RW_ERR_TIMEOUT: return "device-side wait timed out";
-        case RW_ERR_CAPACITY: return "per-row budget exceeds the merge capacity";
+        case RW_ERR_CAPACITY: return "a row exceeds the merge capacity";
     }
     return "unknown status";
 }

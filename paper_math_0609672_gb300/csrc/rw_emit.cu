@@ -23,6 +23,9 @@ constexpr int kLog2SmallHash = 10;              // 1024 slots per warp
 constexpr int kSmallCap = 768;                  // distinct keys a warp table accepts
 constexpr int kLog2BigHash = 14;                // 16384 slots per block
 constexpr int kBigCap = 12288;
+// Rows with more possible keys go to a block with a global-memory table of at
+// least twice their bound (the huge path); those tables take at most this much.
+constexpr size_t kHugeTableBytes = size_t(1) << 30;
 
 struct MergeParams {
     const int32_t* __restrict__ rp;
@@ -46,8 +49,26 @@ struct MergeParams {
     uint32_t* G;
     int32_t* big_rows;
     int32_t* n_big;
+    int32_t* huge_rows;
+    int32_t* n_huge;
+    unsigned long long* huge_bound;  // largest key bound of the huge rows
     DevStatus* st;
 };
+
+// Upper bound on the distinct keys of walk row r: its walks' end points and
+// its lower neighbours are all columns below k.
+__device__ __forceinline__ int64_t key_bound(const MergeParams& P, int32_t r) {
+    const int4 info = P.wrow[r];
+    const int64_t m = P.wbase[r + 1] - P.wbase[r];
+    return min(m + (int64_t)info.w, (int64_t)info.x);
+}
+
+// Slots of the global table of a huge row with key bound b: a power of two >= 2b + 2.
+__host__ __device__ __forceinline__ int huge_log2_slots(int64_t b) {
+    int lg = 1;
+    while ((int64_t(1) << lg) < 2 * b + 2) ++lg;
+    return lg;
+}
 
 template <int TEAM>
 __device__ __forceinline__ void team_sync() {
@@ -97,11 +118,12 @@ __device__ __forceinline__ T team_sum(T v, T* sm) {
     return r;
 }
 
-template <int LOG2HC>
+// Table of 2^lg slots; at most half of them ever hold a key (the callers'
+// key bounds), so the probe always finds the key or an empty slot.
 __device__ __forceinline__ void hash_insert(int* keys, uint32_t* vals, int key, uint32_t add,
-                                            bool flag) {
-    constexpr uint32_t mask = (1u << LOG2HC) - 1u;
-    uint32_t h = ((uint32_t)key * 2654435761u) >> (32 - LOG2HC);
+                                            bool flag, int lg) {
+    const uint32_t mask = (1u << lg) - 1u;
+    uint32_t h = ((uint32_t)key * 2654435761u) >> (32 - lg);
     for (;;) {
         const int prev = atomicCAS(&keys[h], -1, key);
         if (prev == -1 || prev == key) {
@@ -139,10 +161,12 @@ __device__ void team_bitonic(int* keys, uint32_t* vals, int P) {
 
 // Merge the records of walk row r and write its kept entries (ascending
 // columns) to the row's slot of the temporary area.
+// LOG2HC > 0: a table of 2^LOG2HC slots; LOG2HC == 0: 2^lg_rt slots.
 template <int TEAM, int LOG2HC>
 __device__ void merge_row(const MergeParams& P, int32_t r, int* keys, uint32_t* vals, int* wsm,
-                          unsigned long long* sm64) {
-    constexpr int HC = 1 << LOG2HC;
+                          unsigned long long* sm64, int lg_rt = 0) {
+    const int lg = LOG2HC > 0 ? LOG2HC : lg_rt;
+    const int HC = 1 << lg;
     const int t = team_rank<TEAM>();
     const int4 info = P.wrow[r];
     const int32_t k = info.x;
@@ -154,7 +178,7 @@ __device__ void merge_row(const MergeParams& P, int32_t r, int* keys, uint32_t* 
         vals[i] = 0u;
     }
     team_sync<TEAM>();
-    for (int32_t p = rs + t; p < dp; p += TEAM) hash_insert<LOG2HC>(keys, vals, P.col[p], 0u, true);
+    for (int32_t p = rs + t; p < dp; p += TEAM) hash_insert(keys, vals, P.col[p], 0u, true, lg);
 
     unsigned long long jsum = 0;
     unsigned gsum = 0, csum = 0;
@@ -172,7 +196,7 @@ __device__ void merge_row(const MergeParams& P, int32_t r, int* keys, uint32_t* 
         const unsigned em = __ballot_sync(kFull, ep);
         if (ep) {
             const unsigned g = __match_any_sync(em, rc.x);
-            if ((int)lane_id() == __ffs(g) - 1) hash_insert<LOG2HC>(keys, vals, rc.x, __popc(g), false);
+            if ((int)lane_id() == __ffs(g) - 1) hash_insert(keys, vals, rc.x, __popc(g), false, lg);
         }
     }
     team_sync<TEAM>();
@@ -264,9 +288,7 @@ __global__ void __launch_bounds__(32 * kMergeWarps) k_merge_small(const MergePar
     const int32_t gw = blockIdx.x * kMergeWarps + warp;
     const int32_t nwarps = gridDim.x * kMergeWarps;
     for (int32_t r = gw; r < P.nw; r += nwarps) {
-        const int64_t m = P.wbase[r + 1] - P.wbase[r];
-        const int4 info = P.wrow[r];
-        if (m + info.w > kSmallCap) {
+        if (key_bound(P, r) > kSmallCap) {
             if (lane_id() == 0) P.big_rows[atomicAdd(P.n_big, 1)] = r;
             continue;
         }
@@ -283,13 +305,31 @@ __global__ void __launch_bounds__(256) k_merge_big(const MergeParams P, int32_t 
     __shared__ unsigned long long sm64;
     for (int32_t i = blockIdx.x; i < nbig; i += gridDim.x) {
         const int32_t r = P.big_rows[i];
-        const int64_t m = P.wbase[r + 1] - P.wbase[r];
-        const int4 info = P.wrow[r];
-        if (m + info.w > kBigCap) {
-            if (threadIdx.x == 0) atomicAdd(&P.st->capacity, 1u);
+        const int64_t b = key_bound(P, r);
+        if (b > kBigCap) {
+            if (threadIdx.x == 0) {
+                P.huge_rows[atomicAdd(P.n_huge, 1)] = r;
+                atomicMax(P.huge_bound, (unsigned long long)b);
+            }
             continue;
         }
         merge_row<256, kLog2BigHash>(P, r, keys, vals, wsm, &sm64);
+    }
+}
+
+// Huge rows: one block per row, the table in this block's part of a global
+// area (2 * 2^lg_max words per block), sized per row by its key bound.
+__global__ void __launch_bounds__(256) k_merge_huge(const MergeParams P, int32_t nhuge, int* area,
+                                                    int64_t words_per_block) {
+    __shared__ int wsm[8];
+    __shared__ unsigned long long sm64;
+    int* base = area + (size_t)blockIdx.x * (size_t)words_per_block;
+    for (int32_t i = blockIdx.x; i < nhuge; i += gridDim.x) {
+        const int32_t r = P.huge_rows[i];
+        const int lg = huge_log2_slots(key_bound(P, r));
+        int* keys = base;
+        uint32_t* vals = reinterpret_cast<uint32_t*>(base + (size_t(1) << lg));
+        merge_row<256, 0>(P, r, keys, vals, wsm, &sm64, lg);
     }
 }
 
@@ -362,9 +402,13 @@ rw_status emit_factor(rw_context* ctx, const rw_csr* A, const Tables& T, const W
     fo.G = alloc_n<uint32_t>(pool, n);
     int64_t* tbase = alloc_n<int64_t>(scratch, nw + 1);
     int32_t* big_rows = alloc_n<int32_t>(scratch, nw);
-    int32_t* n_big = alloc_n<int32_t>(scratch, 1);
-    if (!fo.y_rp || !fo.d || !fo.M || !fo.J || !fo.G || !tbase || !big_rows || !n_big)
+    int32_t* huge_rows = alloc_n<int32_t>(scratch, nw);
+    // n_big, n_huge, huge_bound (as 64-bit words)
+    unsigned long long* counters = alloc_n<unsigned long long>(scratch, 3);
+    if (!fo.y_rp || !fo.d || !fo.M || !fo.J || !fo.G || !tbase || !big_rows || !huge_rows || !counters)
         return RW_ERR_ALLOC;
+    int32_t* n_big = reinterpret_cast<int32_t*>(counters);
+    int32_t* n_huge = reinterpret_cast<int32_t*>(counters + 1);
     const int blocks = grid_for(std::max(n, nw), 256, ctx->num_sms * 8);
     if (nw > 0) {
         RW_COUNT_LAUNCH();
@@ -380,7 +424,8 @@ rw_status emit_factor(rw_context* ctx, const rw_csr* A, const Tables& T, const W
     int32_t* tcol = alloc_n<int32_t>(scratch, tslots);
     double* tval = alloc_n<double>(scratch, tslots);
     if (!tcol || !tval) return RW_ERR_ALLOC;
-    if ((rc = check_cuda(cudaMemsetAsync(n_big, 0, sizeof(int32_t), s), "memset"))) return rc;
+    if ((rc = check_cuda(cudaMemsetAsync(counters, 0, 3 * sizeof(unsigned long long), s), "memset")))
+        return rc;
 
     MergeParams P;
     P.rp = A->row_ptr;
@@ -404,6 +449,9 @@ rw_status emit_factor(rw_context* ctx, const rw_csr* A, const Tables& T, const W
     P.G = fo.G;
     P.big_rows = big_rows;
     P.n_big = n_big;
+    P.huge_rows = huge_rows;
+    P.n_huge = n_huge;
+    P.huge_bound = counters + 2;
     P.st = ctx->d_status;
 
     if (ms_merge) cudaEventRecord(ctx->ev[2], s);
@@ -445,6 +493,28 @@ rw_status emit_factor(rw_context* ctx, const rw_csr* A, const Tables& T, const W
             RW_COUNT_LAUNCH();
             k_merge_big<<<grid_for(nbig, 1, ctx->num_sms), 256, sm_big, s>>>(P, nbig);
             if ((rc = check_launch("merge (block tables)"))) return rc;
+            unsigned long long* hc = static_cast<unsigned long long*>(ctx->h_small);
+            if ((rc = check_cuda(cudaMemcpyAsync(hc, counters, 3 * sizeof(unsigned long long),
+                                                 cudaMemcpyDeviceToHost, s),
+                                 "copy")))
+                return rc;
+            if ((rc = check_cuda(cudaStreamSynchronize(s), "sync"))) return rc;
+            const int32_t nhuge = (int32_t)(uint32_t)hc[1];
+            if (nhuge > 0) {
+                const int lg = huge_log2_slots((int64_t)hc[2]);
+                if (lg > 30) {
+                    set_error("merge: a row has %llu possible end points, above the 2^29 limit", hc[2]);
+                    return RW_ERR_CAPACITY;
+                }
+                const int64_t words = int64_t(2) << lg;  // keys and values
+                int64_t blocks_h = (int64_t)(kHugeTableBytes / (sizeof(int) * (size_t)words));
+                blocks_h = std::max<int64_t>(1, std::min<int64_t>(blocks_h, std::min(nhuge, 2 * ctx->num_sms)));
+                int* area = alloc_n<int>(scratch, blocks_h * words);
+                if (!area) return RW_ERR_ALLOC;
+                RW_COUNT_LAUNCH();
+                k_merge_huge<<<(int)blocks_h, 256, 0, s>>>(P, nhuge, area, words);
+                if ((rc = check_launch("merge (global tables)"))) return rc;
+            }
         }
     }
     RW_COUNT_LAUNCH();

@@ -106,13 +106,26 @@ def test_per_row_budgets_bit_exact(P, ctx):
 
 
 def test_large_row_budgets_use_block_merge(P, ctx):
-    # rows whose walks + lower neighbours exceed the warp table (768) go to the
-    # block-level merge; both paths must agree with the oracle
+    # rows with more than 768 possible end points (min(walks + lower
+    # neighbours, k)) go to the block-level merge; both paths must agree with
+    # the oracle.  Rows below 768 stay on the warp tables whatever their budget.
     rng = np.random.default_rng(8)
-    A = W.grid2d_5pt(12, 12)
+    A = W.grid2d_5pt(40, 40)
     budget = np.where(rng.random(A.n) < 0.3, 3000, 40).astype(np.uint32)
     t = gpu_factor(P, ctx, A, 0, 5, 0.0, budget=budget)
     ref = oracle.build_factor(A, budget, 5, 0.0, records=True)
+    assert_factor_equal(t, ref)
+
+
+def test_huge_row_budgets_use_global_tables(P, ctx):
+    # rows with more than 12288 possible end points merge in global-memory
+    # tables; a low row with a huge budget stays on the block tables (k bounds it)
+    A = W.grid2d_5pt(120, 115)
+    budget = np.full(A.n, 2, np.uint32)
+    budget[[A.n - 200, A.n - 150, A.n - 121, A.n - 2]] = [14000, 30000, 13000, 20000]
+    budget[[5, 900]] = [40000, 20000]
+    t = gpu_factor(P, ctx, A, 0, 12, 0.0, budget=budget)
+    ref = oracle.build_factor(A, budget, 12, 0.0, records=True)
     assert_factor_equal(t, ref)
 
 
