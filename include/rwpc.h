@@ -90,6 +90,7 @@ typedef struct {
     int32_t walk_blocks_per_sm; /* 0 = from the occupancy calculator */
     int32_t timing;          /* 1: record per-phase device times (default 1) */
     int32_t solve_blocks_per_sm; /* triangular solves: 256-thread blocks per SM (0 = 2) */
+    int32_t graphs;          /* 1: batched PCG replays each iteration from a CUDA graph (default 1) */
 } rw_options;
 
 typedef struct rw_context rw_context;
@@ -182,7 +183,11 @@ void rw_factor_destroy(rw_factor* F);
  * (the tolerance of the paper's Sec. 6); tol = 0 runs exactly max_iter
  * iterations.  prec = RW_FP32_MIXED: FP32 vectors, SpMV, factor and triangular
  * solves; FP64 dot products, alpha/beta and x, and the residual replaced by an
- * FP64 b - A x every refine_every iterations.  Returns RW_ERR_NO_CONVERGENCE
+ * FP64 b - A x every refine_every iterations.  The FP32 SpMV applies A in
+ * excess + difference form, e_i x_i + sum_{j != i} A_ij (x_j - x_i) with the
+ * FP32 excess e_i = A_ii + sum_j A_ij computed in FP64, so rounding perturbs
+ * edge weights and excesses relatively and a weakly grounded matrix keeps its
+ * near-null space in FP32.  Returns RW_ERR_NO_CONVERGENCE
  * (x still written) if some right-hand side did not reach tol in max_iter.
  * h_iters/h_relres (host, [nrhs], may be NULL) receive per right-hand side
  * iterations and true relative residuals. */
@@ -194,12 +199,42 @@ rw_status pcg_solve(rw_context* ctx, const rw_csr* A, const rw_factor* F, const 
  * right-hand-side / solution pointers), each with nrhs node-major right-hand
  * sides.  stats: host [nmat] (may be NULL); h_iters/h_relres: host
  * [nmat * nrhs] (may be NULL).  Returns RW_ERR_NO_CONVERGENCE if any right-hand
- * side missed tol, the first other error otherwise. */
+ * side missed tol, the first other error otherwise.  Same as rw_batch_create +
+ * pcg_solve_batch + rw_batch_destroy. */
 rw_status pcg_solve_batched(rw_context* ctx, int32_t nmat, const rw_csr* As,
                             const rw_factor* const* Fs, const double* const* d_b,
                             double* const* d_x, int32_t nrhs, double tol, int32_t max_iter,
                             rw_precision prec, rw_pcg_stats* stats, int32_t* h_iters,
                             double* h_relres);
+
+/* Batched solves.  A batch joins nmat matrices and their factors into one
+ * block-diagonal system: concatenated CSR arrays (rows of matrix m offset by
+ * the sizes of matrices 0..m-1), concatenated factors, and one level schedule
+ * for each triangular solve over all factors (its depth is the largest single
+ * depth).  Each PCG iteration (Algorithm 1) then runs one SpMV, one backward
+ * and one forward solve and a few vector kernels for every matrix and
+ * right-hand side at once; alpha, beta and the stopping test are per
+ * (matrix, right-hand side), computed in FP64 from per-matrix sums in a fixed
+ * order, so every system follows the same iterates as pcg_solve on its own
+ * matrix up to rounding.  With rw_options.graphs the iteration is captured
+ * once in a CUDA graph and replayed; the host reads one flag word per
+ * iteration.  The batch copies what it needs (it does not reference the
+ * factors afterwards); its arrays are allocated through the context.
+ * Limits: sum of n and sum of nnz(A) below 2^31. */
+typedef struct rw_batch rw_batch;
+rw_status rw_batch_create(rw_context* ctx, int32_t nmat, const rw_csr* As, const rw_factor* const* Fs,
+                          rw_batch** out);
+void rw_batch_destroy(rw_batch* B);
+/* Combined size, stored factor entries and the depths of the two solves. */
+rw_status rw_batch_info(const rw_batch* B, int32_t* n_total, int64_t* nnz_y, int32_t* fwd_levels,
+                        int32_t* bwd_levels);
+/* pcg_solve over the batch: d_b[m], d_x[m] as in pcg_solve_batched.  stats
+ * (host [nmat], may be NULL): per matrix the iterations and true residual
+ * (max over its right-hand sides), and the device time and kernel launches of
+ * the whole call. */
+rw_status pcg_solve_batch(rw_context* ctx, rw_batch* B, const double* const* d_b, double* const* d_x,
+                          int32_t nrhs, double tol, int32_t max_iter, rw_precision prec,
+                          rw_pcg_stats* stats, int32_t* h_iters, double* h_relres);
 
 /* z = (Y^T diag(D) Y)^-1 r for nrhs node-major right-hand sides (FP64): the
  * preconditioner application inside pcg_solve (backward solve with Y^T,

@@ -574,11 +574,31 @@ static void spmv64(int32_t n, const int32_t* rp, const int32_t* ci, const double
     }
 }
 
+/* FP32 operator of the mixed mode in excess + difference form: an R-matrix
+ * row is A_ii x_i + sum_j A_ij x_j = e_i x_i + sum_{j != i} A_ij (x_j - x_i)
+ * with the diagonal excess e_i = A_ii + sum_{j != i} A_ij >= 0 (the ground
+ * weight of the walk game, Eq. map).  a[] holds A_ij (j != i) rounded to FP32
+ * and, at the diagonal position, e_i computed in FP64 (sum of the row in
+ * column order) and rounded to FP32.  Rounding then perturbs each edge weight
+ * and each excess by a relative 2^-24 only, so the FP32 operator keeps the
+ * near-null space of a weakly grounded matrix; rounding A_ii itself would
+ * shift row sums by 2^-24 A_ii, which swamps a small excess. */
+static void to_fp32_diff(int32_t n, const int32_t* rp, const int32_t* ci, const double* v,
+                         float* a) {
+    for (int32_t i = 0; i < n; ++i) {
+        double e = 0.0;
+        for (int32_t p = rp[i]; p < rp[i + 1]; ++p) e = e + v[p];
+        for (int32_t p = rp[i]; p < rp[i + 1]; ++p) a[p] = ci[p] == i ? (float)e : (float)v[p];
+    }
+}
+
 static void spmv32(int32_t n, const int32_t* rp, const int32_t* ci, const float* a,
                    const float* x, float* y) {
     for (int32_t i = 0; i < n; ++i) {
         float s = 0.0f;
-        for (int32_t p = rp[i]; p < rp[i + 1]; ++p) s = s + a[p] * x[ci[p]];
+        const float xi = x[i];
+        for (int32_t p = rp[i]; p < rp[i + 1]; ++p)
+            s = s + (ci[p] == i ? a[p] * xi : a[p] * (x[ci[p]] - xi));
         y[i] = s;
     }
 }
@@ -684,7 +704,7 @@ static int pcg_mixed(int32_t n, const int32_t* Arp, const int32_t* Acol, const d
     double *t = malloc(sizeof(double) * nn);
     int rc = -5;
     if (!A32 || !Y32 || !D32 || !r || !z || !p || !q || !w || !t) { rc = -4; goto done; }
-    for (int64_t i = 0; i < annz; ++i) A32[i] = (float)Aval[i];
+    to_fp32_diff(n, Arp, Acol, Aval, A32);
     for (int64_t i = 0; i < ynnz; ++i) Y32[i] = (float)Yval[i];
     for (int32_t i = 0; i < n; ++i) D32[i] = (float)D[i];
     for (int32_t i = 0; i < n; ++i) { x[i] = 0.0; r[i] = (float)b[i]; }

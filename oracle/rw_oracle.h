@@ -81,7 +81,9 @@ int orc_precond_apply(int32_t n, const int64_t* Yrp, const int32_t* Ycol, const 
  * Preconditioned conjugate gradients with M = Y^T D Y (Algorithm 1, "solve").
  * One right-hand side.  mixed=0: FP64 throughout.  mixed=1: FP32 vectors, SpMV,
  * factor and triangular solves; FP64 dot products, alpha/beta and x; the residual
- * is recomputed in FP64 every refine_every iterations.  Stops when the true
+ * is recomputed in FP64 every refine_every iterations.  The FP32 SpMV applies A
+ * in excess + difference form (FP32 off-diagonals A_ij and FP32 excesses
+ * e_i = A_ii + sum_j A_ij: y_i = e_i x_i + sum_j A_ij (x_j - x_i)).  Stops when the true
  * residual ||b - A x|| < tol ||b||; tol = 0 runs exactly max_iter iterations.
  */
 int orc_pcg(int32_t n, const int32_t* Arp, const int32_t* Acol, const double* Aval,

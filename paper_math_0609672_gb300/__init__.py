@@ -32,6 +32,7 @@ __all__ = [
     "Mlp", "rw_row_features", "rw_pilot_stats", "rw_mlp_create", "rw_mlp_predict",
     "rw_mlp_gradient", "rw_mlp_train", "rw_budget_normalize", "rw_budget_predict",
     "RW_NUM_FEATURES", "RW_FEATURE_STRIDE", "RW_MLP_PARAMS",
+    "Batch", "rw_batch_create", "pcg_solve_batch",
 ]
 
 RW_NUM_FEATURES = 12
@@ -57,7 +58,7 @@ class rw_csr_t(ctypes.Structure):
 class rw_options_t(ctypes.Structure):
     _fields_ = [("max_steps", _u64), ("keep_records", _i32), ("record_lengths", _i32),
                 ("store_fp32", _i32), ("refine_every", _i32), ("walk_blocks_per_sm", _i32),
-                ("timing", _i32), ("solve_blocks_per_sm", _i32)]
+                ("timing", _i32), ("solve_blocks_per_sm", _i32), ("graphs", _i32)]
 
 
 class rw_factor_desc_t(ctypes.Structure):
@@ -146,12 +147,17 @@ def load():
         "rw_mlp_train": [vp, vp, vp, vp, vp, ctypes.c_int64, _i32, _i32, ctypes.c_float, _u64, _i32, vp],
         "rw_budget_normalize": [vp, P(rw_csr_t), vp, _f64, _u32, vp],
         "rw_budget_predict": [vp, P(rw_csr_t), vp, _f64, _u32, vp],
+        "rw_batch_create": [vp, _i32, P(rw_csr_t), P(vp), P(vp)],
+        "rw_batch_info": [vp, P(_i32), P(ctypes.c_int64), P(_i32), P(_i32)],
+        "pcg_solve_batch": [vp, vp, P(vp), P(vp), _i32, _f64, _i32, ctypes.c_int, P(rw_pcg_stats_t), vp, vp],
     }
     for name, args in sigs.items():
         getattr(lib, name).argtypes = args
         getattr(lib, name).restype = ctypes.c_int
     lib.rw_mlp_destroy.argtypes = [vp]
     lib.rw_mlp_destroy.restype = None
+    lib.rw_batch_destroy.argtypes = [vp]
+    lib.rw_batch_destroy.restype = None
     _lib = lib
     return lib
 
@@ -242,6 +248,7 @@ class Context:
         self._keep = []
         self._factors = weakref.WeakSet()  # factors free through the context: close them first
         self._mlps = weakref.WeakSet()
+        self._batches = weakref.WeakSet()
         if torch_allocator:
             dev = torch.cuda.current_device()
 
@@ -269,6 +276,8 @@ class Context:
                 f.destroy()
             for m in list(self._mlps):
                 m.destroy()
+            for b in list(self._batches):
+                b.destroy()
             load().rw_context_destroy(self.handle)
             self.handle = None
 
@@ -554,3 +563,59 @@ def rw_budget_normalize(ctx, A, weight, mean_budget, min_budget, budget):
 def rw_budget_predict(ctx, A, M, mean_budget, min_budget, budget):
     _check(load().rw_budget_predict(ctx.handle, ctypes.byref(A.c), M.handle, float(mean_budget),
                                     int(min_budget), _ptr(budget)), "rw_budget_predict")
+
+
+# ---------------------------------------------------------------------------
+# Batched solves
+# ---------------------------------------------------------------------------
+
+class Batch:
+    """Block-diagonal system of several matrices and their factors."""
+
+    def __init__(self, ctx, As, Fs):
+        self.ctx = ctx
+        self.nmat = len(As)
+        arr = (rw_csr_t * self.nmat)(*[A.c for A in As])
+        fh = (_c_void_p * self.nmat)(*[F.handle.value if hasattr(F.handle, "value") else F.handle for F in Fs])
+        h = _c_void_p()
+        _check(load().rw_batch_create(ctx.handle, self.nmat, arr, fh, ctypes.byref(h)), "rw_batch_create")
+        self.handle = h
+        ctx._batches.add(self)
+
+    def info(self):
+        n, nnz, fl, bl = _i32(), ctypes.c_int64(), _i32(), _i32()
+        _check(load().rw_batch_info(self.handle, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(fl),
+                                    ctypes.byref(bl)), "rw_batch_info")
+        return dict(n=n.value, nnz_y=nnz.value, fwd_levels=fl.value, bwd_levels=bl.value)
+
+    def destroy(self):
+        if self.handle and self.ctx.handle:
+            load().rw_batch_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def rw_batch_create(ctx, As, Fs):
+    return Batch(ctx, As, Fs)
+
+
+def pcg_solve_batch(ctx, B, bs, xs, tol, max_iter, prec=RW_FP64):
+    """Returns (status, stats list, iterations [nmat, nrhs], relres [nmat, nrhs])."""
+    import numpy as np
+    nmat = B.nmat
+    nrhs = 1 if bs[0].dim() == 1 else bs[0].shape[1]
+    bp = (_c_void_p * nmat)(*[b.data_ptr() for b in bs])
+    xp = (_c_void_p * nmat)(*[x.data_ptr() for x in xs])
+    st = (rw_pcg_stats_t * nmat)()
+    its = np.zeros((nmat, nrhs), np.int32)
+    rel = np.zeros((nmat, nrhs), np.float64)
+    rc = load().pcg_solve_batch(ctx.handle, B.handle, bp, xp, nrhs, float(tol), int(max_iter), int(prec), st,
+                                its.ctypes.data_as(_c_void_p), rel.ctypes.data_as(_c_void_p))
+    if rc not in (RW_OK, -5):
+        raise RwError(rc, "pcg_solve_batch")
+    return rc, list(st), its, rel

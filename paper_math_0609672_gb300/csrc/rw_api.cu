@@ -110,7 +110,7 @@ void Pool::release_all() {
     bufs.clear();
 }
 
-static rw_status check_csr(const rw_csr* A) {
+rw_status check_csr(const rw_csr* A) {
     if (!A) {
         set_error("matrix is NULL");
         return RW_ERR_ARG;
@@ -142,6 +142,7 @@ void rw_options_default(rw_options* opt) {
     opt->refine_every = 50;
     opt->walk_blocks_per_sm = 0;
     opt->timing = 1;
+    opt->graphs = 1;
 }
 
 const char* rw_status_string(rw_status s) {
@@ -634,18 +635,13 @@ rw_status pcg_solve_batched(rw_context* ctx, int32_t nmat, const rw_csr* As,
         set_error("pcg_solve_batched: bad arguments");
         return RW_ERR_ARG;
     }
-    rw_status worst = RW_OK;
-    for (int32_t m = 0; m < nmat; ++m) {
-        rw_pcg_stats st{};
-        rw_status rc = pcg_solve(ctx, &As[m], Fs[m], d_b[m], d_x[m], nrhs, tol, max_iter, prec, &st,
-                                 h_iters ? h_iters + (size_t)m * nrhs : nullptr,
-                                 h_relres ? h_relres + (size_t)m * nrhs : nullptr);
-        if (stats) stats[m] = st;
-        if (rc != RW_OK && rc != RW_ERR_NO_CONVERGENCE) return rc;
-        if (rc == RW_ERR_NO_CONVERGENCE) worst = rc;
-    }
-    if (worst) set_error("pcg_solve_batched: some right-hand sides did not converge");
-    return worst;
+    // one block-diagonal system for the whole batch
+    rw_batch* B = nullptr;
+    rw_status rc = rw_batch_create(ctx, nmat, As, Fs, &B);
+    if (rc) return rc;
+    rc = pcg_solve_batch(ctx, B, d_b, d_x, nrhs, tol, max_iter, prec, stats, h_iters, h_relres);
+    rw_batch_destroy(B);
+    return rc;
 }
 
 rw_status rw_precond_apply(rw_context* ctx, const rw_factor* F, const double* d_r, double* d_z,

@@ -233,12 +233,25 @@ struct FactorView {
 };
 
 void launch_to_fp32(const double* in, float* out, int64_t cnt, cudaStream_t s, int num_sms);
+// FP32 operator of the mixed mode: off-diagonals rounded, the diagonal slot
+// holding the row's excess e_i = A_ii + sum_j A_ij (applied by the FP32 SpMV as
+// e_i x_i + sum_j A_ij (x_j - x_i)).
+void launch_to_fp32_diff(int32_t n, const int32_t* rp, const int32_t* col, const double* val, float* a32,
+                         cudaStream_t s, int num_sms);
 rw_status spmv_fp64(rw_context* ctx, const rw_csr* A, const double* x, double* y, int nrhs);
 rw_status precond_fp64(rw_context* ctx, const FactorView& F, const double* r, double* z,
                        int nrhs, Pool& scratch);
 rw_status pcg_run(rw_context* ctx, const rw_csr* A, const FactorView& F, const double* b,
                   double* x, int nrhs, double tol, int max_iter, rw_precision prec,
                   rw_pcg_stats* stats, int32_t* h_iters, double* h_relres);
+
+// y = A x (node-major, nrhs <= 16) for T = double or float.
+template <typename T>
+rw_status spmv_launch(rw_context* ctx, int32_t n, const int32_t* rp, const int32_t* col, const T* val,
+                      const T* x, T* y, int nrhs);
+
+// Size and pointer checks of a matrix argument (RW_ERR_ARG / RW_ERR_NOT_RMATRIX).
+rw_status check_csr(const rw_csr* A);
 
 // Launch-and-check helper: returns RW_ERR_CUDA with a message on failure.
 rw_status check_cuda(cudaError_t e, const char* what);

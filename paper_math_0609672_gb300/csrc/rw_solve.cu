@@ -23,8 +23,15 @@ constexpr int kDotParts = 1024;  // blocks of the dot-product producing kernels
 // SpMV: y = A x for node-major vectors.  GS lanes per row, each lane keeps one
 // accumulator per right-hand side.  Optionally accumulates per-block partial
 // dot products x.y (per right-hand side) for the PCG step.
+//
+// DIFF (the FP32 operator of the mixed mode): val holds A_ij (j != i) and, at
+// the diagonal position, the excess e_i = A_ii + sum_j A_ij, and the row is
+// applied as e_i x_i + sum_{j != i} A_ij (x_j - x_i).  Rounding an R-matrix to
+// FP32 this way perturbs edge weights and excesses by a relative 2^-24 each,
+// so the operator keeps the near-null space of a weakly grounded matrix
+// (rounding A_ii itself would move a row sum by 2^-24 A_ii).
 // ---------------------------------------------------------------------------
-template <typename TA, typename TV, int NR, int GS>
+template <typename TA, typename TV, int NR, int GS, bool DIFF>
 __global__ void __launch_bounds__(256) k_spmv(int32_t n, const int32_t* __restrict__ rp,
                                               const int32_t* __restrict__ col,
                                               const TA* __restrict__ val, const TV* __restrict__ x,
@@ -39,16 +46,22 @@ __global__ void __launch_bounds__(256) k_spmv(int32_t n, const int32_t* __restri
 #pragma unroll
     for (int j = 0; j < NR; ++j) mydot[j] = 0.0;
     for (int64_t row = grp; row < n; row += ngrp) {
-        TV acc[NR];
+        TV acc[NR], xi[NR];
 #pragma unroll
-        for (int j = 0; j < NR; ++j) acc[j] = TV(0);
+        for (int j = 0; j < NR; ++j) {
+            acc[j] = TV(0);
+            xi[j] = (DIFF && j < nrhs) ? x[(size_t)row * nrhs + j] : TV(0);
+        }
         const int32_t s = rp[row], e = rp[row + 1];
         for (int32_t p = s + g; p < e; p += GS) {
             const int32_t c = col[p];
             const TV a = (TV)val[p];
 #pragma unroll
             for (int j = 0; j < NR; ++j)
-                if (j < nrhs) acc[j] += a * x[(size_t)c * nrhs + j];
+                if (j < nrhs) {
+                    if (DIFF) acc[j] += (c == row) ? a * xi[j] : a * (x[(size_t)c * nrhs + j] - xi[j]);
+                    else acc[j] += a * x[(size_t)c * nrhs + j];
+                }
         }
 #pragma unroll
         for (int j = 0; j < NR; ++j)
@@ -72,6 +85,25 @@ __global__ void __launch_bounds__(256) k_spmv(int32_t n, const int32_t* __restri
         __syncthreads();
         if (threadIdx.x < NR) part[(size_t)blockIdx.x * 16 + threadIdx.x] = sdot[threadIdx.x];
     }
+}
+
+// FP32 operator of the mixed mode (see k_spmv): off-diagonals rounded, the
+// diagonal slot replaced by the row's excess (FP64 sum of the row in column
+// order, then rounded).  One thread per row.
+__global__ void k_to_fp32_diff(int32_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                               const double* __restrict__ val, float* __restrict__ a32) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int32_t s = rp[i], e = rp[i + 1];
+        double ex = 0.0;
+        for (int32_t p = s; p < e; ++p) ex = __dadd_rn(ex, val[p]);
+        for (int32_t p = s; p < e; ++p) a32[p] = col[p] == i ? (float)ex : (float)val[p];
+    }
+}
+
+void launch_to_fp32_diff(int32_t n, const int32_t* rp, const int32_t* col, const double* val, float* a32,
+                         cudaStream_t s, int num_sms) {
+    RW_COUNT_LAUNCH();
+    k_to_fp32_diff<<<grid_for(n, 256, num_sms * 8), 256, 0, s>>>(n, rp, col, val, a32);
 }
 
 template <typename T>
@@ -308,7 +340,8 @@ template <typename TA, typename TV, int NR>
 static void launch_spmv_nr(int32_t n, const int32_t* rp, const int32_t* col, const TA* val,
                            const TV* x, TV* y, int nrhs, double* part, int blocks, cudaStream_t s) {
     RW_COUNT_LAUNCH();
-    k_spmv<TA, TV, NR, 8><<<blocks, 256, 0, s>>>(n, rp, col, val, x, y, nrhs, part);
+    // FP32 values are always the excess + difference form of the mixed mode
+    k_spmv<TA, TV, NR, 8, sizeof(TA) == 4><<<blocks, 256, 0, s>>>(n, rp, col, val, x, y, nrhs, part);
 }
 
 template <typename TA, typename TV>
@@ -326,6 +359,16 @@ static rw_status launch_spmv(rw_context* ctx, int32_t n, const int32_t* rp, cons
     }
     return check_launch("spmv");
 }
+
+template <typename T>
+rw_status spmv_launch(rw_context* ctx, int32_t n, const int32_t* rp, const int32_t* col, const T* val,
+                      const T* x, T* y, int nrhs) {
+    return launch_spmv<T, T>(ctx, n, rp, col, val, x, y, nrhs, nullptr);
+}
+template rw_status spmv_launch<double>(rw_context*, int32_t, const int32_t*, const int32_t*, const double*,
+                                       const double*, double*, int);
+template rw_status spmv_launch<float>(rw_context*, int32_t, const int32_t*, const int32_t*, const float*,
+                                      const float*, float*, int);
 
 template <typename T>
 static rw_status fill_pending(rw_context* ctx, T* x, int64_t cnt) {
@@ -559,9 +602,7 @@ rw_status pcg_run(rw_context* ctx, const rw_csr* A, const FactorView& F, const d
         }
         float* a32 = alloc_n<float>(sc, A->nnz);
         if (!a32) return RW_ERR_ALLOC;
-        RW_COUNT_LAUNCH();
-        k_convert<double, float><<<grid_for(A->nnz, 256, ctx->num_sms * 8), 256, 0, s>>>(
-            A->val, a32, A->nnz);
+        launch_to_fp32_diff(A->n, A->row_ptr, A->col, A->val, a32, s, ctx->num_sms);
         if ((rc = check_launch("convert A"))) return rc;
         rc = pcg_t<float>(ctx, A, F, b, x, nrhs, tol, max_iter, stats, h_iters, h_relres, sc, a32,
                           F.y_val32, F.yt_val32, F.d32, true);

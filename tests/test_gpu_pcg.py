@@ -182,3 +182,63 @@ def test_batched_pcg_matches_single(P, ctx):
             assert np.linalg.norm(xg[:, j] - xr) / np.linalg.norm(xr) < 1e-10
     for F in Fs:
         F.destroy()
+
+
+def test_batch_graphs_match_direct_launches_and_oracle(P):
+    """The combined block-diagonal solve: 16 right-hand sides over matrices of
+    uneven size (rows of several reduction chunks and a ragged tail); replaying
+    the captured iteration gives the same bits as launching it directly, and
+    every system matches the oracle PCG on its own matrix."""
+    import torch
+    rng = np.random.default_rng(12)
+    mats = [W.rgg(int(n), rng) for n in (3000, 700, 5000, 1)] + [W.grid2d_5pt(30, 20)]
+    seeds = [5, 6, 7, 8, 9]
+    out = {}
+    for graphs in (1, 0):
+        ctx = P.Context(options=P.rw_options_default(graphs=graphs))
+        dAs = [P.CSR.from_host(A) for A in mats]
+        Fs = P.rw_build_factor_batched(ctx, dAs, 40, seeds, 1e-3)
+        bs = [np.random.default_rng(100 + m).standard_normal((A.n, 16)) for m, A in enumerate(mats)]
+        xs = [_dev(np.zeros_like(b)) for b in bs]
+        B = P.Batch(ctx, dAs, Fs)
+        info = B.info()
+        assert info["n"] == sum(A.n for A in mats)
+        rc, st, its, rel = P.pcg_solve_batch(ctx, B, [_dev(b) for b in bs], xs, 1e-9, 400)
+        assert rc == 0 and np.all(rel < 1e-9), rel.max()
+        out[graphs] = ([x.cpu().numpy() for x in xs], its, bs)
+        B.destroy()
+        for F in Fs:
+            F.destroy()
+        ctx.close()
+    for a, b in zip(out[0][0], out[1][0]):
+        assert np.array_equal(a, b)
+    assert np.array_equal(out[0][1], out[1][1])
+    xs, its, bs = out[1]
+    for m, A in enumerate(mats):
+        ref = oracle.build_factor(A, 40, seeds[m], 1e-3, matrix_index=m)
+        for j in (0, 7, 15):
+            xr, itr, rr, _ = oracle.pcg(A, ref, bs[m][:, j], 1e-9, 400)
+            assert its[m, j] == itr, (m, j, its[m, j], itr)
+            assert np.linalg.norm(xs[m][:, j] - xr) <= 1e-10 * max(1e-300, np.linalg.norm(xr))
+    del torch
+
+
+def test_batch_fp32_mixed(P, ctx):
+    rng = np.random.default_rng(13)
+    mats = [W.rgg(int(n), rng) for n in (4000, 900, 2500)]
+    dAs = [P.CSR.from_host(A) for A in mats]
+    Fs = P.rw_build_factor_batched(ctx, dAs, 60, [1, 2, 3], 1e-3)
+    bs = [rng.standard_normal((A.n, 4)) for A in mats]
+    xs = [_dev(np.zeros_like(b)) for b in bs]
+    rc, st, its, rel = P.pcg_solve_batched(ctx, dAs, Fs, [_dev(b) for b in bs], xs, 1e-6, 1000,
+                                           P.RW_FP32_MIXED)
+    assert rc == 0 and np.all(rel < 1e-6)
+    for m, A in enumerate(mats):
+        xg = xs[m].cpu().numpy()
+        true = np.linalg.norm(bs[m] - A.to_scipy() @ xg, axis=0) / np.linalg.norm(bs[m], axis=0)
+        assert np.all(true < 1e-6)
+        ref = oracle.build_factor(A, 60, m + 1, 1e-3, matrix_index=m)
+        xr, itr, rr, _ = oracle.pcg(A, ref, bs[m][:, 0], 1e-6, 1000, mixed=True)
+        assert abs(int(its[m, 0]) - itr) <= max(2, itr // 5)
+    for F in Fs:
+        F.destroy()
