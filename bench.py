@@ -1,22 +1,36 @@
 """Benchmark: random-walk factor construction + PCG on one GB300.
 
-Workload: 3D 7-point grid 64^3 (n = 262,144), conductances log-uniform in
-[0.1, 10], diagonal excess U[0, 1e-3] * row sum, seeded random symmetric
-ordering, 500 walks per row, drop tolerance 1e-3, 4 right-hand sides ~ N(0,1),
-PCG to 1e-6 true relative residual in FP64.  Synthetic, seeded inputs.
-
-One step = the whole hot path on one batch: build the factor
+Default workload (2): 3D 7-point grid 64^3 (n = 262,144), conductances
+log-uniform in [0.1, 10], diagonal excess U[0, 1e-3] * row sum, seeded random
+symmetric ordering, 500 walks per row, drop tolerance 1e-3, 4 right-hand sides
+~ N(0,1), PCG to 1e-6 true relative residual in FP64.  Synthetic, seeded
+inputs.  One step = the whole hot path on one batch: build the factor
 (rw_build_factor: tables, walks, merge, emission, transpose, levels) and solve
 the 4 right-hand sides (pcg_solve), then release the factor.  The headline
 value is walk-hops per second of step time (hops of the build / step time);
 factor-build seconds and PCG seconds are reported beside it.
+
+Other workloads (--workload N):
+  3  2D 1000^2 grid + 2 long-range edges per row (n = 1e6), 200 walks, factor
+     stored FP32, PCG FP32 (FP64 dots / alpha / beta / x, residual replacement
+     every 50 iterations) to 1e-6; the FP32 solution's error against the FP64
+     solve of the same factor is stated.
+  4  256 random geometric graph Laplacians (n log-uniform in [1e3, 2e5]),
+     16 right-hand sides each, 200 walks: one walk launch for all matrices
+     (rw_build_factor_batched), one block-diagonal PCG with the iteration
+     replayed from a CUDA graph (rw_batch_create + pcg_solve_batch).
+  5  3D 27-point grid 128^3 (n = 2,097,152), excess 1e-4 * row sum: learned
+     budget (network trained on pilot-walk labels of seeded 64^3 instances of
+     the same distribution, mean 300, min 20) + FP32 PCG on the batched
+     engine, against the plain form (uniform 300 walks, FP64 PCG); value =
+     seconds to 1e-6 (build + solve) of the learned form.
 
 Timing: W warm-up steps, then K steps, each bracketed by CUDA events on the
 library's stream, with an L2 flush (a 512 MB write) between steps outside
 the timed events, and a barrier + synchronize on both sides of the timed
 region.  Under torchrun each rank runs its own replica (the factor build and
 the solves of independent matrices do not exchange data); value = all ranks'
-hops / max-over-ranks time.
+work / max-over-ranks time.
 
 --impl reference times the CPU oracle on a bounded row sample of the same
 workload (the oracle is the baseline: a plain single-threaded C program).
@@ -38,7 +52,6 @@ sys.path.insert(0, ROOT)
 
 import workloads as W  # noqa: E402
 
-WORKLOAD = 2
 METRIC = "walk-hops/s, factor-build s; PCG s to 1e-6 rel. residual (learned+FP32 vs plain)"
 
 
@@ -106,17 +119,15 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_inputs():
-    cfg = W.make_config(WORKLOAD)
-    return cfg
+# ---------------------------------------------------------------------------
+# CPU oracle baseline (bounded samples)
+# ---------------------------------------------------------------------------
 
-
-def cpu_oracle_sample(cfg, target_s=12.0, seed=2024):
-    """Time the oracle (single thread) on a random sample of rows of the same
+def cpu_oracle_sample(A, walks, seed, drop, label, target_s=12.0, rng_seed=2024):
+    """Time the oracle (single thread) on a random sample of walk rows of the
     matrix with the same walks, until about target_s seconds of CPU work."""
     import oracle
-    A = cfg["A"]
-    rng = np.random.default_rng(seed)
+    rng = np.random.default_rng(rng_seed)
     wr = oracle.walk_rows(A)
     order = rng.permutation(wr)
     done_rows, hops, t_used = 0, 0, 0.0
@@ -124,25 +135,35 @@ def cpu_oracle_sample(cfg, target_s=12.0, seed=2024):
     while t_used < target_s and done_rows < order.size:
         rows = np.sort(order[done_rows:done_rows + chunk])
         t0 = time.perf_counter()
-        F = oracle.build_factor(A, cfg["walks"], cfg["walk_seed"], cfg["drop_tol"], rows=rows)
+        F = oracle.build_factor(A, walks, seed, drop, rows=rows)
         t_used += time.perf_counter() - t0
         hops += int(F["hops"].sum())
         done_rows += rows.size
         chunk = min(chunk * 2, 8192)
     return {"value": hops / t_used, "unit": "hops/s", "cores": 1, "kind": "oracle",
-            "sample": f"{done_rows} random walk rows of the 64^3 workload x {cfg['walks']} walks "
+            "sample": f"{done_rows} random walk rows of {label} x {walks} walks "
                       f"({hops} hops) in {t_used:.1f} s, single thread, factor rows only"}
+
+
+def _oracle_sample_for(workload, cfg, target_s, rng_seed):
+    if workload == 4:
+        A = cfg["A"][int(np.argmax([a.n for a in cfg["A"]]))]
+        return cpu_oracle_sample(A, cfg["walks"], cfg["walk_seed"], cfg["drop_tol"],
+                                 "the largest matrix of the 256-RGG batch", target_s, rng_seed)
+    walks = 300 if workload == 5 else cfg["walks"]
+    return cpu_oracle_sample(cfg["A"], walks, cfg["walk_seed"], cfg["drop_tol"],
+                             f"the {W.CONFIGS[workload]['name']} workload", target_s, rng_seed)
 
 
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return
-    cfg = make_inputs()
+    cfg = W.make_config(args.workload)
     vals = []
     for i in range(args.warmup + args.steps):
-        r = cpu_oracle_sample(cfg, target_s=max(2.0, 60.0 / max(1, args.warmup + args.steps)),
-                              seed=100 + i)
+        r = _oracle_sample_for(args.workload, cfg, max(2.0, 60.0 / max(1, args.warmup + args.steps)),
+                               100 + i)
         if i >= args.warmup:
             vals.append(r)
     v = statistics.mean(r["value"] for r in vals)
@@ -150,35 +171,97 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": W.CONFIGS[WORKLOAD]["name"], "n": cfg["A"].n,
-                       "walks_per_row": cfg["walks"], "drop_tol": cfg["drop_tol"],
-                       "nrhs": cfg["nrhs"]},
+            "config": {"workload": W.CONFIGS[args.workload]["name"]},
             "cpu_baseline": {"value": v, "unit": "hops/s", "cores": 1, "kind": "oracle",
                              "sample": vals[-1]["sample"]},
             "e2e": {"value": v, "unit": "hops/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def run_gpu(args):
-    import torch
-    import paper_math_0609672_gb300 as P
-    ws, rank, local = _dist()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    cfg = make_inputs()
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+class Timer:
+    """Per-step CUDA-event timing with an L2 flush between steps."""
+
+    def __init__(self, torch, dev, stream):
+        self.torch, self.stream = torch, stream
+        self.flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def run(self, fn, steps, warmup, ws, local):
+        torch = self.torch
+        for _ in range(warmup):
+            fn()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        infos = []
+        clocks = ClockSampler(local)
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        clocks.start()
+        for i in range(steps):
+            self.flush.fill_(float(i))
+            ev[i][0].record(self.stream)
+            infos.append(fn())
+            ev[i][1].record(self.stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        if ws > 1:
+            torch.distributed.barrier()
+        ms = statistics.mean(a.elapsed_time(b_) for a, b_ in ev)
+        if ws > 1:
+            t = torch.tensor([ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, infos, clk
+
+
+def _walk_roofline(peaks, hops, walks_total, walk_ms, bytes_per_hop=64.0):
+    # algorithmic bytes of the walk kernel: per hop the threshold sectors of
+    # the current node and one sector for the chosen successor; per walk one
+    # 8-byte record
+    alg_bytes = bytes_per_hop * hops + 8.0 * walks_total
+    achieved = alg_bytes / (walk_ms * 1e-3) / 1e9 if walk_ms > 0 else 0.0
+    return {"kernel": "k_walk", "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+            "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+            "ms_per_launch": walk_ms}
+
+
+def _solve_roofline(peaks, napply, nnz_y, n, nrhs, tri_ms, vbytes, ybytes):
+    # per application of the preconditioner the factor (Y and Y^T) and the
+    # vectors (read and written per solve) must be touched once
+    tri_bytes = napply * (2 * ybytes * nnz_y + 2 * 3 * vbytes * nrhs * n)
+    achieved = tri_bytes / (tri_ms * 1e-3) / 1e9 if tri_ms > 0 else 0.0
+    return {"kernel": "k_thin/k_wide (triangular solves)", "bound": "hbm", "achieved": achieved,
+            "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+            "traffic": None, "ms_per_step": tri_ms,
+            "note": "latency-bound: dependency DAG depth x dependent memory round trips"}
+
+
+def _base_line(args, ws, ms, dtype, config):
+    return {"metric": METRIC, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+            "data": "synthetic", "config": config}
+
+
+def run_gpu_single(args, P, torch, dev, stream, ws, rank, local):
+    """Workloads 2 and 3: one matrix, build + PCG per step."""
+    cfg = W.make_config(args.workload)
     A, b = cfg["A"], cfg["b"]
     walks, seed, drop, tol = cfg["walks"], cfg["walk_seed"], cfg["drop_tol"], cfg["tol"]
+    mixed = cfg["precision"] == "fp32"
+    prec = P.RW_FP32_MIXED if mixed else P.RW_FP64
     nrhs = b.shape[1]
-    stream = torch.cuda.current_stream(dev)
     ctx = P.Context(stream=stream)
     dA = P.CSR.from_host(A, device=dev)
     db = torch.as_tensor(b, device=dev)
     dx = torch.zeros_like(db)
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def step():
         F = P.rw_build_factor(ctx, dA, walks, seed, drop)
-        rc, st, its, rel = P.pcg_solve(ctx, dA, F, db, dx, tol, 2000)
+        rc, st, its, rel = P.pcg_solve(ctx, dA, F, db, dx, tol, 3000, prec)
         d = F.desc
         info = dict(hops=int(d.total_hops), walks=int(d.total_walks), nnz=int(d.nnz),
                     phase=list(d.phase_ms), fwd=d.fwd_levels, bwd=d.bwd_levels,
@@ -188,35 +271,12 @@ def run_gpu(args):
         F.destroy()
         return info
 
-    for _ in range(args.warmup):
-        step()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    infos = []
-    clocks = ClockSampler(local)
-    if ws > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    for i in range(args.steps):
-        flush.fill_(float(i))
-        ev[i][0].record(stream)
-        infos.append(step())
-        ev[i][1].record(stream)
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    if ws > 1:
-        torch.distributed.barrier()
-    step_ms = [a.elapsed_time(b_) for a, b_ in ev]
-    ms = statistics.mean(step_ms)
+    timer = Timer(torch, dev, stream)
+    ms, infos, clk = timer.run(step, args.steps, args.warmup, ws, local)
     hops = statistics.mean(i["hops"] for i in infos)
     walk_ms = statistics.mean(i["phase"][1] for i in infos)
     build_ms = statistics.mean(i["phase"][7] for i in infos)
     solve_ms = statistics.mean(i["solve_ms"] for i in infos)
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
 
     # end to end through the C ABI with host buffers: H2D of A and b from
     # pinned memory, build, solve, D2H of x, every step
@@ -231,56 +291,51 @@ def run_gpu(args):
     d2h = hx.numel() * hx.element_size()
     e2e_ms = []
     for i in range(max(1, args.steps)):
-        flush.fill_(float(i))
+        timer.flush.fill_(float(i))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for d_, h_ in zip(dA2, hA):
             d_.copy_(h_, non_blocking=True)
         db2.copy_(hb, non_blocking=True)
         F = P.rw_build_factor(ctx, A2, walks, seed, drop)
-        P.pcg_solve(ctx, A2, F, db2, dx2, tol, 2000)
+        P.pcg_solve(ctx, A2, F, db2, dx2, tol, 3000, prec)
         hx.copy_(dx2, non_blocking=True)
         torch.cuda.synchronize()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
         F.destroy()
     e2e = statistics.mean(e2e_ms)
 
+    extra = {}
+    if mixed:
+        # the same factor solved in FP64 (untimed comparison run): error of the
+        # FP32 solution, iteration counts and solve times of both
+        F = P.rw_build_factor(ctx, dA, walks, seed, drop)
+        x32 = torch.zeros_like(db)
+        x64 = torch.zeros_like(db)
+        _, st32, it32, rel32 = P.pcg_solve(ctx, dA, F, db, x32, tol, 3000, P.RW_FP32_MIXED)
+        _, st64, it64, rel64 = P.pcg_solve(ctx, dA, F, db, x64, tol, 3000, P.RW_FP64)
+        err = float(torch.linalg.norm(x32 - x64) / torch.linalg.norm(x64))
+        extra["fp32_vs_fp64"] = {"rel_error_x": err, "iters_fp32": it32.tolist(), "iters_fp64": it64.tolist(),
+                                 "rel_residual_fp32": rel32.tolist(), "rel_residual_fp64": rel64.tolist(),
+                                 "pcg_s_fp32": st32.solve_ms * 1e-3, "pcg_s_fp64": st64.solve_ms * 1e-3}
+        F.destroy()
+    ctx.close()
     if rank != 0:
         return
     peaks, peak_kind = _peaks()
-    walks_total = infos[-1]["walks"]
-    nnz_y = infos[-1]["nnz"]
-    # algorithmic bytes of the walk kernel: per hop one 32-byte sector of
-    # thresholds (degree <= 6 here) + one sector for the chosen successor; per
-    # walk one 8-byte record
-    alg_bytes = 64.0 * hops + 8.0 * walks_total
-    achieved = alg_bytes / (walk_ms * 1e-3) / 1e9
-    walk_roof = {"kernel": "k_walk", "bound": "hbm", "achieved": achieved,
-                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-                 "traffic": None, "ms_per_launch": walk_ms}
-    # triangular solves: per application of the preconditioner the factor
-    # (12 B per stored entry, twice: Y and Y^T) and the vectors (8 B x nrhs x
-    # n read and written per solve) must be touched once
-    napply = statistics.mean(len(i["iters"]) and max(i["iters"]) for i in infos)
+    walk_roof = _walk_roofline(peaks, hops, infos[-1]["walks"], walk_ms)
+    napply = statistics.mean(max(i["iters"]) for i in infos)
     tri_ms = statistics.mean(i["bwd_ms"] + i["fwd_ms"] for i in infos)
-    applies = napply  # one application per iteration (the first before the loop, none after the last)
-    tri_bytes = applies * (2 * 12.0 * nnz_y + 2 * 3 * 8.0 * nrhs * A.n)
-    tri_achieved = tri_bytes / (tri_ms * 1e-3) / 1e9 if tri_ms > 0 else 0.0
-    solve_roof = {"kernel": "k_thin/k_wide (triangular solves)", "bound": "hbm",
-                  "achieved": tri_achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                  "frac": tri_achieved / peaks["hbm_gbs"], "traffic": None,
-                  "ms_per_step": tri_ms,
-                  "note": "latency-bound: dependency DAG depth x dependent memory round trips"}
+    solve_roof = _solve_roofline(peaks, napply, infos[-1]["nnz"], A.n, nrhs, tri_ms,
+                                 4.0 if mixed else 8.0, 8.0 if mixed else 12.0)
     dominant = solve_roof if tri_ms > walk_ms else walk_roof
-    line = {
-        "metric": METRIC, "value": hops * ws / (ms * 1e-3), "unit": "hops/s",
-        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
-        "config": {"workload": W.CONFIGS[WORKLOAD]["name"], "n": A.n, "nnz": A.nnz,
-                   "walks_per_row": walks, "drop_tol": drop, "nrhs": nrhs, "pcg_tol": tol,
-                   "precision": "fp64", "l2": "flushed between steps (512 MB write)",
-                   "parallelism": f"replicas x{ws}"},
+    line = _base_line(args, ws, ms, "f32-mixed" if mixed else "f64",
+                      {"workload": W.CONFIGS[args.workload]["name"], "n": A.n, "nnz": A.nnz,
+                       "walks_per_row": walks, "drop_tol": drop, "nrhs": nrhs, "pcg_tol": tol,
+                       "precision": cfg["precision"], "l2": "flushed between steps (512 MB write)",
+                       "parallelism": f"replicas x{ws}"})
+    line.update({
+        "value": hops * ws / (ms * 1e-3), "unit": "hops/s", "higher_is_better": True,
         "factor_build_s": build_ms * 1e-3, "pcg_s": solve_ms * 1e-3,
         "walk_kernel_hops_per_s": hops / (walk_ms * 1e-3),
         "pcg_iterations": infos[-1]["iters"], "pcg_rel_residual": infos[-1]["rel"],
@@ -296,10 +351,207 @@ def run_gpu(args):
         "e2e": {"value": hops * ws / (e2e * 1e-3), "unit": "hops/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e},
         "gpu_launches": infos[-1]["launches"],
-    }
+    })
+    line.update(extra)
     if not args.no_cpu_baseline and ws == 1:
-        line["cpu_baseline"] = cpu_oracle_sample(cfg)
+        line["cpu_baseline"] = cpu_oracle_sample(A, walks, seed, drop,
+                                                 f"the {W.CONFIGS[args.workload]['name']} workload")
     print(json.dumps(line), flush=True)
+
+
+def run_gpu_batched(args, P, torch, dev, stream, ws, rank, local):
+    """Workload 4: 256 matrices, one walk launch, one block-diagonal PCG."""
+    cfg = W.make_config(4, nmat=args.nmat)
+    As, bs = cfg["A"], cfg["b"]
+    walks, drop, tol = cfg["walks"], cfg["drop_tol"], cfg["tol"]
+    nmat = len(As)
+    seeds = [cfg["walk_seed"] + 7919 * m for m in range(nmat)]
+    nrhs = bs[0].shape[1]
+    ctx = P.Context(stream=stream)
+    dAs = [P.CSR.from_host(A, device=dev) for A in As]
+    dbs = [torch.as_tensor(b, device=dev) for b in bs]
+    dxs = [torch.zeros_like(b) for b in dbs]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+
+    def step():
+        ev[0].record(stream)
+        Fs = P.rw_build_factor_batched(ctx, dAs, walks, seeds, drop)
+        ev[1].record(stream)
+        B = P.Batch(ctx, dAs, Fs)
+        ev[2].record(stream)
+        rc, st, its, rel = P.pcg_solve_batch(ctx, B, dbs, dxs, tol, 3000)
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        d0 = Fs[0].desc
+        info = dict(hops=sum(int(F.desc.total_hops) for F in Fs), walks=sum(int(F.desc.total_walks) for F in Fs),
+                    nnz=sum(int(F.desc.nnz) for F in Fs), walk_ms=d0.phase_ms[1],
+                    build_ms=ev[0].elapsed_time(ev[1]), batch_ms=ev[1].elapsed_time(ev[2]),
+                    pcg_ms=ev[2].elapsed_time(ev[3]), iters=its, rel=float(rel.max()), rc=rc,
+                    info=B.info(), launches=int(d0.kernel_launches) + int(st[0].kernel_launches))
+        B.destroy()
+        for F in Fs:
+            F.destroy()
+        return info
+
+    timer = Timer(torch, dev, stream)
+    ms, infos, clk = timer.run(step, args.steps, args.warmup, ws, local)
+    hops = statistics.mean(i["hops"] for i in infos)
+    last = infos[-1]
+    ctx.close()
+    if rank != 0:
+        return
+    peaks, peak_kind = _peaks()
+    walk_roof = _walk_roofline(peaks, hops, last["walks"], last["walk_ms"], 96.0)
+    line = _base_line(args, ws, ms, "f64",
+                      {"workload": W.CONFIGS[4]["name"], "nmat": nmat, "n_total": sum(A.n for A in As),
+                       "nnz_total": sum(A.nnz for A in As), "walks_per_row": walks, "drop_tol": drop,
+                       "nrhs": nrhs, "pcg_tol": tol, "precision": "fp64", "graphs": True,
+                       "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{ws}"})
+    its = last["iters"]
+    line.update({
+        "value": hops * ws / (ms * 1e-3), "unit": "hops/s", "higher_is_better": True,
+        "factor_build_s": statistics.mean(i["build_ms"] for i in infos) * 1e-3,
+        "batch_create_s": statistics.mean(i["batch_ms"] for i in infos) * 1e-3,
+        "pcg_s": statistics.mean(i["pcg_ms"] for i in infos) * 1e-3,
+        "walk_kernel_hops_per_s": hops / (last["walk_ms"] * 1e-3) if last["walk_ms"] > 0 else None,
+        "pcg_iterations": {"max": int(its.max()), "median": float(np.median(its)), "min": int(its.min())},
+        "pcg_rel_residual_max": last["rel"], "factor_nnz_total": last["nnz"], "batch": last["info"],
+        "roofline": dict(walk_roof, peak_kind=peak_kind),
+        "clocks": clk,
+        "gpu_launches": last["launches"],
+    })
+    if not args.no_cpu_baseline and ws == 1:
+        line["cpu_baseline"] = _oracle_sample_for(4, cfg, 12.0, 2024)
+    print(json.dumps(line), flush=True)
+
+
+def train_budget_model(P, torch, ctx, dev, ninst, edge, epochs, pilot_walks=64):
+    """Features and pilot-walk labels of `ninst` training instances (seeds
+    100 + j), then Adam training; returns the model and a summary."""
+    feats, labels, masks = [], [], []
+    t0 = time.time()
+    for j in range(ninst):
+        A = W.training_instance(j, edge=edge)
+        dA = P.CSR.from_host(A, device=dev)
+        f = torch.zeros((A.n, 16), device=dev)
+        P.rw_row_features(ctx, dA, f)
+        out = [torch.zeros(A.n, device=dev) for _ in range(4)]
+        P.rw_pilot_stats(ctx, dA, pilot_walks, 1000 + j, *out)
+        feats.append(f)
+        labels.append(out[2])
+        masks.append(out[3])
+    F = torch.cat(feats)
+    Y = torch.cat(labels)
+    Mk = torch.cat(masks)
+    t_data = time.time() - t0
+    M = P.Mlp(ctx, seed=0)
+    t0 = time.time()
+    losses = P.rw_mlp_train(ctx, M, F, Y, Mk, epochs=epochs, batch=4096, lr=2e-3, seed=1)
+    torch.cuda.synchronize()
+    t_train = time.time() - t0
+    yv = Y[Mk > 0]
+    return M, {"instances": ninst, "edge": edge, "rows": int(yv.numel()), "epochs": epochs,
+               "pilot_walks": pilot_walks, "data_s": t_data, "train_s": t_train,
+               "loss_first": float(losses[0]), "loss_last": float(losses[-1]),
+               "label_var": float(yv.var()), "r2": 1.0 - float(losses[-1]) / float(yv.var())}
+
+
+def run_gpu_learned(args, P, torch, dev, stream, ws, rank, local):
+    """Workload 5: learned budget + FP32 on the batched engine vs plain."""
+    cfg = W.make_config(5, scale=args.scale)
+    A, b = cfg["A"], cfg["b"]
+    drop, tol, seed = cfg["drop_tol"], cfg["tol"], cfg["walk_seed"]
+    ctx = P.Context(stream=stream)
+    M, train = train_budget_model(P, torch, ctx, dev, args.train_instances, args.train_edge, args.epochs)
+    dA = P.CSR.from_host(A, device=dev)
+    db = torch.as_tensor(b, device=dev)
+    dx = torch.zeros_like(db)
+    budget = torch.zeros(A.n, dtype=torch.int32, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+
+    def learned():
+        ev[0].record(stream)
+        P.rw_budget_predict(ctx, dA, M, 300.0, 20, budget)
+        F = P.rw_build_factor_budget(ctx, dA, budget, seed, drop)
+        ev[1].record(stream)
+        B = P.Batch(ctx, [dA], [F])
+        rc, st, its, rel = P.pcg_solve_batch(ctx, B, [db], [dx], tol, 3000, P.RW_FP32_MIXED)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        d = F.desc
+        info = dict(hops=int(d.total_hops), walks=int(d.total_walks), nnz=int(d.nnz),
+                    build_ms=ev[0].elapsed_time(ev[1]), pcg_ms=ev[1].elapsed_time(ev[2]),
+                    iters=int(its.max()), rel=float(rel.max()), rc=rc, walk_ms=d.phase_ms[1],
+                    launches=int(d.kernel_launches) + int(st[0].kernel_launches))
+        B.destroy()
+        F.destroy()
+        return info
+
+    def plain():
+        ev[0].record(stream)
+        F = P.rw_build_factor(ctx, dA, 300, seed, drop)
+        ev[1].record(stream)
+        rc, st, its, rel = P.pcg_solve(ctx, dA, F, db, dx, tol, 3000, P.RW_FP64)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        d = F.desc
+        info = dict(hops=int(d.total_hops), walks=int(d.total_walks), nnz=int(d.nnz),
+                    build_ms=ev[0].elapsed_time(ev[1]), pcg_ms=ev[1].elapsed_time(ev[2]),
+                    iters=int(its.max()), rel=float(rel.max()), rc=rc, walk_ms=d.phase_ms[1],
+                    launches=int(d.kernel_launches) + int(st.kernel_launches))
+        F.destroy()
+        return info
+
+    timer = Timer(torch, dev, stream)
+    ms_l, inf_l, clk = timer.run(learned, args.steps, args.warmup, ws, local)
+    ms_p, inf_p, clk_p = timer.run(plain, args.steps, args.warmup, ws, local)
+    M.destroy()
+    ctx.close()
+    if rank != 0:
+        return
+    peaks, peak_kind = _peaks()
+    L, Pn = inf_l[-1], inf_p[-1]
+    walk_roof = _walk_roofline(peaks, L["hops"], L["walks"], L["walk_ms"], 192.0)
+    name = W.CONFIGS[5]["name"] + ("" if args.scale == 1.0 else f" (edge scale {args.scale})")
+    line = _base_line(args, ws, ms_l, "f32-mixed",
+                      {"workload": name, "n": A.n, "nnz": A.nnz, "mean_budget": 300, "min_budget": 20,
+                       "drop_tol": drop, "nrhs": 1, "pcg_tol": tol,
+                       "learned": "predict + build + FP32 PCG (batched engine, graphs)",
+                       "plain": "uniform 300 + FP64 PCG", "l2": "flushed between steps (512 MB write)",
+                       "parallelism": f"replicas x{ws}"})
+    line.update({
+        "value": ms_l * 1e-3, "unit": "s to 1e-6 (build + solve)", "higher_is_better": False,
+        "plain_s": ms_p * 1e-3, "speedup_vs_plain": ms_p / ms_l,
+        "learned": {"build_s": statistics.mean(i["build_ms"] for i in inf_l) * 1e-3,
+                    "pcg_s": statistics.mean(i["pcg_ms"] for i in inf_l) * 1e-3, "iterations": L["iters"],
+                    "rel_residual": L["rel"], "factor_nnz": L["nnz"], "walks": L["walks"], "hops": L["hops"]},
+        "plain": {"build_s": statistics.mean(i["build_ms"] for i in inf_p) * 1e-3,
+                  "pcg_s": statistics.mean(i["pcg_ms"] for i in inf_p) * 1e-3, "iterations": Pn["iters"],
+                  "rel_residual": Pn["rel"], "factor_nnz": Pn["nnz"], "walks": Pn["walks"], "hops": Pn["hops"]},
+        "training": train,
+        "walk_kernel_hops_per_s": L["hops"] / (L["walk_ms"] * 1e-3) if L["walk_ms"] > 0 else None,
+        "roofline": dict(walk_roof, peak_kind=peak_kind),
+        "clocks": clk, "clocks_plain": clk_p,
+        "gpu_launches": L["launches"],
+    })
+    if not args.no_cpu_baseline and ws == 1:
+        line["cpu_baseline"] = _oracle_sample_for(5, cfg, 12.0, 2024)
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args):
+    import torch
+    import paper_math_0609672_gb300 as P
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    if args.workload in (2, 3):
+        run_gpu_single(args, P, torch, dev, stream, ws, rank, local)
+    elif args.workload == 4:
+        run_gpu_batched(args, P, torch, dev, stream, ws, rank, local)
+    else:
+        run_gpu_learned(args, P, torch, dev, stream, ws, rank, local)
 
 
 def main():
@@ -308,7 +560,13 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", type=int, default=2, choices=[2, 3, 4, 5])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nmat", type=int, default=None, help="workload 4: number of matrices (default 256)")
+    ap.add_argument("--scale", type=float, default=1.0, help="workload 5: grid edge scale (default 1)")
+    ap.add_argument("--train-instances", type=int, default=50, help="workload 5: training instances")
+    ap.add_argument("--train-edge", type=int, default=64, help="workload 5: training grid edge")
+    ap.add_argument("--epochs", type=int, default=10, help="workload 5: training epochs")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -89,8 +89,14 @@ typedef struct {
     int32_t refine_every;    /* FP32 PCG: true-residual replacement period (default 50) */
     int32_t walk_blocks_per_sm; /* 0 = from the occupancy calculator */
     int32_t timing;          /* 1: record per-phase device times (default 1) */
-    int32_t solve_blocks_per_sm; /* triangular solves: 256-thread blocks per SM (0 = 2) */
+    int32_t solve_blocks_per_sm; /* wide-level solves: 512-thread blocks per SM (0 = 1) */
     int32_t graphs;          /* 1: batched PCG replays each iteration from a CUDA graph (default 1) */
+    int32_t wide_slices;     /* wide-level solves: entry slices per row (lanes per row = slices x
+                                right-hand sides, power of two <= 32); 0 = one row per warp */
+    int32_t spmv_slices;     /* SpMV: entry slices per row, as wide_slices; 0 = one row per warp */
+    int32_t cluster_width;   /* levels of at most this many rows (above the thin-run width) run on
+                                one thread-block cluster with hardware barriers; 0 = never */
+    int32_t cluster_size;    /* CTAs of that cluster (2..16; 0 = 16) */
 } rw_options;
 
 typedef struct rw_context rw_context;
@@ -218,8 +224,10 @@ rw_status pcg_solve_batched(rw_context* ctx, int32_t nmat, const rw_csr* As,
  * order, so every system follows the same iterates as pcg_solve on its own
  * matrix up to rounding.  With rw_options.graphs the iteration is captured
  * once in a CUDA graph and replayed; the host reads one flag word per
- * iteration.  The batch copies what it needs (it does not reference the
- * factors afterwards); its arrays are allocated through the context.
+ * iteration.  A batch of several matrices copies what it needs (it does not
+ * reference the matrices or factors afterwards); a batch of one matrix uses
+ * that matrix and factor in place, so both must outlive it.  Its arrays are
+ * allocated through the context.
  * Limits: sum of n and sum of nnz(A) below 2^31. */
 typedef struct rw_batch rw_batch;
 rw_status rw_batch_create(rw_context* ctx, int32_t nmat, const rw_csr* As, const rw_factor* const* Fs,

@@ -58,7 +58,9 @@ class rw_csr_t(ctypes.Structure):
 class rw_options_t(ctypes.Structure):
     _fields_ = [("max_steps", _u64), ("keep_records", _i32), ("record_lengths", _i32),
                 ("store_fp32", _i32), ("refine_every", _i32), ("walk_blocks_per_sm", _i32),
-                ("timing", _i32), ("solve_blocks_per_sm", _i32), ("graphs", _i32)]
+                ("timing", _i32), ("solve_blocks_per_sm", _i32), ("graphs", _i32),
+                ("wide_slices", _i32), ("spmv_slices", _i32), ("cluster_width", _i32),
+                ("cluster_size", _i32)]
 
 
 class rw_factor_desc_t(ctypes.Structure):

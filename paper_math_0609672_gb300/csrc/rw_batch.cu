@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(256) k_seg_update_xr(int32_t N, int nrhs, cons
                                                        const T* __restrict__ p, const T* __restrict__ q) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const double* al = alpha + (size_t)rowseg[i] * nrhs;
+        const double* al = alpha + (rowseg ? (size_t)rowseg[i] * nrhs : 0);
         for (int j = 0; j < nrhs; ++j) {
             const double a = al[j];
             if (a != 0.0) {
@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(256) k_seg_update_p(int32_t N, int nrhs, const
                                                       T* p) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const double* be = beta + (size_t)rowseg[i] * nrhs;
+        const double* be = beta + (rowseg ? (size_t)rowseg[i] * nrhs : 0);
         for (int j = 0; j < nrhs; ++j) {
             const size_t o = (size_t)i * nrhs + j;
             p[o] = (T)((double)z[o] + be[j] * (double)p[o]);
@@ -298,7 +298,7 @@ __global__ void k_seg_gather_b(int32_t N, int nrhs, const int32_t* __restrict__ 
                                double* b, T* r, double* x, DevStatus* st) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const int m = rowseg[i];
+        const int m = rowseg ? rowseg[i] : 0;
         const double* src = bs[m] + (size_t)(i - row0[m]) * nrhs;
         for (int j = 0; j < nrhs; ++j) {
             const double v = src[j];
@@ -315,7 +315,7 @@ __global__ void k_seg_scatter_x(int32_t N, int nrhs, const int32_t* __restrict__
                                 double* const* __restrict__ xs) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const int m = rowseg[i];
+        const int m = rowseg ? rowseg[i] : 0;
         double* dst = xs[m] + (size_t)(i - row0[m]) * nrhs;
         for (int j = 0; j < nrhs; ++j) dst[j] = x[(size_t)i * nrhs + j];
     }
@@ -341,7 +341,7 @@ struct rw_batch {
     int64_t nnzA = 0, nnzY = 0;
     std::vector<int32_t> row0_h;
     int32_t* row0 = nullptr;    // [nmat + 1]
-    int32_t* rowseg = nullptr;  // [N]
+    int32_t* rowseg = nullptr;  // [N] (NULL for a batch of one matrix)
     int32_t nchunks = 0;
     int32_t* chunk_row0 = nullptr;  // [nchunks + 1]
     int32_t* seg_chunk0 = nullptr;  // [nmat + 1]
@@ -366,6 +366,7 @@ struct rw_batch {
     int32_t fwd_depth = 0, bwd_depth = 0;
     rw::SolveSchedule fwd_sched, bwd_sched;
     unsigned* bar = nullptr;
+    bool refs = false;  // one matrix: the arrays and schedules are the caller's matrix and factor
     explicit rw_batch(rw_context* c) : ctx(c), pool(c) {}
 };
 
@@ -620,6 +621,66 @@ rw_status rw_batch_create(rw_context* ctx, int32_t nmat, const rw_csr* As, const
     };
     cudaStream_t s = ctx->stream;
     Pool sc(ctx);
+    if (nmat == 1) {
+        // a batch of one matrix uses the matrix and its factor in place (both
+        // must outlive it): no concatenation, the factor's own schedules
+        const rw_factor* F = Fs[0];
+        const rw_factor_desc& d = F->desc;
+        const int32_t n = As[0].n;
+        B->refs = true;
+        B->nmat = 1;
+        B->N = n;
+        B->nnzA = As[0].nnz;
+        B->nnzY = d.nnz;
+        B->row0_h = {0, n};
+        std::vector<int32_t> chunk_row0, seg_chunk0 = {0, 0};
+        for (int64_t c = 0; c < n; c += kChunkRows) chunk_row0.push_back((int32_t)c);
+        seg_chunk0[1] = (int32_t)chunk_row0.size();
+        B->nchunks = (int32_t)chunk_row0.size();
+        chunk_row0.push_back(n);
+        Pool& P = B->pool;
+        B->row0 = alloc_n<int32_t>(P, 2);
+        B->chunk_row0 = alloc_n<int32_t>(P, B->nchunks + 1);
+        B->seg_chunk0 = alloc_n<int32_t>(P, 2);
+        if (!B->row0 || !B->chunk_row0 || !B->seg_chunk0) return fail(RW_ERR_ALLOC);
+        rw_status rc;
+        if ((rc = check_cuda(cudaMemcpyAsync(B->row0, B->row0_h.data(), sizeof(int32_t) * 2, cudaMemcpyHostToDevice, s),
+                             "copy")) ||
+            (rc = check_cuda(cudaMemcpyAsync(B->chunk_row0, chunk_row0.data(), sizeof(int32_t) * chunk_row0.size(),
+                                             cudaMemcpyHostToDevice, s),
+                             "copy")) ||
+            (rc = check_cuda(cudaMemcpyAsync(B->seg_chunk0, seg_chunk0.data(), sizeof(int32_t) * 2,
+                                             cudaMemcpyHostToDevice, s),
+                             "copy")))
+            return fail(rc);
+        B->a_rp = const_cast<int32_t*>(As[0].row_ptr);
+        B->a_col = const_cast<int32_t*>(As[0].col);
+        B->a_val = const_cast<double*>(As[0].val);
+        B->y_rp = const_cast<int64_t*>(d.y_row_ptr);
+        B->y_col = const_cast<int32_t*>(d.y_col);
+        B->y_val = const_cast<double*>(d.y_val);
+        B->yt_rp = const_cast<int64_t*>(d.yt_row_ptr);
+        B->yt_col = const_cast<int32_t*>(d.yt_col);
+        B->yt_val = const_cast<double*>(d.yt_val);
+        B->d = const_cast<double*>(d.d);
+        B->y_val32 = const_cast<float*>(d.y_val32);
+        B->yt_val32 = const_cast<float*>(d.yt_val32);
+        B->d32 = const_cast<float*>(d.d32);
+        B->fwd_sched = F->fwd_sched;
+        B->bwd_sched = F->bwd_sched;
+        B->fwd_depth = d.fwd_levels;
+        B->bwd_depth = d.bwd_levels;
+        B->bar = F->bar;
+        if (d.y_val32 && n > 0) {
+            B->a_val32 = alloc_n<float>(P, B->nnzA);
+            if (!B->a_val32) return fail(RW_ERR_ALLOC);
+            launch_to_fp32_diff(n, As[0].row_ptr, As[0].col, As[0].val, B->a_val32, s, ctx->num_sms);
+            if ((rc = check_launch("batch fp32 operator"))) return fail(rc);
+        }
+        if ((rc = read_status(ctx, "batch create"))) return fail(rc);
+        *out = B;
+        return RW_OK;
+    }
     B->nmat = nmat;
     B->N = (int32_t)N;
     B->nnzA = nnzA;

@@ -126,30 +126,36 @@ __device__ __forceinline__ bool wait_gives_up(unsigned& spins, unsigned* timeout
     return (spins % kAbortPoll) == 0 && ld_relaxed_u32(timeout_flag) != 0u;
 }
 
-// Software grid barrier for a co-resident (cooperatively launched) grid.
-// bar[0] counts arrivals, bar[1] is the generation.  Every wait is bounded;
-// returns false when it gave up (the timeout flag is then set).
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, DevStatus* st) {
+// Software grid barrier for a co-resident (cooperatively launched) grid:
+// *count (zero at launch) only grows; barrier number `epoch` (1, 2, ...) is
+// passed once it reaches epoch * gridDim.x.  One thread per block arrives
+// with a release atomic (cumulative over the block's stores, ordered by the
+// preceding __syncthreads) and polls with acquire loads, so a barrier costs
+// about two L2 round trips and no reset.  Every wait is bounded; returns false
+// when it gave up (the timeout flag is then set).
+__device__ __forceinline__ void atom_add_release(unsigned* p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned epoch, DevStatus* st) {
     __shared__ int give_up;
     __syncthreads();
     if (threadIdx.x == 0) {
         give_up = 0;
-        const unsigned gen = ld_relaxed_u32(&bar[1]);
-        __threadfence();
-        if (atomicAdd(&bar[0], 1u) == gridDim.x - 1u) {
-            atomicExch(&bar[0], 0u);
-            __threadfence();
-            atomicAdd(&bar[1], 1u);
-        } else {
-            unsigned spins = 0;
-            while (ld_relaxed_u32(&bar[1]) == gen) {
-                if (wait_gives_up(spins, &st->timeout)) {
-                    give_up = 1;
-                    break;
-                }
+        const unsigned target = epoch * gridDim.x;
+        atom_add_release(count, 1u);
+        unsigned spins = 0;
+        while (ld_acquire_u32(count) < target) {
+            if (wait_gives_up(spins, &st->timeout)) {
+                give_up = 1;
+                break;
             }
         }
-        __threadfence();
     }
     __syncthreads();
     return give_up == 0;

@@ -14,8 +14,9 @@
 //     outside the run (already final); phase 2 walks the levels with a
 //     block barrier between them, keeping the run's x values in shared memory
 //     and the next level's entries prefetched in registers.
-//   wide run: level-synchronous over the whole co-resident grid, one warp
-//     per row, a software grid barrier between levels.
+//   wide run: level-synchronous over the whole co-resident grid, a group of
+//     lanes per row (one lane per right-hand side and entry slice), a
+//     software grid barrier between levels.
 // Every row sums its terms in a fixed order, so results do not depend on
 // timing.
 #include <algorithm>
@@ -373,76 +374,275 @@ struct WideParams {
     DevStatus* st;
 };
 
-template <typename T, int NR>
-__global__ void __launch_bounds__(256) k_wide(const WideParams<T> P) {
-    const int lane = (int)lane_id();
-    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    // the first row of this warp in the next level and its first 32 entries are
-    // loaded before the barrier that precedes that level
-    int32_t nrow = -1;
-    int64_t ns = 0, ne = 0;
-    int32_t nc = 0;
-    T ny = T(0);
-    auto prefetch = [&](int32_t l) {
-        nrow = -1;
-        if (l < P.lev_end) {
-            const int64_t pos = P.lptr[l] + gw;
-            if (pos < P.lptr[l + 1]) {
-                nrow = P.order[pos];
-                ns = P.rp[nrow];
-                ne = P.rp[nrow + 1];
-                const int64_t q = ns + lane;
-                nc = q < ne ? P.col[q] : 0;
-                ny = q < ne ? P.val[q] : T(0);
+// Wide and cluster runs: a group of G = NR * ES lanes per row, 32 / G rows
+// per warp.  Lane (es, j) of a group owns right-hand side j and entries
+// s + es, s + es + ES, ...: the NR values of x a row entry needs arrive in one
+// contiguous load, and only the ES entry slices are summed across lanes.
+//
+// A level's own chain after the barrier is one round of x loads; the row
+// structure it reads (position -> row -> row pointers -> first entries) does
+// not depend on x and is loaded two levels ahead, so its dependent loads
+// overlap the levels in between.
+constexpr int kPreEntries = 4;  // entries per lane held ahead
+
+template <typename T>
+struct RowPre {
+    int32_t row;  // -1: no row for this group in that level
+    int64_t s, e;
+    int32_t c[kPreEntries];
+    T y[kPreEntries];
+};
+
+template <typename T, int NR, int ES>
+struct RowGroup {
+    static constexpr int G = NR * ES;
+    static constexpr int R = 32 / G;
+    int j, es;
+    unsigned gmask;
+    bool jok;
+    __device__ RowGroup(int lane, int nrhs) {
+        const int gl = lane % G;
+        j = gl % NR;
+        es = gl / NR;
+        gmask = G == 32 ? kFull : (((1u << G) - 1u) << (lane - gl));
+        jok = j < nrhs;
+    }
+    __device__ __forceinline__ void load(const WideParams<T>& P, int32_t row, RowPre<T>& R0) const {
+        R0.row = row;
+        R0.s = P.rp[row];
+        R0.e = P.rp[row + 1];
+#pragma unroll
+        for (int u = 0; u < kPreEntries; ++u) {
+            const int64_t q = R0.s + es + (int64_t)u * ES;
+            R0.c[u] = q < R0.e ? P.col[q] : 0;
+            R0.y[u] = q < R0.e ? P.val[q] : T(0);
+        }
+    }
+    // x_row = rhs_row / scale_row - sum_q val_q x_{col_q}
+    __device__ __forceinline__ void row(const WideParams<T>& P, const RowPre<T>& R0) const {
+        const T* __restrict__ x = P.x;
+        const int nr = P.nrhs;
+        T acc = T(0);
+        T v[kPreEntries];
+#pragma unroll
+        for (int u = 0; u < kPreEntries; ++u)
+            v[u] = (jok && R0.s + es + (int64_t)u * ES < R0.e) ? __ldcg(x + (size_t)R0.c[u] * nr + j) : T(0);
+#pragma unroll
+        for (int u = 0; u < kPreEntries; ++u) acc += R0.y[u] * v[u];
+        int64_t q = R0.s + es + (int64_t)kPreEntries * ES;
+        for (; q + 3 * ES < R0.e; q += 4 * ES) {
+            int32_t c[4];
+            T y[4], w[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                c[u] = P.col[q + u * ES];
+                y[u] = P.val[q + u * ES];
             }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) w[u] = jok ? __ldcg(x + (size_t)c[u] * nr + j) : T(0);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc += y[u] * w[u];
+        }
+        for (; q < R0.e; q += ES) {
+            const int32_t c = P.col[q];
+            const T y = P.val[q];
+            if (jok) acc += y * __ldcg(x + (size_t)c * nr + j);
+        }
+#pragma unroll
+        for (int o = NR; o < G; o <<= 1) acc += __shfl_xor_sync(gmask, acc, o);
+        if (es == 0 && jok) {
+            T b = P.rhs[(size_t)R0.row * nr + j];
+            if (P.scale) b = b / P.scale[R0.row];
+            __stcg(P.x + (size_t)R0.row * nr + j, b - acc);
+        }
+    }
+};
+
+// The levels of a run over `ngroups` row groups numbered from gid, with a
+// barrier between levels.  Returns false if a barrier gave up.
+template <typename T, int NR, int ES, typename Barrier>
+__device__ __forceinline__ bool run_levels(const WideParams<T>& P, int64_t gid, int64_t ngroups,
+                                           const RowGroup<T, NR, ES>& g, Barrier barrier) {
+    RowPre<T> pre[2];
+    auto prefetch = [&](int32_t l, RowPre<T>& R0) {
+        R0.row = -1;
+        if (l < P.lev_end) {
+            const int64_t pos = P.lptr[l] + gid;
+            if (pos < P.lptr[l + 1]) g.load(P, P.order[pos], R0);
         }
     };
-    prefetch(P.lev_begin);
+    prefetch(P.lev_begin, pre[0]);
+    prefetch(P.lev_begin + 1, pre[1]);
     for (int32_t l = P.lev_begin; l < P.lev_end; ++l) {
-        const int64_t lb = P.lptr[l], le = P.lptr[l + 1];
-        const int32_t row0 = nrow;
-        const int64_t s0 = ns, e0 = ne;
-        const int32_t c0 = nc;
-        const T y0 = ny;
-        for (int64_t pos = lb + gw; pos < le; pos += nw) {
-            int32_t row;
-            int64_t s, e;
-            if (pos == lb + gw) {
-                row = row0;
-                s = s0;
-                e = e0;
-            } else {
-                row = P.order[pos];
-                s = P.rp[row];
-                e = P.rp[row + 1];
-            }
-            T acc[NR];
-#pragma unroll
-            for (int j = 0; j < NR; ++j) acc[j] = T(0);
-            for (int64_t q = s + lane; q < e; q += 32) {
-                const bool first = pos == lb + gw && q == s + lane;
-                const int32_t c = first ? c0 : P.col[q];
-                const T y = first ? y0 : P.val[q];
-#pragma unroll
-                for (int j = 0; j < NR; ++j)
-                    if (j < P.nrhs) acc[j] += y * __ldcg(P.x + (size_t)c * P.nrhs + j);
-            }
-            const T mine = warp_sums<T, NR>(acc);
-            if (lane < P.nrhs && lane < NR) {
-                T b = P.rhs[(size_t)row * P.nrhs + lane];
-                if (P.scale) b = b / P.scale[row];
-                __stcg(P.x + (size_t)row * P.nrhs + lane, b - mine);
+        const RowPre<T> cur = pre[0];
+        pre[0] = pre[1];
+        prefetch(l + 2, pre[1]);  // in flight during this level and the next
+        if (cur.row >= 0) {
+            g.row(P, cur);
+            const int64_t le = P.lptr[l + 1];
+            for (int64_t pos = P.lptr[l] + gid + ngroups; pos < le; pos += ngroups) {
+                RowPre<T> more;
+                g.load(P, P.order[pos], more);
+                g.row(P, more);
             }
         }
-        prefetch(l + 1);
-        if (l + 1 < P.lev_end && !grid_barrier(P.bar, P.st)) return;
+        if (l + 1 < P.lev_end && !barrier()) return false;
     }
+    return true;
+}
+
+// Wide run: the whole co-resident grid, a software grid barrier between levels.
+constexpr int kWideThreads = 512;  // one block per SM: fewer arrivals per grid barrier
+
+template <typename T, int NR, int ES>
+__global__ void __launch_bounds__(kWideThreads, 1) k_wide(const WideParams<T> P) {
+    const RowGroup<T, NR, ES> g((int)lane_id(), P.nrhs);
+    constexpr int R = RowGroup<T, NR, ES>::R;
+    const int64_t gid = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * R + lane_id() / (32 / R);
+    const int64_t ngroups = (((int64_t)gridDim.x * blockDim.x) >> 5) * R;
+    unsigned epoch = 0;
+    run_levels<T, NR, ES>(P, gid, ngroups, g, [&]() { return grid_barrier(P.bar, ++epoch, P.st); });
+}
+
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ unsigned cluster_size() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+
+// Cluster run: one thread-block cluster (launched as the whole grid); the
+// hardware cluster barrier with release / acquire semantics orders each
+// level's x stores before the next level's loads (both through L2).  It waits
+// only for the CTAs of the cluster, which the hardware schedules together.
+template <typename T, int NR, int ES>
+__global__ void __launch_bounds__(1024, 1) k_cluster(const WideParams<T> P) {
+    const RowGroup<T, NR, ES> g((int)lane_id(), P.nrhs);
+    constexpr int R = RowGroup<T, NR, ES>::R;
+    const int64_t warps = blockDim.x >> 5;
+    const int64_t gid = ((int64_t)cluster_rank() * warps + (threadIdx.x >> 5)) * R + lane_id() / (32 / R);
+    const int64_t ngroups = (int64_t)cluster_size() * warps * R;
+    run_levels<T, NR, ES>(P, gid, ngroups, g, []() {
+        asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+        asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+        return true;
+    });
 }
 
 // ---------------------------------------------------------------------------
 // Host dispatch
 // ---------------------------------------------------------------------------
+// Entry slices of the lane groups: an explicit option, else 32 / NR (one
+// row per warp), as a power of two with NR * ES <= 32.
+static int lane_slices(int opt, int NR) {
+    const int es = opt > 0 ? opt : 32 / NR;
+    int p = 1;
+    while (p * 2 <= es && p * 2 * NR <= 32) p *= 2;
+    return p;
+}
+
+template <typename T, int NR, int ES>
+static rw_status launch_wide(rw_context* ctx, const SolveSchedule& S, int32_t lev_begin, int32_t lev_end,
+                             const int64_t* rp, const int32_t* col, const T* val, const T* rhs, const T* scale,
+                             T* x, int nrhs, unsigned* bar) {
+    if constexpr (NR * ES > 32) {
+        return RW_ERR_ARG;
+    } else {
+        cudaStream_t s = ctx->stream;
+        static int per_sm = -1;
+        if (per_sm < 0) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wide<T, NR, ES>, kWideThreads, 0);
+            if (per_sm < 1) per_sm = 1;
+        }
+        rw_status rc;
+        if ((rc = check_cuda(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s), "memset"))) return rc;
+        const int bps = ctx->opt.solve_blocks_per_sm > 0 ? ctx->opt.solve_blocks_per_sm : 1;
+        int64_t blocks = (int64_t)std::min(per_sm, bps) * ctx->num_sms;
+        int64_t maxw = 0;
+        for (int32_t l = lev_begin; l < lev_end; ++l) maxw = std::max(maxw, S.lptr_h[l + 1] - S.lptr_h[l]);
+        constexpr int64_t rows_per_block = (kWideThreads / 32) * (32 / (NR * ES));
+        const int64_t need = (maxw + rows_per_block - 1) / rows_per_block;
+        if (blocks > need) blocks = need;
+        if (blocks < 1) blocks = 1;
+        WideParams<T> P{lev_begin, lev_end, S.lptr, S.order, rp, col, val, rhs, scale, x, nrhs, bar, ctx->d_status};
+        void* args[] = {(void*)&P};
+        RW_COUNT_LAUNCH();
+        return check_cuda(cudaLaunchCooperativeKernel((const void*)k_wide<T, NR, ES>, dim3((unsigned)blocks),
+                                                      dim3(kWideThreads), args, 0, s),
+                          "wide-run solve");
+    }
+}
+
+template <typename T, int NR, int ES>
+static rw_status launch_cluster(rw_context* ctx, const SolveSchedule& S, int32_t lev_begin, int32_t lev_end,
+                                const int64_t* rp, const int32_t* col, const T* val, const T* rhs,
+                                const T* scale, T* x, int nrhs, unsigned* bar, int csize) {
+    if constexpr (NR * ES > 32) {
+        return RW_ERR_ARG;
+    } else {
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_cluster<T, NR, ES>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            attr = true;
+        }
+        WideParams<T> P{lev_begin, lev_end, S.lptr, S.order, rp, col, val, rhs, scale, x, nrhs, bar, ctx->d_status};
+        cudaLaunchConfig_t cfg = {};
+        cfg.blockDim = dim3(NR >= 8 ? 512u : 1024u);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = ctx->stream;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        // the largest size up to csize that the device can place (once per size)
+        static int placeable[17] = {};
+        if (csize < 1 || csize > 16) csize = 16;
+        while (csize > 1) {
+            if (placeable[csize] == 0) {
+                cfg.gridDim = dim3((unsigned)csize);
+                at[0].val.clusterDim.x = (unsigned)csize;
+                int nc = 0;
+                placeable[csize] =
+                    (cudaOccupancyMaxActiveClusters(&nc, k_cluster<T, NR, ES>, &cfg) == cudaSuccess && nc >= 1) ? 1 : -1;
+                cudaGetLastError();
+            }
+            if (placeable[csize] > 0) break;
+            csize >>= 1;
+        }
+        cfg.gridDim = dim3((unsigned)csize);
+        at[0].val.clusterDim.x = (unsigned)csize;
+        RW_COUNT_LAUNCH();
+        return check_cuda(cudaLaunchKernelEx(&cfg, k_cluster<T, NR, ES>, P), "cluster-run solve");
+    }
+}
+
+template <typename T, int NR, int ES>
+static rw_status launch_nonthin(rw_context* ctx, const SolveSchedule& S, const SolveRun& run, const int64_t* rp,
+                                const int32_t* col, const T* val, const T* rhs, const T* scale, T* x, int nrhs,
+                                unsigned* bar) {
+    // consecutive levels up to the cluster width go to one cluster, the rest
+    // to the whole grid
+    const int64_t cw = ctx->opt.cluster_width > 0 ? ctx->opt.cluster_width : 0;
+    const int csize = ctx->opt.cluster_size > 0 ? ctx->opt.cluster_size : 16;
+    int32_t l = run.lev_begin;
+    while (l < run.lev_end) {
+        const bool narrow = cw > 0 && S.lptr_h[l + 1] - S.lptr_h[l] <= cw;
+        int32_t e = l + 1;
+        while (e < run.lev_end && (cw > 0 && S.lptr_h[e + 1] - S.lptr_h[e] <= cw) == narrow) ++e;
+        rw_status rc = narrow ? launch_cluster<T, NR, ES>(ctx, S, l, e, rp, col, val, rhs, scale, x, nrhs, bar, csize)
+                              : launch_wide<T, NR, ES>(ctx, S, l, e, rp, col, val, rhs, scale, x, nrhs, bar);
+        if (rc) return rc;
+        l = e;
+    }
+    return RW_OK;
+}
+
 template <typename T, int NR>
 static rw_status solve_runs_nr(rw_context* ctx, const SolveSchedule& S, const int64_t* rp,
                                const int32_t* col, const T* val, const T* tval, const T* rhs,
@@ -450,17 +650,13 @@ static rw_status solve_runs_nr(rw_context* ctx, const SolveSchedule& S, const in
     cudaStream_t s = ctx->stream;
     T* ext = reinterpret_cast<T*>(bar + 64);  // the factor's solve workspace (see build_factor)
     rw_status rc;
-    static int wide_per_sm = -1;
-    if (wide_per_sm < 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&wide_per_sm, k_wide<T, NR>, 256, 0);
-        if (wide_per_sm < 1) wide_per_sm = 1;
-    }
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_thin<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kThinSmemBudget + 16 * 1024);
         attr = true;
     }
+    const int es = lane_slices(ctx->opt.wide_slices, NR);
     for (const SolveRun& run : S.runs) {
         const int64_t rows = run.pos_end - run.pos_begin;
         if (rows == 0) continue;
@@ -478,24 +674,15 @@ static rw_status solve_runs_nr(rw_context* ctx, const SolveSchedule& S, const in
             k_thin<T, NR><<<1, kThinThreads, smem, s>>>(P);
             if ((rc = check_launch("thin-run solve"))) return rc;
         } else {
-            if ((rc = check_cuda(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s), "memset")))
-                return rc;
-            int64_t blocks = (int64_t)std::min(wide_per_sm, 2) * ctx->num_sms;
-            int64_t maxw = 0;
-            for (int32_t l = run.lev_begin; l < run.lev_end; ++l)
-                maxw = std::max(maxw, S.lptr_h[l + 1] - S.lptr_h[l]);
-            const int64_t need = (maxw + 7) / 8;
-            if (blocks > need) blocks = need;
-            if (blocks < 1) blocks = 1;
-            WideParams<T> P{run.lev_begin, run.lev_end, S.lptr, S.order, rp, col, val, rhs, scale,
-                            x, nrhs, bar, ctx->d_status};
-            void* args[] = {(void*)&P};
-            RW_COUNT_LAUNCH();
-            if ((rc = check_cuda(cudaLaunchCooperativeKernel((const void*)k_wide<T, NR>,
-                                                             dim3((unsigned)blocks), dim3(256),
-                                                             args, 0, s),
-                                 "wide-run solve")))
-                return rc;
+            switch (es) {
+                case 1: rc = launch_nonthin<T, NR, 1>(ctx, S, run, rp, col, val, rhs, scale, x, nrhs, bar); break;
+                case 2: rc = launch_nonthin<T, NR, 2>(ctx, S, run, rp, col, val, rhs, scale, x, nrhs, bar); break;
+                case 4: rc = launch_nonthin<T, NR, 4>(ctx, S, run, rp, col, val, rhs, scale, x, nrhs, bar); break;
+                case 8: rc = launch_nonthin<T, NR, 8>(ctx, S, run, rp, col, val, rhs, scale, x, nrhs, bar); break;
+                case 16: rc = launch_nonthin<T, NR, 16>(ctx, S, run, rp, col, val, rhs, scale, x, nrhs, bar); break;
+                default: rc = launch_nonthin<T, NR, 32>(ctx, S, run, rp, col, val, rhs, scale, x, nrhs, bar); break;
+            }
+            if (rc) return rc;
         }
     }
     return RW_OK;

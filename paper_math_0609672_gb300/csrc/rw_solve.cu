@@ -31,57 +31,48 @@ constexpr int kDotParts = 1024;  // blocks of the dot-product producing kernels
 // so the operator keeps the near-null space of a weakly grounded matrix
 // (rounding A_ii itself would move a row sum by 2^-24 A_ii).
 // ---------------------------------------------------------------------------
-template <typename TA, typename TV, int NR, int GS, bool DIFF>
+template <typename TA, typename TV, int NR, int ES, bool DIFF>
 __global__ void __launch_bounds__(256) k_spmv(int32_t n, const int32_t* __restrict__ rp,
                                               const int32_t* __restrict__ col,
                                               const TA* __restrict__ val, const TV* __restrict__ x,
                                               TV* __restrict__ y, int nrhs, double* part) {
+    // a group of G = NR * ES lanes per row: lane (es, j) owns right-hand side j
+    // and entries s + es, s + es + ES, ... (one contiguous load of NR values per
+    // entry); the ES entry slices are summed across lanes
+    constexpr int G = NR * ES;
+    constexpr int R = 32 / G;
+    static_assert(G <= 32 && 32 % G == 0, "lane group");
     __shared__ double sdot[NR];
     if (part && threadIdx.x < NR) sdot[threadIdx.x] = 0.0;
     if (part) __syncthreads();
-    const int g = (int)(lane_id() % GS);
-    const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / GS;
-    const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / GS;
-    double mydot[NR];
-#pragma unroll
-    for (int j = 0; j < NR; ++j) mydot[j] = 0.0;
-    for (int64_t row = grp; row < n; row += ngrp) {
-        TV acc[NR], xi[NR];
-#pragma unroll
-        for (int j = 0; j < NR; ++j) {
-            acc[j] = TV(0);
-            xi[j] = (DIFF && j < nrhs) ? x[(size_t)row * nrhs + j] : TV(0);
-        }
+    const int lane = (int)lane_id();
+    const int gl = lane % G, j = gl % NR, es = gl / NR;
+    const unsigned gmask = G == 32 ? kFull : (((1u << G) - 1u) << (lane - gl));
+    const int64_t gid = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * R + lane / G;
+    const int64_t ngroups = (((int64_t)gridDim.x * blockDim.x) >> 5) * R;
+    const bool jok = j < nrhs;
+    double mydot = 0.0;
+    for (int64_t row = gid; row < n; row += ngroups) {
+        const TV xi = (DIFF && jok) ? x[(size_t)row * nrhs + j] : TV(0);
+        TV acc = TV(0);
         const int32_t s = rp[row], e = rp[row + 1];
-        for (int32_t p = s + g; p < e; p += GS) {
+        for (int32_t p = s + es; p < e; p += ES) {
             const int32_t c = col[p];
             const TV a = (TV)val[p];
-#pragma unroll
-            for (int j = 0; j < NR; ++j)
-                if (j < nrhs) {
-                    if (DIFF) acc[j] += (c == row) ? a * xi[j] : a * (x[(size_t)c * nrhs + j] - xi[j]);
-                    else acc[j] += a * x[(size_t)c * nrhs + j];
-                }
+            if (jok) {
+                if (DIFF) acc += (c == row) ? a * xi : a * (x[(size_t)c * nrhs + j] - xi);
+                else acc += a * x[(size_t)c * nrhs + j];
+            }
         }
 #pragma unroll
-        for (int j = 0; j < NR; ++j)
-#pragma unroll
-            for (int o = GS / 2; o > 0; o >>= 1) acc[j] += __shfl_xor_sync(kFull, acc[j], o, GS);
-        if (g == 0) {
-#pragma unroll
-            for (int j = 0; j < NR; ++j)
-                if (j < nrhs) {
-                    y[(size_t)row * nrhs + j] = acc[j];
-                    if (part) mydot[j] += (double)x[(size_t)row * nrhs + j] * (double)acc[j];
-                }
+        for (int o = NR; o < G; o <<= 1) acc += __shfl_xor_sync(gmask, acc, o);
+        if (es == 0 && jok) {
+            y[(size_t)row * nrhs + j] = acc;
+            if (part) mydot += (double)x[(size_t)row * nrhs + j] * (double)acc;
         }
     }
     if (part) {
-#pragma unroll
-        for (int j = 0; j < NR; ++j) {
-            double v = warp_sum(mydot[j]);
-            if (lane_id() == 0 && j < nrhs) atomicAdd(&sdot[j], v);
-        }
+        if (es == 0 && jok && mydot != 0.0) atomicAdd(&sdot[j], mydot);
         __syncthreads();
         if (threadIdx.x < NR) part[(size_t)blockIdx.x * 16 + threadIdx.x] = sdot[threadIdx.x];
     }
@@ -336,12 +327,33 @@ static int pow2_at_least(int v) {
     return p;
 }
 
+template <typename TA, typename TV, int NR, int ES>
+static void launch_spmv_es(int32_t n, const int32_t* rp, const int32_t* col, const TA* val, const TV* x, TV* y,
+                           int nrhs, double* part, int blocks, cudaStream_t s) {
+    if constexpr (NR * ES <= 32) {
+        RW_COUNT_LAUNCH();
+        // FP32 values are always the excess + difference form of the mixed mode
+        k_spmv<TA, TV, NR, ES, sizeof(TA) == 4><<<blocks, 256, 0, s>>>(n, rp, col, val, x, y, nrhs, part);
+    }
+}
+
 template <typename TA, typename TV, int NR>
-static void launch_spmv_nr(int32_t n, const int32_t* rp, const int32_t* col, const TA* val,
-                           const TV* x, TV* y, int nrhs, double* part, int blocks, cudaStream_t s) {
-    RW_COUNT_LAUNCH();
-    // FP32 values are always the excess + difference form of the mixed mode
-    k_spmv<TA, TV, NR, 8, sizeof(TA) == 4><<<blocks, 256, 0, s>>>(n, rp, col, val, x, y, nrhs, part);
+static void launch_spmv_nr(const rw_context* ctx, int32_t n, const int32_t* rp, const int32_t* col,
+                           const TA* val, const TV* x, TV* y, int nrhs, double* part, cudaStream_t s) {
+    int es = ctx->opt.spmv_slices > 0 ? ctx->opt.spmv_slices : 32 / NR;
+    int p = 1;
+    while (p * 2 <= es && p * 2 * NR <= 32) p *= 2;
+    const int rows_per_block = 8 * (32 / (NR * p));
+    const int blocks = part ? kDotParts : grid_for(((int64_t)n + rows_per_block - 1) / rows_per_block, 1,
+                                                   ctx->num_sms * 16);
+    switch (p) {
+        case 1: launch_spmv_es<TA, TV, NR, 1>(n, rp, col, val, x, y, nrhs, part, blocks, s); break;
+        case 2: launch_spmv_es<TA, TV, NR, 2>(n, rp, col, val, x, y, nrhs, part, blocks, s); break;
+        case 4: launch_spmv_es<TA, TV, NR, 4>(n, rp, col, val, x, y, nrhs, part, blocks, s); break;
+        case 8: launch_spmv_es<TA, TV, NR, 8>(n, rp, col, val, x, y, nrhs, part, blocks, s); break;
+        case 16: launch_spmv_es<TA, TV, NR, 16>(n, rp, col, val, x, y, nrhs, part, blocks, s); break;
+        default: launch_spmv_es<TA, TV, NR, 32>(n, rp, col, val, x, y, nrhs, part, blocks, s); break;
+    }
 }
 
 template <typename TA, typename TV>
@@ -349,13 +361,12 @@ static rw_status launch_spmv(rw_context* ctx, int32_t n, const int32_t* rp, cons
                              const TA* val, const TV* x, TV* y, int nrhs, double* part) {
     cudaStream_t s = ctx->stream;
     const int nr = pow2_at_least(nrhs);
-    const int blocks = part ? kDotParts : grid_for((int64_t)n * 8, 256, ctx->num_sms * 16);
     switch (nr) {
-        case 1: launch_spmv_nr<TA, TV, 1>(n, rp, col, val, x, y, nrhs, part, blocks, s); break;
-        case 2: launch_spmv_nr<TA, TV, 2>(n, rp, col, val, x, y, nrhs, part, blocks, s); break;
-        case 4: launch_spmv_nr<TA, TV, 4>(n, rp, col, val, x, y, nrhs, part, blocks, s); break;
-        case 8: launch_spmv_nr<TA, TV, 8>(n, rp, col, val, x, y, nrhs, part, blocks, s); break;
-        default: launch_spmv_nr<TA, TV, 16>(n, rp, col, val, x, y, nrhs, part, blocks, s); break;
+        case 1: launch_spmv_nr<TA, TV, 1>(ctx, n, rp, col, val, x, y, nrhs, part, s); break;
+        case 2: launch_spmv_nr<TA, TV, 2>(ctx, n, rp, col, val, x, y, nrhs, part, s); break;
+        case 4: launch_spmv_nr<TA, TV, 4>(ctx, n, rp, col, val, x, y, nrhs, part, s); break;
+        case 8: launch_spmv_nr<TA, TV, 8>(ctx, n, rp, col, val, x, y, nrhs, part, s); break;
+        default: launch_spmv_nr<TA, TV, 16>(ctx, n, rp, col, val, x, y, nrhs, part, s); break;
     }
     return check_launch("spmv");
 }

@@ -242,3 +242,26 @@ def test_batch_fp32_mixed(P, ctx):
         assert abs(int(its[m, 0]) - itr) <= max(2, itr // 5)
     for F in Fs:
         F.destroy()
+
+
+def test_batch_of_one_uses_the_factor_in_place(P, ctx):
+    cfg = W.make_config(2, scale=0.2)
+    A, b = cfg["A"], cfg["b"]
+    dA = P.CSR.from_host(A)
+    F = P.rw_build_factor(ctx, dA, 80, 3, 1e-3)
+    ref = oracle.build_factor(A, 80, 3, 1e-3)
+    B = P.Batch(ctx, [dA], [F])
+    assert B.info()["fwd_levels"] == F.desc.fwd_levels
+    x = _dev(np.zeros_like(b))
+    rc, st, its, rel = P.pcg_solve_batch(ctx, B, [_dev(b)], [x], 1e-8, 500)
+    assert rc == 0 and np.all(rel < 1e-8)
+    xg = x.cpu().numpy()
+    for j in range(b.shape[1]):
+        xr, itr, rr, _ = oracle.pcg(A, ref, b[:, j], 1e-8, 500)
+        assert its[0, j] == itr
+        assert np.linalg.norm(xg[:, j] - xr) / np.linalg.norm(xr) < 1e-10
+    x32 = _dev(np.zeros_like(b))
+    rc, st, its32, rel32 = P.pcg_solve_batch(ctx, B, [_dev(b)], [x32], 1e-6, 500, P.RW_FP32_MIXED)
+    assert rc == 0 and np.all(rel32 < 1e-6)
+    B.destroy()
+    F.destroy()
