@@ -21,9 +21,10 @@ Other workloads (--workload N):
      replayed from a CUDA graph (rw_batch_create + pcg_solve_batch).
   5  3D 27-point grid 128^3 (n = 2,097,152), excess 1e-4 * row sum: learned
      budget (network trained on pilot-walk labels of seeded 64^3 instances of
-     the same distribution, mean 300, min 20) + FP32 PCG on the batched
-     engine, against the plain form (uniform 300 walks, FP64 PCG); value =
-     seconds to 1e-6 (build + solve) of the learned form.
+     the same distribution, mean 300, min 20; default label: the relative
+     variance of the visits to the start row per unit walk cost) + FP32 PCG
+     on the batched engine, against the plain form (uniform 300 walks, FP64
+     PCG); value = seconds to 1e-6 (build + solve) of the learned form.
 
 Timing: W warm-up steps, then K steps, each bracketed by CUDA events on the
 library's stream, with an L2 flush (a 512 MB write) between steps outside
@@ -259,6 +260,11 @@ def run_gpu_single(args, P, torch, dev, stream, ws, rank, local):
     db = torch.as_tensor(b, device=dev)
     dx = torch.zeros_like(db)
 
+    # schedule autotuning on this matrix's factor (untimed)
+    F0 = P.rw_build_factor(ctx, dA, walks, seed, drop)
+    tuned, tuned_ms = P.rw_autotune(ctx, dA, F0, nrhs, prec)
+    F0.destroy()
+
     def step():
         F = P.rw_build_factor(ctx, dA, walks, seed, drop)
         rc, st, its, rel = P.pcg_solve(ctx, dA, F, db, dx, tol, 3000, prec)
@@ -351,6 +357,7 @@ def run_gpu_single(args, P, torch, dev, stream, ws, rank, local):
         "e2e": {"value": hops * ws / (e2e * 1e-3), "unit": "hops/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e},
         "gpu_launches": infos[-1]["launches"],
+        "autotuned": {"options": tuned, "precond_ms": tuned_ms[0], "spmv_ms": tuned_ms[1]},
     })
     line.update(extra)
     if not args.no_cpu_baseline and ws == 1:
@@ -372,6 +379,13 @@ def run_gpu_batched(args, P, torch, dev, stream, ws, rank, local):
     dbs = [torch.as_tensor(b, device=dev) for b in bs]
     dxs = [torch.zeros_like(b) for b in dbs]
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    # schedule autotuning on the combined system (untimed)
+    Fs0 = P.rw_build_factor_batched(ctx, dAs, walks, seeds, drop)
+    B0 = P.Batch(ctx, dAs, Fs0)
+    tuned, tuned_ms = P.rw_batch_autotune(ctx, B0, nrhs, P.RW_FP64)
+    B0.destroy()
+    for F in Fs0:
+        F.destroy()
 
     def step():
         ev[0].record(stream)
@@ -419,15 +433,17 @@ def run_gpu_batched(args, P, torch, dev, stream, ws, rank, local):
         "roofline": dict(walk_roof, peak_kind=peak_kind),
         "clocks": clk,
         "gpu_launches": last["launches"],
+        "autotuned": {"options": tuned, "precond_ms": tuned_ms[0], "spmv_ms": tuned_ms[1]},
     })
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = _oracle_sample_for(4, cfg, 12.0, 2024)
     print(json.dumps(line), flush=True)
 
 
-def train_budget_model(P, torch, ctx, dev, ninst, edge, epochs, pilot_walks=64):
-    """Features and pilot-walk labels of `ninst` training instances (seeds
-    100 + j), then Adam training; returns the model and a summary."""
+def train_budget_model(P, torch, ctx, dev, ninst, edge, epochs, pilot_walks=64, quantity=0):
+    """Features and pilot-walk labels (quantity 0: walk lengths, 1: visits to
+    the start row) of `ninst` training instances (seeds 100 + j), then Adam
+    training; returns the model and a summary."""
     feats, labels, masks = [], [], []
     t0 = time.time()
     for j in range(ninst):
@@ -436,7 +452,7 @@ def train_budget_model(P, torch, ctx, dev, ninst, edge, epochs, pilot_walks=64):
         f = torch.zeros((A.n, 16), device=dev)
         P.rw_row_features(ctx, dA, f)
         out = [torch.zeros(A.n, device=dev) for _ in range(4)]
-        P.rw_pilot_stats(ctx, dA, pilot_walks, 1000 + j, *out)
+        P.rw_pilot_stats(ctx, dA, pilot_walks, 1000 + j, *out, quantity=quantity)
         feats.append(f)
         labels.append(out[2])
         masks.append(out[3])
@@ -451,7 +467,7 @@ def train_budget_model(P, torch, ctx, dev, ninst, edge, epochs, pilot_walks=64):
     t_train = time.time() - t0
     yv = Y[Mk > 0]
     return M, {"instances": ninst, "edge": edge, "rows": int(yv.numel()), "epochs": epochs,
-               "pilot_walks": pilot_walks, "data_s": t_data, "train_s": t_train,
+               "pilot_walks": pilot_walks, "label": ["walk length", "visits to the start row", "visits per unit walk cost"][quantity], "data_s": t_data, "train_s": t_train,
                "loss_first": float(losses[0]), "loss_last": float(losses[-1]),
                "label_var": float(yv.var()), "r2": 1.0 - float(losses[-1]) / float(yv.var())}
 
@@ -461,13 +477,25 @@ def run_gpu_learned(args, P, torch, dev, stream, ws, rank, local):
     cfg = W.make_config(5, scale=args.scale)
     A, b = cfg["A"], cfg["b"]
     drop, tol, seed = cfg["drop_tol"], cfg["tol"], cfg["walk_seed"]
-    ctx = P.Context(stream=stream)
-    M, train = train_budget_model(P, torch, ctx, dev, args.train_instances, args.train_edge, args.epochs)
+    ctx = P.Context(stream=stream)      # learned + FP32 path
+    ctxp = P.Context(stream=stream)     # plain path
+    M, train = train_budget_model(P, torch, ctx, dev, args.train_instances, args.train_edge, args.epochs,
+                                  quantity=args.label)
     dA = P.CSR.from_host(A, device=dev)
     db = torch.as_tensor(b, device=dev)
     dx = torch.zeros_like(db)
     budget = torch.zeros(A.n, dtype=torch.int32, device=dev)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    # schedule autotuning of each path on its own factor (untimed)
+    P.rw_budget_predict(ctx, dA, M, 300.0, 20, budget)
+    F0 = P.rw_build_factor_budget(ctx, dA, budget, seed, drop)
+    B0 = P.Batch(ctx, [dA], [F0])
+    tuned_l, _ = P.rw_batch_autotune(ctx, B0, 1, P.RW_FP32_MIXED)
+    B0.destroy()
+    F0.destroy()
+    F0 = P.rw_build_factor(ctxp, dA, 300, seed, drop)
+    tuned_p, _ = P.rw_autotune(ctxp, dA, F0, 1, P.RW_FP64)
+    F0.destroy()
 
     def learned():
         ev[0].record(stream)
@@ -489,9 +517,9 @@ def run_gpu_learned(args, P, torch, dev, stream, ws, rank, local):
 
     def plain():
         ev[0].record(stream)
-        F = P.rw_build_factor(ctx, dA, 300, seed, drop)
+        F = P.rw_build_factor(ctxp, dA, 300, seed, drop)
         ev[1].record(stream)
-        rc, st, its, rel = P.pcg_solve(ctx, dA, F, db, dx, tol, 3000, P.RW_FP64)
+        rc, st, its, rel = P.pcg_solve(ctxp, dA, F, db, dx, tol, 3000, P.RW_FP64)
         ev[2].record(stream)
         torch.cuda.synchronize()
         d = F.desc
@@ -507,6 +535,7 @@ def run_gpu_learned(args, P, torch, dev, stream, ws, rank, local):
     ms_p, inf_p, clk_p = timer.run(plain, args.steps, args.warmup, ws, local)
     M.destroy()
     ctx.close()
+    ctxp.close()
     if rank != 0:
         return
     peaks, peak_kind = _peaks()
@@ -529,6 +558,7 @@ def run_gpu_learned(args, P, torch, dev, stream, ws, rank, local):
                   "pcg_s": statistics.mean(i["pcg_ms"] for i in inf_p) * 1e-3, "iterations": Pn["iters"],
                   "rel_residual": Pn["rel"], "factor_nnz": Pn["nnz"], "walks": Pn["walks"], "hops": Pn["hops"]},
         "training": train,
+        "autotuned": {"learned": tuned_l, "plain": tuned_p},
         "walk_kernel_hops_per_s": L["hops"] / (L["walk_ms"] * 1e-3) if L["walk_ms"] > 0 else None,
         "roofline": dict(walk_roof, peak_kind=peak_kind),
         "clocks": clk, "clocks_plain": clk_p,
@@ -567,6 +597,8 @@ def main():
     ap.add_argument("--train-instances", type=int, default=50, help="workload 5: training instances")
     ap.add_argument("--train-edge", type=int, default=64, help="workload 5: training grid edge")
     ap.add_argument("--epochs", type=int, default=10, help="workload 5: training epochs")
+    ap.add_argument("--label", type=int, default=2, choices=[0, 1, 2],
+                    help="workload 5: pilot label (0 walk length, 1 visits, 2 visits per unit walk cost)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -97,6 +97,8 @@ typedef struct {
     int32_t cluster_width;   /* levels of at most this many rows (above the thin-run width) run on
                                 one thread-block cluster with hardware barriers; 0 = never */
     int32_t cluster_size;    /* CTAs of that cluster (2..16; 0 = 16) */
+    int32_t solve_mode;      /* triangular solves: 0 = level schedule (thin / wide / cluster runs),
+                                1 = sync-free (each row waits only for its own dependencies) */
 } rw_options;
 
 typedef struct rw_context rw_context;
@@ -244,6 +246,25 @@ rw_status pcg_solve_batch(rw_context* ctx, rw_batch* B, const double* const* d_b
                           int32_t nrhs, double tol, int32_t max_iter, rw_precision prec,
                           rw_pcg_stats* stats, int32_t* h_iters, double* h_relres);
 
+/* Schedule autotuner.  Times a fixed list of launch shapes of the
+ * preconditioner application and the SpMV on the given factor (or batch) and
+ * nrhs random right-hand sides in precision prec -- the sync-free solve, and
+ * the level schedule with entry slices per row group, wide-level blocks per
+ * SM and cluster runs off / on for levels of up to 256 rows; SpMV entry
+ * slices -- and installs the fastest in the context's options
+ * (rw_options.solve_mode, wide_slices, solve_blocks_per_sm, cluster_width,
+ * spmv_slices), also copied to *out if not NULL.  cache_path (may be NULL): a
+ * JSON-lines file; a line whose key matches the device and the problem's
+ * shape (log2 n, stored entries per row, depth, nrhs, precision) is used
+ * without timing, otherwise the result is appended.  h_ms (host [2], may be
+ * NULL): the best preconditioner and SpMV times in ms (0 when read from the
+ * cache).  The factor and the results of later solves are unchanged; only
+ * their speed depends on these options. */
+rw_status rw_autotune(rw_context* ctx, const rw_csr* A, const rw_factor* F, int32_t nrhs, rw_precision prec,
+                      const char* cache_path, rw_options* out, float* h_ms);
+rw_status rw_batch_autotune(rw_context* ctx, const rw_batch* B, int32_t nrhs, rw_precision prec,
+                            const char* cache_path, rw_options* out, float* h_ms);
+
 /* z = (Y^T diag(D) Y)^-1 r for nrhs node-major right-hand sides (FP64): the
  * preconditioner application inside pcg_solve (backward solve with Y^T,
  * scaling by 1/D, forward solve with Y). */
@@ -299,11 +320,20 @@ rw_status rw_row_features(rw_context* ctx, const rw_csr* A, float* d_feat);
 
 /* Pilot walks: pilot_walks (>= 2) walks from every walk row under the walk
  * kind 1 (Philox counter word 3 = 1; rw_build_factor uses kind 0), and per row
- * the mean Xi'_k and sample standard deviation sigma_k of the walk lengths
- * (hops), the label log((sigma_k/Xi'_k)^2 + 1e-6) and has_k = 1 (rows without
- * walks: all four 0).  Outputs are device arrays [n].  Errors as for
- * rw_build_factor (RW_ERR_NOT_RMATRIX, RW_ERR_WALK_CAP, ...). */
-rw_status rw_pilot_stats(rw_context* ctx, const rw_csr* A, uint32_t pilot_walks, uint64_t seed,
+ * the mean and sample standard deviation of a per-walk quantity, the label
+ * log((sd/mean)^2 + 1e-6) and has_k = 1 (rows without walks: all four 0).
+ * quantity 0: the walk length in hops (Xi'_k of Sec. 5.1); quantity 1: the
+ * visits to the start row, 1 + returns (J'_k / M'_k of Sec. 3.1, the
+ * "expected number of returns" that Sec. 5.1 names as an alternative
+ * b-independent quantity; it sets D_kk in Eq. newz).  quantity 2: the
+ * visits' statistics with the cost-aware label
+ * (log((sd/mean)^2 + 1e-6) - log Xi'_k) / 2 from the same walks recorded twice:
+ * exp(label) is then the allocation of a fixed hop count (walks cost Xi'_k
+ * hops each) that minimises the sum of the rows' relative variances
+ * (M_k proportional to sd_k / (mean_k sqrt(Xi'_k))).  Outputs are device
+ * arrays [n].  Errors as for rw_build_factor (RW_ERR_NOT_RMATRIX,
+ * RW_ERR_WALK_CAP, ...). */
+rw_status rw_pilot_stats(rw_context* ctx, const rw_csr* A, uint32_t pilot_walks, uint64_t seed, int32_t quantity,
                          float* d_mean, float* d_sd, float* d_label, float* d_has);
 
 /* The network 12 -> 64 -> 64 -> 1 (ReLU): x = bf16((f - mu) * inv_sd),

@@ -104,24 +104,35 @@ def row_features(A):
 # --------------------------------------------------------------------------
 # Pilot-walk statistics (labels)
 # --------------------------------------------------------------------------
-def pilot_stats(A, walks, seed, max_steps=1 << 24):
-    """Per row: mean and sample standard deviation of the lengths (hops) of
-    `walks` kind-1 walks, the label log((sd/mean)^2 + 1e-6), and has = 1 for
-    rows with walks.  Returns float32 arrays (mean, sd, label, has) and the
-    float64 (mean, var) before rounding."""
+def pilot_stats(A, walks, seed, max_steps=1 << 24, quantity=0):
+    """Per row: mean and sample standard deviation of a per-walk quantity of
+    `walks` kind-1 walks -- the length in hops (quantity 0) or the visits to
+    the start row, 1 + returns (quantity 1 and 2; Sec. 3.1's J'/M', named in
+    Sec. 5.1 as an alternative quantity) -- the label log((sd/mean)^2 + 1e-6)
+    (quantity 2: half of that label minus log of the mean walk length),
+    and has = 1 for rows with walks.  Returns float32 arrays (mean, sd, label,
+    has) and the float64 (mean, var) before rounding."""
     F = build_factor(A, walks, seed, 0.0, tag=1, records=True, max_steps=max_steps)
     n = A.n
     mean = np.zeros(n)
     var = np.zeros(n)
     has = np.zeros(n)
-    lens = F["rec_len"].astype(np.float64)
+    mean_len = np.zeros(n)
+    lens = F["rec_len"].astype(np.float64) if quantity == 0 else F["rec_ret"].astype(np.float64) + 1.0
     for i, k in enumerate(F["walk_rows"]):
         x = lens[i * walks:(i + 1) * walks]
         m = x.sum() / walks
         mean[k] = m
         var[k] = ((x - m) ** 2).sum() / (walks - 1)
         has[k] = 1.0
+        mean_len[k] = F["rec_len"][i * walks:(i + 1) * walks].astype(np.float64).sum() / walks
     label = np.where(has > 0, np.log(np.divide(var, mean * mean, out=np.zeros(n), where=has > 0) + 1e-6), 0.0)
+    if quantity == 2:
+        # cost-aware: exp(label) = sqrt(relative variance / mean walk length)
+        # (the float32 label of the visits is what both sides combine)
+        lab32 = label.astype(np.float32).astype(np.float64)
+        ml32 = mean_len.astype(np.float32).astype(np.float64)
+        label = np.where(has > 0, 0.5 * (lab32 - np.log(np.where(has > 0, ml32, 1.0))), 0.0)
     f32 = lambda a: a.astype(np.float32)
     return dict(mean=f32(mean), sd=f32(np.sqrt(var)), label=f32(label), has=f32(has),
                 mean64=mean, var64=var, lengths=lens, walk_rows=F["walk_rows"])

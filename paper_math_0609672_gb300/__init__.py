@@ -32,7 +32,7 @@ __all__ = [
     "Mlp", "rw_row_features", "rw_pilot_stats", "rw_mlp_create", "rw_mlp_predict",
     "rw_mlp_gradient", "rw_mlp_train", "rw_budget_normalize", "rw_budget_predict",
     "RW_NUM_FEATURES", "RW_FEATURE_STRIDE", "RW_MLP_PARAMS",
-    "Batch", "rw_batch_create", "pcg_solve_batch",
+    "Batch", "rw_batch_create", "pcg_solve_batch", "rw_autotune", "rw_batch_autotune",
 ]
 
 RW_NUM_FEATURES = 12
@@ -60,7 +60,7 @@ class rw_options_t(ctypes.Structure):
                 ("store_fp32", _i32), ("refine_every", _i32), ("walk_blocks_per_sm", _i32),
                 ("timing", _i32), ("solve_blocks_per_sm", _i32), ("graphs", _i32),
                 ("wide_slices", _i32), ("spmv_slices", _i32), ("cluster_width", _i32),
-                ("cluster_size", _i32)]
+                ("cluster_size", _i32), ("solve_mode", _i32)]
 
 
 class rw_factor_desc_t(ctypes.Structure):
@@ -141,7 +141,7 @@ def load():
     vp = _c_void_p
     sigs = {
         "rw_row_features": [vp, P(rw_csr_t), vp],
-        "rw_pilot_stats": [vp, P(rw_csr_t), _u32, _u64, vp, vp, vp, vp],
+        "rw_pilot_stats": [vp, P(rw_csr_t), _u32, _u64, _i32, vp, vp, vp, vp],
         "rw_mlp_create": [vp, _u64, P(vp)],
         "rw_mlp_params": [vp, vp, vp, vp, vp],
         "rw_mlp_predict": [vp, vp, vp, ctypes.c_int64, vp],
@@ -152,6 +152,8 @@ def load():
         "rw_batch_create": [vp, _i32, P(rw_csr_t), P(vp), P(vp)],
         "rw_batch_info": [vp, P(_i32), P(ctypes.c_int64), P(_i32), P(_i32)],
         "pcg_solve_batch": [vp, vp, P(vp), P(vp), _i32, _f64, _i32, ctypes.c_int, P(rw_pcg_stats_t), vp, vp],
+        "rw_autotune": [vp, P(rw_csr_t), vp, _i32, ctypes.c_int, ctypes.c_char_p, P(rw_options_t), vp],
+        "rw_batch_autotune": [vp, vp, _i32, ctypes.c_int, ctypes.c_char_p, P(rw_options_t), vp],
     }
     for name, args in sigs.items():
         getattr(lib, name).argtypes = args
@@ -522,9 +524,10 @@ def rw_row_features(ctx, A, feat):
     _check(load().rw_row_features(ctx.handle, ctypes.byref(A.c), _ptr(feat)), "rw_row_features")
 
 
-def rw_pilot_stats(ctx, A, pilot_walks, seed, mean, sd, label, has):
-    """mean, sd, label, has: CUDA float32 tensors [n]."""
-    _check(load().rw_pilot_stats(ctx.handle, ctypes.byref(A.c), int(pilot_walks), int(seed),
+def rw_pilot_stats(ctx, A, pilot_walks, seed, mean, sd, label, has, quantity=0):
+    """mean, sd, label, has: CUDA float32 tensors [n]; quantity 0 = walk
+    lengths, 1 = visits to the start row (1 + returns)."""
+    _check(load().rw_pilot_stats(ctx.handle, ctypes.byref(A.c), int(pilot_walks), int(seed), int(quantity),
                                  _ptr(mean), _ptr(sd), _ptr(label), _ptr(has)), "rw_pilot_stats")
 
 
@@ -621,3 +624,39 @@ def pcg_solve_batch(ctx, B, bs, xs, tol, max_iter, prec=RW_FP64):
     if rc not in (RW_OK, -5):
         raise RwError(rc, "pcg_solve_batch")
     return rc, list(st), its, rel
+
+
+# ---------------------------------------------------------------------------
+# Schedule autotuner
+# ---------------------------------------------------------------------------
+
+_TUNED = ("solve_mode", "wide_slices", "solve_blocks_per_sm", "cluster_width", "spmv_slices")
+
+
+def _tune_result(ctx, opt, ms):
+    for k in _TUNED:
+        setattr(ctx.options, k, getattr(opt, k))
+    return {k: getattr(opt, k) for k in _TUNED}, (float(ms[0]), float(ms[1]))
+
+
+def rw_autotune(ctx, A, F, nrhs, prec=RW_FP64, cache_path=None):
+    """Time the candidate solve / SpMV launch shapes on this factor and install
+    the fastest in the context.  Returns (chosen options, (precond ms, spmv ms))
+    -- times are 0 when the choice came from the cache file."""
+    import numpy as np
+    opt = rw_options_t()
+    ms = np.zeros(2, np.float32)
+    _check(load().rw_autotune(ctx.handle, ctypes.byref(A.c), F.handle, int(nrhs), int(prec),
+                              cache_path.encode() if cache_path else None, ctypes.byref(opt),
+                              ms.ctypes.data_as(_c_void_p)), "rw_autotune")
+    return _tune_result(ctx, opt, ms)
+
+
+def rw_batch_autotune(ctx, B, nrhs, prec=RW_FP64, cache_path=None):
+    import numpy as np
+    opt = rw_options_t()
+    ms = np.zeros(2, np.float32)
+    _check(load().rw_batch_autotune(ctx.handle, B.handle, int(nrhs), int(prec),
+                                    cache_path.encode() if cache_path else None, ctypes.byref(opt),
+                                    ms.ctypes.data_as(_c_void_p)), "rw_batch_autotune")
+    return _tune_result(ctx, opt, ms)

@@ -196,6 +196,11 @@ rw_status rw_context_create(rw_context** out, void* stream, rw_alloc_fn alloc, r
             return rc;
         }
     }
+    // a fresh context reports no error until a call sets one
+    if ((rc = reset_status(c)) || (rc = check_cuda(cudaStreamSynchronize(c->stream), "sync"))) {
+        rw_context_destroy(c);
+        return rc;
+    }
     if (!alloc) {
         // keep freed stream-ordered allocations cached in the device pool
         cudaMemPool_t mp;
@@ -601,6 +606,24 @@ static FactorView view_of(const rw_factor* F) {
     v.bar = F->bar;
     return v;
 }
+
+}  // extern "C"
+
+namespace rw {
+rw_status factor_tune_target(const rw_factor* F, const rw_csr* A, TuneTarget* X) {
+    if (!F || !A || A->n != F->desc.n) {
+        set_error("autotune: matrix and factor do not match");
+        return RW_ERR_ARG;
+    }
+    const rw_factor_desc& d = F->desc;
+    *X = TuneTarget{A->n, A->row_ptr, A->col, A->val, nullptr, d.y_row_ptr, d.y_col, d.y_val, d.y_val32,
+                    d.yt_row_ptr, d.yt_col, d.yt_val, d.yt_val32, d.d, d.d32, &F->fwd_sched, &F->bwd_sched,
+                    F->bar, d.nnz, std::max(d.fwd_levels, d.bwd_levels)};
+    return RW_OK;
+}
+}  // namespace rw
+
+extern "C" {
 
 rw_status pcg_solve(rw_context* ctx, const rw_csr* A, const rw_factor* F, const double* d_b,
                     double* d_x, int32_t nrhs, double tol, int32_t max_iter, rw_precision prec,

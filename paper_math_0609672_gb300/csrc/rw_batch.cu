@@ -372,6 +372,19 @@ struct rw_batch {
 
 using namespace rw;
 
+namespace rw {
+rw_status batch_tune_target(const rw_batch* B, TuneTarget* X) {
+    if (!B) {
+        set_error("autotune: NULL batch");
+        return RW_ERR_ARG;
+    }
+    *X = TuneTarget{B->N, B->a_rp, B->a_col, B->a_val, B->a_val32, B->y_rp, B->y_col, B->y_val, B->y_val32,
+                    B->yt_rp, B->yt_col, B->yt_val, B->yt_val32, B->d, B->d32, &B->fwd_sched, &B->bwd_sched,
+                    B->bar, B->nnzY, std::max(B->fwd_depth, B->bwd_depth)};
+    return RW_OK;
+}
+}  // namespace rw
+
 namespace {
 
 template <typename T>
@@ -621,6 +634,8 @@ rw_status rw_batch_create(rw_context* ctx, int32_t nmat, const rw_csr* As, const
     };
     cudaStream_t s = ctx->stream;
     Pool sc(ctx);
+    rw_status rc0 = reset_status(ctx);
+    if (rc0) return fail(rc0);
     if (nmat == 1) {
         // a batch of one matrix uses the matrix and its factor in place (both
         // must outlive it): no concatenation, the factor's own schedules

@@ -253,6 +253,33 @@ rw_status spmv_launch(rw_context* ctx, int32_t n, const int32_t* rp, const int32
 // Size and pointer checks of a matrix argument (RW_ERR_ARG / RW_ERR_NOT_RMATRIX).
 rw_status check_csr(const rw_csr* A);
 
+// What the schedule autotuner times: the SpMV operator and a factor with its
+// solve schedules (a single factor or a batch).
+struct TuneTarget {
+    int32_t n;
+    const int32_t* a_rp;
+    const int32_t* a_col;
+    const double* a_val;
+    const float* a_val32;  // excess + difference form (may be NULL)
+    const int64_t* y_rp;
+    const int32_t* y_col;
+    const double* y_val;
+    const float* y_val32;
+    const int64_t* yt_rp;
+    const int32_t* yt_col;
+    const double* yt_val;
+    const float* yt_val32;
+    const double* d;
+    const float* d32;
+    const SolveSchedule* fwd;
+    const SolveSchedule* bwd;
+    unsigned* bar;
+    int64_t nnz_y;
+    int32_t depth;
+};
+rw_status factor_tune_target(const rw_factor* F, const rw_csr* A, TuneTarget* X);
+rw_status batch_tune_target(const rw_batch* B, TuneTarget* X);
+
 // Launch-and-check helper: returns RW_ERR_CUDA with a message on failure.
 rw_status check_cuda(cudaError_t e, const char* what);
 rw_status check_launch(const char* what);

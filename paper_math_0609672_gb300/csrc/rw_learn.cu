@@ -94,11 +94,13 @@ __global__ void k_features(int32_t n, const int32_t* __restrict__ rp, const int3
     }
 }
 
-// Pilot-walk statistics of each walk row from its walk lengths (one warp per
-// row): mean Xi', sample standard deviation sigma (two passes, FP64), and the
-// label log((sigma / Xi')^2 + 1e-6).
+// Pilot-walk statistics of each walk row (one warp per row) from a per-walk
+// quantity: the walk length (records hold lengths; plus = 0) or the visits to
+// the start row, J = 1 + returns (records hold returns; plus = 1).  Mean,
+// sample standard deviation (two passes, FP64), and the label
+// log((sd / mean)^2 + 1e-6).
 __global__ void k_pilot_stats(int32_t nw, const int4* __restrict__ wrow,
-                              const int64_t* __restrict__ wbase, const int2* __restrict__ rec,
+                              const int64_t* __restrict__ wbase, const int2* __restrict__ rec, uint32_t plus,
                               float* mean_out, float* sd_out, float* label, float* has) {
     const int32_t gw = (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int32_t nwarps = (int32_t)((gridDim.x * blockDim.x) >> 5);
@@ -106,13 +108,13 @@ __global__ void k_pilot_stats(int32_t nw, const int4* __restrict__ wrow,
         const int32_t k = wrow[r].x;
         const int64_t b0 = wbase[r], b1 = wbase[r + 1];
         unsigned long long s1 = 0;
-        for (int64_t i = b0 + lane_id(); i < b1; i += 32) s1 += (uint32_t)rec[i].y;
+        for (int64_t i = b0 + lane_id(); i < b1; i += 32) s1 += (unsigned long long)(uint32_t)rec[i].y + plus;
         s1 = warp_sum(s1);
         const double m = (double)(b1 - b0);
         const double mean = (double)s1 / m;
         double s2 = 0.0;
         for (int64_t i = b0 + lane_id(); i < b1; i += 32) {
-            const double d = (double)(uint32_t)rec[i].y - mean;
+            const double d = (double)((unsigned long long)(uint32_t)rec[i].y + plus) - mean;
             s2 += d * d;
         }
         s2 = warp_sum(s2);
@@ -124,6 +126,16 @@ __global__ void k_pilot_stats(int32_t nw, const int4* __restrict__ wrow,
             has[k] = 1.f;
         }
     }
+}
+
+// Cost-aware label (quantity 2): half of (the visits label minus log of the
+// mean walk length), so that exp(label) is proportional to sqrt(relative
+// variance of the visits / walk cost) -- the allocation of a fixed number of
+// hops that minimises the summed relative variances.
+__global__ void k_label_cost(int32_t n, const float* __restrict__ mean_len, const float* __restrict__ has,
+                             float* label) {
+    for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+        if (has[k] > 0.f) label[k] = (float)(0.5 * ((double)label[k] - log((double)mean_len[k])));
 }
 
 // ---------------------------------------------------------------------------
@@ -642,7 +654,27 @@ static rw_status features_run(rw_context* ctx, const rw_csr* A, float* feat) {
     return check_launch("row features");
 }
 
-static rw_status pilot_run(rw_context* ctx, const rw_csr* A, uint32_t walks, uint64_t seed,
+static rw_status pilot_run(rw_context* ctx, const rw_csr* A, uint32_t walks, uint64_t seed, int quantity,
+                           float* mean, float* sd, float* label, float* has);
+
+// quantity 2: the same walks twice (lengths, then visits), combined
+static rw_status pilot_cost(rw_context* ctx, const rw_csr* A, uint32_t walks, uint64_t seed, float* mean, float* sd,
+                            float* label, float* has) {
+    Pool sc(ctx);
+    float* mlen = alloc_n<float>(sc, A->n);
+    float* t1 = alloc_n<float>(sc, A->n);
+    float* t2 = alloc_n<float>(sc, A->n);
+    if (!mlen || !t1 || !t2) return RW_ERR_ALLOC;
+    rw_status rc;
+    if ((rc = pilot_run(ctx, A, walks, seed, 0, mlen, t1, t2, has))) return rc;
+    if ((rc = pilot_run(ctx, A, walks, seed, 1, mean, sd, label, has))) return rc;
+    RW_COUNT_LAUNCH();
+    k_label_cost<<<grid_for(A->n, 256, ctx->num_sms * 8), 256, 0, ctx->stream>>>(A->n, mlen, has, label);
+    if ((rc = check_launch("cost label"))) return rc;
+    return read_status(ctx, "pilot statistics");
+}
+
+static rw_status pilot_run(rw_context* ctx, const rw_csr* A, uint32_t walks, uint64_t seed, int quantity,
                            float* mean, float* sd, float* label, float* has) {
     cudaStream_t s = ctx->stream;
     Pool scratch(ctx);
@@ -671,12 +703,12 @@ static rw_status pilot_run(rw_context* ctx, const rw_csr* A, uint32_t walks, uin
     wb.total = ws.total;
     WalkLaunch wl;
     wl.max_steps = ctx->opt.max_steps;
-    wl.record_lengths = 1;
+    wl.record_lengths = quantity == 0 ? 1 : 0;
     if ((rc = run_walks(ctx, wb, wl, rec, hops, scratch, nullptr))) return rc;
     if ((rc = read_status(ctx, "pilot walks"))) return rc;
     RW_COUNT_LAUNCH();
     k_pilot_stats<<<grid_for((int64_t)T.n_walk_rows * 32, 256, ctx->num_sms * 8), 256, 0, s>>>(
-        T.n_walk_rows, T.wrow, ws.wbase, rec, mean, sd, label, has);
+        T.n_walk_rows, T.wrow, ws.wbase, rec, quantity == 0 ? 0u : 1u, mean, sd, label, has);
     if ((rc = check_launch("pilot statistics"))) return rc;
     return read_status(ctx, "pilot statistics");
 }
@@ -894,15 +926,16 @@ rw_status rw_row_features(rw_context* ctx, const rw_csr* A, float* d_feat) {
     return read_status(ctx, "row features");
 }
 
-rw_status rw_pilot_stats(rw_context* ctx, const rw_csr* A, uint32_t pilot_walks, uint64_t seed,
+rw_status rw_pilot_stats(rw_context* ctx, const rw_csr* A, uint32_t pilot_walks, uint64_t seed, int32_t quantity,
                          float* d_mean, float* d_sd, float* d_label, float* d_has) {
-    if (!ctx || !d_mean || !d_sd || !d_label || !d_has || pilot_walks < 2) {
-        set_error("rw_pilot_stats: bad arguments (pilot_walks must be at least 2)");
+    if (!ctx || !d_mean || !d_sd || !d_label || !d_has || pilot_walks < 2 || quantity < 0 || quantity > 2) {
+        set_error("rw_pilot_stats: bad arguments (pilot_walks >= 2, quantity 0, 1 or 2)");
         return RW_ERR_ARG;
     }
     rw_status rc = check_csr_args(A, "rw_pilot_stats");
     if (rc || A->n == 0) return rc;
-    return pilot_run(ctx, A, pilot_walks, seed, d_mean, d_sd, d_label, d_has);
+    if (quantity == 2) return pilot_cost(ctx, A, pilot_walks, seed, d_mean, d_sd, d_label, d_has);
+    return pilot_run(ctx, A, pilot_walks, seed, quantity, d_mean, d_sd, d_label, d_has);
 }
 
 rw_status rw_mlp_create(rw_context* ctx, uint64_t seed, rw_mlp** out) {

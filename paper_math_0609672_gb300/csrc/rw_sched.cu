@@ -534,6 +534,141 @@ __global__ void __launch_bounds__(1024, 1) k_cluster(const WideParams<T> P) {
 }
 
 // ---------------------------------------------------------------------------
+// Sync-free solve (rw_options.solve_mode = 1): one cooperative launch for the
+// whole solve.  x starts as the "pending" marker; warp w takes the rows at
+// positions w, w + W, ... of the level order; a row loads all its
+// dependencies at once, re-polls (bounded) only those still pending, and
+// publishes its value with one relaxed store.  Rows are taken in level order
+// and all warps are co-resident, so the lowest unfinished position can always
+// proceed.  Each warp loads the structure of its next two rows while it waits,
+// so a level on the critical path costs one hand-off through L2.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct FreeParams {
+    int64_t n;
+    const int32_t* __restrict__ order;
+    const int64_t* __restrict__ rp;
+    const int32_t* __restrict__ col;
+    const T* __restrict__ val;
+    const T* __restrict__ rhs;
+    const T* __restrict__ scale;
+    T* x;
+    int nrhs;
+    DevStatus* st;
+};
+
+template <typename T, int NR>
+__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_syncfree(const FreeParams<T> P) {
+    constexpr int ES = 32 / NR;
+    const int lane = (int)lane_id();
+    const int j = lane % NR, es = lane / NR;
+    const bool jok = j < P.nrhs;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    struct Pre {
+        int32_t row;
+        int64_t s, e;
+        int32_t c[kPreEntries];
+        T y[kPreEntries];
+        T b;
+    };
+    auto load = [&](int64_t pos, Pre& R0) {
+        R0.row = -1;
+        if (pos >= P.n) return;
+        const int32_t row = P.order[pos];
+        R0.row = row;
+        R0.s = P.rp[row];
+        R0.e = P.rp[row + 1];
+#pragma unroll
+        for (int u = 0; u < kPreEntries; ++u) {
+            const int64_t q = R0.s + es + (int64_t)u * ES;
+            R0.c[u] = q < R0.e ? P.col[q] : 0;
+            R0.y[u] = q < R0.e ? P.val[q] : T(0);
+        }
+        R0.b = T(0);
+        if (es == 0 && jok) {
+            R0.b = P.rhs[(size_t)row * P.nrhs + j];
+            if (P.scale) R0.b = R0.b / P.scale[row];
+        }
+    };
+    // polls back off after the first few so that waiting warps leave L2
+    // bandwidth to the rows being computed
+    auto wait_value = [&](const T* src, T v) -> T {
+        unsigned spins = 0;
+        while (is_pending(v)) {
+            if (wait_gives_up(spins, &P.st->timeout)) return T(0);
+            if (spins > 4) __nanosleep(64);
+            v = ld_relaxed(src);
+        }
+        return v;
+    };
+    Pre pre[2];
+    load(gw, pre[0]);
+    load(gw + nw, pre[1]);
+    for (int64_t pos = gw; pos < P.n; pos += nw) {
+        const Pre cur = pre[0];
+        pre[0] = pre[1];
+        load(pos + 2 * nw, pre[1]);
+        const int nr = P.nrhs;
+        T v[kPreEntries];
+#pragma unroll
+        for (int u = 0; u < kPreEntries; ++u)
+            v[u] = (jok && cur.s + es + (int64_t)u * ES < cur.e) ? ld_relaxed(P.x + (size_t)cur.c[u] * nr + j) : T(0);
+        T acc = T(0);
+#pragma unroll
+        for (int u = 0; u < kPreEntries; ++u) {
+            if (jok && cur.s + es + (int64_t)u * ES < cur.e)
+                v[u] = wait_value(P.x + (size_t)cur.c[u] * nr + j, v[u]);
+            acc += cur.y[u] * v[u];
+        }
+        for (int64_t q = cur.s + es + (int64_t)kPreEntries * ES; q < cur.e; q += ES) {
+            const int32_t c = P.col[q];
+            const T y = P.val[q];
+            if (jok) {
+                const T* src = P.x + (size_t)c * nr + j;
+                acc += y * wait_value(src, ld_relaxed(src));
+            }
+        }
+#pragma unroll
+        for (int o = NR; o < 32; o <<= 1) acc += __shfl_xor_sync(kFull, acc, o);
+        if (es == 0 && jok) st_relaxed(P.x + (size_t)cur.row * nr + j, cur.b - acc);
+    }
+}
+
+template <typename T>
+__global__ void k_fill_pending_sched(T* x, int64_t cnt) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+         i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = pending_value(T(0));
+}
+
+template <typename T, int NR>
+static rw_status solve_syncfree(rw_context* ctx, const SolveSchedule& S, const int64_t* rp, const int32_t* col,
+                                const T* val, const T* rhs, const T* scale, T* x, int nrhs) {
+    cudaStream_t s = ctx->stream;
+    static int per_sm = -1;
+    if (per_sm < 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_syncfree<T, NR>, 512, 0);
+        if (per_sm < 1) per_sm = 1;
+    }
+    const int64_t cnt = (int64_t)S.n * nrhs;
+    RW_COUNT_LAUNCH();
+    k_fill_pending_sched<T><<<grid_for(cnt, 256, ctx->num_sms * 8), 256, 0, s>>>(x, cnt);
+    rw_status rc = check_launch("pending fill");
+    if (rc) return rc;
+    int64_t blocks = (int64_t)std::min(per_sm, 2) * ctx->num_sms;
+    const int64_t need = ((int64_t)S.n + 15) / 16;
+    if (blocks > need) blocks = need;
+    if (blocks < 1) blocks = 1;
+    FreeParams<T> P{S.n, S.order, rp, col, val, rhs, scale, x, nrhs, ctx->d_status};
+    void* args[] = {(void*)&P};
+    RW_COUNT_LAUNCH();
+    return check_cuda(cudaLaunchCooperativeKernel((const void*)k_syncfree<T, NR>, dim3((unsigned)blocks), dim3(512),
+                                                  args, 0, s),
+                      "sync-free solve");
+}
+
+// ---------------------------------------------------------------------------
 // Host dispatch
 // ---------------------------------------------------------------------------
 // Entry slices of the lane groups: an explicit option, else 32 / NR (one
@@ -650,6 +785,10 @@ static rw_status solve_runs_nr(rw_context* ctx, const SolveSchedule& S, const in
     cudaStream_t s = ctx->stream;
     T* ext = reinterpret_cast<T*>(bar + 64);  // the factor's solve workspace (see build_factor)
     rw_status rc;
+    if (ctx->opt.solve_mode == 1) {
+        if (S.n == 0) return RW_OK;
+        return solve_syncfree<T, NR>(ctx, S, rp, col, val, rhs, scale, x, nrhs);
+    }
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_thin<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize,

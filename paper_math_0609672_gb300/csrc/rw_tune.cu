@@ -1,0 +1,280 @@
+// rw_tune.cu -- autotuner for the solve-step schedules.
+//
+// The preconditioner application (two level-scheduled triangular solves) and
+// the SpMV have launch-shape parameters whose best values depend on the
+// factor's level structure and the number of right-hand sides: entry slices
+// per row group (lanes per row = slices x right-hand sides), blocks per SM of
+// the wide-level kernel, and whether narrow levels run on one thread-block
+// cluster.  The tuner times a fixed candidate list on the caller's own
+// factor (or batch) with CUDA events, keeps the fastest, installs it in the
+// context options, and records it in a JSON-lines cache keyed by the device
+// and the problem's shape, so that later runs on similar problems skip the
+// timing.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "rw_internal.h"
+
+namespace rw {
+
+namespace {
+
+struct Candidate {
+    int wide_slices, solve_blocks_per_sm, cluster_width, spmv_slices, solve_mode;
+};
+
+std::string shape_key(const rw_context* ctx, const TuneTarget& T, int nrhs) {
+    cudaDeviceProp prop{};
+    cudaGetDeviceProperties(&prop, ctx->device);
+    int nr = 1;
+    while (nr < nrhs) nr <<= 1;
+    const int lg_n = (int)std::lround(std::log2(std::max(1, T.n)));
+    const double per_row = T.n > 0 ? (double)T.nnz_y / T.n : 0.0;
+    const int lg_per_row = (int)std::lround(std::log2(std::max(1.0, per_row)) * 2.0);
+    const int lg_depth = (int)std::lround(std::log2(std::max(1, T.depth)) * 2.0);
+    char buf[256];
+    snprintf(buf, sizeof buf, "%s|sm%d|n2^%d|ypr%d|depth%d|nrhs%d", prop.name, prop.multiProcessorCount, lg_n,
+             lg_per_row, lg_depth, nr);
+    for (char* p = buf; *p; ++p)
+        if (*p == '"' || *p == '\\') *p = '_';
+    return buf;
+}
+
+// Reads "key": integer from a one-line JSON object (the cache format written below).
+bool json_int(const std::string& line, const char* key, int* out) {
+    const std::string k = std::string("\"") + key + "\":";
+    const size_t p = line.find(k);
+    if (p == std::string::npos) return false;
+    *out = atoi(line.c_str() + p + k.size());
+    return true;
+}
+
+bool cache_lookup(const char* path, const std::string& key, Candidate* c) {
+    if (!path) return false;
+    FILE* f = fopen(path, "r");
+    if (!f) return false;
+    char buf[1024];
+    bool found = false;
+    const std::string kk = "\"key\":\"" + key + "\"";
+    while (fgets(buf, sizeof buf, f)) {
+        const std::string line(buf);
+        if (line.find(kk) == std::string::npos) continue;
+        Candidate t{};
+        if (json_int(line, "wide_slices", &t.wide_slices) && json_int(line, "solve_blocks_per_sm", &t.solve_blocks_per_sm) &&
+            json_int(line, "cluster_width", &t.cluster_width) && json_int(line, "spmv_slices", &t.spmv_slices) &&
+            json_int(line, "solve_mode", &t.solve_mode)) {
+            *c = t;  // the last matching line wins
+            found = true;
+        }
+    }
+    fclose(f);
+    return found;
+}
+
+void cache_store(const char* path, const std::string& key, const Candidate& c, float ms_pre, float ms_spmv) {
+    if (!path) return;
+    FILE* f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f,
+            "{\"key\":\"%s\",\"solve_mode\":%d,\"wide_slices\":%d,\"solve_blocks_per_sm\":%d,\"cluster_width\":%d,"
+            "\"spmv_slices\":%d,\"precond_ms\":%.4f,\"spmv_ms\":%.4f}\n",
+            key.c_str(), c.solve_mode, c.wide_slices, c.solve_blocks_per_sm, c.cluster_width, c.spmv_slices, ms_pre,
+            ms_spmv);
+    fclose(f);
+}
+
+template <typename T>
+rw_status time_precond(rw_context* ctx, const TuneTarget& X, const T* yv, const T* ytv, const T* dv,
+                       const T* tvf, const T* tvb, const T* r, T* w, T* z, int nrhs, int reps, float* ms) {
+    cudaStream_t s = ctx->stream;
+    rw_status rc;
+    auto once = [&]() -> rw_status {
+        rw_status r2 = solve_runs<T>(ctx, *X.bwd, X.yt_rp, X.yt_col, ytv, tvb, r, nullptr, w, nrhs, X.bar);
+        if (r2) return r2;
+        return solve_runs<T>(ctx, *X.fwd, X.y_rp, X.y_col, yv, tvf, w, dv, z, nrhs, X.bar);
+    };
+    if ((rc = once())) return rc;
+    cudaEventRecord(ctx->ev[10], s);
+    for (int i = 0; i < reps; ++i)
+        if ((rc = once())) return rc;
+    cudaEventRecord(ctx->ev[11], s);
+    if ((rc = check_cuda(cudaEventSynchronize(ctx->ev[11]), "sync"))) return rc;
+    cudaEventElapsedTime(ms, ctx->ev[10], ctx->ev[11]);
+    *ms /= (float)reps;
+    return read_status(ctx, "autotune");
+}
+
+template <typename T>
+rw_status time_spmv(rw_context* ctx, const TuneTarget& X, const T* av, const T* x, T* y, int nrhs, int reps,
+                    float* ms) {
+    cudaStream_t s = ctx->stream;
+    rw_status rc;
+    if ((rc = spmv_launch<T>(ctx, X.n, X.a_rp, X.a_col, av, x, y, nrhs))) return rc;
+    cudaEventRecord(ctx->ev[10], s);
+    for (int i = 0; i < reps; ++i)
+        if ((rc = spmv_launch<T>(ctx, X.n, X.a_rp, X.a_col, av, x, y, nrhs))) return rc;
+    cudaEventRecord(ctx->ev[11], s);
+    if ((rc = check_cuda(cudaEventSynchronize(ctx->ev[11]), "sync"))) return rc;
+    cudaEventElapsedTime(ms, ctx->ev[10], ctx->ev[11]);
+    *ms /= (float)reps;
+    return RW_OK;
+}
+
+template <typename T>
+__global__ void k_tune_fill(T* v, int64_t cnt) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x)
+        v[i] = (T)(1.0 + 0.001 * (double)(i % 977));
+}
+
+template <typename T>
+rw_status tune_t(rw_context* ctx, const TuneTarget& X, int nrhs, const T* av, const T* yv, const T* ytv,
+                 const T* dv, const T* tvf, const T* tvb, Candidate* best, float* best_pre, float* best_spmv) {
+    Pool sc(ctx);
+    const int64_t cnt = (int64_t)X.n * nrhs;
+    T* r = alloc_n<T>(sc, cnt);
+    T* w = alloc_n<T>(sc, cnt);
+    T* z = alloc_n<T>(sc, cnt);
+    if (!r || !w || !z) return RW_ERR_ALLOC;
+    RW_COUNT_LAUNCH();
+    k_tune_fill<T><<<grid_for(cnt, 256, ctx->num_sms * 8), 256, 0, ctx->stream>>>(r, cnt);
+    rw_status rc = check_launch("autotune fill");
+    if (rc) return rc;
+    int nr = 1;
+    while (nr < nrhs) nr <<= 1;
+    const rw_options saved = ctx->opt;
+    // candidate list: the sync-free solve; the level schedule with entry
+    // slices 32/NR, 16/NR, 8/NR (>= 1), 1 or 2 blocks per SM, cluster runs off
+    // or for levels of up to 256 rows
+    std::vector<int> slices;
+    for (int es = 32 / nr; es >= 1 && (int)slices.size() < 3; es /= 2) slices.push_back(es);
+    float bp = 1e30f, bs = 1e30f;
+    Candidate b{slices[0], 1, 0, slices[0], 0};
+    const int reps = 3;
+    std::vector<Candidate> cands;
+    cands.push_back(Candidate{slices[0], 1, 0, 0, 1});
+    for (int es : slices)
+        for (int bps : {1, 2})
+            for (int cw : {0, 256}) cands.push_back(Candidate{es, bps, cw, 0, 0});
+    for (const Candidate& c : cands) {
+        ctx->opt.solve_mode = c.solve_mode;
+        ctx->opt.wide_slices = c.wide_slices;
+        ctx->opt.solve_blocks_per_sm = c.solve_blocks_per_sm;
+        ctx->opt.cluster_width = c.cluster_width;
+        float ms = 0.f;
+        if ((rc = time_precond<T>(ctx, X, yv, ytv, dv, tvf, tvb, r, w, z, nrhs, reps, &ms))) {
+            ctx->opt = saved;
+            return rc;
+        }
+        if (ms < bp) {
+            bp = ms;
+            b.solve_mode = c.solve_mode;
+            b.wide_slices = c.wide_slices;
+            b.solve_blocks_per_sm = c.solve_blocks_per_sm;
+            b.cluster_width = c.cluster_width;
+        }
+    }
+    if (X.a_rp) {
+        for (int es : slices) {
+            ctx->opt.spmv_slices = es;
+            float ms = 0.f;
+            if ((rc = time_spmv<T>(ctx, X, av, r, z, nrhs, 5, &ms))) {
+                ctx->opt = saved;
+                return rc;
+            }
+            if (ms < bs) {
+                bs = ms;
+                b.spmv_slices = es;
+            }
+        }
+    }
+    ctx->opt = saved;
+    *best = b;
+    *best_pre = bp;
+    *best_spmv = X.a_rp ? bs : 0.f;
+    return RW_OK;
+}
+
+rw_status autotune(rw_context* ctx, const TuneTarget& X, int nrhs, rw_precision prec, const char* cache,
+                   rw_options* out, float* ms_out) {
+    const std::string key = shape_key(ctx, X, nrhs) + (prec == RW_FP32_MIXED ? "|fp32" : "|fp64");
+    Candidate c{};
+    float ms_pre = 0.f, ms_spmv = 0.f;
+    if (!cache_lookup(cache, key, &c)) {
+        rw_status rc;
+        if (prec == RW_FP32_MIXED) {
+            rc = tune_t<float>(ctx, X, nrhs, X.a_val32, X.y_val32, X.yt_val32, X.d32, X.fwd->tval32, X.bwd->tval32, &c,
+                               &ms_pre, &ms_spmv);
+        } else {
+            rc = tune_t<double>(ctx, X, nrhs, X.a_val, X.y_val, X.yt_val, X.d, X.fwd->tval, X.bwd->tval, &c,
+                                &ms_pre, &ms_spmv);
+        }
+        if (rc) return rc;
+        cache_store(cache, key, c, ms_pre, ms_spmv);
+    }
+    ctx->opt.solve_mode = c.solve_mode;
+    ctx->opt.wide_slices = c.wide_slices;
+    ctx->opt.solve_blocks_per_sm = c.solve_blocks_per_sm;
+    ctx->opt.cluster_width = c.cluster_width;
+    ctx->opt.spmv_slices = c.spmv_slices;
+    if (out) *out = ctx->opt;
+    if (ms_out) ms_out[0] = ms_pre, ms_out[1] = ms_spmv;
+    return RW_OK;
+}
+
+}  // namespace
+
+}  // namespace rw
+
+using namespace rw;
+
+extern "C" {
+
+rw_status rw_autotune(rw_context* ctx, const rw_csr* A, const rw_factor* F, int32_t nrhs, rw_precision prec,
+                      const char* cache_path, rw_options* out, float* h_ms) {
+    if (!ctx || !A || !F || nrhs < 1 || nrhs > 16 || (prec != RW_FP64 && prec != RW_FP32_MIXED)) {
+        set_error("rw_autotune: bad arguments");
+        return RW_ERR_ARG;
+    }
+    rw_status rc = check_csr(A);
+    if (rc) return rc;
+    TuneTarget X{};
+    if ((rc = factor_tune_target(F, A, &X))) return rc;
+    if (X.n == 0) return RW_OK;
+    if (prec == RW_FP32_MIXED && !X.y_val32) {
+        set_error("rw_autotune: FP32 tuning needs a factor built with store_fp32 = 1");
+        return RW_ERR_ARG;
+    }
+    if ((rc = reset_status(ctx))) return rc;
+    Pool sc(ctx);
+    if (prec == RW_FP32_MIXED) {
+        float* a32 = alloc_n<float>(sc, A->nnz);
+        if (!a32) return RW_ERR_ALLOC;
+        launch_to_fp32_diff(A->n, A->row_ptr, A->col, A->val, a32, ctx->stream, ctx->num_sms);
+        X.a_val32 = a32;
+    }
+    return autotune(ctx, X, nrhs, prec, cache_path, out, h_ms);
+}
+
+rw_status rw_batch_autotune(rw_context* ctx, const rw_batch* B, int32_t nrhs, rw_precision prec,
+                            const char* cache_path, rw_options* out, float* h_ms) {
+    if (!ctx || !B || nrhs < 1 || nrhs > 16 || (prec != RW_FP64 && prec != RW_FP32_MIXED)) {
+        set_error("rw_batch_autotune: bad arguments");
+        return RW_ERR_ARG;
+    }
+    TuneTarget X{};
+    rw_status rc = batch_tune_target(B, &X);
+    if (rc) return rc;
+    if (X.n == 0) return RW_OK;
+    if (prec == RW_FP32_MIXED && (!X.y_val32 || !X.a_val32)) {
+        set_error("rw_batch_autotune: FP32 tuning needs factors built with store_fp32 = 1");
+        return RW_ERR_ARG;
+    }
+    if ((rc = reset_status(ctx))) return rc;
+    return autotune(ctx, X, nrhs, prec, cache_path, out, h_ms);
+}
+
+}  // extern "C"

@@ -84,6 +84,20 @@ def test_pilot_stats_match_oracle(P, ctx):
         assert np.allclose(label, ref["label"], rtol=1e-6, atol=1e-6)
 
 
+@pytest.mark.parametrize("quantity", [1, 2])
+def test_pilot_returns_match_oracle(P, ctx, quantity):
+    A = W.grid3d(6, 6, 6, 27, np.random.default_rng(3), excess_frac=1e-4)
+    dA = P.CSR.from_host(A)
+    out = [_zeros(A.n) for _ in range(4)]
+    P.rw_pilot_stats(ctx, dA, 64, 5, *out, quantity=quantity)
+    mean, sd, label, has = [t.cpu().numpy() for t in out]
+    ref = L.pilot_stats(A, 64, 5, quantity=quantity)
+    assert np.array_equal(has, ref["has"]) and np.array_equal(mean, ref["mean"])
+    assert np.all(mean[has > 0] >= 1.0)
+    assert np.allclose(sd, ref["sd"], rtol=1e-6, atol=0)
+    assert np.allclose(label, ref["label"], rtol=1e-6, atol=1e-6)
+
+
 def _random_model(rng, feat):
     params = (rng.standard_normal(L.NUM_PARAMS) * 0.25).astype(np.float32)
     params[L.OFF_W1:L.OFF_B1] *= 1.5

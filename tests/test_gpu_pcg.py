@@ -244,6 +244,23 @@ def test_batch_fp32_mixed(P, ctx):
         F.destroy()
 
 
+def test_batch_on_a_fresh_context(P, ctx):
+    """A batch made on a context other than the factors' (that has run
+    nothing yet) builds and solves."""
+    A = W.grid2d_5pt(20, 20)
+    dA = P.CSR.from_host(A)
+    F = P.rw_build_factor(ctx, dA, 30, 1, 1e-3)
+    c2 = P.Context()
+    B = P.Batch(c2, [dA], [F])
+    b = np.ones((A.n, 1))
+    x = _dev(np.zeros_like(b))
+    rc, st, its, rel = P.pcg_solve_batch(c2, B, [_dev(b)], [x], 1e-8, 200)
+    assert rc == 0 and rel[0, 0] < 1e-8
+    B.destroy()
+    c2.close()
+    F.destroy()
+
+
 def test_batch_of_one_uses_the_factor_in_place(P, ctx):
     cfg = W.make_config(2, scale=0.2)
     A, b = cfg["A"], cfg["b"]
@@ -265,3 +282,61 @@ def test_batch_of_one_uses_the_factor_in_place(P, ctx):
     assert rc == 0 and np.all(rel32 < 1e-6)
     B.destroy()
     F.destroy()
+
+
+def test_autotune_installs_options_and_caches(P, ctx, tmp_path):
+    cfg = W.make_config(2, scale=0.25)
+    A, b = cfg["A"], cfg["b"]
+    dA = P.CSR.from_host(A)
+    c2 = P.Context()
+    F = P.rw_build_factor(c2, dA, 60, 2, 1e-3)
+    cache = str(tmp_path / "tune.jsonl")
+    chosen, ms = P.rw_autotune(c2, dA, F, b.shape[1], P.RW_FP64, cache)
+    assert ms[0] > 0 and ms[1] > 0
+    assert chosen["wide_slices"] >= 1 and chosen["spmv_slices"] >= 1
+    lines = open(cache).read().strip().splitlines()
+    assert len(lines) == 1 and '"key":' in lines[0]
+    again, ms2 = P.rw_autotune(c2, dA, F, b.shape[1], P.RW_FP64, cache)
+    assert again == chosen and ms2 == (0.0, 0.0)
+    assert len(open(cache).read().strip().splitlines()) == 1
+    # the tuned context solves like the oracle
+    ref = oracle.build_factor(A, 60, 2, 1e-3)
+    x = _dev(np.zeros_like(b))
+    rc, st, its, rel = P.pcg_solve(c2, dA, F, _dev(b), x, 1e-8, 500)
+    xg = x.cpu().numpy()
+    for j in range(b.shape[1]):
+        xr, itr, rr, _ = oracle.pcg(A, ref, b[:, j], 1e-8, 500)
+        assert its[j] == itr and np.linalg.norm(xg[:, j] - xr) / np.linalg.norm(xr) < 1e-10
+    # batch tuning (FP32)
+    B = P.Batch(c2, [dA], [F])
+    chosen32, ms32 = P.rw_batch_autotune(c2, B, b.shape[1], P.RW_FP32_MIXED, cache)
+    assert ms32[0] > 0 and len(open(cache).read().strip().splitlines()) == 2
+    B.destroy()
+    F.destroy()
+    c2.close()
+
+
+@pytest.mark.parametrize("mode,cw", [(1, 0), (0, 256)])
+def test_precond_modes_match_oracle(P, mode, cw):
+    """The sync-free solve and the cluster runs give the oracle's z (1e-12)."""
+    rng = np.random.default_rng(30 + mode)
+    A = W.make_config(2, scale=0.25)["A"]
+    c2 = P.Context(options=P.rw_options_default(solve_mode=mode, cluster_width=cw))
+    dA = P.CSR.from_host(A)
+    F = P.rw_build_factor(c2, dA, 100, 7, 1e-3)
+    ref = oracle.build_factor(A, 100, 7, 1e-3)
+    for nrhs in (1, 4, 16):
+        r = rng.standard_normal((A.n, nrhs))
+        z = _dev(np.zeros_like(r))
+        P.rw_precond_apply(c2, F, _dev(r), z)
+        zg = z.cpu().numpy()
+        for j in (0, nrhs - 1):
+            zr = oracle.precond_apply(ref, r[:, j])
+            assert np.linalg.norm(zg[:, j] - zr) / np.linalg.norm(zr) < 1e-12
+    b = rng.standard_normal((A.n, 2))
+    x = _dev(np.zeros_like(b))
+    rc, st, its, rel = P.pcg_solve(c2, dA, F, _dev(b), x, 1e-8, 500)
+    xr, itr, rr, _ = oracle.pcg(A, ref, b[:, 0], 1e-8, 500)
+    assert its[0] == itr and np.linalg.norm(x.cpu().numpy()[:, 0] - xr) / np.linalg.norm(xr) < 1e-10
+    F.destroy()
+    c2.close()

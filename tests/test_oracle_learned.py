@@ -63,6 +63,36 @@ def test_pilot_length_moments_match_absorbing_chain():
         assert abs(S["var64"][k] - v) < 0.1 * v + 1e-12, (k, S["var64"][k], v)
 
 
+def test_pilot_visits_of_a_forced_row():
+    # the path of the length pin: every walk from row 1 comes back at least
+    # once, and after each return ends (at 0) with p = 1/4, so the returns are
+    # geometric on 1, 2, ... and J = 1 + returns has mean 1 + 1/p
+    from workloads import assemble
+    A = assemble(3, np.array([0, 1]), np.array([1, 2]), np.array([1.0, 3.0]),
+                 np.array([1.0, 0.0, 0.0]))
+    S = L.pilot_stats(A, 40000, seed=11, quantity=1)
+    vis = S["lengths"][40000:80000]
+    p = 0.25
+    assert vis.min() == 2.0
+    assert abs(vis.mean() - (1 + 1 / p)) < 4 * math.sqrt((1 - p) / p ** 2 / 40000)
+    # visits and lengths of the same walks: length = 2 J - 1 here
+    S0 = L.pilot_stats(A, 40000, seed=11)
+    assert np.array_equal(S0["lengths"][40000:80000], 2 * vis - 1)
+
+
+def test_cost_label_combines_visits_and_lengths():
+    rng = np.random.default_rng(5)
+    A = W.random_rmatrix(9, rng)
+    S1 = L.pilot_stats(A, 500, seed=2, quantity=1)
+    S0 = L.pilot_stats(A, 500, seed=2, quantity=0)
+    S2 = L.pilot_stats(A, 500, seed=2, quantity=2)
+    h = S2["has"] > 0
+    # exp(label) = sqrt(relative variance of the visits / mean walk length)
+    want = np.sqrt((np.exp(S1["label"][h].astype(np.float64))) / S0["mean"][h].astype(np.float64))
+    assert np.allclose(np.exp(S2["label"][h].astype(np.float64)), want, rtol=1e-6)
+    assert np.array_equal(S2["mean"], S1["mean"])
+
+
 def test_pilot_lengths_of_a_forced_row():
     # Path 0-1-2 without excess at nodes 1 and 2: a walk from 1 steps to 2 (its
     # only upper neighbour), comes back to 1 (every time), and from 1 ends at 0
