@@ -204,9 +204,11 @@ class Timer:
         clocks.start()
         for i in range(steps):
             self.flush.fill_(float(i))
+            torch.cuda.nvtx.range_push("bench_step")  # profilers select the timed steps by this range
             ev[i][0].record(self.stream)
             infos.append(fn())
             ev[i][1].record(self.stream)
+            torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         clk = clocks.stop()
         if ws > 1:
