@@ -72,6 +72,21 @@ def _dist():
     return ws, int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def aggregate(units, ms, ws):
+    """Whole-job figures of a replicated run: the units every rank processed
+    (sum) and the slowest rank's time (max).  Single process: unchanged."""
+    if ws <= 1:
+        return float(units), float(ms)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    u = torch.tensor([float(units)], dtype=torch.float64, device=dev)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=dev)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(u.item()), float(t.item())
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons during the timed region."""
 
@@ -214,10 +229,6 @@ class Timer:
         if ws > 1:
             torch.distributed.barrier()
         ms = statistics.mean(a.elapsed_time(b_) for a, b_ in ev)
-        if ws > 1:
-            t = torch.tensor([ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
         return ms, infos, clk
 
 
@@ -282,6 +293,7 @@ def run_gpu_single(args, P, torch, dev, stream, ws, rank, local):
     timer = Timer(torch, dev, stream)
     ms, infos, clk = timer.run(step, args.steps, args.warmup, ws, local)
     hops = statistics.mean(i["hops"] for i in infos)
+    all_hops, ms = aggregate(hops, ms, ws)
     walk_ms = statistics.mean(i["phase"][1] for i in infos)
     build_ms = statistics.mean(i["phase"][7] for i in infos)
     solve_ms = statistics.mean(i["solve_ms"] for i in infos)
@@ -343,7 +355,7 @@ def run_gpu_single(args, P, torch, dev, stream, ws, rank, local):
                        "precision": cfg["precision"], "l2": "flushed between steps (512 MB write)",
                        "parallelism": f"replicas x{ws}"})
     line.update({
-        "value": hops * ws / (ms * 1e-3), "unit": "hops/s", "higher_is_better": True,
+        "value": all_hops / (ms * 1e-3), "unit": "hops/s", "higher_is_better": True,
         "factor_build_s": build_ms * 1e-3, "pcg_s": solve_ms * 1e-3,
         "walk_kernel_hops_per_s": hops / (walk_ms * 1e-3),
         "pcg_iterations": infos[-1]["iters"], "pcg_rel_residual": infos[-1]["rel"],
@@ -356,7 +368,8 @@ def run_gpu_single(args, P, torch, dev, stream, ws, rank, local):
         "solve_phase_ms": {"spmv": infos[-1]["spmv_ms"], "bwd": infos[-1]["bwd_ms"],
                            "fwd": infos[-1]["fwd_ms"]},
         "clocks": clk,
-        "e2e": {"value": hops * ws / (e2e * 1e-3), "unit": "hops/s", "h2d_bytes_per_step": h2d,
+        "e2e": {"value": aggregate(hops, e2e, ws)[0] / (aggregate(0, e2e, ws)[1] * 1e-3), "unit": "hops/s",
+                "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e},
         "gpu_launches": infos[-1]["launches"],
         "autotuned": {"options": tuned, "precond_ms": tuned_ms[0], "spmv_ms": tuned_ms[1]},
@@ -412,6 +425,7 @@ def run_gpu_batched(args, P, torch, dev, stream, ws, rank, local):
     timer = Timer(torch, dev, stream)
     ms, infos, clk = timer.run(step, args.steps, args.warmup, ws, local)
     hops = statistics.mean(i["hops"] for i in infos)
+    all_hops, ms = aggregate(hops, ms, ws)
     last = infos[-1]
     ctx.close()
     if rank != 0:
@@ -425,7 +439,7 @@ def run_gpu_batched(args, P, torch, dev, stream, ws, rank, local):
                        "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{ws}"})
     its = last["iters"]
     line.update({
-        "value": hops * ws / (ms * 1e-3), "unit": "hops/s", "higher_is_better": True,
+        "value": all_hops / (ms * 1e-3), "unit": "hops/s", "higher_is_better": True,
         "factor_build_s": statistics.mean(i["build_ms"] for i in infos) * 1e-3,
         "batch_create_s": statistics.mean(i["batch_ms"] for i in infos) * 1e-3,
         "pcg_s": statistics.mean(i["pcg_ms"] for i in infos) * 1e-3,
@@ -535,6 +549,8 @@ def run_gpu_learned(args, P, torch, dev, stream, ws, rank, local):
     timer = Timer(torch, dev, stream)
     ms_l, inf_l, clk = timer.run(learned, args.steps, args.warmup, ws, local)
     ms_p, inf_p, clk_p = timer.run(plain, args.steps, args.warmup, ws, local)
+    _, ms_l = aggregate(0, ms_l, ws)
+    _, ms_p = aggregate(0, ms_p, ws)
     M.destroy()
     ctx.close()
     ctxp.close()

@@ -246,6 +246,31 @@ rw_status pcg_solve_batch(rw_context* ctx, rw_batch* B, const double* const* d_b
                           int32_t nrhs, double tol, int32_t max_iter, rw_precision prec,
                           rw_pcg_stats* stats, int32_t* h_iters, double* h_relres);
 
+/* ---- Factor files and orderings -------------------------------------------
+ * rw_factor_save writes the factor's rows (Y in CSR, D, and the counters M', J',
+ * G' of Sec. 3.1) after a 56-byte header ("RWPCFAC1", version 1, n, walk rows,
+ * nnz(Y), walks, hops, levels), followed by the SHA-256 of the payload.
+ * rw_factor_load reads such a file, checks the digest and the row structure,
+ * and rebuilds the transpose, levels, FP32 copies and solve schedules on the
+ * context's device (RW_ERR_ARG for a missing, truncated, foreign or corrupted
+ * file).  The loaded factor equals the saved one in every array. */
+rw_status rw_factor_save(const rw_factor* F, const char* path);
+rw_status rw_factor_load(rw_context* ctx, const char* path, rw_factor** out);
+/* SHA-256 (FIPS 180-4) of a host buffer (host code, no device work). */
+void rw_sha256(const void* data, size_t len, uint8_t out[32]);
+/* A seeded random permutation of 0..n-1 (the random symmetric ordering the
+ * paper uses, Sec. 5.4): node i gets the rank of its key, word 0 of
+ * Philox-4x32-10 with counter (lo32(i), hi32(i), 0, 2) and key (lo32(seed),
+ * hi32(seed)), ties by i.  d_perm (device [n]) receives the new index of each
+ * old index. */
+rw_status rw_random_permutation(rw_context* ctx, int32_t n, uint64_t seed, int32_t* d_perm);
+/* B = P A P^T for a permutation d_perm (old index -> new index): row perm[i] of
+ * B holds row i of A with columns perm[j], ascending.  d_row_ptr [n+1], d_col
+ * and d_val [nnz] are caller-allocated device arrays.  RW_ERR_ARG if d_perm is
+ * not a permutation. */
+rw_status rw_permute_csr(rw_context* ctx, const rw_csr* A, const int32_t* d_perm, int32_t* d_row_ptr, int32_t* d_col,
+                         double* d_val);
+
 /* Schedule autotuner.  Times a fixed list of launch shapes of the
  * preconditioner application and the SpMV on the given factor (or batch) and
  * nrhs random right-hand sides in precision prec -- the sync-free solve, and

@@ -33,6 +33,7 @@ __all__ = [
     "rw_mlp_gradient", "rw_mlp_train", "rw_budget_normalize", "rw_budget_predict",
     "RW_NUM_FEATURES", "RW_FEATURE_STRIDE", "RW_MLP_PARAMS",
     "Batch", "rw_batch_create", "pcg_solve_batch", "rw_autotune", "rw_batch_autotune",
+    "rw_factor_save", "rw_factor_load", "rw_sha256", "rw_random_permutation", "rw_permute_csr",
 ]
 
 RW_NUM_FEATURES = 12
@@ -154,6 +155,10 @@ def load():
         "pcg_solve_batch": [vp, vp, P(vp), P(vp), _i32, _f64, _i32, ctypes.c_int, P(rw_pcg_stats_t), vp, vp],
         "rw_autotune": [vp, P(rw_csr_t), vp, _i32, ctypes.c_int, ctypes.c_char_p, P(rw_options_t), vp],
         "rw_batch_autotune": [vp, vp, _i32, ctypes.c_int, ctypes.c_char_p, P(rw_options_t), vp],
+        "rw_factor_save": [vp, ctypes.c_char_p],
+        "rw_factor_load": [vp, ctypes.c_char_p, P(vp)],
+        "rw_random_permutation": [vp, _i32, _u64, vp],
+        "rw_permute_csr": [vp, P(rw_csr_t), vp, vp, vp, vp],
     }
     for name, args in sigs.items():
         getattr(lib, name).argtypes = args
@@ -162,6 +167,8 @@ def load():
     lib.rw_mlp_destroy.restype = None
     lib.rw_batch_destroy.argtypes = [vp]
     lib.rw_batch_destroy.restype = None
+    lib.rw_sha256.argtypes = [vp, ctypes.c_size_t, vp]
+    lib.rw_sha256.restype = None
     _lib = lib
     return lib
 
@@ -660,3 +667,40 @@ def rw_batch_autotune(ctx, B, nrhs, prec=RW_FP64, cache_path=None):
                                     cache_path.encode() if cache_path else None, ctypes.byref(opt),
                                     ms.ctypes.data_as(_c_void_p)), "rw_batch_autotune")
     return _tune_result(ctx, opt, ms)
+
+
+# ---------------------------------------------------------------------------
+# Factor files and orderings
+# ---------------------------------------------------------------------------
+
+def rw_factor_save(F, path):
+    _check(load().rw_factor_save(F.handle, str(path).encode()), "rw_factor_save")
+
+
+def rw_factor_load(ctx, path):
+    h = _c_void_p()
+    _check(load().rw_factor_load(ctx.handle, str(path).encode(), ctypes.byref(h)), "rw_factor_load")
+    return Factor(ctx, h)
+
+
+def rw_sha256(data: bytes) -> bytes:
+    out = ctypes.create_string_buffer(32)
+    buf = ctypes.create_string_buffer(data, len(data))
+    load().rw_sha256(ctypes.cast(buf, _c_void_p), len(data), ctypes.cast(out, _c_void_p))
+    return out.raw
+
+
+def rw_random_permutation(ctx, n, seed, perm):
+    """perm: CUDA int32 tensor [n] (new index of each old index)."""
+    _check(load().rw_random_permutation(ctx.handle, int(n), int(seed), _ptr(perm)), "rw_random_permutation")
+
+
+def rw_permute_csr(ctx, A, perm):
+    """B = P A P^T as a new device CSR."""
+    import torch
+    rp = torch.empty(A.n + 1, dtype=torch.int32, device=A.rowptr.device)
+    col = torch.empty(A.nnz, dtype=torch.int32, device=A.rowptr.device)
+    val = torch.empty(A.nnz, dtype=torch.float64, device=A.rowptr.device)
+    _check(load().rw_permute_csr(ctx.handle, ctypes.byref(A.c), _ptr(perm), _ptr(rp), _ptr(col), _ptr(val)),
+           "rw_permute_csr")
+    return CSR(rp, col, val)

@@ -238,28 +238,22 @@ struct MatBuild {
     int64_t launches = 0;
 };
 
-// The rest of the build of one matrix after the walks: merge and emission,
-// transpose, levels, FP32 copies, solve schedules, description.
-static rw_status finish_factor(rw_context* ctx, MatBuild& mb, const int2* rec, bool rec_owned,
-                               double drop_tol, uint64_t hops, float ms_walk, Pool& scratch) {
+}  // extern "C"
+
+// Transpose, levels, FP32 copies and solve schedules of a factor whose rows
+// (Y, D and the counters in fo) are in place; fills the description's arrays.
+// Events 12-14 mark the transpose, levels and FP32/schedule phases when
+// timing is on.
+rw_status rw::complete_factor(rw_context* ctx, rw_factor* F, const FactorOut& fo, Pool& scratch) {
     cudaStream_t s = ctx->stream;
     const bool timing = ctx->opt.timing != 0;
-    rw_factor* F = mb.F;
     rw_factor_desc& d = F->desc;
-    const rw_csr* A = mb.A;
-    const int32_t n = A->n;
-    FactorOut fo;
-    float ms_merge = 0.f, ms_emit = 0.f;
+    const int32_t n = d.n;
     int64_t* fwd_lptr = nullptr;
     int64_t* bwd_lptr = nullptr;
     float* y32 = nullptr;
     float* yt32 = nullptr;
     rw_status rc;
-    const int64_t launches0 = g_launches;
-    if (timing) cudaEventRecord(ctx->ev[11], s);
-    if ((rc = emit_factor(ctx, A, mb.T, mb.ws, rec, drop_tol, fo, F->pool, scratch,
-                          timing ? &ms_merge : nullptr, timing ? &ms_emit : nullptr)))
-        return rc;
     int64_t* yt_rp = alloc_n<int64_t>(F->pool, n + 1);
     int32_t* yt_col = alloc_n<int32_t>(F->pool, fo.nnz);
     double* yt_val = alloc_n<double>(F->pool, fo.nnz);
@@ -298,8 +292,6 @@ static rw_status finish_factor(rw_context* ctx, MatBuild& mb, const int2* rec, b
                              d.bwd_levels, F->bwd_sched, F->pool, scratch)))
         return rc;
     if (timing) cudaEventRecord(ctx->ev[14], s);
-    if ((rc = read_status(ctx, "factor build"))) return rc;
-    d.total_hops = hops;
     d.nnz = fo.nnz;
     d.y_row_ptr = fo.y_rp;
     d.y_col = fo.y_col;
@@ -311,6 +303,31 @@ static rw_status finish_factor(rw_context* ctx, MatBuild& mb, const int2* rec, b
     d.walks = fo.M;
     d.visits = fo.J;
     d.ground = fo.G;
+    return RW_OK;
+}
+
+extern "C" {
+
+// The rest of the build of one matrix after the walks: merge and emission,
+// then complete_factor, and the description.
+static rw_status finish_factor(rw_context* ctx, MatBuild& mb, const int2* rec, bool rec_owned,
+                               double drop_tol, uint64_t hops, float ms_walk, Pool& scratch) {
+    cudaStream_t s = ctx->stream;
+    const bool timing = ctx->opt.timing != 0;
+    rw_factor* F = mb.F;
+    rw_factor_desc& d = F->desc;
+    const rw_csr* A = mb.A;
+    FactorOut fo;
+    float ms_merge = 0.f, ms_emit = 0.f;
+    rw_status rc;
+    const int64_t launches0 = g_launches;
+    if (timing) cudaEventRecord(ctx->ev[11], s);
+    if ((rc = emit_factor(ctx, A, mb.T, mb.ws, rec, drop_tol, fo, F->pool, scratch,
+                          timing ? &ms_merge : nullptr, timing ? &ms_emit : nullptr)))
+        return rc;
+    if ((rc = complete_factor(ctx, F, fo, scratch))) return rc;
+    if ((rc = read_status(ctx, "factor build"))) return rc;
+    d.total_hops = hops;
     d.n_walk_rows = mb.T.n_walk_rows;
     d.total_walks = mb.ws.total;
     if (ctx->opt.keep_records && rec_owned) {

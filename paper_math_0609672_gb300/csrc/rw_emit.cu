@@ -660,6 +660,29 @@ __global__ void k_transpose_gather(int64_t nnz, const uint32_t* __restrict__ pos
     }
 }
 
+rw_status radix_sort_pairs(rw_context* ctx, uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, int64_t cnt,
+                           int bits, Pool& scratch, uint32_t** ko, uint32_t** vo) {
+    cudaStream_t s = ctx->stream;
+    rw_status rc;
+    const int64_t ntiles = (cnt + kRadixTile - 1) / kRadixTile;
+    uint32_t* hist = alloc_n<uint32_t>(scratch, ntiles * kRadix + 1);
+    if (!hist) return RW_ERR_ALLOC;
+    for (int shift = 0; shift < bits && cnt > 0; shift += kRadixBits) {
+        RW_COUNT_LAUNCH();
+        k_radix_hist<<<(unsigned)ntiles, kRadixThreads, 0, s>>>(k0, cnt, shift, ntiles, hist);
+        if ((rc = check_launch("radix histogram"))) return rc;
+        if ((rc = check_cuda(scan_u32(hist, hist, ntiles * kRadix, s, scratch), "scan"))) return rc;
+        RW_COUNT_LAUNCH();
+        k_radix_scatter<<<(unsigned)ntiles, kRadixThreads, 0, s>>>(k0, v0, cnt, shift, ntiles, hist, k1, v1);
+        if ((rc = check_launch("radix scatter"))) return rc;
+        std::swap(k0, k1);
+        std::swap(v0, v1);
+    }
+    *ko = k0;
+    *vo = v0;
+    return RW_OK;
+}
+
 rw_status transpose_factor(rw_context* ctx, int32_t n, const FactorOut& fo, int64_t* yt_rp,
                            int32_t* yt_col, double* yt_val, Pool& scratch) {
     cudaStream_t s = ctx->stream;
@@ -685,27 +708,14 @@ rw_status transpose_factor(rw_context* ctx, int32_t n, const FactorOut& fo, int6
     uint32_t* k1 = alloc_n<uint32_t>(scratch, nnz);
     uint32_t* v1 = alloc_n<uint32_t>(scratch, nnz);
     int32_t* row_of = alloc_n<int32_t>(scratch, nnz);
-    const int64_t ntiles = (nnz + kRadixTile - 1) / kRadixTile;
-    uint32_t* hist = alloc_n<uint32_t>(scratch, ntiles * kRadix + 1);
-    if (!k0 || !v0 || !k1 || !v1 || !row_of || !hist) return RW_ERR_ALLOC;
+    if (!k0 || !v0 || !k1 || !v1 || !row_of) return RW_ERR_ALLOC;
     RW_COUNT_LAUNCH();
     k_transpose_pairs<<<grid_for(n, 256, ctx->num_sms * 8), 256, 0, s>>>(n, fo.y_rp, fo.y_col, k0,
                                                                           v0, row_of);
     if ((rc = check_launch("transpose pairs"))) return rc;
     int bits = 1;
     while (bits < 31 && ((int64_t)1 << bits) < n) ++bits;
-    for (int shift = 0; shift < bits; shift += kRadixBits) {
-        RW_COUNT_LAUNCH();
-        k_radix_hist<<<(unsigned)ntiles, kRadixThreads, 0, s>>>(k0, nnz, shift, ntiles, hist);
-        if ((rc = check_launch("radix histogram"))) return rc;
-        if ((rc = check_cuda(scan_u32(hist, hist, ntiles * kRadix, s, scratch), "scan"))) return rc;
-        RW_COUNT_LAUNCH();
-        k_radix_scatter<<<(unsigned)ntiles, kRadixThreads, 0, s>>>(k0, v0, nnz, shift, ntiles, hist,
-                                                                    k1, v1);
-        if ((rc = check_launch("radix scatter"))) return rc;
-        std::swap(k0, k1);
-        std::swap(v0, v1);
-    }
+    if ((rc = radix_sort_pairs(ctx, k0, v0, k1, v1, nnz, bits, scratch, &k0, &v0))) return rc;
     RW_COUNT_LAUNCH();
     k_transpose_gather<<<grid_for(nnz, 256, ctx->num_sms * 8), 256, 0, s>>>(nnz, v0, row_of,
                                                                             fo.y_val, yt_col, yt_val);

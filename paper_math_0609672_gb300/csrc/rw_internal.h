@@ -166,6 +166,12 @@ rw_status emit_factor(rw_context* ctx, const rw_csr* A, const Tables& T, const W
                       const int2* rec, double drop_tol, FactorOut& fo, Pool& pool,
                       Pool& scratch, float* ms_merge, float* ms_emit);
 
+// Stable LSD radix sort (9-bit digits) of cnt (key, value) pairs on the low
+// `bits` bits of the keys, ping-ponging between (k0, v0) and (k1, v1); *ko, *vo
+// receive the pair of buffers that holds the result.
+rw_status radix_sort_pairs(rw_context* ctx, uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, int64_t cnt,
+                           int bits, Pool& scratch, uint32_t** ko, uint32_t** vo);
+
 rw_status transpose_factor(rw_context* ctx, int32_t n, const FactorOut& fo, int64_t* yt_rp,
                            int32_t* yt_col, double* yt_val, Pool& scratch);
 
@@ -278,6 +284,10 @@ struct TuneTarget {
     int32_t depth;
 };
 rw_status factor_tune_target(const rw_factor* F, const rw_csr* A, TuneTarget* X);
+
+// Transpose, levels, FP32 copies and solve schedules of a factor whose rows
+// are in fo (allocated from F->pool); fills F->desc's arrays.
+rw_status complete_factor(rw_context* ctx, rw_factor* F, const FactorOut& fo, Pool& scratch);
 rw_status batch_tune_target(const rw_batch* B, TuneTarget* X);
 
 // Launch-and-check helper: returns RW_ERR_CUDA with a message on failure.

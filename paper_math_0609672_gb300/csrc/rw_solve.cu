@@ -42,9 +42,7 @@ __global__ void __launch_bounds__(256) k_spmv(int32_t n, const int32_t* __restri
     constexpr int G = NR * ES;
     constexpr int R = 32 / G;
     static_assert(G <= 32 && 32 % G == 0, "lane group");
-    __shared__ double sdot[NR];
-    if (part && threadIdx.x < NR) sdot[threadIdx.x] = 0.0;
-    if (part) __syncthreads();
+    __shared__ double sdot[8][R][NR];  // per (warp, row group, rhs): summed in a fixed order
     const int lane = (int)lane_id();
     const int gl = lane % G, j = gl % NR, es = gl / NR;
     const unsigned gmask = G == 32 ? kFull : (((1u << G) - 1u) << (lane - gl));
@@ -72,9 +70,14 @@ __global__ void __launch_bounds__(256) k_spmv(int32_t n, const int32_t* __restri
         }
     }
     if (part) {
-        if (es == 0 && jok && mydot != 0.0) atomicAdd(&sdot[j], mydot);
+        if (es == 0) sdot[threadIdx.x >> 5][lane / G][j] = jok ? mydot : 0.0;
         __syncthreads();
-        if (threadIdx.x < NR) part[(size_t)blockIdx.x * 16 + threadIdx.x] = sdot[threadIdx.x];
+        if (threadIdx.x < NR) {
+            double t = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+                for (int g = 0; g < R; ++g) t += sdot[w][g][threadIdx.x];
+            part[(size_t)blockIdx.x * 16 + threadIdx.x] = t;
+        }
     }
 }
 
@@ -204,13 +207,26 @@ __global__ void __launch_bounds__(256) k_scalars(PcgScalars* S, const double* pa
     }
 }
 
+// Fixed-order block sum of one value per (thread, right-hand side j < 16):
+// warp sums, then the warps' sums in warp order, into part[blockIdx][j].
+__device__ __forceinline__ void block_parts16(double (&acc)[16], double* part) {
+    __shared__ double ws[8][16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) acc[j] = warp_sum(acc[j]);
+    if (lane_id() == 0)
+#pragma unroll
+        for (int j = 0; j < 16; ++j) ws[threadIdx.x >> 5][j] = acc[j];
+    __syncthreads();
+    if (threadIdx.x < 16) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w][threadIdx.x];
+        part[(size_t)blockIdx.x * 16 + threadIdx.x] = t;
+    }
+}
+
 // Block-level partial sums of a.b per right-hand side into part[blockIdx][j].
 template <typename TA, typename TB>
 __device__ void block_dot_parts(const TA* a, const TB* b, int64_t n, int nrhs, double* part) {
-    __shared__ double sd[16];
-    if (threadIdx.x < 16) sd[threadIdx.x] = 0.0;
-    __syncthreads();
-    const int64_t total = n * nrhs;
     double acc[16];
     for (int j = 0; j < 16; ++j) acc[j] = 0.0;
     // thread handles whole nodes so that each accumulator belongs to one rhs
@@ -218,13 +234,7 @@ __device__ void block_dot_parts(const TA* a, const TB* b, int64_t n, int nrhs, d
          i += (int64_t)gridDim.x * blockDim.x)
         for (int j = 0; j < nrhs; ++j)
             acc[j] += (double)a[i * nrhs + j] * (double)b[i * nrhs + j];
-    (void)total;
-    for (int j = 0; j < nrhs; ++j) {
-        const double v = warp_sum(acc[j]);
-        if (lane_id() == 0) atomicAdd(&sd[j], v);
-    }
-    __syncthreads();
-    if (threadIdx.x < 16) part[(size_t)blockIdx.x * 16 + threadIdx.x] = sd[threadIdx.x];
+    block_parts16(acc, part);
 }
 
 template <typename TA, typename TB>
@@ -281,9 +291,6 @@ __global__ void __launch_bounds__(256) k_true_resid(int32_t n, const int32_t* __
                                                     const double* __restrict__ b,
                                                     const double* __restrict__ x, int nrhs,
                                                     T* r_out, double* part) {
-    __shared__ double sd[16];
-    if (threadIdx.x < 16) sd[threadIdx.x] = 0.0;
-    __syncthreads();
     double acc2[16];
     for (int j = 0; j < 16; ++j) acc2[j] = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -297,12 +304,7 @@ __global__ void __launch_bounds__(256) k_true_resid(int32_t n, const int32_t* __
             acc2[j] += t * t;
         }
     }
-    for (int j = 0; j < nrhs; ++j) {
-        const double v = warp_sum(acc2[j]);
-        if (lane_id() == 0) atomicAdd(&sd[j], v);
-    }
-    __syncthreads();
-    if (threadIdx.x < 16) part[(size_t)blockIdx.x * 16 + threadIdx.x] = sd[threadIdx.x];
+    block_parts16(acc2, part);
 }
 
 template <typename Tin, typename Tout>

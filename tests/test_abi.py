@@ -55,3 +55,17 @@ def test_product_path_has_no_cpu_fallback():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "rw_oracle" not in txt, f
+
+
+def test_sha256_matches_hashlib():
+    """The factor-file digest (host code of the library) against hashlib on
+    the FIPS 180-4 example and random buffers spanning the padding cases."""
+    import hashlib
+    import numpy as np
+    import paper_math_0609672_gb300 as P
+    P.load()
+    assert P.rw_sha256(b"abc") == hashlib.sha256(b"abc").digest()
+    rng = np.random.default_rng(0)
+    for size in (0, 1, 55, 56, 63, 64, 65, 119, 120, 1000, 100000):
+        data = rng.integers(0, 256, size, dtype=np.uint8).tobytes()
+        assert P.rw_sha256(data) == hashlib.sha256(data).digest(), size
