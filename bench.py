@@ -24,7 +24,10 @@ Other workloads (--workload N):
      the same distribution, mean 300, min 20; default label: the relative
      variance of the visits to the start row per unit walk cost) + FP32 PCG
      on the batched engine, against the plain form (uniform 300 walks, FP64
-     PCG); value = seconds to 1e-6 (build + solve) of the learned form.
+     PCG); value = seconds to 1e-6 (build + solve) of the learned form.  A
+     third arm sets the walk counts by the adaptive rule of Sec. 5.1
+     (margin --adapt-delta, confidence 99 %, at least 20 walks) and solves on
+     the same engine as the learned form.
 
 Timing: W warm-up steps, then K steps, each bracketed by CUDA events on the
 library's stream, with an L2 flush (a 512 MB write) between steps outside
@@ -531,6 +534,25 @@ def run_gpu_learned(args, P, torch, dev, stream, ws, rank, local):
         F.destroy()
         return info
 
+    z99 = 2.5758293035489004           # Q^-1((1 - 0.99) / 2): alpha = 99 %
+
+    def adaptive():
+        ev[0].record(stream)
+        rounds = P.rw_adaptive_budget(ctx, dA, seed, args.adapt_delta, z99, 20, 65535, 12, budget)
+        F = P.rw_build_factor_budget(ctx, dA, budget, seed, drop)
+        ev[1].record(stream)
+        B = P.Batch(ctx, [dA], [F])
+        rc, st, its, rel = P.pcg_solve_batch(ctx, B, [db], [dx], tol, 3000, P.RW_FP32_MIXED)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        d = F.desc
+        info = dict(hops=int(d.total_hops), walks=int(d.total_walks), nnz=int(d.nnz),
+                    build_ms=ev[0].elapsed_time(ev[1]), pcg_ms=ev[1].elapsed_time(ev[2]),
+                    iters=int(its.max()), rel=float(rel.max()), rc=rc, rounds=rounds)
+        B.destroy()
+        F.destroy()
+        return info
+
     def plain():
         ev[0].record(stream)
         F = P.rw_build_factor(ctxp, dA, 300, seed, drop)
@@ -551,6 +573,17 @@ def run_gpu_learned(args, P, torch, dev, stream, ws, rank, local):
     ms_p, inf_p, clk_p = timer.run(plain, args.steps, args.warmup, ws, local)
     _, ms_l = aggregate(0, ms_l, ws)
     _, ms_p = aggregate(0, ms_p, ws)
+    adapt = None
+    if args.adapt_delta > 0:
+        ms_a, inf_a, _ = timer.run(adaptive, args.steps, args.warmup, ws, local)
+        _, ms_a = aggregate(0, ms_a, ws)
+        Ad = inf_a[-1]
+        adapt = {"delta": args.adapt_delta, "alpha": 0.99, "min_walks": 20, "s": ms_a * 1e-3,
+                 "build_s": statistics.mean(i["build_ms"] for i in inf_a) * 1e-3,
+                 "pcg_s": statistics.mean(i["pcg_ms"] for i in inf_a) * 1e-3, "iterations": Ad["iters"],
+                 "rel_residual": Ad["rel"], "factor_nnz": Ad["nnz"], "walks": Ad["walks"], "hops": Ad["hops"],
+                 "rounds": Ad["rounds"],
+                 "form": "Sec. 5.1 counts (walks run twice: rounds, then build) + FP32 PCG (batched engine)"}
     M.destroy()
     ctx.close()
     ctxp.close()
@@ -575,6 +608,7 @@ def run_gpu_learned(args, P, torch, dev, stream, ws, rank, local):
         "plain": {"build_s": statistics.mean(i["build_ms"] for i in inf_p) * 1e-3,
                   "pcg_s": statistics.mean(i["pcg_ms"] for i in inf_p) * 1e-3, "iterations": Pn["iters"],
                   "rel_residual": Pn["rel"], "factor_nnz": Pn["nnz"], "walks": Pn["walks"], "hops": Pn["hops"]},
+        "adaptive": adapt,
         "training": train,
         "autotuned": {"learned": tuned_l, "plain": tuned_p},
         "walk_kernel_hops_per_s": L["hops"] / (L["walk_ms"] * 1e-3) if L["walk_ms"] > 0 else None,
@@ -617,6 +651,8 @@ def main():
     ap.add_argument("--epochs", type=int, default=10, help="workload 5: training epochs")
     ap.add_argument("--label", type=int, default=2, choices=[0, 1, 2],
                     help="workload 5: pilot label (0 walk length, 1 visits, 2 visits per unit walk cost)")
+    ap.add_argument("--adapt-delta", type=float, default=0.25,
+                    help="workload 5: relative margin of the Sec. 5.1 adaptive-count arm (0 skips it)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

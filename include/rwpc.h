@@ -416,6 +416,28 @@ rw_status rw_budget_normalize(rw_context* ctx, const rw_csr* A, const float* d_w
 rw_status rw_budget_predict(rw_context* ctx, const rw_csr* A, const rw_mlp* M, double mean_budget,
                             uint32_t min_budget, uint32_t* d_budget);
 
+/* Adaptive walk counts of Sec. 5.1 (Eq. lengthdelta).  The paper keeps
+ * adding walks from row k until Delta Xi' sqrt(M_k) / sigma > z, where Xi' and
+ * sigma are the mean and sample standard deviation of the row's walk lengths
+ * and z = Q^-1((1 - alpha)/2) for confidence alpha.  All rows advance together
+ * in rounds: round 1 runs min_walks factor walks per walk row; after each
+ * round a row failing Delta^2 Xi'^2 M > z^2 sigma^2 (with M < max_walks) grows
+ * to max(M + 1, ceil(z^2 sigma^2 / (Delta^2 Xi'^2))), capped at max_walks, and
+ * the next round runs walks M, M+1, ... of those rows only; at most max_rounds
+ * rounds.  Walks are the factor walks (walk kind 0) of matrix index 0 with
+ * `seed`, so rw_build_factor_budget(seed, d_budget) afterwards consists of
+ * exactly the walks that fixed the counts.  Length sums are exact 64-bit
+ * integers and the test is FP64 with each operation rounded once, so the
+ * counts are deterministic.
+ *   d_budget [n] device uint32, written: M_k for walk rows, 0 for the others.
+ *   h_rounds host, optional: rounds run.
+ * Errors: RW_ERR_ARG (delta, z <= 0; min_walks < 2; max_walks < min_walks or
+ * > 65535; max_rounds < 1), RW_ERR_NOT_RMATRIX, RW_ERR_WALK_CAP (a walk hit
+ * rw_options.max_steps), RW_ERR_ALLOC, RW_ERR_CUDA.  Synchronous. */
+rw_status rw_adaptive_budget(rw_context* ctx, const rw_csr* A, uint64_t seed, double delta, double z,
+                             uint32_t min_walks, uint32_t max_walks, int32_t max_rounds, uint32_t* d_budget,
+                             int32_t* h_rounds);
+
 const char* rw_status_string(rw_status s);
 const char* rw_last_error(void);
 

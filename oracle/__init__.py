@@ -92,6 +92,10 @@ def _load():
     lib.orc_pcg.restype = ctypes.c_int
     lib.orc_precond_apply.argtypes = [ctypes.c_int32, i64p, i32p, f64p, f64p, f64p, f64p]
     lib.orc_precond_apply.restype = ctypes.c_int
+    lib.orc_adaptive_budget.argtypes = [ctypes.c_int32, i32p, i32p, f64p, ctypes.c_uint64, ctypes.c_uint32,
+                                        ctypes.c_double, ctypes.c_double, ctypes.c_uint32, ctypes.c_uint32,
+                                        ctypes.c_int32, ctypes.c_uint64, u32p, i32p]
+    lib.orc_adaptive_budget.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -197,6 +201,23 @@ def build_factor(A, walks, seed, drop_tol, matrix_index=0, tag=0, max_steps=1 <<
     if records:
         out["rec_end"], out["rec_ret"], out["rec_len"] = rec_end[:cap], rec_ret[:cap], rec_len[:cap]
     return out
+
+
+def adaptive_budget(A, seed, delta, z, min_walks=20, max_walks=4096, max_rounds=8, max_steps=1 << 24,
+                    matrix_index=0):
+    """Adaptive walk counts of Sec. 5.1 (rounds; see orc_adaptive_budget).
+    Returns (budget uint32 [n], rounds)."""
+    lib = _load()
+    budget = np.zeros(max(1, A.n), dtype=np.uint32)
+    rounds = ctypes.c_int32()
+    rc = lib.orc_adaptive_budget(A.n, _ptr(A.rowptr, ctypes.c_int32), _ptr(A.col, ctypes.c_int32),
+                                 _ptr(A.val, ctypes.c_double), ctypes.c_uint64(int(seed)), int(matrix_index),
+                                 ctypes.c_double(delta), ctypes.c_double(z), int(min_walks), int(max_walks),
+                                 int(max_rounds), ctypes.c_uint64(int(max_steps)), _ptr(budget, ctypes.c_uint32),
+                                 ctypes.byref(rounds))
+    if rc:
+        raise OracleError(rc, "oracle adaptive budget")
+    return budget[:A.n], rounds.value
 
 
 def reuse_trace(seq, nlabels):

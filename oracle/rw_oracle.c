@@ -767,3 +767,70 @@ int orc_pcg(int32_t n, const int32_t* Arp, const int32_t* Acol, const double* Av
     return pcg64(n, Arp, Acol, Aval, Yrp, Ycol, Yval, D, b, x, tol, max_iter, iters_out,
                  relres_out);
 }
+
+
+/*
+ * Adaptive walk counts of Sec. 5.1 (Eq. lengthdelta): walks from row k run
+ * until Delta Xi' sqrt(M) / sigma > z for the mean Xi' and sample standard
+ * deviation sigma of their lengths, checked in rounds: min_walks walks first;
+ * after each round, if Delta^2 Xi'^2 M > z^2 sigma^2 fails (and M < max_walks),
+ * the row's count grows to max(M + 1, ceil(z^2 sigma^2 / (Delta^2 Xi'^2)))
+ * (at most max_walks), running walks M, M+1, ...; at most max_rounds rounds.
+ * Lengths are the factor walks' hops (walk kind 0).  Sums of lengths and
+ * squared lengths are exact integers; the test is FP64 with each operation
+ * rounded once.  budget[k] = M_k (0 for rows without an upper neighbour).
+ */
+int orc_adaptive_budget(int32_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                        uint64_t seed, uint32_t matrix_index, double delta, double z,
+                        uint32_t min_walks, uint32_t max_walks, int32_t max_rounds,
+                        uint64_t max_steps, uint32_t* budget, int32_t* rounds_out) {
+    if (n < 0 || !(delta > 0.0) || !(z > 0.0) || min_walks < 2 || max_walks < min_walks ||
+        max_walks > 65535u || max_rounds < 1 || max_steps < 1)
+        return -1;
+    int rc = orc_validate(n, rowptr, col, val);
+    if (rc) return rc;
+    tables t;
+    if ((rc = tables_build(n, rowptr, col, val, &t))) return rc;
+    const double d2 = delta * delta, z2 = z * z;
+    int32_t rounds_max = 0;
+    for (int32_t k = 0; k < n; ++k) {
+        budget[k] = 0;
+        if (t.up0[k] < 0) continue;
+        uint32_t m = 0, inc = min_walks;
+        uint64_t s1 = 0, s2 = 0;
+        int32_t round;
+        for (round = 0; round < max_rounds && inc > 0; ++round) {
+            for (uint32_t w = m; w < m + inc; ++w) {
+                int32_t end;
+                uint32_t ret;
+                uint64_t h;
+                if ((rc = one_walk(&t, seed, matrix_index, 0, k, w, max_steps, &end, &ret, &h, NULL, 0, NULL))) {
+                    tables_free(&t);
+                    return rc;
+                }
+                s1 += h;
+                s2 += h * h;
+            }
+            m += inc;
+            inc = 0;
+            if (m > 1 && m < max_walks) {
+                const double md = (double)m;
+                const double mean = (double)s1 / md;
+                const double var = ((double)s2 - (double)s1 * mean) / (md - 1.0);
+                const double lhs = d2 * (mean * mean) * md;
+                const double rhs = z2 * var;
+                if (!(lhs > rhs)) {
+                    const double need = rhs / (d2 * (mean * mean));
+                    uint32_t target = need >= (double)max_walks ? max_walks : (uint32_t)ceil(need);
+                    if (target < m + 1) target = m + 1;
+                    inc = target - m;
+                }
+            }
+        }
+        if (round > rounds_max) rounds_max = round;
+        budget[k] = m;
+    }
+    tables_free(&t);
+    if (rounds_out) *rounds_out = rounds_max;
+    return 0;
+}

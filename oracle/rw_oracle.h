@@ -91,6 +91,12 @@ int orc_pcg(int32_t n, const int32_t* Arp, const int32_t* Acol, const double* Av
             const double* b, double* x, double tol, int32_t max_iter, int32_t mixed,
             int32_t refine_every, int32_t* iters_out, double* relres_out);
 
+/* Adaptive walk counts of Sec. 5.1 (Eq. lengthdelta), in rounds; see rw_oracle.c. */
+int orc_adaptive_budget(int32_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                        uint64_t seed, uint32_t matrix_index, double delta, double z,
+                        uint32_t min_walks, uint32_t max_walks, int32_t max_rounds,
+                        uint64_t max_steps, uint32_t* budget, int32_t* rounds_out);
+
 #ifdef __cplusplus
 }
 #endif

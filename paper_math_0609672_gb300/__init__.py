@@ -31,6 +31,7 @@ __all__ = [
     "rw_last_error", "RW_FP64", "RW_FP32_MIXED",
     "Mlp", "rw_row_features", "rw_pilot_stats", "rw_mlp_create", "rw_mlp_predict",
     "rw_mlp_gradient", "rw_mlp_train", "rw_budget_normalize", "rw_budget_predict",
+    "rw_adaptive_budget",
     "RW_NUM_FEATURES", "RW_FEATURE_STRIDE", "RW_MLP_PARAMS",
     "Batch", "rw_batch_create", "pcg_solve_batch", "rw_autotune", "rw_batch_autotune",
     "rw_factor_save", "rw_factor_load", "rw_sha256", "rw_random_permutation", "rw_permute_csr",
@@ -150,6 +151,7 @@ def load():
         "rw_mlp_train": [vp, vp, vp, vp, vp, ctypes.c_int64, _i32, _i32, ctypes.c_float, _u64, _i32, vp],
         "rw_budget_normalize": [vp, P(rw_csr_t), vp, _f64, _u32, vp],
         "rw_budget_predict": [vp, P(rw_csr_t), vp, _f64, _u32, vp],
+        "rw_adaptive_budget": [vp, P(rw_csr_t), _u64, _f64, _f64, _u32, _u32, _i32, vp, P(_i32)],
         "rw_batch_create": [vp, _i32, P(rw_csr_t), P(vp), P(vp)],
         "rw_batch_info": [vp, P(_i32), P(ctypes.c_int64), P(_i32), P(_i32)],
         "pcg_solve_batch": [vp, vp, P(vp), P(vp), _i32, _f64, _i32, ctypes.c_int, P(rw_pcg_stats_t), vp, vp],
@@ -575,6 +577,16 @@ def rw_budget_normalize(ctx, A, weight, mean_budget, min_budget, budget):
 def rw_budget_predict(ctx, A, M, mean_budget, min_budget, budget):
     _check(load().rw_budget_predict(ctx.handle, ctypes.byref(A.c), M.handle, float(mean_budget),
                                     int(min_budget), _ptr(budget)), "rw_budget_predict")
+
+
+def rw_adaptive_budget(ctx, A, seed, delta, z, min_walks, max_walks, max_rounds, budget):
+    """Adaptive walk counts of Sec. 5.1 into the device uint32 tensor `budget`;
+    returns the number of rounds run."""
+    rounds = _i32()
+    _check(load().rw_adaptive_budget(ctx.handle, ctypes.byref(A.c), _u64(int(seed)), float(delta), float(z),
+                                     int(min_walks), int(max_walks), int(max_rounds), _ptr(budget),
+                                     ctypes.byref(rounds)), "rw_adaptive_budget")
+    return rounds.value
 
 
 # ---------------------------------------------------------------------------

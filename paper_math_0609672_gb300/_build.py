@@ -23,7 +23,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]
 SOURCES = ["rw_api.cu", "rw_tables.cu", "rw_walk.cu", "rw_emit.cu", "rw_levels.cu", "rw_sched.cu",
-           "rw_solve.cu", "rw_learn.cu", "rw_batch.cu", "rw_tune.cu", "rw_io.cu"]
+           "rw_solve.cu", "rw_learn.cu", "rw_batch.cu", "rw_tune.cu", "rw_io.cu",
+           "rw_adapt.cu"]
 
 
 def _nvcc():

@@ -112,7 +112,7 @@ struct WalkSpace {
 constexpr int kWalkChunk = 32;
 
 rw_status build_walk_space(rw_context* ctx, const Tables& T, uint32_t uniform,
-                           const uint32_t* d_budget, WalkSpace& ws, Pool& pool);
+                           const uint32_t* d_budget, WalkSpace& ws, Pool& pool, bool allow_zero = false);
 // chunk_row[c] = the walk row holding walk c * kWalkChunk (wbase: [nw+1]).
 rw_status build_chunk_rows(rw_context* ctx, int32_t nw, const int64_t* wbase, int32_t* chunk_row);
 
@@ -138,6 +138,7 @@ struct WalkBatch {
     const int32_t* wmat = nullptr; // [walk rows] matrix of each walk row (nmat > 1)
     const int4* wrow = nullptr;
     const int64_t* wbase = nullptr;
+    const uint32_t* wofs = nullptr;  // first walk index of each walk row (NULL: 0)
     const int32_t* chunk_row = nullptr;
     int64_t total = 0;
 };

@@ -289,10 +289,10 @@ rw_status build_tables(rw_context* ctx, const rw_csr* A, Tables& T, Pool& pool) 
 // chunk_row[c] = the walk row that holds walk c * kWalkChunk.
 // ---------------------------------------------------------------------------
 __global__ void k_budgets(int32_t nw, const int4* __restrict__ wrow, uint32_t uniform,
-                          const uint32_t* __restrict__ budget, int64_t* out, DevStatus* st) {
+                          const uint32_t* __restrict__ budget, int64_t* out, DevStatus* st, int allow_zero) {
     for (int32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < nw; r += gridDim.x * blockDim.x) {
         const uint32_t b = budget ? budget[wrow[r].x] : uniform;
-        if (b == 0u) atomicAdd(&st->bad_budget, 1u);
+        if (b == 0u && !allow_zero) atomicAdd(&st->bad_budget, 1u);
         out[r] = (int64_t)b;
     }
 }
@@ -313,7 +313,7 @@ rw_status build_chunk_rows(rw_context* ctx, int32_t nw, const int64_t* wbase, in
 }
 
 rw_status build_walk_space(rw_context* ctx, const Tables& T, uint32_t uniform,
-                           const uint32_t* d_budget, WalkSpace& ws, Pool& pool) {
+                           const uint32_t* d_budget, WalkSpace& ws, Pool& pool, bool allow_zero) {
     cudaStream_t s = ctx->stream;
     const int32_t nw = T.n_walk_rows;
     ws.wbase = alloc_n<int64_t>(pool, nw + 1);
@@ -322,7 +322,7 @@ rw_status build_walk_space(rw_context* ctx, const Tables& T, uint32_t uniform,
     rw_status rc;
     if (nw > 0) {
         RW_COUNT_LAUNCH();
-        k_budgets<<<blocks, 256, 0, s>>>(nw, T.wrow, uniform, d_budget, ws.wbase, ctx->d_status);
+        k_budgets<<<blocks, 256, 0, s>>>(nw, T.wrow, uniform, d_budget, ws.wbase, ctx->d_status, allow_zero ? 1 : 0);
         if ((rc = check_launch("budgets"))) return rc;
     }
     if ((rc = check_cuda(scan_i64(ws.wbase, ws.wbase, nw, s, pool), "scan"))) return rc;

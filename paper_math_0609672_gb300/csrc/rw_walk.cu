@@ -26,6 +26,7 @@ struct WalkParams {
     const int32_t* __restrict__ wmat;   // matrix of each walk row (batched launches)
     const int4* __restrict__ wrow;
     const int64_t* __restrict__ wbase;
+    const uint32_t* __restrict__ wofs;  // first walk index of each walk row (NULL: 0)
     const int32_t* __restrict__ chunk_row;
     int64_t total;
     unsigned long long* cursor;
@@ -114,7 +115,7 @@ __global__ void __launch_bounds__(256) k_walk(const WalkParams P) {
                     tag = mw.tag;
                 }
                 k = (uint32_t)info.x;
-                w = (uint32_t)(widx - P.wbase[r]);
+                w = (uint32_t)(widx - P.wbase[r]) + (P.wofs ? P.wofs[r] : 0u);
                 rnd = philox4x32_10(0u, w, k, tag, key0, key1);
                 const uint32_t u = rnd.v0;
                 // first step: least m with u < ft_m among the upper neighbours, else the last
@@ -225,6 +226,7 @@ rw_status run_walks(rw_context* ctx, const WalkBatch& wb, const WalkLaunch& wl, 
     P.wmat = wb.wmat;
     P.wrow = wb.wrow;
     P.wbase = wb.wbase;
+    P.wofs = wb.wofs;
     P.chunk_row = wb.chunk_row;
     P.total = wb.total;
     P.cursor = cursor;
