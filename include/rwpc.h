@@ -99,6 +99,12 @@ typedef struct {
     int32_t cluster_size;    /* CTAs of that cluster (2..16; 0 = 16) */
     int32_t solve_mode;      /* triangular solves: 0 = level schedule (thin / wide / cluster runs),
                                 1 = sync-free (each row waits only for its own dependencies) */
+    int32_t reuse;           /* 1: walk reuse (Algorithm 2 of Sec. 5.3) in single-matrix builds:
+                                every simulated walk also counts, for each later node k' it
+                                passes, the legal sub-walk from k' (k' its least node until it
+                                ends below k' or at ground; one-step sub-walks excluded; walks of
+                                one start row never overlap).  Y, D and the counters then hold
+                                all these walks (default 0) */
 } rw_options;
 
 typedef struct rw_context rw_context;
@@ -119,19 +125,21 @@ typedef struct {
     const float* y_val32;      /* FP32 copies (NULL unless store_fp32) */
     const float* yt_val32;
     const float* d32;
-    const uint32_t* walks;     /* [n] M'_k: walks from row k (0 for exact rows) */
+    const uint32_t* walks;     /* [n] M'_k: walks from row k (0 for exact rows); with reuse the
+                                  simulated walks plus the sub-walks that start at k */
     const uint64_t* visits;    /* [n] J'_k: visits to k by walks from k, start included */
     const uint32_t* ground;    /* [n] G'_k: walks from k absorbed at ground */
     const int32_t* walk_rows;  /* [n_walk_rows] rows that ran walks, ascending */
     const int64_t* walk_base;  /* [n_walk_rows+1] first record of each walk row */
     const int32_t* records;    /* [2*total_walks] (end, returns|length) or NULL; end -1 = ground */
     int32_t n_walk_rows;
-    int64_t total_walks;
+    int64_t total_walks;       /* simulated walks */
     uint64_t total_hops;       /* sum of walk lengths (hops), first step included */
     int32_t fwd_levels;        /* depth of the DAG of Y z = v */
     int32_t bwd_levels;        /* depth of the DAG of Y^T w = r */
     float phase_ms[8];         /* tables, walk, merge, emit, transpose, levels, fp32, total */
     int64_t kernel_launches;   /* kernels launched by the build */
+    int64_t extra_walks;       /* walk reuse: sub-walks counted besides the simulated walks */
 } rw_factor_desc;
 
 typedef struct {

@@ -62,7 +62,7 @@ class rw_options_t(ctypes.Structure):
                 ("store_fp32", _i32), ("refine_every", _i32), ("walk_blocks_per_sm", _i32),
                 ("timing", _i32), ("solve_blocks_per_sm", _i32), ("graphs", _i32),
                 ("wide_slices", _i32), ("spmv_slices", _i32), ("cluster_width", _i32),
-                ("cluster_size", _i32), ("solve_mode", _i32)]
+                ("cluster_size", _i32), ("solve_mode", _i32), ("reuse", _i32)]
 
 
 class rw_factor_desc_t(ctypes.Structure):
@@ -73,7 +73,8 @@ class rw_factor_desc_t(ctypes.Structure):
                 ("visits", _c_void_p), ("ground", _c_void_p), ("walk_rows", _c_void_p),
                 ("walk_base", _c_void_p), ("records", _c_void_p), ("n_walk_rows", _i32),
                 ("total_walks", _i64), ("total_hops", _u64), ("fwd_levels", _i32),
-                ("bwd_levels", _i32), ("phase_ms", ctypes.c_float * 8), ("kernel_launches", _i64)]
+                ("bwd_levels", _i32), ("phase_ms", ctypes.c_float * 8), ("kernel_launches", _i64),
+                ("extra_walks", _i64)]
 
 
 class rw_pcg_stats_t(ctypes.Structure):

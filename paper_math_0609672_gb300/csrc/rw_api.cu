@@ -310,7 +310,7 @@ extern "C" {
 
 // The rest of the build of one matrix after the walks: merge and emission,
 // then complete_factor, and the description.
-static rw_status finish_factor(rw_context* ctx, MatBuild& mb, const int2* rec, bool rec_owned,
+static rw_status finish_factor(rw_context* ctx, MatBuild& mb, const int2* rec, const Extras* X, bool rec_owned,
                                double drop_tol, uint64_t hops, float ms_walk, Pool& scratch) {
     cudaStream_t s = ctx->stream;
     const bool timing = ctx->opt.timing != 0;
@@ -322,7 +322,7 @@ static rw_status finish_factor(rw_context* ctx, MatBuild& mb, const int2* rec, b
     rw_status rc;
     const int64_t launches0 = g_launches;
     if (timing) cudaEventRecord(ctx->ev[11], s);
-    if ((rc = emit_factor(ctx, A, mb.T, mb.ws, rec, drop_tol, fo, F->pool, scratch,
+    if ((rc = emit_factor(ctx, A, mb.T, mb.ws, rec, X, drop_tol, fo, F->pool, scratch,
                           timing ? &ms_merge : nullptr, timing ? &ms_emit : nullptr)))
         return rc;
     if ((rc = complete_factor(ctx, F, fo, scratch))) return rc;
@@ -330,6 +330,7 @@ static rw_status finish_factor(rw_context* ctx, MatBuild& mb, const int2* rec, b
     d.total_hops = hops;
     d.n_walk_rows = mb.T.n_walk_rows;
     d.total_walks = mb.ws.total;
+    d.extra_walks = X ? X->count : 0;
     if (ctx->opt.keep_records && rec_owned) {
         d.records = reinterpret_cast<const int32_t*>(rec);
         d.walk_base = mb.ws.wbase;
@@ -383,10 +384,17 @@ static rw_status build_factors(rw_context* ctx, std::vector<MatBuild>& mbs, uint
     const int nmat = (int)mbs.size();
     rw_status rc = RW_OK;
     Pool scratch(ctx);
+    Pool xpool(ctx);  // walk reuse: extra records (until the merge is done)
+    Extras X;
+    const bool reuse = ctx->opt.reuse != 0;
     int2* rec = nullptr;
     unsigned long long* d_hops = nullptr;
     float ms_walk = 0.f;
     WalkBatch wb;
+    if (reuse && nmat != 1) {
+        set_error("walk reuse applies to single-matrix builds");
+        return RW_ERR_ARG;
+    }
     std::vector<MatWalk> hmats(nmat);
     if ((rc = reset_status(ctx))) return rc;
     for (auto& mb : mbs) {
@@ -474,8 +482,14 @@ static rw_status build_factors(rw_context* ctx, std::vector<MatBuild>& mbs, uint
         wl.max_steps = ctx->opt.max_steps;
         wl.record_lengths = ctx->opt.record_lengths;
         const int64_t launches0 = g_launches;
-        if ((rc = run_walks(ctx, wb, wl, rec, d_hops, scratch, timing ? &ms_walk : nullptr)))
+        if (reuse) {
+            wl.record_lengths = 0;
+            if ((rc = run_walks_reuse(ctx, wb, wl, mbs[0].T, rec, d_hops, scratch, xpool,
+                                      timing ? &ms_walk : nullptr, X)))
+                goto fail;
+        } else if ((rc = run_walks(ctx, wb, wl, rec, d_hops, scratch, timing ? &ms_walk : nullptr))) {
             goto fail;
+        }
         if ((rc = read_status(ctx, "walks"))) goto fail;  // no merge of stopped walks
         mbs[0].launches += g_launches - launches0;
     }
@@ -487,7 +501,7 @@ static rw_status build_factors(rw_context* ctx, std::vector<MatBuild>& mbs, uint
             goto fail;
         for (int m = 0; m < nmat; ++m) {
             MatBuild& mb = mbs[m];
-            if ((rc = finish_factor(ctx, mb, rec + mb.rec_base, nmat == 1, drop_tol, hops[m],
+            if ((rc = finish_factor(ctx, mb, rec + mb.rec_base, reuse ? &X : nullptr, nmat == 1, drop_tol, hops[m],
                                     ms_walk, scratch)))
                 goto fail;
             mb.F->desc.kernel_launches = mb.launches;

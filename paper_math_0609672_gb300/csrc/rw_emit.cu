@@ -36,6 +36,8 @@ struct MergeParams {
     const int64_t* __restrict__ wbase;
     const int64_t* __restrict__ tbase;
     const int2* __restrict__ rec;
+    const int64_t* __restrict__ xbase;  // walk reuse: extra records per walk row (NULL: none)
+    const int2* __restrict__ xrec;
     const double* __restrict__ S;
     const double* __restrict__ diag;
     double drop_tol;
@@ -57,9 +59,13 @@ struct MergeParams {
 
 // Upper bound on the distinct keys of walk row r: its walks' end points and
 // its lower neighbours are all columns below k.
+__device__ __forceinline__ int64_t row_walks(const MergeParams& P, int32_t r) {
+    return P.wbase[r + 1] - P.wbase[r] + (P.xbase ? P.xbase[r + 1] - P.xbase[r] : 0);
+}
+
 __device__ __forceinline__ int64_t key_bound(const MergeParams& P, int32_t r) {
     const int4 info = P.wrow[r];
-    const int64_t m = P.wbase[r + 1] - P.wbase[r];
+    const int64_t m = row_walks(P, r);
     return min(m + (int64_t)info.w, (int64_t)info.x);
 }
 
@@ -182,21 +188,32 @@ __device__ void merge_row(const MergeParams& P, int32_t r, int* keys, uint32_t* 
 
     unsigned long long jsum = 0;
     unsigned gsum = 0, csum = 0;
-    for (int64_t base = b0; base < b1; base += TEAM) {
-        const int64_t idx = base + t;
-        const bool valid = idx < b1;
-        int2 rc = make_int2(-3, 0);
-        if (valid) rc = P.rec[idx];
-        if (valid) {
-            jsum += (unsigned)rc.y;
-            gsum += rc.x == -1;
-            csum += (rc.x < -1 || rc.x >= k);  // step cap (or a record that is not an end node)
+    // the row's own walks, then (walk reuse) the sub-walks that start at k
+    const int2* src = P.rec;
+    int64_t e0 = b0, e1 = b1;
+    for (int part = 0; part < 2; ++part) {
+        if (part == 1) {
+            if (!P.xbase) break;
+            src = P.xrec;
+            e0 = P.xbase[r];
+            e1 = P.xbase[r + 1];
         }
-        const bool ep = valid && rc.x >= 0 && rc.x < k;
-        const unsigned em = __ballot_sync(kFull, ep);
-        if (ep) {
-            const unsigned g = __match_any_sync(em, rc.x);
-            if ((int)lane_id() == __ffs(g) - 1) hash_insert(keys, vals, rc.x, __popc(g), false, lg);
+        for (int64_t base = e0; base < e1; base += TEAM) {
+            const int64_t idx = base + t;
+            const bool valid = idx < e1;
+            int2 rc = make_int2(-3, 0);
+            if (valid) rc = src[idx];
+            if (valid) {
+                jsum += (unsigned)rc.y;
+                gsum += rc.x == -1;
+                csum += (rc.x < -1 || rc.x >= k);  // step cap (or a record that is not an end node)
+            }
+            const bool ep = valid && rc.x >= 0 && rc.x < k;
+            const unsigned em = __ballot_sync(kFull, ep);
+            if (ep) {
+                const unsigned g = __match_any_sync(em, rc.x);
+                if ((int)lane_id() == __ffs(g) - 1) hash_insert(keys, vals, rc.x, __popc(g), false, lg);
+            }
         }
     }
     team_sync<TEAM>();
@@ -228,7 +245,8 @@ __device__ void merge_row(const MergeParams& P, int32_t r, int* keys, uint32_t* 
 
     const double akk = P.diag[k];
     const double a = __ddiv_rn(P.S[k], akk);
-    const double Mk = (double)(b1 - b0);
+    const int64_t walks = row_walks(P, r);
+    const double Mk = (double)walks;
     const int64_t tb = P.tbase[r];
     int kept = 0;
     for (int base = 0; base < u; base += TEAM) {
@@ -265,10 +283,10 @@ __device__ void merge_row(const MergeParams& P, int32_t r, int* keys, uint32_t* 
     const unsigned long long g_all = team_sum<TEAM, unsigned long long>(gsum, sm64);
     const unsigned long long c_all = team_sum<TEAM, unsigned long long>(csum, sm64);
     if (t == 0) {
-        const uint64_t Jk = (uint64_t)(b1 - b0) + jsum;
+        const uint64_t Jk = (uint64_t)walks + jsum;
         const double q = __ddiv_rn((double)Jk, Mk);
         P.D[k] = __ddiv_rn(akk, __dadd_rn(1.0, __dmul_rn(a, __dadd_rn(1.0, -q))));
-        P.M[k] = (uint32_t)(b1 - b0);
+        P.M[k] = (uint32_t)walks;
         P.J[k] = Jk;
         P.G[k] = (uint32_t)g_all;
         P.ycnt[k] = kept;
@@ -335,9 +353,9 @@ __global__ void __launch_bounds__(256) k_merge_huge(const MergeParams P, int32_t
 
 // Temporary slot capacity per walk row: walks + lower neighbours.
 __global__ void k_slot_sizes(int32_t nw, const int4* __restrict__ wrow,
-                             const int64_t* __restrict__ wbase, int64_t* cap) {
+                             const int64_t* __restrict__ wbase, const int64_t* __restrict__ xbase, int64_t* cap) {
     for (int32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < nw; r += gridDim.x * blockDim.x)
-        cap[r] = wbase[r + 1] - wbase[r] + wrow[r].w;
+        cap[r] = wbase[r + 1] - wbase[r] + (xbase ? xbase[r + 1] - xbase[r] : 0) + wrow[r].w;
 }
 
 // Exact rows (no upper neighbour, Sec. 5.2): count pass and fill pass.
@@ -390,8 +408,8 @@ __global__ void k_copy_rows(int32_t nw, const int4* __restrict__ wrow,
 }
 
 rw_status emit_factor(rw_context* ctx, const rw_csr* A, const Tables& T, const WalkSpace& ws,
-                      const int2* rec, double drop_tol, FactorOut& fo, Pool& pool, Pool& scratch,
-                      float* ms_merge, float* ms_emit) {
+                      const int2* rec, const Extras* X, double drop_tol, FactorOut& fo, Pool& pool,
+                      Pool& scratch, float* ms_merge, float* ms_emit) {
     cudaStream_t s = ctx->stream;
     const int32_t n = A->n, nw = T.n_walk_rows;
     rw_status rc;
@@ -412,7 +430,7 @@ rw_status emit_factor(rw_context* ctx, const rw_csr* A, const Tables& T, const W
     const int blocks = grid_for(std::max(n, nw), 256, ctx->num_sms * 8);
     if (nw > 0) {
         RW_COUNT_LAUNCH();
-        k_slot_sizes<<<blocks, 256, 0, s>>>(nw, T.wrow, ws.wbase, tbase);
+        k_slot_sizes<<<blocks, 256, 0, s>>>(nw, T.wrow, ws.wbase, X ? X->xbase : nullptr, tbase);
         if ((rc = check_launch("slot sizes"))) return rc;
     }
     if ((rc = check_cuda(scan_i64(tbase, tbase, nw, s, scratch), "scan"))) return rc;
@@ -436,6 +454,8 @@ rw_status emit_factor(rw_context* ctx, const rw_csr* A, const Tables& T, const W
     P.wbase = ws.wbase;
     P.tbase = tbase;
     P.rec = rec;
+    P.xbase = X ? X->xbase : nullptr;
+    P.xrec = X ? X->xrec : nullptr;
     P.S = T.S;
     P.diag = T.diag;
     P.drop_tol = drop_tol;

@@ -21,6 +21,7 @@ struct rw_context {
     rw::DevStatus* d_status = nullptr;  // device copy
     rw::DevStatus* h_status = nullptr;  // pinned host copy
     void* h_small = nullptr;            // pinned host scratch (256 bytes)
+    double reuse_ratio = 8.0;           // walk reuse: extra records per walk to allocate for
     cudaEvent_t ev[16] = {};
 };
 
@@ -151,6 +152,22 @@ inline MatWalk mat_walk(const Tables& T, uint64_t seed, uint32_t matrix_index, u
 rw_status run_walks(rw_context* ctx, const WalkBatch& wb, const WalkLaunch& wl, int2* rec,
                     unsigned long long* d_hops, Pool& pool, float* ms);
 
+// Sub-walks extracted by walk reuse (Algorithm 2), bucketed per walk row:
+// row r's records {end node or -1, returns} are xrec[xbase[r] .. xbase[r+1]).
+struct Extras {
+    int64_t count = 0;
+    int64_t* xbase = nullptr;  // [n_walk_rows + 1]
+    int2* xrec = nullptr;      // [count]
+    int32_t* xnode = nullptr;  // unbucketed: start node, end, returns
+    int32_t* xend = nullptr;
+    uint32_t* xret = nullptr;
+};
+
+// The walks of a single-matrix launch with reuse: rec as run_walks, and the
+// extracted sub-walks in X (allocated from xpool, which must outlive the merge).
+rw_status run_walks_reuse(rw_context* ctx, const WalkBatch& wb, const WalkLaunch& wl, const Tables& T, int2* rec,
+                          unsigned long long* d_hops, Pool& pool, Pool& xpool, float* ms, Extras& X);
+
 // Merge + emission: per-walk records -> Y (CSR), D, counters.
 struct FactorOut {
     int64_t nnz = 0;
@@ -163,8 +180,10 @@ struct FactorOut {
     uint32_t* G = nullptr;
 };
 
+// X: the sub-walks of walk reuse (NULL without reuse); each counts as a walk
+// of its start row.
 rw_status emit_factor(rw_context* ctx, const rw_csr* A, const Tables& T, const WalkSpace& ws,
-                      const int2* rec, double drop_tol, FactorOut& fo, Pool& pool,
+                      const int2* rec, const Extras* X, double drop_tol, FactorOut& fo, Pool& pool,
                       Pool& scratch, float* ms_merge, float* ms_emit);
 
 // Stable LSD radix sort (9-bit digits) of cnt (key, value) pairs on the low

@@ -260,4 +260,383 @@ rw_status run_walks(rw_context* ctx, const WalkBatch& wb, const WalkLaunch& wl, 
     return RW_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Walk reuse (Algorithm 2 of Sec. 5.3).  The simulated walk is the one k_walk
+// runs; besides its own record it yields the legal sub-walks that start at a
+// later node k' > k: k' is the least node of the sub-walk until it ends at a
+// node below k' (a home of k') or at ground.  The lane keeps the increasing
+// stack of such candidate starts above k (the top in registers, the rest in
+// local memory, each with its returns so far); a hop to node e first pops
+// every candidate above e -- each popped candidate is a finished sub-walk
+// ending at e, counted unless it started at the previous hop (a one-step walk,
+// whose contribution the first-step rule of Sec. 5.2 makes exact) -- then
+// pushes e if it is above the new top, or counts a return if it equals it.
+// Sub-walks of one start row never overlap (a start is popped before the same
+// node can be pushed again), as the paper requires.  Finished sub-walks go to
+// the warp's shared-memory stage and from there, in bulk, to the global
+// extra-record arrays {start node, end node or -1, returns}.
+struct ReuseParams {
+    int32_t* xnode;
+    int32_t* xend;
+    uint32_t* xret;
+    unsigned long long* xcount;  // records produced (may exceed xcap: then none past xcap is written)
+    int64_t xcap;
+    unsigned* overflow;          // walks whose stack outgrew CAP
+};
+
+constexpr int kReuseStage = 128;
+
+template <int CAP>
+__global__ void __launch_bounds__(256) k_walk_reuse(const WalkParams P, const ReuseParams R) {
+    __shared__ int32_t s_node[8][kReuseStage];
+    __shared__ int32_t s_end[8][kReuseStage];
+    __shared__ uint32_t s_ret[8][kReuseStage];
+    const unsigned lane = lane_id();
+    const unsigned lt = lanemask_lt();
+    const unsigned warp = threadIdx.x >> 5;
+
+    int64_t pool_next = 0, pool_end = 0;
+    int32_t pool_row = 0;
+    bool exhausted = false;
+
+    bool active = false;
+    int64_t widx = 0;
+    uint32_t k = 0, w = 0, coff = 0, ret = 0;
+    const uint32_t* thr = P.m0.thr;
+    const uint2* nxt = P.m0.nxt;
+    const uint32_t key0 = P.m0.key0, key1 = P.m0.key1, tag = P.m0.tag;
+    uint64_t h = 0;
+    Philox4 rnd{0u, 0u, 0u, 0u};
+    unsigned long long my_hops = 0;
+
+    uint2 stk[CAP];      // candidates below the top: {node, returns}
+    int32_t depth = 0;   // candidates above k (the top one in registers)
+    uint32_t top = 0, top_ret = 0;
+    bool fresh = false;  // the top was pushed by the previous hop
+    int stage_n = 0;     // warp-uniform
+
+    auto flush = [&]() {
+        __syncwarp();
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(R.xcount, (unsigned long long)stage_n);
+        base = __shfl_sync(kFull, base, 0);
+        for (int i = (int)lane; i < stage_n; i += 32) {
+            const unsigned long long p = base + (unsigned long long)i;
+            if (p < (unsigned long long)R.xcap) {
+                R.xnode[p] = s_node[warp][i];
+                R.xend[p] = s_end[warp][i];
+                R.xret[p] = s_ret[warp][i];
+            }
+        }
+        __syncwarp();
+        stage_n = 0;
+    };
+
+    for (;;) {
+        unsigned idle = __ballot_sync(kFull, !active);
+        while (idle != 0u && !exhausted) {
+            if (pool_next >= pool_end) {
+                unsigned long long base = 0;
+                if (lane == 0)
+                    base = (ld_relaxed_u32(&P.st->walk_cap) | ld_relaxed_u32(R.overflow)) != 0u
+                               ? (unsigned long long)P.total
+                               : atomicAdd(P.cursor, (unsigned long long)kWalkChunk);
+                base = __shfl_sync(kFull, base, 0);
+                if ((int64_t)base >= P.total) {
+                    exhausted = true;
+                    break;
+                }
+                pool_next = (int64_t)base;
+                pool_end = min((int64_t)base + kWalkChunk, P.total);
+                pool_row = P.chunk_row[base / kWalkChunk];
+            }
+            const int avail = (int)(pool_end - pool_next);
+            const int rank = __popc(idle & lt);
+            const bool take = !active && rank < avail;
+            int32_t r = pool_row;
+            if (take) {
+                widx = pool_next + rank;
+                while (P.wbase[r + 1] <= widx) ++r;
+                const int4 info = P.wrow[r];
+                k = (uint32_t)info.x;
+                w = (uint32_t)(widx - P.wbase[r]) + (P.wofs ? P.wofs[r] : 0u);
+                rnd = philox4x32_10(0u, w, k, tag, key0, key1);
+                const uint32_t u = rnd.v0;
+                const uint32_t* fb = P.m0.fthr + (size_t)info.y * 8u;
+                const uint4 a = ld_nc4(fb), b = ld_nc4(fb + 4);
+                const uint32_t up = a.x;
+                uint32_t m = (uint32_t)(a.z <= u) + (uint32_t)(a.w <= u) + (uint32_t)(b.x <= u) +
+                             (uint32_t)(b.y <= u) + (uint32_t)(b.z <= u) + (uint32_t)(b.w <= u);
+                if (m == 6u && up > 6u) {
+                    for (uint32_t blk = 1;; ++blk) {
+                        const uint4 c = ld_nc4(fb + 8u * blk), d = ld_nc4(fb + 8u * blk + 4u);
+                        const uint32_t cnt = count_le8(c, d, u);
+                        m += cnt;
+                        if (cnt < 8u || m >= up) break;
+                    }
+                }
+                if (m > up - 1u) m = up - 1u;
+                const uint2 e = __ldg(nxt + (size_t)info.z * 8u + 1u + (uint32_t)info.w + m);
+                coff = e.y;
+                h = 1;
+                ret = 0;
+                depth = 1;  // the first step's upper neighbour starts the stack
+                top = e.x;
+                top_ret = 0;
+                fresh = true;
+                active = true;
+            }
+            const int ntake = min(__popc(idle), avail);
+            const unsigned tm = __ballot_sync(kFull, take);
+            pool_row = __shfl_sync(kFull, r, 31 - __clz(tm));
+            pool_next += ntake;
+            idle = __ballot_sync(kFull, !active);
+        }
+        if (__ballot_sync(kFull, active) == 0u) break;
+
+        // ---- one hop of every active lane ----
+        // outcome: 0 idle, 1 moved to node `to`, 2 ended at `to` (home, or -1 ground),
+        // 3 stopped (step cap or stack overflow)
+        int outcome = 0;
+        int32_t to = 0;
+        uint32_t to_off = 0;
+        if (active) {
+            if (h >= P.max_steps ||
+                ((h & 4095u) == 0u && (ld_relaxed_u32(&P.st->walk_cap) | ld_relaxed_u32(R.overflow)) != 0u)) {
+                outcome = 3;
+                if (h >= P.max_steps) atomicAdd(&P.st->walk_cap, 1u);
+            } else {
+                const uint32_t sidx = (uint32_t)h;
+                if ((sidx & 3u) == 0u) rnd = philox4x32_10(sidx >> 2, w, k, tag, key0, key1);
+                const uint32_t q = sidx & 3u;
+                const uint32_t u = q == 0u ? rnd.v0 : q == 1u ? rnd.v1 : q == 2u ? rnd.v2 : rnd.v3;
+                ++h;
+                const uint32_t* blk = thr + (size_t)coff * 8u;
+                const uint4 a = ld_nc4(blk), b = ld_nc4(blk + 4);
+                const uint32_t deg = a.x;
+                uint32_t m = (uint32_t)(a.y <= u) + (uint32_t)(a.z <= u) + (uint32_t)(a.w <= u) +
+                             (uint32_t)(b.x <= u) + (uint32_t)(b.y <= u) + (uint32_t)(b.z <= u) +
+                             (uint32_t)(b.w <= u);
+                if (m == 7u && deg > 7u) {
+                    for (uint32_t bi = 1;; ++bi) {
+                        const uint4 c = ld_nc4(blk + 8u * bi), d = ld_nc4(blk + 8u * bi + 4u);
+                        const uint32_t cnt = count_le8(c, d, u);
+                        m += cnt;
+                        if (cnt < 8u || m >= deg) break;
+                    }
+                }
+                if (m >= deg) {
+                    outcome = 2;
+                    to = -1;  // ground
+                } else {
+                    const uint2 e = __ldg(nxt + (size_t)coff * 8u + 1u + m);
+                    to = (int32_t)e.x;
+                    to_off = e.y;
+                    outcome = e.x < k ? 2 : 1;
+                }
+            }
+        }
+        // ---- pop the candidates above `to` (warp-wide, one per round) ----
+        bool pop = (outcome == 1 || outcome == 2) && depth > 0 && to < (int32_t)top;
+        while (__any_sync(kFull, pop)) {
+            const bool emit = pop && !fresh;
+            const unsigned em = __ballot_sync(kFull, emit);
+            const int cnt = __popc(em);
+            if (stage_n + cnt > kReuseStage) flush();
+            if (emit) {
+                const int pos = stage_n + __popc(em & lt);
+                s_node[warp][pos] = (int32_t)top;
+                s_end[warp][pos] = to;
+                s_ret[warp][pos] = top_ret;
+            }
+            stage_n += cnt;
+            if (pop) {
+                fresh = false;
+                --depth;
+                if (depth > 0) {
+                    const uint2 t = stk[depth - 1];
+                    top = t.x;
+                    top_ret = t.y;
+                }
+                pop = depth > 0 && to < (int32_t)top;
+            }
+        }
+        if (outcome == 1) {
+            if ((uint32_t)to == k) {
+                ++ret;  // every candidate is above k, so the stack is empty here
+                fresh = false;
+            } else if (depth > 0 && (uint32_t)to == top) {
+                ++top_ret;
+                fresh = false;
+            } else if (depth > CAP) {
+                atomicAdd(R.overflow, 1u);
+                outcome = 3;
+            } else {
+                if (depth > 0) stk[depth - 1] = make_uint2(top, top_ret);
+                ++depth;
+                top = (uint32_t)to;
+                top_ret = 0;
+                fresh = true;
+            }
+            coff = to_off;
+        }
+        if (outcome >= 2) {
+            P.rec[widx] = make_int2(outcome == 2 ? to : -2, (int32_t)ret);
+            my_hops += h;
+            active = false;
+            depth = 0;
+        }
+    }
+    if (stage_n > 0) flush();
+    my_hops = warp_sum(my_hops);
+    if (lane == 0 && my_hops) atomicAdd(P.hops, my_hops);
+}
+
+// Extra records -> per walk row: counts, then a scatter into row order (the
+// order inside a row is immaterial: the merge only sums them).
+__global__ void k_extra_count(int64_t cnt, const int32_t* __restrict__ xnode, const uint32_t* __restrict__ wflag,
+                              unsigned long long* rows) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(rows + wflag[xnode[i]], 1ull);
+}
+
+__global__ void k_extra_scatter(int64_t cnt, const int32_t* __restrict__ xnode, const int32_t* __restrict__ xend,
+                                const uint32_t* __restrict__ xret, const uint32_t* __restrict__ wflag,
+                                const int64_t* __restrict__ xbase, unsigned long long* fill, int2* xrec) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t r = wflag[xnode[i]];
+        const int64_t p = xbase[r] + (int64_t)atomicAdd(fill + r, 1ull);
+        xrec[p] = make_int2(xend[i], (int32_t)xret[i]);
+    }
+}
+
+template <int CAP>
+static rw_status launch_reuse(rw_context* ctx, const WalkParams& P, const ReuseParams& R) {
+    int per_sm = ctx->opt.walk_blocks_per_sm;
+    rw_status rc;
+    if (per_sm <= 0) {
+        if ((rc = check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk_reuse<CAP>, 256, 0),
+                             "occupancy")))
+            return rc;
+        if (per_sm < 1) per_sm = 1;
+    }
+    int64_t blocks = (int64_t)per_sm * ctx->num_sms;
+    const int64_t need = (P.total + 255) / 256;
+    if (blocks > need) blocks = need;
+    RW_COUNT_LAUNCH();
+    k_walk_reuse<CAP><<<(unsigned)blocks, 256, 0, ctx->stream>>>(P, R);
+    return check_launch("walk kernel (reuse)");
+}
+
+rw_status run_walks_reuse(rw_context* ctx, const WalkBatch& wb, const WalkLaunch& wl, const Tables& T, int2* rec,
+                          unsigned long long* d_hops, Pool& pool, Pool& xpool, float* ms, Extras& X) {
+    cudaStream_t s = ctx->stream;
+    const int32_t nw = T.n_walk_rows;
+    rw_status rc;
+    X = Extras{};
+    X.xbase = alloc_n<int64_t>(xpool, nw + 1);
+    unsigned long long* cursor = alloc_n<unsigned long long>(pool, 1);
+    unsigned long long* xcount = alloc_n<unsigned long long>(pool, 1);
+    unsigned* overflow = alloc_n<unsigned>(pool, 1);
+    if (!X.xbase || !cursor || !xcount || !overflow) return RW_ERR_ALLOC;
+    if ((rc = check_cuda(cudaMemsetAsync(X.xbase, 0, sizeof(int64_t) * (size_t)(nw + 1), s), "memset")) ||
+        (rc = check_cuda(cudaMemsetAsync(d_hops, 0, sizeof(unsigned long long), s), "memset")))
+        return rc;
+    if (wb.total == 0) {
+        if (ms) *ms = 0.f;
+        return RW_OK;
+    }
+    WalkParams P{};
+    P.wrow = wb.wrow;
+    P.wbase = wb.wbase;
+    P.wofs = wb.wofs;
+    P.chunk_row = wb.chunk_row;
+    P.total = wb.total;
+    P.cursor = cursor;
+    P.rec = rec;
+    P.hops = d_hops;
+    P.st = ctx->d_status;
+    P.max_steps = wl.max_steps;
+    P.record_lengths = 0;
+    P.m0 = wb.m0;
+    int64_t cap = (int64_t)(ctx->reuse_ratio * (double)wb.total) + (1 << 16);
+    int stack = 64;
+    unsigned long long* h64 = static_cast<unsigned long long*>(ctx->h_small);
+    for (int attempt = 0;; ++attempt) {
+        ReuseParams R;
+        R.xnode = alloc_n<int32_t>(xpool, cap);
+        R.xend = alloc_n<int32_t>(xpool, cap);
+        R.xret = alloc_n<uint32_t>(xpool, cap);
+        if (!R.xnode || !R.xend || !R.xret) return RW_ERR_ALLOC;
+        R.xcount = xcount;
+        R.xcap = cap;
+        R.overflow = overflow;
+        if ((rc = check_cuda(cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), s), "memset")) ||
+            (rc = check_cuda(cudaMemsetAsync(d_hops, 0, sizeof(unsigned long long), s), "memset")) ||
+            (rc = check_cuda(cudaMemsetAsync(xcount, 0, sizeof(unsigned long long), s), "memset")) ||
+            (rc = check_cuda(cudaMemsetAsync(overflow, 0, sizeof(unsigned), s), "memset")))
+            return rc;
+        if (ms) cudaEventRecord(ctx->ev[0], s);
+        rc = stack == 64 ? launch_reuse<64>(ctx, P, R) : launch_reuse<1024>(ctx, P, R);
+        if (rc) return rc;
+        if (ms) cudaEventRecord(ctx->ev[1], s);
+        if ((rc = check_cuda(cudaMemcpyAsync(h64, xcount, 8, cudaMemcpyDeviceToHost, s), "copy")) ||
+            (rc = check_cuda(cudaMemcpyAsync(h64 + 1, overflow, 4, cudaMemcpyDeviceToHost, s), "copy")) ||
+            (rc = check_cuda(cudaStreamSynchronize(s), "sync")))
+            return rc;
+        if (ms) cudaEventElapsedTime(ms, ctx->ev[0], ctx->ev[1]);
+        const uint64_t produced = h64[0];
+        const unsigned over = static_cast<unsigned>(h64[1] & 0xFFFFFFFFull);
+        bool again = false;
+        if (over) {
+            if (stack == 1024) {
+                set_error("walk reuse: %u walks have more than 1024 pending sub-walk starts", over);
+                return RW_ERR_CAPACITY;
+            }
+            stack = 1024;
+            again = true;
+        } else if ((int64_t)produced > cap) {
+            cap = (int64_t)produced;
+            again = true;
+        }
+        if (!again) {
+            X.count = (int64_t)produced;
+            X.xnode = R.xnode;
+            X.xend = R.xend;
+            X.xret = R.xret;
+            const double ratio = 1.125 * (double)produced / (double)wb.total;
+            if (ratio > ctx->reuse_ratio) ctx->reuse_ratio = ratio;
+            break;
+        }
+        xpool.release(R.xnode);
+        xpool.release(R.xend);
+        xpool.release(R.xret);
+        if (attempt >= 2) {
+            set_error("walk reuse: extra-record capacity did not settle");
+            return RW_ERR_CAPACITY;
+        }
+    }
+    // bucket the extra records by walk row
+    unsigned long long* rows = alloc_n<unsigned long long>(pool, nw);
+    X.xrec = alloc_n<int2>(xpool, X.count);
+    if (!rows || !X.xrec) return RW_ERR_ALLOC;
+    if ((rc = check_cuda(cudaMemsetAsync(rows, 0, sizeof(unsigned long long) * (size_t)nw, s), "memset")))
+        return rc;
+    const int g = grid_for(X.count, 256, ctx->num_sms * 16);
+    if (X.count > 0) {
+        RW_COUNT_LAUNCH();
+        k_extra_count<<<g, 256, 0, s>>>(X.count, X.xnode, T.walk_flag, rows);
+        if ((rc = check_launch("extra counts"))) return rc;
+    }
+    if ((rc = check_cuda(scan_i64(reinterpret_cast<const int64_t*>(rows), X.xbase, nw, s, pool), "scan")) ||
+        (rc = check_cuda(cudaMemsetAsync(rows, 0, sizeof(unsigned long long) * (size_t)nw, s), "memset")))
+        return rc;
+    if (X.count > 0) {
+        RW_COUNT_LAUNCH();
+        k_extra_scatter<<<g, 256, 0, s>>>(X.count, X.xnode, X.xend, X.xret, T.walk_flag, X.xbase, rows, X.xrec);
+        if ((rc = check_launch("extra scatter"))) return rc;
+    }
+    return RW_OK;
+}
+
 }  // namespace rw

@@ -271,3 +271,68 @@ def test_batched_build_matches_per_matrix_oracle(P, ctx):
         ref = oracle.build_factor(A, walks, seeds[m], 1e-3, matrix_index=m)
         assert_factor_equal(t, ref, records=False)
         F.destroy()
+
+
+# ---------------------------------------------------------------------------
+# Walk reuse (Algorithm 2 of Sec. 5.3): the simulated walks are the plain
+# build's; every legal sub-walk they contain counts for its start row.  Y, D
+# and the counters must equal the oracle's reuse build bit for bit.
+
+@pytest.fixture(scope="module")
+def ctx_reuse(P):
+    c = P.Context(options=P.rw_options_default(keep_records=1, reuse=1))
+    yield c
+    c.close()
+
+
+def _reuse_cases():
+    rng = np.random.default_rng(301)
+    yield "grid2d", W.grid2d_5pt(23, 19), 30, 1e-3
+    yield "grid7", W.make_config(2, scale=0.25)["A"], 40, 1e-3
+    yield "grid27", W.make_config(5, scale=0.125)["A"], 12, 1e-3
+    yield "rgg", W.rgg(3000, rng), 25, 0.0
+    yield "longrange", W.make_config(3, scale=0.04)["A"], 20, 2e-2
+    for j in range(3):
+        n = int(rng.integers(2, 300))
+        A = W.random_rmatrix(n, rng, p_edge=float(rng.uniform(0.01, 0.2)),
+                             excess_hi=float(rng.uniform(0.001, 0.5)))
+        yield f"random{j}", A, int(rng.integers(1, 50)), [0.0, 1e-3, 0.1][j]
+
+
+@pytest.mark.parametrize("case", list(range(8)))
+def test_reuse_bit_exact(P, ctx_reuse, case):
+    name, A, walks, drop = list(_reuse_cases())[case]
+    t = gpu_factor(P, ctx_reuse, A, walks, 17 + case, drop)
+    ref = oracle.build_factor(A, walks, 17 + case, drop, reuse=True, records=True)
+    assert_factor_equal(t, ref)
+    wr = ref["walk_rows"]
+    assert int(ref["M"].sum()) > len(wr) * walks or A.n < 4   # sub-walks were counted
+
+
+def test_reuse_per_row_budgets_and_big_rows(P, ctx_reuse):
+    # large budgets push the later rows (which collect most sub-walks) onto the
+    # block merge tables
+    rng = np.random.default_rng(9)
+    A = W.grid2d_5pt(60, 50)
+    budget = np.where(rng.random(A.n) < 0.2, 800, 6).astype(np.uint32)
+    t = gpu_factor(P, ctx_reuse, A, 0, 3, 0.0, budget=budget)
+    ref = oracle.build_factor(A, budget, 3, 0.0, reuse=True, records=True)
+    assert_factor_equal(t, ref)
+    assert ref["M"].max() > 768
+
+
+def test_reuse_extra_walks_reported(P):
+    c = P.Context(options=P.rw_options_default(reuse=1))
+    try:
+        A = W.grid2d_5pt(30, 30)
+        F = P.rw_build_factor(c, P.CSR.from_host(A), 20, 5, 1e-3)
+        ref = oracle.build_factor(A, 20, 5, 1e-3, reuse=True)
+        assert F.desc.total_walks == 20 * len(ref["walk_rows"])
+        assert F.desc.extra_walks == int(ref["M"].sum()) - F.desc.total_walks > 0
+        F.destroy()
+        # reuse is single-matrix only
+        with pytest.raises(P.RwError) as e:
+            P.rw_build_factor_batched(c, [P.CSR.from_host(A), P.CSR.from_host(A)], 4, [1, 2], 0.0)
+        assert e.value.code == -1
+    finally:
+        c.close()
