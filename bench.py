@@ -28,6 +28,11 @@ Other workloads (--workload N):
      third arm sets the walk counts by the adaptive rule of Sec. 5.1
      (margin --adapt-delta, confidence 99 %, at least 20 walks) and solves on
      the same engine as the learned form.
+  6  the paper's Table 1 grids: 7-point Dirichlet Laplacians 50^3 .. 100^3,
+     random order, b = 1, walk reuse (Sec. 5.3), no dropping (as the paper's
+     implementation), the walks per row of each grid set so that the factor
+     size C is Table 1's; value = seconds for the six builds and solves, with
+     C, I, M2 per matrix beside the paper's.
 
 Timing: W warm-up steps, then K steps, each bracketed by CUDA events on the
 library's stream, with an L2 flush (a 512 MB write) between steps outside
@@ -169,6 +174,9 @@ def _oracle_sample_for(workload, cfg, target_s, rng_seed):
         A = cfg["A"][int(np.argmax([a.n for a in cfg["A"]]))]
         return cpu_oracle_sample(A, cfg["walks"], cfg["walk_seed"], cfg["drop_tol"],
                                  "the largest matrix of the 256-RGG batch", target_s, rng_seed)
+    if workload == 6:
+        return cpu_oracle_sample(cfg["A"][0], cfg["walks"], cfg["walk_seed"], 1e-3,
+                                 "the 50^3 Dirichlet grid (m1)", target_s, rng_seed)
     walks = 300 if workload == 5 else cfg["walks"]
     return cpu_oracle_sample(cfg["A"], walks, cfg["walk_seed"], cfg["drop_tol"],
                              f"the {W.CONFIGS[workload]['name']} workload", target_s, rng_seed)
@@ -621,6 +629,121 @@ def run_gpu_learned(args, P, torch, dev, stream, ws, rank, local):
     print(json.dumps(line), flush=True)
 
 
+# Table 1 of the paper, hybrid-solver columns for m1..m6 (the 50^3 .. 100^3
+# Dirichlet grids): factor size C (entries of the Cholesky-like factor,
+# diagonal included), iterations I to 1e-6, total multiplications M2; and
+# Table 4: preconditioning time T1 and solve time T2 (s, one 2.8 GHz CPU).
+PAPER_TABLE1 = {
+    "C": [1.6e6, 2.8e6, 4.4e6, 6.7e6, 9.6e6, 1.3e7],
+    "I": [18, 19, 19, 19, 20, 20],
+    "M2": [8.1e7, 1.5e8, 2.4e8, 3.6e8, 5.5e8, 7.5e8],
+    "T1": [5.38, 10.39, 17.97, 28.78, 44.01, 71.57],
+    "T2": [2.52, 5.80, 10.59, 17.50, 28.61, 41.07],
+}
+
+
+def run_gpu_table1(args, P, torch, dev, stream, ws, rank, local):
+    """Workload 6: the paper's Table 1 grids, regenerated.  Each matrix is put in
+    random order on the GPU (Sec. 5.4).  As in the paper's implementation no
+    entry is dropped (footnote of Sec. 4): the factor size is set by the walks,
+    so the walks per row of each matrix are the integer (bisection, untimed
+    builds) whose factor size C is nearest the paper's (scaled by N when the
+    grids are scaled).  A step builds all six factors (walk reuse of Sec. 5.3
+    unless --no-reuse) and solves b = 1 to 1e-6 in FP64."""
+    cfg = W.make_config(6, scale=args.scale)
+    seed, tol = cfg["walk_seed"], cfg["tol"]
+    reuse = 0 if args.no_reuse else 1
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    mats = []
+    for j, (m, A, b) in enumerate(zip(cfg["edges"], cfg["A"], cfg["b"])):
+        ctx = P.Context(stream=stream, options=P.rw_options_default(reuse=reuse))
+        dA0 = P.CSR.from_host(A, device=dev)
+        perm = torch.empty(A.n, dtype=torch.int32, device=dev)
+        P.rw_random_permutation(ctx, A.n, seed + j, perm)
+        dA = P.rw_permute_csr(ctx, dA0, perm)
+        m_paper = W.CONFIGS[6]["edges"][j]
+        c_target = PAPER_TABLE1["C"][j] * A.n / m_paper ** 3
+        sizes = {}
+
+        def size(walks):
+            if walks not in sizes:
+                F = P.rw_build_factor(ctx, dA, walks, seed, 0.0)
+                sizes[walks] = int(F.desc.nnz) + A.n
+                F.destroy()
+            return sizes[walks]
+
+        if args.walks:
+            walks = args.walks
+        else:
+            lo, hi = 1, 512                       # smallest walks with C >= target, then the nearer neighbour
+            while lo < hi:
+                mid = (lo + hi) // 2
+                if size(mid) >= c_target:
+                    hi = mid
+                else:
+                    lo = mid + 1
+            walks = lo
+            if walks > 1 and abs(size(walks - 1) - c_target) < abs(size(walks) - c_target):
+                walks -= 1
+        F1 = P.rw_build_factor(ctx, dA, walks, seed, 0.0)
+        tuned, _ = P.rw_autotune(ctx, dA, F1, 1, P.RW_FP64)
+        F1.destroy()
+        db = torch.as_tensor(b, device=dev)
+        mats.append(dict(m=m, n=A.n, E=A.nnz, ctx=ctx, dA=dA, db=db, dx=torch.zeros_like(db), walks=walks,
+                         c_target=c_target, tuned=tuned, probes=len(sizes)))
+
+    def step():
+        out = []
+        launches = 0
+        for M in mats:
+            ev[0].record(stream)
+            F = P.rw_build_factor(M["ctx"], M["dA"], M["walks"], seed, 0.0)
+            ev[1].record(stream)
+            rc, st, its, rel = P.pcg_solve(M["ctx"], M["dA"], F, M["db"], M["dx"], tol, 3000, P.RW_FP64)
+            ev[2].record(stream)
+            torch.cuda.synchronize()
+            d = F.desc
+            out.append(dict(T1=ev[0].elapsed_time(ev[1]) * 1e-3, T2=ev[1].elapsed_time(ev[2]) * 1e-3,
+                            I=int(its.max()), rel=float(rel.max()), C=int(d.nnz) + M["n"], hops=int(d.total_hops),
+                            walks=int(d.total_walks), extra=int(d.extra_walks), walk_ms=d.phase_ms[1], rc=rc))
+            launches += int(d.kernel_launches) + int(st.kernel_launches)
+            F.destroy()
+        return dict(rows=out, launches=launches)
+
+    timer = Timer(torch, dev, stream)
+    ms, infos, clk = timer.run(step, args.steps, args.warmup, ws, local)
+    _, ms = aggregate(0, ms, ws)
+    for M in mats:
+        M["ctx"].close()
+    if rank != 0:
+        return
+    rows = []
+    for j, M in enumerate(mats):
+        r = infos[-1]["rows"][j]
+        M1 = 2 * r["C"] + M["E"] + 4 * M["n"]
+        rows.append({"matrix": f"m{j + 1}", "edge": M["m"], "N": M["n"], "E": M["E"], "walks_per_row": M["walks"],
+                     "C": r["C"], "C_paper_scaled": round(M["c_target"]), "M1": M1, "I": r["I"],
+                     "M2": M1 * r["I"], "rel_residual": r["rel"],
+                     "T1_s": statistics.mean(i["rows"][j]["T1"] for i in infos),
+                     "T2_s": statistics.mean(i["rows"][j]["T2"] for i in infos),
+                     "walks": r["walks"], "extra_walks": r["extra"], "hops": r["hops"],
+                     "walk_kernel_ms": r["walk_ms"], "size_probes": M["probes"],
+                     "paper": {k: PAPER_TABLE1[k][j] for k in PAPER_TABLE1}})
+    name = W.CONFIGS[6]["name"] + ("" if args.scale == 1.0 else f" (edge scale {args.scale})")
+    line = _base_line(args, ws, ms, "f64",
+                      {"workload": name, "reuse": bool(reuse), "ordering": "random (GPU)",
+                       "walks_per_row": "per matrix: factor size C of Table 1" if not args.walks else args.walks,
+                       "drop_tol": 0.0, "rhs": "b = 1", "pcg_tol": tol,
+                       "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{ws}"})
+    line.update({
+        "value": ms * 1e-3, "unit": "s (build + solve, m1-m6)", "higher_is_better": False,
+        "paper_s": sum(PAPER_TABLE1["T1"]) + sum(PAPER_TABLE1["T2"]),
+        "matrices": rows, "clocks": clk, "gpu_launches": infos[-1]["launches"],
+        "autotuned": [M["tuned"] for M in mats],
+    })
+    print(json.dumps(line), flush=True)
+
+
 def run_gpu(args):
     import torch
     import paper_math_0609672_gb300 as P
@@ -632,6 +755,8 @@ def run_gpu(args):
         run_gpu_single(args, P, torch, dev, stream, ws, rank, local)
     elif args.workload == 4:
         run_gpu_batched(args, P, torch, dev, stream, ws, rank, local)
+    elif args.workload == 6:
+        run_gpu_table1(args, P, torch, dev, stream, ws, rank, local)
     else:
         run_gpu_learned(args, P, torch, dev, stream, ws, rank, local)
 
@@ -642,10 +767,13 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", type=int, default=2, choices=[2, 3, 4, 5])
+    ap.add_argument("--workload", type=int, default=2, choices=[2, 3, 4, 5, 6])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nmat", type=int, default=None, help="workload 4: number of matrices (default 256)")
-    ap.add_argument("--scale", type=float, default=1.0, help="workload 5: grid edge scale (default 1)")
+    ap.add_argument("--scale", type=float, default=1.0, help="workloads 5, 6: grid edge scale (default 1)")
+    ap.add_argument("--walks", type=int, default=0,
+                    help="workload 6: walks per row (default: the count that gives Table 1's factor size)")
+    ap.add_argument("--no-reuse", action="store_true", help="workload 6: no walk reuse")
     ap.add_argument("--train-instances", type=int, default=50, help="workload 5: training instances")
     ap.add_argument("--train-edge", type=int, default=64, help="workload 5: training grid edge")
     ap.add_argument("--epochs", type=int, default=10, help="workload 5: training epochs")

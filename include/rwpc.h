@@ -105,6 +105,10 @@ typedef struct {
                                 ends below k' or at ground; one-step sub-walks excluded; walks of
                                 one start row never overlap).  Y, D and the counters then hold
                                 all these walks (default 0) */
+    int32_t walk_fuse;       /* walk kernel, nodes of more than 7 neighbours: 1 = read each
+                                scanned block's successor words with its thresholds (fewer
+                                dependent loads), 0 = read only the chosen block's (fewer bytes),
+                                -1 = 1 when the walk tables fit in 3/4 of L2 (default -1) */
 } rw_options;
 
 typedef struct rw_context rw_context;

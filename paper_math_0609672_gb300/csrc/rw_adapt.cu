@@ -143,6 +143,8 @@ rw_status rw_adaptive_budget(rw_context* ctx, const rw_csr* A, uint64_t seed, do
         if (!rec) return RW_ERR_ALLOC;
         WalkBatch wb;
         wb.m0 = mat_walk(T, seed, 0, 0);  // factor walks: the ones rw_build_factor_budget runs
+        wb.table_bytes = table_bytes(T);
+    wb.nrows = T.n_walk_rows;
         wb.wrow = T.wrow;
         wb.wbase = ws.wbase;
         wb.wofs = M;  // walks M, M+1, ... of each row

@@ -143,6 +143,7 @@ void rw_options_default(rw_options* opt) {
     opt->walk_blocks_per_sm = 0;
     opt->timing = 1;
     opt->graphs = 1;
+    opt->walk_fuse = -1;
 }
 
 const char* rw_status_string(rw_status s) {
@@ -180,10 +181,12 @@ rw_status rw_context_create(rw_context** out, void* stream, rw_alloc_fn alloc, r
     else rw_options_default(&c->opt);
     if (c->opt.max_steps < 1) c->opt.max_steps = 1ull << 24;
     rw_status rc;
+    int l2 = 0;
     if ((rc = check_cuda(cudaGetDevice(&c->device), "cudaGetDevice")) ||
         (rc = check_cuda(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount,
                                                 c->device),
                          "device attribute")) ||
+        (rc = check_cuda(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, c->device), "device attribute")) ||
         (rc = check_cuda(cudaMalloc(&c->d_status, sizeof(DevStatus)), "cudaMalloc status")) ||
         (rc = check_cuda(cudaMallocHost(&c->h_status, sizeof(DevStatus)), "cudaMallocHost")) ||
         (rc = check_cuda(cudaMallocHost(&c->h_small, 4096), "cudaMallocHost"))) {
@@ -196,6 +199,7 @@ rw_status rw_context_create(rw_context** out, void* stream, rw_alloc_fn alloc, r
             return rc;
         }
     }
+    c->l2_bytes = (size_t)(l2 > 0 ? l2 : 0);
     // a fresh context reports no error until a call sets one
     if ((rc = reset_status(c)) || (rc = check_cuda(cudaStreamSynchronize(c->stream), "sync"))) {
         rw_context_destroy(c);
@@ -430,6 +434,8 @@ static rw_status build_factors(rw_context* ctx, std::vector<MatBuild>& mbs, uint
         }
         wb.nmat = nmat;
         wb.total = total;
+        for (const auto& mb : mbs) wb.table_bytes += table_bytes(mb.T);
+        wb.nrows = (int32_t)rows;
         if (nmat == 1) {
             wb.m0 = hmats[0];
             wb.wrow = mbs[0].T.wrow;

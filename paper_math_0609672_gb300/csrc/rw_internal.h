@@ -22,6 +22,7 @@ struct rw_context {
     rw::DevStatus* h_status = nullptr;  // pinned host copy
     void* h_small = nullptr;            // pinned host scratch (256 bytes)
     double reuse_ratio = 8.0;           // walk reuse: extra records per walk to allocate for
+    size_t l2_bytes = 0;                // L2 cache size of the device
     cudaEvent_t ev[16] = {};
 };
 
@@ -77,18 +78,26 @@ inline int grid_for(int64_t work, int block, int max_blocks) {
 // ---- build path (rw_tables.cu, rw_walk.cu, rw_emit.cu, rw_levels.cu) -------
 
 // Walk tables of one matrix, in the layout read by the walk kernel.
-//  thr:  per node a block of 8*blk32 uint32 words: [deg, t_0 .. t_{deg-1}, pad]
-//  nxt:  same indexing: nxt[w] = {column of threshold word w, block offset of that column}
-//  fthr: per walk row a block [updeg, lowdeg, ft_0 .. ft_{updeg-1}, pad]
-// Block offsets are in units of 8 words (32 bytes): every block starts on a
-// DRAM sector boundary.  Padding thresholds are 0xFFFFFFFF.
+//  tab:   per node ceil((1 + deg) / 8) blocks of 16 uint32 words (64 bytes).
+//         Slot j of a node's slot sequence (slot 0 = header, slot s + 1 =
+//         successor s in ascending column order) lives in block j / 8 at
+//         word j % 8 (threshold; the header slot holds deg) and word
+//         8 + j % 8 (the successor word: the index of that successor's first
+//         block, bit 31 set when the successor has more than one block; 0
+//         for the header and padding).  A hop to a node of one block reads
+//         that block: the thresholds and the successor words arrive together.
+//  bnode: [blocks] the node each block belongs to.
+//  fthr:  per walk row a block [updeg, lowdeg, ft_0 .. ft_{updeg-1}, pad].
+// First-block indices increase with the node index, so the walk compares
+// block indices instead of node indices (home: below the start row's block,
+// return: equal to it).  Padding thresholds are 0xFFFFFFFF.
 struct Tables {
     int32_t n = 0;
-    uint32_t* thr = nullptr;
-    uint2* nxt = nullptr;
+    uint32_t* tab = nullptr;
+    int32_t* bnode = nullptr;
     uint32_t* fthr = nullptr;
-    uint32_t* toff8 = nullptr;    // [n+1]
-    uint32_t* foff8 = nullptr;    // [n+1]
+    uint32_t* toff = nullptr;     // [n+1] first block of each node (64-byte blocks)
+    uint32_t* foff8 = nullptr;    // [n+1] first-step blocks (32-byte blocks)
     int32_t* deg = nullptr;       // [n] off-diagonal count
     int32_t* lowdeg = nullptr;    // [n] entries with column < row
     double* S = nullptr;          // [n] sum_{j>k} A_kj
@@ -96,9 +105,9 @@ struct Tables {
     int32_t* diag_pos = nullptr;  // [n] CSR position of the diagonal
     uint32_t* walk_flag = nullptr;    // [n+1] scanned into the walk-row index
     int32_t n_walk_rows = 0;
-    int4* wrow = nullptr;         // [n_walk_rows] {k, foff8_k, toff8_k, lowdeg_k}
+    int4* wrow = nullptr;         // [n_walk_rows] {k, foff8_k, toff_k, lowdeg_k}
     int32_t* walk_rows = nullptr; // [n_walk_rows] k ascending
-    uint64_t table_words = 0, first_words = 0;
+    uint64_t blocks = 0, first_words = 0;
 };
 
 rw_status build_tables(rw_context* ctx, const rw_csr* A, Tables& T, Pool& pool);
@@ -125,8 +134,8 @@ struct WalkLaunch {
 // Tables, key and tag of one matrix as the walk kernel reads them.  The tag
 // is (matrix_index << 2) | kind (kind 0: factor walks, 1: pilot walks).
 struct MatWalk {
-    const uint32_t* thr;
-    const uint2* nxt;
+    const uint32_t* tab;
+    const int32_t* bnode;
     const uint32_t* fthr;
     uint32_t key0, key1, tag, pad;
 };
@@ -134,6 +143,8 @@ struct MatWalk {
 // The walk index space of one launch (one matrix, or several concatenated).
 struct WalkBatch {
     int nmat = 1;
+    uint64_t table_bytes = 0;      // walk-table bytes of all matrices
+    int32_t nrows = 0;             // walk rows of all matrices
     MatWalk m0{};                  // the single matrix (nmat == 1)
     const MatWalk* mats = nullptr; // [nmat] device (nmat > 1)
     const int32_t* wmat = nullptr; // [walk rows] matrix of each walk row (nmat > 1)
@@ -144,8 +155,10 @@ struct WalkBatch {
     int64_t total = 0;
 };
 
+inline uint64_t table_bytes(const Tables& T) { return T.blocks * 64u; }
+
 inline MatWalk mat_walk(const Tables& T, uint64_t seed, uint32_t matrix_index, uint32_t kind) {
-    return MatWalk{T.thr, T.nxt, T.fthr, (uint32_t)seed, (uint32_t)(seed >> 32),
+    return MatWalk{T.tab, T.bnode, T.fthr, (uint32_t)seed, (uint32_t)(seed >> 32),
                    (matrix_index << 2) | (kind & 3u), 0u};
 }
 

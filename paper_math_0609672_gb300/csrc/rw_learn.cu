@@ -697,6 +697,8 @@ static rw_status pilot_run(rw_context* ctx, const rw_csr* A, uint32_t walks, uin
     if (!rec || !hops) return RW_ERR_ALLOC;
     WalkBatch wb;
     wb.m0 = mat_walk(T, seed, 0, 1);  // kind 1: pilot walks
+    wb.table_bytes = table_bytes(T);
+    wb.nrows = T.n_walk_rows;
     wb.wrow = T.wrow;
     wb.wbase = ws.wbase;
     wb.chunk_row = ws.chunk_row;

@@ -167,36 +167,40 @@ __global__ void k_row_info(int32_t n, int64_t nnz, const int32_t* __restrict__ r
     }
 }
 
-// Thresholds and successor entries.  One thread per row; the sums run
+// Thresholds and successor block indices.  One thread per row; the sums run
 // sequentially over the row in ascending column order, each addition and
 // division rounded once (the same order the sampling rule is defined in).
 __global__ void k_fill_tables(int32_t n, const int32_t* __restrict__ rp,
                               const int32_t* __restrict__ col, const double* __restrict__ val,
                               const int32_t* __restrict__ deg, const int32_t* __restrict__ lowdeg,
-                              const int32_t* __restrict__ dpos, const uint32_t* __restrict__ toff8,
-                              const uint32_t* __restrict__ foff8, uint32_t* thr, uint2* nxt,
+                              const int32_t* __restrict__ dpos, const uint32_t* __restrict__ toff,
+                              const uint32_t* __restrict__ foff8, uint32_t* tab, int32_t* bnode,
                               uint32_t* fthr, double* S, double* diag) {
     for (int32_t l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x) {
         const int32_t s = rp[l], e = rp[l + 1], dp = dpos[l], d = deg[l], lo = lowdeg[l];
         const double dg = val[dp];
         diag[l] = dg;
-        const uint64_t tb = (uint64_t)toff8[l] * 8u;
-        const uint64_t tend = (uint64_t)toff8[l + 1] * 8u;
-        thr[tb] = (uint32_t)d;
-        nxt[tb] = make_uint2(0u, 0u);
+        const uint64_t b0 = toff[l], b1 = toff[l + 1];
+        for (uint64_t b = b0; b < b1; ++b) bnode[b] = l;
+        // slot j: threshold at word 16 * (b0 + j / 8) + j % 8, successor at + 8
+        auto word = [&](uint64_t j) -> uint32_t* { return tab + (b0 + j / 8u) * 16u + (j % 8u); };
+        *word(0) = (uint32_t)d;
+        word(0)[8] = 0u;
         double c = 0.0;
-        uint64_t w = tb + 1;
+        uint64_t j = 1;
         for (int32_t p = s; p < e; ++p) {
             if (p == dp) continue;
             c = __dadd_rn(c, -val[p]);
-            thr[w] = cumulative_threshold(c, dg);
-            const int32_t j = col[p];
-            nxt[w] = make_uint2((uint32_t)j, toff8[j]);
-            ++w;
+            uint32_t* w = word(j);
+            w[0] = cumulative_threshold(c, dg);
+            const int32_t jc = col[p];
+            w[8] = toff[jc] | (toff[jc + 1] - toff[jc] > 1u ? 0x80000000u : 0u);  // flag: several blocks
+            ++j;
         }
-        for (; w < tend; ++w) {
-            thr[w] = 0xFFFFFFFFu;
-            nxt[w] = make_uint2(0u, 0u);
+        for (; j < (b1 - b0) * 8u; ++j) {
+            uint32_t* w = word(j);
+            w[0] = 0xFFFFFFFFu;
+            w[8] = 0u;
         }
         const int32_t up = d - lo;
         double cu = 0.0;
@@ -219,12 +223,12 @@ __global__ void k_fill_tables(int32_t n, const int32_t* __restrict__ rp,
 }
 
 __global__ void k_walk_rows(int32_t n, const uint32_t* __restrict__ widx,
-                            const uint32_t* __restrict__ toff8, const uint32_t* __restrict__ foff8,
+                            const uint32_t* __restrict__ toff, const uint32_t* __restrict__ foff8,
                             const int32_t* __restrict__ lowdeg, int4* wrow, int32_t* walk_rows) {
     for (int32_t l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x) {
         const uint32_t r = widx[l];
         if (widx[l + 1] != r) {
-            wrow[r] = make_int4(l, (int)foff8[l], (int)toff8[l], lowdeg[l]);
+            wrow[r] = make_int4(l, (int)foff8[l], (int)toff[l], lowdeg[l]);
             walk_rows[r] = l;
         }
     }
@@ -237,25 +241,25 @@ rw_status build_tables(rw_context* ctx, const rw_csr* A, Tables& T, Pool& pool) 
     T.deg = alloc_n<int32_t>(pool, n);
     T.lowdeg = alloc_n<int32_t>(pool, n);
     T.diag_pos = alloc_n<int32_t>(pool, n);
-    T.toff8 = alloc_n<uint32_t>(pool, n + 1);
+    T.toff = alloc_n<uint32_t>(pool, n + 1);
     T.foff8 = alloc_n<uint32_t>(pool, n + 1);
     T.walk_flag = alloc_n<uint32_t>(pool, n + 1);
     T.S = alloc_n<double>(pool, n);
     T.diag = alloc_n<double>(pool, n);
-    if (!T.deg || !T.lowdeg || !T.diag_pos || !T.toff8 || !T.foff8 || !T.walk_flag || !T.S ||
+    if (!T.deg || !T.lowdeg || !T.diag_pos || !T.toff || !T.foff8 || !T.walk_flag || !T.S ||
         !T.diag)
         return RW_ERR_ALLOC;
     const int blocks = grid_for(n, 256, ctx->num_sms * 8);
     RW_COUNT_LAUNCH();
     k_row_info<<<blocks, 256, 0, s>>>(n, A->nnz, A->row_ptr, A->col, A->val, T.deg, T.lowdeg, T.diag_pos,
-                                      T.toff8, T.foff8, T.walk_flag, ctx->d_status);
+                                      T.toff, T.foff8, T.walk_flag, ctx->d_status);
     rw_status rc = check_launch("row info");
     if (rc) return rc;
-    if ((rc = check_cuda(scan_u32(T.toff8, T.toff8, n, s, pool), "scan"))) return rc;
+    if ((rc = check_cuda(scan_u32(T.toff, T.toff, n, s, pool), "scan"))) return rc;
     if ((rc = check_cuda(scan_u32(T.foff8, T.foff8, n, s, pool), "scan"))) return rc;
     if ((rc = check_cuda(scan_u32(T.walk_flag, T.walk_flag, n, s, pool), "scan"))) return rc;
     uint32_t* hs = static_cast<uint32_t*>(ctx->h_small);
-    if ((rc = check_cuda(cudaMemcpyAsync(hs, T.toff8 + n, 4, cudaMemcpyDeviceToHost, s), "copy")))
+    if ((rc = check_cuda(cudaMemcpyAsync(hs, T.toff + n, 4, cudaMemcpyDeviceToHost, s), "copy")))
         return rc;
     if ((rc = check_cuda(cudaMemcpyAsync(hs + 1, T.foff8 + n, 4, cudaMemcpyDeviceToHost, s),
                          "copy")))
@@ -264,22 +268,26 @@ rw_status build_tables(rw_context* ctx, const rw_csr* A, Tables& T, Pool& pool) 
                          "copy")))
         return rc;
     if ((rc = read_status(ctx, "matrix validation"))) return rc;
-    T.table_words = (uint64_t)hs[0] * 8u;
+    T.blocks = hs[0];
+    if (T.blocks >= 0x80000000ull) {
+        set_error("walk tables: %llu blocks exceed the 2^31 block-index range", (unsigned long long)T.blocks);
+        return RW_ERR_CAPACITY;
+    }
     T.first_words = (uint64_t)hs[1] * 8u;
     T.n_walk_rows = (int32_t)hs[2];
-    T.thr = alloc_n<uint32_t>(pool, (int64_t)T.table_words);
-    T.nxt = alloc_n<uint2>(pool, (int64_t)T.table_words);
+    T.tab = alloc_n<uint32_t>(pool, (int64_t)T.blocks * 16);
+    T.bnode = alloc_n<int32_t>(pool, (int64_t)T.blocks);
     T.fthr = alloc_n<uint32_t>(pool, (int64_t)T.first_words);
     T.wrow = alloc_n<int4>(pool, T.n_walk_rows);
     T.walk_rows = alloc_n<int32_t>(pool, T.n_walk_rows);
-    if (!T.thr || !T.nxt || !T.fthr || !T.wrow || !T.walk_rows) return RW_ERR_ALLOC;
+    if (!T.tab || !T.bnode || !T.fthr || !T.wrow || !T.walk_rows) return RW_ERR_ALLOC;
     RW_COUNT_LAUNCH();
     k_fill_tables<<<blocks, 256, 0, s>>>(n, A->row_ptr, A->col, A->val, T.deg, T.lowdeg,
-                                         T.diag_pos, T.toff8, T.foff8, T.thr, T.nxt, T.fthr, T.S,
+                                         T.diag_pos, T.toff, T.foff8, T.tab, T.bnode, T.fthr, T.S,
                                          T.diag);
     if ((rc = check_launch("fill tables"))) return rc;
     RW_COUNT_LAUNCH();
-    k_walk_rows<<<blocks, 256, 0, s>>>(n, T.walk_flag, T.toff8, T.foff8, T.lowdeg, T.wrow,
+    k_walk_rows<<<blocks, 256, 0, s>>>(n, T.walk_flag, T.toff, T.foff8, T.lowdeg, T.wrow,
                                        T.walk_rows);
     return check_launch("walk rows");
 }

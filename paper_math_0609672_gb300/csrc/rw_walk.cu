@@ -4,9 +4,12 @@
 // Persistent kernel, one warp lane per walk.  A warp claims kWalkChunk walk
 // indices at a time from a global cursor; a lane whose walk ends takes the next
 // index of the warp's pool, so the warp stays full although walk lengths vary
-// by orders of magnitude.  A hop reads the 32-byte threshold block of the
-// current node (one DRAM sector for degree <= 7) and one 8-byte successor entry
-// {column, block offset of the column}, so no row-pointer lookup is needed.
+// by orders of magnitude.  A hop reads one 64-byte block of the current node
+// (the whole node for degree <= 7): its thresholds and, beside them, the
+// first-block index of every successor, so the next node is known when the
+// block arrives -- one dependent memory access per hop.  The walk works in
+// block indices (they increase with the node index); the end node's index is
+// looked up once, when the walk ends.
 //
 // Walk w of row k (rows 0..k-1 are homes, ground absorbs):
 //   step 1: draw 0 picks an upper neighbour j > k with probability
@@ -16,7 +19,8 @@
 //   the walk ends at a node < k (home) or at ground; each visit to k counts a
 //   return.  Draw s is word (s mod 4) of Philox(s/4, w, k, tag).
 // Output: one record per walk, {end node (-1 ground, -2 step cap), returns or
-// length}.
+// length}; the kernel writes a home end as its first-block index and
+// k_rec_nodes converts it after the launch.
 #include "rw_internal.h"
 
 namespace rw {
@@ -35,6 +39,7 @@ struct WalkParams {
     DevStatus* st;
     uint64_t max_steps;
     int record_lengths;
+    int fuse_multi;                     // read successor words with every scanned block
     MatWalk m0;                         // the matrix of a single-matrix launch
 };
 
@@ -50,6 +55,76 @@ __device__ __forceinline__ uint4 ld_nc4(const uint32_t* p) {
     return __ldg(reinterpret_cast<const uint4*>(p));
 }
 
+constexpr uint32_t kMultiFlag = 0x80000000u;  // successor word: node of more than one block
+constexpr uint32_t kBlockMask = 0x7FFFFFFFu;
+
+// 32 bytes (eight words) in one load; p must be 32-byte aligned (blocks are
+// 64-byte aligned, their threshold and successor halves 32-byte aligned).
+__device__ __forceinline__ void ld_nc8(const uint32_t* p, uint4& lo, uint4& hi) {
+    asm("ld.global.nc.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=r"(lo.x), "=r"(lo.y), "=r"(lo.z), "=r"(lo.w), "=r"(hi.x), "=r"(hi.y), "=r"(hi.z), "=r"(hi.w)
+        : "l"(p));
+}
+
+// Word j (0..7) of the eight words {c, d}.
+__device__ __forceinline__ uint32_t pick8(const uint4 c, const uint4 d, uint32_t j) {
+    const uint32_t lo = (j & 2u) ? ((j & 1u) ? c.w : c.z) : ((j & 1u) ? c.y : c.x);
+    const uint32_t hi = (j & 2u) ? ((j & 1u) ? d.w : d.z) : ((j & 1u) ? d.y : d.x);
+    return (j & 4u) ? hi : lo;
+}
+
+// One transition from the node of successor word cw (first-block index, bit
+// 31 set when the node has more than 7 neighbours), with draw u: the least
+// successor m whose threshold exceeds u, ground if none.  Returns that
+// successor's word; *ground is set when the walk is absorbed.
+// `together`: the successor half of each scanned block is read with its
+// threshold half (one round trip per block, 64 bytes); otherwise the
+// threshold halves are scanned and only the chosen successor word is read
+// afterwards (36 bytes for a node of one block, a second round trip).  The
+// first suits a lane whose latency is exposed (few walks left in flight), the
+// second a kernel limited by the bytes the L1 delivers.
+__device__ __forceinline__ uint32_t hop_block(const uint32_t* __restrict__ tab, uint32_t cw, uint32_t u,
+                                              bool together, bool* ground) {
+    const uint32_t* blk = tab + (size_t)(cw & kBlockMask) * 16u;
+    uint4 a, b, c = make_uint4(0u, 0u, 0u, 0u), d = c;
+    ld_nc8(blk, a, b);
+    if (together) ld_nc8(blk + 8, c, d);
+    const uint32_t deg = a.x;
+    uint32_t m = (uint32_t)(a.y <= u) + (uint32_t)(a.z <= u) + (uint32_t)(a.w <= u) + (uint32_t)(b.x <= u) +
+                 (uint32_t)(b.y <= u) + (uint32_t)(b.z <= u) + (uint32_t)(b.w <= u);
+    uint32_t bi = 0;
+    if (m == 7u && deg > 7u) {
+        for (bi = 1;; ++bi) {
+            const uint32_t* nb = blk + 16u * bi;
+            uint4 t0, t1;
+            ld_nc8(nb, t0, t1);
+            if (together) ld_nc8(nb + 8, c, d);
+            const uint32_t cnt = count_le8(t0, t1, u);
+            m += cnt;
+            if (cnt < 8u || m >= deg) break;
+        }
+    }
+    *ground = m >= deg;
+    const uint32_t j = (m + 1u) & 7u;
+    if (together) return pick8(c, d, j);
+    return m < deg ? __ldg(blk + 16u * bi + 8u + j) : 0u;
+}
+
+// Whether a hop from successor word cw reads successor words together with
+// thresholds: always in the tail of the launch (the warp has no walks left to
+// claim); for nodes of several blocks also when the tables fit in L2.
+__device__ __forceinline__ bool read_together(uint32_t cw, bool tail, int fuse_multi) {
+    return tail || (fuse_multi != 0 && (cw & kMultiFlag) != 0u);
+}
+
+// First step of a walk from the row with first block kb, lower degree lo:
+// the successor word of successor lo + m.
+__device__ __forceinline__ uint32_t first_successor(const uint32_t* __restrict__ tab, uint32_t kb, uint32_t lo,
+                                                    uint32_t m) {
+    const uint32_t slot = lo + m + 1u;
+    return __ldg(tab + ((size_t)kb + (slot >> 3)) * 16u + 8u + (slot & 7u));
+}
+
 template <bool MULTI>
 __global__ void __launch_bounds__(256) k_walk(const WalkParams P) {
     const unsigned lane = lane_id();
@@ -61,10 +136,9 @@ __global__ void __launch_bounds__(256) k_walk(const WalkParams P) {
 
     bool active = false;
     int64_t widx = 0;
-    uint32_t k = 0, w = 0, coff = 0, ret = 0;
+    uint32_t k = 0, kb = 0, w = 0, coff = 0, ret = 0;
     // the walking lane's matrix (fixed for a single-matrix launch)
-    const uint32_t* thr = P.m0.thr;
-    const uint2* nxt = P.m0.nxt;
+    const uint32_t* tab = P.m0.tab;
     uint32_t key0 = P.m0.key0, key1 = P.m0.key1, tag = P.m0.tag;
     uint64_t h = 0;
     Philox4 rnd{0u, 0u, 0u, 0u};
@@ -107,8 +181,7 @@ __global__ void __launch_bounds__(256) k_walk(const WalkParams P) {
                         my_m = m;
                     }
                     const MatWalk& mw = P.mats[m];
-                    thr = mw.thr;
-                    nxt = mw.nxt;
+                    tab = mw.tab;
                     fthr = mw.fthr;
                     key0 = mw.key0;
                     key1 = mw.key1;
@@ -133,8 +206,8 @@ __global__ void __launch_bounds__(256) k_walk(const WalkParams P) {
                     }
                 }
                 if (m > up - 1u) m = up - 1u;
-                const uint2 e = __ldg(nxt + (size_t)info.z * 8u + 1u + (uint32_t)info.w + m);
-                coff = e.y;
+                kb = (uint32_t)info.z;
+                coff = first_successor(tab, kb, (uint32_t)info.w, m);
                 h = 1;
                 ret = 0;
                 active = true;
@@ -162,32 +235,18 @@ __global__ void __launch_bounds__(256) k_walk(const WalkParams P) {
                 const uint32_t q = sidx & 3u;
                 const uint32_t u = q == 0u ? rnd.v0 : q == 1u ? rnd.v1 : q == 2u ? rnd.v2 : rnd.v3;
                 ++h;
-                const uint32_t* blk = thr + (size_t)coff * 8u;
-                const uint4 a = ld_nc4(blk), b = ld_nc4(blk + 4);
-                const uint32_t deg = a.x;
-                uint32_t m = (uint32_t)(a.y <= u) + (uint32_t)(a.z <= u) + (uint32_t)(a.w <= u) +
-                             (uint32_t)(b.x <= u) + (uint32_t)(b.y <= u) + (uint32_t)(b.z <= u) +
-                             (uint32_t)(b.w <= u);
-                if (m == 7u && deg > 7u) {
-                    for (uint32_t bi = 1;; ++bi) {
-                        const uint4 c = ld_nc4(blk + 8u * bi), d = ld_nc4(blk + 8u * bi + 4u);
-                        const uint32_t cnt = count_le8(c, d, u);
-                        m += cnt;
-                        if (cnt < 8u || m >= deg) break;
-                    }
-                }
-                if (m >= deg) {
-                    end = -1;  // ground
+                bool ground;
+                const uint32_t nw = hop_block(tab, coff, u, read_together(coff, exhausted, P.fuse_multi), &ground);
+                const uint32_t nb = nw & kBlockMask;
+                if (ground) {
+                    end = -1;
+                    done = true;
+                } else if (nb < kb) {
+                    end = (int32_t)nb;  // home, as its first-block index (k_rec_nodes converts it)
                     done = true;
                 } else {
-                    const uint2 e = __ldg(nxt + (size_t)coff * 8u + 1u + m);
-                    if (e.x < k) {
-                        end = (int32_t)e.x;  // home
-                        done = true;
-                    } else {
-                        ret += (e.x == k) ? 1u : 0u;
-                        coff = e.y;
-                    }
+                    ret += (nb == kb) ? 1u : 0u;
+                    coff = nw;
                 }
             }
             if (done) {
@@ -203,6 +262,43 @@ __global__ void __launch_bounds__(256) k_walk(const WalkParams P) {
         my_hops = warp_sum(my_hops);
         if (lane == 0 && my_hops) atomicAdd(P.hops, my_hops);
     }
+}
+
+// Successor words with every scanned block of a node of several blocks when
+// the walk tables fit well inside L2 (rw_options.walk_fuse: 1 always, 0 never,
+// -1 by size).
+static int fuse_multi_blocks(rw_context* ctx, uint64_t table_bytes) {
+    if (ctx->opt.walk_fuse >= 0) return ctx->opt.walk_fuse ? 1 : 0;
+    return table_bytes * 4u <= (uint64_t)ctx->l2_bytes * 3u ? 1 : 0;
+}
+
+// The walk kernels write a home end as its first-block index; this pass turns
+// it into the node index (one warp per walk row; ground -1 and the step-cap
+// mark -2 stay).  Keeping the lookup out of the walk saves a dependent load at
+// the end of every walk.
+__global__ void k_rec_nodes(int32_t nrows, const int64_t* __restrict__ wbase, const int32_t* __restrict__ wmat,
+                            const MatWalk* __restrict__ mats, const int32_t* __restrict__ bnode0, int2* rec) {
+    const int32_t gw = (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int32_t nwarps = (int32_t)((gridDim.x * blockDim.x) >> 5);
+    for (int32_t r = gw; r < nrows; r += nwarps) {
+        const int32_t* bn = wmat ? mats[wmat[r]].bnode : bnode0;
+        for (int64_t i = wbase[r] + lane_id(); i < wbase[r + 1]; i += 32) {
+            int2 v = rec[i];
+            if (v.x >= 0) {
+                v.x = __ldg(bn + v.x);
+                rec[i] = v;
+            }
+        }
+    }
+}
+
+static rw_status rec_nodes(rw_context* ctx, int32_t nrows, const int64_t* wbase, const int32_t* wmat,
+                           const MatWalk* mats, const int32_t* bnode, int2* rec) {
+    if (nrows <= 0) return RW_OK;
+    RW_COUNT_LAUNCH();
+    k_rec_nodes<<<grid_for((int64_t)nrows * 32, 256, ctx->num_sms * 16), 256, 0, ctx->stream>>>(nrows, wbase, wmat,
+                                                                                                 mats, bnode, rec);
+    return check_launch("walk records");
 }
 
 rw_status run_walks(rw_context* ctx, const WalkBatch& wb, const WalkLaunch& wl, int2* rec,
@@ -235,6 +331,7 @@ rw_status run_walks(rw_context* ctx, const WalkBatch& wb, const WalkLaunch& wl, 
     P.st = ctx->d_status;
     P.max_steps = wl.max_steps;
     P.record_lengths = wl.record_lengths;
+    P.fuse_multi = fuse_multi_blocks(ctx, wb.table_bytes);
     P.m0 = wb.m0;
     int per_sm = ctx->opt.walk_blocks_per_sm;
     if (per_sm <= 0) {
@@ -252,6 +349,8 @@ rw_status run_walks(rw_context* ctx, const WalkBatch& wb, const WalkLaunch& wl, 
     if (multi) k_walk<true><<<(unsigned)blocks, 256, 0, s>>>(P);
     else k_walk<false><<<(unsigned)blocks, 256, 0, s>>>(P);
     if ((rc = check_launch("walk kernel"))) return rc;
+    if ((rc = rec_nodes(ctx, wb.nrows, wb.wbase, multi ? wb.wmat : nullptr, wb.mats, wb.m0.bnode, rec)))
+        return rc;
     if (ms) {
         cudaEventRecord(ctx->ev[1], s);
         cudaEventSynchronize(ctx->ev[1]);
@@ -274,10 +373,11 @@ rw_status run_walks(rw_context* ctx, const WalkBatch& wb, const WalkLaunch& wl, 
 // Sub-walks of one start row never overlap (a start is popped before the same
 // node can be pushed again), as the paper requires.  Finished sub-walks go to
 // the warp's shared-memory stage and from there, in bulk, to the global
-// extra-record arrays {start node, end node or -1, returns}.
+// extra-record arrays {start, end or -1, returns}, both as first-block indices
+// (they order like the nodes; the bucketing turns them into node indices).
 struct ReuseParams {
-    int32_t* xnode;
-    int32_t* xend;
+    int32_t* xnode;  // first-block index of the start node
+    int32_t* xend;   // first-block index of the end node, -1 ground
     uint32_t* xret;
     unsigned long long* xcount;  // records produced (may exceed xcap: then none past xcap is written)
     int64_t xcap;
@@ -301,9 +401,8 @@ __global__ void __launch_bounds__(256) k_walk_reuse(const WalkParams P, const Re
 
     bool active = false;
     int64_t widx = 0;
-    uint32_t k = 0, w = 0, coff = 0, ret = 0;
-    const uint32_t* thr = P.m0.thr;
-    const uint2* nxt = P.m0.nxt;
+    uint32_t k = 0, kb = 0, w = 0, coff = 0, ret = 0;
+    const uint32_t* tab = P.m0.tab;
     const uint32_t key0 = P.m0.key0, key1 = P.m0.key1, tag = P.m0.tag;
     uint64_t h = 0;
     Philox4 rnd{0u, 0u, 0u, 0u};
@@ -376,12 +475,12 @@ __global__ void __launch_bounds__(256) k_walk_reuse(const WalkParams P, const Re
                     }
                 }
                 if (m > up - 1u) m = up - 1u;
-                const uint2 e = __ldg(nxt + (size_t)info.z * 8u + 1u + (uint32_t)info.w + m);
-                coff = e.y;
+                kb = (uint32_t)info.z;
+                coff = first_successor(tab, kb, (uint32_t)info.w, m);
                 h = 1;
                 ret = 0;
                 depth = 1;  // the first step's upper neighbour starts the stack
-                top = e.x;
+                top = coff & kBlockMask;
                 top_ret = 0;
                 fresh = true;
                 active = true;
@@ -398,8 +497,8 @@ __global__ void __launch_bounds__(256) k_walk_reuse(const WalkParams P, const Re
         // outcome: 0 idle, 1 moved to node `to`, 2 ended at `to` (home, or -1 ground),
         // 3 stopped (step cap or stack overflow)
         int outcome = 0;
-        int32_t to = 0;
-        uint32_t to_off = 0;
+        int32_t to = 0;        // first-block index of the next node (-1: ground)
+        uint32_t to_word = 0;  // its successor word
         if (active) {
             if (h >= P.max_steps ||
                 ((h & 4095u) == 0u && (ld_relaxed_u32(&P.st->walk_cap) | ld_relaxed_u32(R.overflow)) != 0u)) {
@@ -411,28 +510,15 @@ __global__ void __launch_bounds__(256) k_walk_reuse(const WalkParams P, const Re
                 const uint32_t q = sidx & 3u;
                 const uint32_t u = q == 0u ? rnd.v0 : q == 1u ? rnd.v1 : q == 2u ? rnd.v2 : rnd.v3;
                 ++h;
-                const uint32_t* blk = thr + (size_t)coff * 8u;
-                const uint4 a = ld_nc4(blk), b = ld_nc4(blk + 4);
-                const uint32_t deg = a.x;
-                uint32_t m = (uint32_t)(a.y <= u) + (uint32_t)(a.z <= u) + (uint32_t)(a.w <= u) +
-                             (uint32_t)(b.x <= u) + (uint32_t)(b.y <= u) + (uint32_t)(b.z <= u) +
-                             (uint32_t)(b.w <= u);
-                if (m == 7u && deg > 7u) {
-                    for (uint32_t bi = 1;; ++bi) {
-                        const uint4 c = ld_nc4(blk + 8u * bi), d = ld_nc4(blk + 8u * bi + 4u);
-                        const uint32_t cnt = count_le8(c, d, u);
-                        m += cnt;
-                        if (cnt < 8u || m >= deg) break;
-                    }
-                }
-                if (m >= deg) {
+                bool ground;
+                to_word = hop_block(tab, coff, u, read_together(coff, exhausted, P.fuse_multi), &ground);
+                const uint32_t nb = to_word & kBlockMask;
+                if (ground) {
                     outcome = 2;
-                    to = -1;  // ground
+                    to = -1;
                 } else {
-                    const uint2 e = __ldg(nxt + (size_t)coff * 8u + 1u + m);
-                    to = (int32_t)e.x;
-                    to_off = e.y;
-                    outcome = e.x < k ? 2 : 1;
+                    to = (int32_t)nb;
+                    outcome = nb < kb ? 2 : 1;
                 }
             }
         }
@@ -462,7 +548,7 @@ __global__ void __launch_bounds__(256) k_walk_reuse(const WalkParams P, const Re
             }
         }
         if (outcome == 1) {
-            if ((uint32_t)to == k) {
+            if ((uint32_t)to == kb) {
                 ++ret;  // every candidate is above k, so the stack is empty here
                 fresh = false;
             } else if (depth > 0 && (uint32_t)to == top) {
@@ -478,10 +564,10 @@ __global__ void __launch_bounds__(256) k_walk_reuse(const WalkParams P, const Re
                 top_ret = 0;
                 fresh = true;
             }
-            coff = to_off;
+            coff = to_word;
         }
         if (outcome >= 2) {
-            P.rec[widx] = make_int2(outcome == 2 ? to : -2, (int32_t)ret);
+            P.rec[widx] = make_int2(outcome == 3 ? -2 : to, (int32_t)ret);
             my_hops += h;
             active = false;
             depth = 0;
@@ -494,19 +580,21 @@ __global__ void __launch_bounds__(256) k_walk_reuse(const WalkParams P, const Re
 
 // Extra records -> per walk row: counts, then a scatter into row order (the
 // order inside a row is immaterial: the merge only sums them).
-__global__ void k_extra_count(int64_t cnt, const int32_t* __restrict__ xnode, const uint32_t* __restrict__ wflag,
-                              unsigned long long* rows) {
+__global__ void k_extra_count(int64_t cnt, const int32_t* __restrict__ xnode, const int32_t* __restrict__ bnode,
+                              const uint32_t* __restrict__ wflag, unsigned long long* rows) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x)
-        atomicAdd(rows + wflag[xnode[i]], 1ull);
+        atomicAdd(rows + wflag[bnode[xnode[i]]], 1ull);
 }
 
 __global__ void k_extra_scatter(int64_t cnt, const int32_t* __restrict__ xnode, const int32_t* __restrict__ xend,
-                                const uint32_t* __restrict__ xret, const uint32_t* __restrict__ wflag,
-                                const int64_t* __restrict__ xbase, unsigned long long* fill, int2* xrec) {
+                                const uint32_t* __restrict__ xret, const int32_t* __restrict__ bnode,
+                                const uint32_t* __restrict__ wflag, const int64_t* __restrict__ xbase,
+                                unsigned long long* fill, int2* xrec) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t r = wflag[xnode[i]];
+        const uint32_t r = wflag[bnode[xnode[i]]];
         const int64_t p = xbase[r] + (int64_t)atomicAdd(fill + r, 1ull);
-        xrec[p] = make_int2(xend[i], (int32_t)xret[i]);
+        const int32_t e = xend[i];
+        xrec[p] = make_int2(e >= 0 ? bnode[e] : -1, (int32_t)xret[i]);
     }
 }
 
@@ -558,6 +646,7 @@ rw_status run_walks_reuse(rw_context* ctx, const WalkBatch& wb, const WalkLaunch
     P.st = ctx->d_status;
     P.max_steps = wl.max_steps;
     P.record_lengths = 0;
+    P.fuse_multi = fuse_multi_blocks(ctx, wb.table_bytes);
     P.m0 = wb.m0;
     int64_t cap = (int64_t)(ctx->reuse_ratio * (double)wb.total) + (1 << 16);
     int stack = 64;
@@ -579,6 +668,7 @@ rw_status run_walks_reuse(rw_context* ctx, const WalkBatch& wb, const WalkLaunch
         if (ms) cudaEventRecord(ctx->ev[0], s);
         rc = stack == 64 ? launch_reuse<64>(ctx, P, R) : launch_reuse<1024>(ctx, P, R);
         if (rc) return rc;
+        if ((rc = rec_nodes(ctx, T.n_walk_rows, wb.wbase, nullptr, nullptr, T.bnode, rec))) return rc;
         if (ms) cudaEventRecord(ctx->ev[1], s);
         if ((rc = check_cuda(cudaMemcpyAsync(h64, xcount, 8, cudaMemcpyDeviceToHost, s), "copy")) ||
             (rc = check_cuda(cudaMemcpyAsync(h64 + 1, overflow, 4, cudaMemcpyDeviceToHost, s), "copy")) ||
@@ -625,7 +715,7 @@ rw_status run_walks_reuse(rw_context* ctx, const WalkBatch& wb, const WalkLaunch
     const int g = grid_for(X.count, 256, ctx->num_sms * 16);
     if (X.count > 0) {
         RW_COUNT_LAUNCH();
-        k_extra_count<<<g, 256, 0, s>>>(X.count, X.xnode, T.walk_flag, rows);
+        k_extra_count<<<g, 256, 0, s>>>(X.count, X.xnode, T.bnode, T.walk_flag, rows);
         if ((rc = check_launch("extra counts"))) return rc;
     }
     if ((rc = check_cuda(scan_i64(reinterpret_cast<const int64_t*>(rows), X.xbase, nw, s, pool), "scan")) ||
@@ -633,7 +723,8 @@ rw_status run_walks_reuse(rw_context* ctx, const WalkBatch& wb, const WalkLaunch
         return rc;
     if (X.count > 0) {
         RW_COUNT_LAUNCH();
-        k_extra_scatter<<<g, 256, 0, s>>>(X.count, X.xnode, X.xend, X.xret, T.walk_flag, X.xbase, rows, X.xrec);
+        k_extra_scatter<<<g, 256, 0, s>>>(X.count, X.xnode, X.xend, X.xret, T.bnode, T.walk_flag, X.xbase, rows,
+                                          X.xrec);
         if ((rc = check_launch("extra scatter"))) return rc;
     }
     return RW_OK;

@@ -466,3 +466,24 @@ def test_workload_sizes():
     # Table 1 of the paper: the 50^3 SPARSKIT Laplacian has N = 1.25e5, E = 8.6e5
     t1 = W.grid3d(50, 50, 50, 7, np.random.default_rng(0), excess_frac=0.0, permute=False)
     assert t1.n == 125000 and round(t1.nnz / 1e4) == 86
+
+
+def test_table1_grids():
+    # Table 1: N and E (matrix entries, diagonal included) of m1..m6, printed
+    # to two digits; every row of the Dirichlet Laplacian has diagonal 6 and
+    # the exact factor of the smallest grid gives a PCG solve in one step
+    N = [1.3e5, 2.2e5, 3.4e5, 5.1e5, 7.3e5, 1.0e6]
+    E = [8.6e5, 1.5e6, 2.4e6, 3.5e6, 5.1e6, 6.9e6]
+    for j, m in enumerate((50, 60, 70, 80, 90, 100)):
+        n = m ** 3
+        e = 7 * n - 6 * m * m          # 6 neighbours per node minus the missing boundary ones
+        for got, printed in ((n, N[j]), (e, E[j])):
+            half_unit = 0.5 * 10 ** (math.floor(math.log10(printed)) - 1)
+            assert abs(got - printed) <= half_unit * (1 + 1e-12), (m, got, printed)
+    A = W.laplace3d_dirichlet(6)
+    assert A.n == 216 and A.nnz == 7 * 216 - 6 * 36 and oracle.validate(A) == 0
+    d = A.to_dense()
+    assert np.all(np.diag(d) == 6.0) and set(np.unique(d[d != np.diag(np.diag(d))])) <= {-1.0, 0.0}
+    assert np.allclose(d, d.T) and np.all(np.linalg.eigvalsh(d) > 0)
+    cfg = W.make_config(6, scale=0.1)
+    assert [a.n for a in cfg["A"]] == [e ** 3 for e in cfg["edges"]] and cfg["edges"] == (5, 6, 7, 8, 9, 10)

@@ -193,6 +193,16 @@ def grid3d(nx, ny, nz, stencil, rng, glo=0.1, ghi=10.0, excess_frac_hi=None,
     return assemble(n, ei, ej, g, excess)
 
 
+def laplace3d_dirichlet(m):
+    """7-point finite-difference Laplacian of an m x m x m grid with Dirichlet
+    boundary: every off-diagonal -1 and every diagonal 6, so a boundary node's
+    missing neighbours become its excess (ground).  Natural order."""
+    ei, ej = _grid_edges((m, m, m), _OFF7)
+    n = m * m * m
+    deg = np.bincount(ei, minlength=n) + np.bincount(ej, minlength=n)
+    return assemble(n, ei, ej, np.ones(ei.size), 6.0 - deg)
+
+
 def grid2d_longrange(nx, ny, rng, n_long=2, glo=0.01, ghi=1.0, boundary_excess=1.0,
                      permute=True):
     """2D 5-point unit grid plus `n_long` random long-range edges per row.
@@ -312,6 +322,8 @@ CONFIGS = {
             precision="fp64", gen_seed=3, walk_seed=3, nmat=256),
     5: dict(name="grid3d-27pt-128^3-logU[0.1,10]-excess1e-4", walks=300, drop_tol=1e-3,
             tol=1e-6, nrhs=1, precision="fp32", gen_seed=4, walk_seed=4),
+    6: dict(name="laplace3d-7pt-dirichlet-50^3..100^3", walks=20, drop_tol=None, tol=1e-6, nrhs=1,
+            precision="fp64", gen_seed=5, walk_seed=5, edges=(50, 60, 70, 80, 90, 100)),
 }
 
 
@@ -322,7 +334,7 @@ def _rngs(seed):
 
 
 def make_config(i, scale=1.0, nmat=None):
-    """Inputs for workload i (1..5).
+    """Inputs for workload i (1..6).
 
     Returns dict(A=CSR or list of CSR, b=array or list, plus the settings of
     CONFIGS[i]).  `scale` < 1 shrinks the grid edge lengths (for quick tests);
@@ -355,6 +367,10 @@ def make_config(i, scale=1.0, nmat=None):
         m = max(4, int(round(128 * scale)))
         A = grid3d(m, m, m, 27, rng_a, excess_frac=1e-4)
         b = rhs(A.n, 1, rng_b)
+    elif i == 6:
+        cfg["edges"] = tuple(max(4, int(round(e * scale))) for e in cfg["edges"])
+        A = [laplace3d_dirichlet(e) for e in cfg["edges"]]
+        b = [np.ones(a.n) for a in A]
     else:
         raise ValueError(f"unknown workload {i}")
     cfg["A"] = A
