@@ -92,7 +92,9 @@ typedef struct {
     int32_t solve_blocks_per_sm; /* wide-level solves: 512-thread blocks per SM (0 = 1) */
     int32_t graphs;          /* 1: batched PCG replays each iteration from a CUDA graph (default 1) */
     int32_t wide_slices;     /* wide-level solves: entry slices per row (lanes per row = slices x
-                                right-hand sides, power of two <= 32); 0 = one row per warp */
+                                right-hand sides, power of two <= 32); 0 = one row per warp;
+                                -1 = vector rows: one row per warp, each lane reads all
+                                right-hand sides of its entries */
     int32_t spmv_slices;     /* SpMV: entry slices per row, as wide_slices; 0 = one row per warp */
     int32_t cluster_width;   /* levels of at most this many rows (above the thin-run width) run on
                                 one thread-block cluster with hardware barriers; 0 = never */

@@ -220,6 +220,7 @@ struct SolveRun {
     int thin;                    // 1: one block with shared-memory values; 0: whole grid
     int32_t lev_begin, lev_end;  // levels [begin, end)
     int64_t pos_begin, pos_end;  // positions in the level order
+    int64_t in_entries = 0;      // thin run: entries whose column lies in the run
 };
 struct SolveSchedule {
     int32_t n = 0, depth = 0;

@@ -72,6 +72,20 @@ __global__ void k_sched_count(int32_t n, const int32_t* __restrict__ order,
     }
 }
 
+// In-run entries of each thin run (summed over the warp's lanes of the same
+// run, then one atomic per run and warp).
+__global__ void k_run_in(int32_t n, const int32_t* __restrict__ nin, const int64_t* __restrict__ run_pb,
+                         const int32_t* __restrict__ run_thin, int nruns, unsigned long long* run_in) {
+    for (int32_t b = (blockIdx.x * blockDim.x + threadIdx.x) & ~31; b < n; b += gridDim.x * blockDim.x) {
+        const int32_t p = b + (int32_t)lane_id();
+        const int r = p < n ? run_of_pos(p, run_pb, nruns) : -1;
+        const unsigned v = (p < n && run_thin[r]) ? (unsigned)nin[p] : 0u;
+        const unsigned same = __match_any_sync(kFull, r);  // lanes of the same run
+        const unsigned t = __reduce_add_sync(same, v);
+        if (r >= 0 && (int)lane_id() == __ffs(same) - 1 && t) atomicAdd(run_in + r, (unsigned long long)t);
+    }
+}
+
 // In-run entries first (slot = position - run start), then the external ones
 // (column), each group in the row's original order.
 template <typename TV>
@@ -173,7 +187,23 @@ rw_status build_schedule(rw_context* ctx, int32_t n, const int64_t* rp, const in
     RW_COUNT_LAUNCH();
     k_sched_fill<double><<<blocks, 256, 0, s>>>(n, order, rp, col, val, val32, pos_of, d_pb, d_th,
                                                 nruns, S.tptr, S.tnin, S.tidx, S.tval, S.tval32);
-    return check_launch("schedule fill");
+    if ((rc = check_launch("schedule fill"))) return rc;
+    // in-run entries per thin run (sizes the run's shared-memory copy of them)
+    unsigned long long* run_in = alloc_n<unsigned long long>(scratch, nruns);
+    if (!run_in) return RW_ERR_ALLOC;
+    if ((rc = check_cuda(cudaMemsetAsync(run_in, 0, sizeof(unsigned long long) * nruns, s), "memset")))
+        return rc;
+    RW_COUNT_LAUNCH();
+    k_run_in<<<blocks, 256, 0, s>>>(n, S.tnin, d_pb, d_th, nruns, run_in);
+    if ((rc = check_launch("run entries"))) return rc;
+    std::vector<unsigned long long> hin(nruns);
+    if ((rc = check_cuda(cudaMemcpyAsync(hin.data(), run_in, sizeof(unsigned long long) * nruns,
+                                         cudaMemcpyDeviceToHost, s),
+                         "copy")) ||
+        (rc = check_cuda(cudaStreamSynchronize(s), "sync")))
+        return rc;
+    for (int i = 0; i < nruns; ++i) S.runs[i].in_entries = (int64_t)hin[i];
+    return RW_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -225,7 +255,19 @@ struct ThinParams {
     const T* __restrict__ scale;
     T* x;
     int nrhs;
+    int stage;  // 1: copy the run's in-run entries to shared memory first
+    int stage_entries;
 };
+
+// Shared memory of a thin run: x values [rows][NR], row ids, entry offsets and
+// counts, level starts, staged-entry offsets; then (staged) the in-run values
+// and their slot indices.
+template <typename T, int NR>
+__host__ __device__ __forceinline__ size_t thin_stage_offset(int rows, int nlev) {
+    const size_t base = (size_t)rows * NR * sizeof(T) + (size_t)rows * 12 + (size_t)(nlev + 1) * 4 +
+                        (size_t)(rows + 1) * 4;
+    return (base + 15) & ~(size_t)15;
+}
 
 // in-run entries of one row held in registers: up to 32*U, prefetched ahead
 template <typename T, int U>
@@ -279,6 +321,7 @@ __global__ void __launch_bounds__(kThinThreads) k_thin(const ThinParams<T> P) {
     const int64_t run_e0 = P.tptr[P.pos_begin];
     const int32_t* tidx = P.tidx + run_e0;
     const T* tval = P.tval + run_e0;
+    int32_t* soff = lstart + nlev + 1;  // [rows + 1] staged: first entry of each slot
 
     for (int i = threadIdx.x; i <= nlev; i += blockDim.x)
         lstart[i] = (int32_t)(P.lptr[P.lev_begin + i] - P.pos_begin);
@@ -296,6 +339,68 @@ __global__ void __launch_bounds__(kThinThreads) k_thin(const ThinParams<T> P) {
         }
     }
     __syncthreads();
+    if (P.stage) {
+        // the run's in-run entries to shared memory: offsets by a block scan of
+        // the per-slot counts, then every entry copied by one thread (its slot
+        // found by binary search), so the copy is one round of loads
+        T* sval = reinterpret_cast<T*>(smem + thin_stage_offset<T, NR>(rows, nlev));
+        int32_t* sidx = reinterpret_cast<int32_t*>(sval + P.stage_entries);
+        constexpr int kPer = (kThinMaxRows + kThinThreads - 1) / kThinThreads;
+        int loc[kPer];
+        int sum = 0;
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+            const int sl = threadIdx.x * kPer + i;
+            loc[i] = sl < rows ? ecnt[sl] : 0;
+            sum += loc[i];
+        }
+        __shared__ int wtot[kThinThreads / 32];
+        int incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) wtot[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const int t = wtot[lane];
+            int ti = t;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(kFull, ti, o);
+                if (lane >= o) ti += y;
+            }
+            wtot[lane] = ti - t;
+        }
+        __syncthreads();
+        int pre = wtot[warp] + incl - sum;
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+            const int sl = threadIdx.x * kPer + i;
+            if (sl < rows) soff[sl] = pre;
+            if (sl == rows - 1) soff[rows] = pre + loc[i];
+            pre += loc[i];
+        }
+        __syncthreads();
+        const int total = soff[rows];
+        for (int g = threadIdx.x; g < total; g += blockDim.x) {
+            int lo = 0, hi = rows - 1;  // the last slot whose offset is <= g
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (soff[mid] <= g) lo = mid;
+                else hi = mid - 1;
+            }
+            const int src = eoff[lo] + (g - soff[lo]);
+            sidx[g] = tidx[src];
+            sval[g] = tval[src];
+        }
+        __syncthreads();
+        for (int sl = threadIdx.x; sl < rows; sl += blockDim.x) eoff[sl] = soff[sl];
+        tidx = sidx;
+        tval = sval;
+        __syncthreads();
+    }
 
     // phase 2: the levels in order; in each level warp w takes rows w, w+32, ...
     auto fetch = [&](int li, RowRegs<T, U>& R) {
@@ -458,11 +563,153 @@ struct RowGroup {
     }
 };
 
+// Vector rows (rw_options.wide_slices = -1): one warp per row; lane l owns
+// entries s + l, s + l + 32, ... and reads all right-hand sides of each entry
+// in one vector load, so each entry's column and value are loaded once (not
+// once per right-hand side) and 4 entries per lane prefetched cover rows of
+// up to 128 entries: a long row costs one round of x loads like a short one.
+// The NR partial sums are reduced by halving: at each of the first log2(NR)
+// butterfly steps a lane keeps half of its sums and adds its partner's half,
+// then plain butterfly steps; lane j * 32 / NR ends with the sum of
+// right-hand side j.
+template <typename T, int NR>
+__device__ __forceinline__ T halving_sum(T (&a)[NR], int lane) {
+    int cnt = NR;
+    int off = 16;
+#pragma unroll
+    for (int st = 0; st < 5; ++st) {
+        if (cnt > 1) {
+            const bool upper = (lane & off) != 0;
+            const int h = cnt / 2;
+#pragma unroll
+            for (int i = 0; i < NR / 2; ++i) {
+                if (i < h) {
+                    const T send = upper ? a[i] : a[i + h];
+                    const T keep = upper ? a[i + h] : a[i];
+                    a[i] = keep + __shfl_xor_sync(kFull, send, off);
+                }
+            }
+            cnt = h;
+        } else {
+            a[0] += __shfl_xor_sync(kFull, a[0], off);
+        }
+        off >>= 1;
+    }
+    return a[0];
+}
+
+template <typename T, int NR>
+struct RowVec {
+    static constexpr int G = 32;
+    static constexpr int R = 1;
+    int lane;
+    __device__ RowVec(int lane_, int) : lane(lane_) {}
+    __device__ __forceinline__ void load(const WideParams<T>& P, int32_t row, RowPre<T>& R0) const {
+        R0.row = row;
+        R0.s = P.rp[row];
+        R0.e = P.rp[row + 1];
+#pragma unroll
+        for (int u = 0; u < kPreEntries; ++u) {
+            const int64_t q = R0.s + lane + (int64_t)u * 32;
+            R0.c[u] = q < R0.e ? P.col[q] : 0;
+            R0.y[u] = q < R0.e ? P.val[q] : T(0);
+        }
+    }
+    // the nrhs values of x at node c (vector loads when nrhs == NR)
+    __device__ __forceinline__ void xload(const WideParams<T>& P, int32_t c, T (&v)[NR]) const {
+        const T* p = P.x + (size_t)c * P.nrhs;
+        if constexpr (NR >= 2 && sizeof(T) == 8) {
+            if (P.nrhs == NR) {
+#pragma unroll
+                for (int j = 0; j < NR; j += 2) {
+                    const double2 d = __ldcg(reinterpret_cast<const double2*>(p + j));
+                    v[j] = d.x;
+                    v[j + 1] = d.y;
+                }
+                return;
+            }
+        } else if constexpr (NR >= 4 && sizeof(T) == 4) {
+            if (P.nrhs == NR) {
+#pragma unroll
+                for (int j = 0; j < NR; j += 4) {
+                    const float4 d = __ldcg(reinterpret_cast<const float4*>(p + j));
+                    v[j] = d.x;
+                    v[j + 1] = d.y;
+                    v[j + 2] = d.z;
+                    v[j + 3] = d.w;
+                }
+                return;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < NR; ++j) v[j] = j < P.nrhs ? __ldcg(p + j) : T(0);
+    }
+    __device__ __forceinline__ void row(const WideParams<T>& P, const RowPre<T>& R0) const {
+        T acc[NR];
+#pragma unroll
+        for (int j = 0; j < NR; ++j) acc[j] = T(0);
+        T v[kPreEntries][NR];
+#pragma unroll
+        for (int u = 0; u < kPreEntries; ++u) {
+            if (R0.s + lane + (int64_t)u * 32 < R0.e) {
+                xload(P, R0.c[u], v[u]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < NR; ++j) v[u][j] = T(0);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kPreEntries; ++u)
+#pragma unroll
+            for (int j = 0; j < NR; ++j) acc[j] += R0.y[u] * v[u][j];
+        for (int64_t q = R0.s + lane + (int64_t)kPreEntries * 32; q < R0.e; q += 4 * 32) {
+            int32_t c[4];
+            T y[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const bool ok = q + u * 32 < R0.e;
+                c[u] = ok ? P.col[q + u * 32] : 0;
+                y[u] = ok ? P.val[q + u * 32] : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                T w[NR];
+                xload(P, c[u], w);
+#pragma unroll
+                for (int j = 0; j < NR; ++j) acc[j] += y[u] * w[j];
+            }
+        }
+        const T sum = halving_sum<T, NR>(acc, lane);
+        constexpr int span = 32 / NR;
+        const int j = lane / span;
+        if (lane % span == 0 && j < P.nrhs) {
+            T b = P.rhs[(size_t)R0.row * P.nrhs + j];
+            if (P.scale) b = b / P.scale[R0.row];
+            __stcg(P.x + (size_t)R0.row * P.nrhs + j, b - sum);
+        }
+    }
+};
+
+// The row type of a wide or cluster run: lane groups of NR * ES lanes, or
+// vector rows when ES == 0.
+template <typename T, int NR, int ES>
+struct RowSel {
+    using type = RowGroup<T, NR, ES>;
+};
+template <typename T, int NR>
+struct RowSel<T, NR, 0> {
+    using type = RowVec<T, NR>;
+};
+template <int NR, int ES>
+constexpr int group_lanes() {
+    return ES == 0 ? 32 : NR * ES;
+}
+
 // The levels of a run over `ngroups` row groups numbered from gid, with a
 // barrier between levels.  Returns false if a barrier gave up.
-template <typename T, int NR, int ES, typename Barrier>
-__device__ __forceinline__ bool run_levels(const WideParams<T>& P, int64_t gid, int64_t ngroups,
-                                           const RowGroup<T, NR, ES>& g, Barrier barrier) {
+template <typename T, typename Group, typename Barrier>
+__device__ __forceinline__ bool run_levels(const WideParams<T>& P, int64_t gid, int64_t ngroups, const Group& g,
+                                           Barrier barrier) {
     RowPre<T> pre[2];
     auto prefetch = [&](int32_t l, RowPre<T>& R0) {
         R0.row = -1;
@@ -496,12 +743,13 @@ constexpr int kWideThreads = 512;  // one block per SM: fewer arrivals per grid 
 
 template <typename T, int NR, int ES>
 __global__ void __launch_bounds__(kWideThreads, 1) k_wide(const WideParams<T> P) {
-    const RowGroup<T, NR, ES> g((int)lane_id(), P.nrhs);
-    constexpr int R = RowGroup<T, NR, ES>::R;
+    using Group = typename RowSel<T, NR, ES>::type;
+    const Group g((int)lane_id(), P.nrhs);
+    constexpr int R = Group::R;
     const int64_t gid = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * R + lane_id() / (32 / R);
     const int64_t ngroups = (((int64_t)gridDim.x * blockDim.x) >> 5) * R;
     unsigned epoch = 0;
-    run_levels<T, NR, ES>(P, gid, ngroups, g, [&]() { return grid_barrier(P.bar, ++epoch, P.st); });
+    run_levels<T>(P, gid, ngroups, g, [&]() { return grid_barrier(P.bar, ++epoch, P.st); });
 }
 
 __device__ __forceinline__ unsigned cluster_rank() {
@@ -521,12 +769,13 @@ __device__ __forceinline__ unsigned cluster_size() {
 // only for the CTAs of the cluster, which the hardware schedules together.
 template <typename T, int NR, int ES>
 __global__ void __launch_bounds__(1024, 1) k_cluster(const WideParams<T> P) {
-    const RowGroup<T, NR, ES> g((int)lane_id(), P.nrhs);
-    constexpr int R = RowGroup<T, NR, ES>::R;
+    using Group = typename RowSel<T, NR, ES>::type;
+    const Group g((int)lane_id(), P.nrhs);
+    constexpr int R = Group::R;
     const int64_t warps = blockDim.x >> 5;
     const int64_t gid = ((int64_t)cluster_rank() * warps + (threadIdx.x >> 5)) * R + lane_id() / (32 / R);
     const int64_t ngroups = (int64_t)cluster_size() * warps * R;
-    run_levels<T, NR, ES>(P, gid, ngroups, g, []() {
+    run_levels<T>(P, gid, ngroups, g, []() {
         asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
         asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
         return true;
@@ -635,6 +884,143 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_syncfree(const 
     }
 }
 
+// Vector-row variant (rw_options.wide_slices = -1): one warp per row, lane l
+// owns entries s + l, s + l + 32, ... and reads all right-hand sides of an
+// entry in one relaxed vector load, so 4 entries per lane held ahead cover
+// rows of up to 128 entries and a long row on the critical path costs one
+// round of loads, not one per few entries.
+template <typename T, int NR>
+__device__ __forceinline__ void xload_relaxed(const T* x, int nrhs, int32_t c, T (&v)[NR]) {
+    const T* p = x + (size_t)c * nrhs;
+    if constexpr (NR >= 2 && sizeof(T) == 8) {
+        if (nrhs == NR) {
+#pragma unroll
+            for (int j = 0; j < NR; j += 2) ld_relaxed_v2(reinterpret_cast<const double*>(p + j), v[j], v[j + 1]);
+            return;
+        }
+    } else if constexpr (NR >= 4 && sizeof(T) == 4) {
+        if (nrhs == NR) {
+#pragma unroll
+            for (int j = 0; j < NR; j += 4)
+                ld_relaxed_v4(reinterpret_cast<const float*>(p + j), v[j], v[j + 1], v[j + 2], v[j + 3]);
+            return;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < NR; ++j) v[j] = j < nrhs ? ld_relaxed(p + j) : T(0);
+}
+
+template <typename T, int NR>
+__device__ __forceinline__ bool any_pending(const T (&v)[NR], int nrhs) {
+    bool pend = false;
+#pragma unroll
+    for (int j = 0; j < NR; ++j) pend |= (j < nrhs) && is_pending(v[j]);
+    return pend;
+}
+
+template <typename T, int NR>
+__global__ void __launch_bounds__(512, 1) k_syncfree_vec(const FreeParams<T> P) {
+    const int lane = (int)lane_id();
+    constexpr int span = 32 / NR;
+    const int jo = lane / span;  // the right-hand side this lane stores
+    const bool owner = (lane % span) == 0 && jo < P.nrhs;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    struct Pre {
+        int32_t row;
+        int64_t s, e;
+        int32_t c[kPreEntries];
+        T y[kPreEntries];
+        T b;
+    };
+    auto load = [&](int64_t pos, Pre& R0) {
+        R0.row = -1;
+        if (pos >= P.n) return;
+        const int32_t row = P.order[pos];
+        R0.row = row;
+        R0.s = P.rp[row];
+        R0.e = P.rp[row + 1];
+#pragma unroll
+        for (int u = 0; u < kPreEntries; ++u) {
+            const int64_t q = R0.s + lane + (int64_t)u * 32;
+            R0.c[u] = q < R0.e ? P.col[q] : 0;
+            R0.y[u] = q < R0.e ? P.val[q] : T(0);
+        }
+        R0.b = T(0);
+        if (owner) {
+            R0.b = P.rhs[(size_t)row * P.nrhs + jo];
+            if (P.scale) R0.b = R0.b / P.scale[row];
+        }
+    };
+    // re-polls (bounded, backing off) while any of the vector is pending
+    auto wait_vec = [&](int32_t c, T (&v)[NR]) {
+        unsigned spins = 0;
+        while (any_pending<T, NR>(v, P.nrhs)) {
+            if (wait_gives_up(spins, &P.st->timeout)) {
+#pragma unroll
+                for (int j = 0; j < NR; ++j) v[j] = T(0);
+                return;
+            }
+            if (spins > 4) __nanosleep(32);
+            xload_relaxed<T, NR>(P.x, P.nrhs, c, v);
+        }
+    };
+    Pre pre[2];
+    load(gw, pre[0]);
+    load(gw + nw, pre[1]);
+    for (int64_t pos = gw; pos < P.n; pos += nw) {
+        const Pre cur = pre[0];
+        pre[0] = pre[1];
+        load(pos + 2 * nw, pre[1]);
+        T acc[NR];
+#pragma unroll
+        for (int j = 0; j < NR; ++j) acc[j] = T(0);
+        T v[kPreEntries][NR];
+#pragma unroll
+        for (int u = 0; u < kPreEntries; ++u) {
+            if (cur.s + lane + (int64_t)u * 32 < cur.e) {
+                xload_relaxed<T, NR>(P.x, P.nrhs, cur.c[u], v[u]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < NR; ++j) v[u][j] = T(0);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kPreEntries; ++u) {
+            if (cur.s + lane + (int64_t)u * 32 < cur.e) wait_vec(cur.c[u], v[u]);
+#pragma unroll
+            for (int j = 0; j < NR; ++j) acc[j] += cur.y[u] * v[u][j];
+        }
+        for (int64_t q = cur.s + lane + (int64_t)kPreEntries * 32; q < cur.e; q += 4 * 32) {
+            int32_t c[4];
+            T y[4], w[4][NR];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const bool ok = q + u * 32 < cur.e;
+                c[u] = ok ? P.col[q + u * 32] : 0;
+                y[u] = ok ? P.val[q + u * 32] : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (q + u * 32 < cur.e) {
+                    xload_relaxed<T, NR>(P.x, P.nrhs, c[u], w[u]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < NR; ++j) w[u][j] = T(0);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (q + u * 32 < cur.e) wait_vec(c[u], w[u]);
+#pragma unroll
+                for (int j = 0; j < NR; ++j) acc[j] += y[u] * w[u][j];
+            }
+        }
+        const T sum = halving_sum<T, NR>(acc, lane);
+        if (owner) st_relaxed(P.x + (size_t)cur.row * P.nrhs + jo, cur.b - sum);
+    }
+}
+
 template <typename T>
 __global__ void k_fill_pending_sched(T* x, int64_t cnt) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
@@ -642,13 +1028,16 @@ __global__ void k_fill_pending_sched(T* x, int64_t cnt) {
         x[i] = pending_value(T(0));
 }
 
-template <typename T, int NR>
+template <typename T, int NR, bool VEC>
 static rw_status solve_syncfree(rw_context* ctx, const SolveSchedule& S, const int64_t* rp, const int32_t* col,
                                 const T* val, const T* rhs, const T* scale, T* x, int nrhs) {
     cudaStream_t s = ctx->stream;
+    const void* kern;
+    if constexpr (VEC) kern = (const void*)k_syncfree_vec<T, NR>;
+    else kern = (const void*)k_syncfree<T, NR>;
     static int per_sm = -1;
     if (per_sm < 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_syncfree<T, NR>, 512, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 512, 0);
         if (per_sm < 1) per_sm = 1;
     }
     const int64_t cnt = (int64_t)S.n * nrhs;
@@ -663,8 +1052,7 @@ static rw_status solve_syncfree(rw_context* ctx, const SolveSchedule& S, const i
     FreeParams<T> P{S.n, S.order, rp, col, val, rhs, scale, x, nrhs, ctx->d_status};
     void* args[] = {(void*)&P};
     RW_COUNT_LAUNCH();
-    return check_cuda(cudaLaunchCooperativeKernel((const void*)k_syncfree<T, NR>, dim3((unsigned)blocks), dim3(512),
-                                                  args, 0, s),
+    return check_cuda(cudaLaunchCooperativeKernel(kern, dim3((unsigned)blocks), dim3(512), args, 0, s),
                       "sync-free solve");
 }
 
@@ -674,6 +1062,7 @@ static rw_status solve_syncfree(rw_context* ctx, const SolveSchedule& S, const i
 // Entry slices of the lane groups: an explicit option, else 32 / NR (one
 // row per warp), as a power of two with NR * ES <= 32.
 static int lane_slices(int opt, int NR) {
+    if (opt < 0) return 0;  // vector rows
     const int es = opt > 0 ? opt : 32 / NR;
     int p = 1;
     while (p * 2 <= es && p * 2 * NR <= 32) p *= 2;
@@ -699,7 +1088,7 @@ static rw_status launch_wide(rw_context* ctx, const SolveSchedule& S, int32_t le
         int64_t blocks = (int64_t)std::min(per_sm, bps) * ctx->num_sms;
         int64_t maxw = 0;
         for (int32_t l = lev_begin; l < lev_end; ++l) maxw = std::max(maxw, S.lptr_h[l + 1] - S.lptr_h[l]);
-        constexpr int64_t rows_per_block = (kWideThreads / 32) * (32 / (NR * ES));
+        constexpr int64_t rows_per_block = (kWideThreads / 32) * (32 / group_lanes<NR, ES>());
         const int64_t need = (maxw + rows_per_block - 1) / rows_per_block;
         if (blocks > need) blocks = need;
         if (blocks < 1) blocks = 1;
@@ -770,7 +1159,9 @@ static rw_status launch_nonthin(rw_context* ctx, const SolveSchedule& S, const S
         const bool narrow = cw > 0 && S.lptr_h[l + 1] - S.lptr_h[l] <= cw;
         int32_t e = l + 1;
         while (e < run.lev_end && (cw > 0 && S.lptr_h[e + 1] - S.lptr_h[e] <= cw) == narrow) ++e;
-        rw_status rc = narrow ? launch_cluster<T, NR, ES>(ctx, S, l, e, rp, col, val, rhs, scale, x, nrhs, bar, csize)
+        // cluster runs (1024-thread blocks, 64 registers) keep lane groups
+        constexpr int CES = ES == 0 ? 32 / NR : ES;
+        rw_status rc = narrow ? launch_cluster<T, NR, CES>(ctx, S, l, e, rp, col, val, rhs, scale, x, nrhs, bar, csize)
                               : launch_wide<T, NR, ES>(ctx, S, l, e, rp, col, val, rhs, scale, x, nrhs, bar);
         if (rc) return rc;
         l = e;
@@ -787,7 +1178,11 @@ static rw_status solve_runs_nr(rw_context* ctx, const SolveSchedule& S, const in
     rw_status rc;
     if (ctx->opt.solve_mode == 1) {
         if (S.n == 0) return RW_OK;
-        return solve_syncfree<T, NR>(ctx, S, rp, col, val, rhs, scale, x, nrhs);
+        // vector rows while one entry's right-hand sides fit in 32 bytes of registers
+        if constexpr (NR * sizeof(T) <= 32) {
+            if (ctx->opt.wide_slices < 0) return solve_syncfree<T, NR, true>(ctx, S, rp, col, val, rhs, scale, x, nrhs);
+        }
+        return solve_syncfree<T, NR, false>(ctx, S, rp, col, val, rhs, scale, x, nrhs);
     }
     static bool attr = false;
     if (!attr) {
@@ -800,20 +1195,30 @@ static rw_status solve_runs_nr(rw_context* ctx, const SolveSchedule& S, const in
         const int64_t rows = run.pos_end - run.pos_begin;
         if (rows == 0) continue;
         const int nlev = run.lev_end - run.lev_begin;
-        const size_t smem =
-            (size_t)rows * NR * sizeof(T) + (size_t)rows * 12 + (size_t)(nlev + 1) * 4;
+        size_t smem = thin_stage_offset<T, NR>((int)rows, nlev);
+        const size_t staged = smem + (size_t)run.in_entries * (sizeof(T) + 4);
+        const bool stage = run.thin && staged <= kThinSmemBudget + 16 * 1024;
+        if (stage) smem = staged;
         if (run.thin && smem <= kThinSmemBudget + 16 * 1024 && rows <= kThinMaxRows) {
             const int eb = grid_for(rows * 32, 256, ctx->num_sms * 4);
             RW_COUNT_LAUNCH();
             k_thin_ext<T, NR><<<eb, 256, 0, s>>>(run.pos_begin, run.pos_end, S.tptr, S.tnin, S.tidx,
                                                   tval, x, nrhs, ext);
             ThinParams<T> P{run.pos_begin, run.pos_end, run.lev_begin, run.lev_end, S.lptr, S.order,
-                            S.tptr, S.tnin, S.tidx, tval, ext, rhs, scale, x, nrhs};
+                            S.tptr, S.tnin, S.tidx, tval, ext, rhs, scale, x, nrhs, stage ? 1 : 0,
+                            (int)run.in_entries};
             RW_COUNT_LAUNCH();
             k_thin<T, NR><<<1, kThinThreads, smem, s>>>(P);
             if ((rc = check_launch("thin-run solve"))) return rc;
         } else {
             switch (es) {
+                case 0:
+                    // vector rows while one entry's right-hand sides fit in 64 bytes of registers
+                    if constexpr (NR * sizeof(T) <= 64)
+                        rc = launch_nonthin<T, NR, 0>(ctx, S, run, rp, col, val, rhs, scale, x, nrhs, bar);
+                    else
+                        rc = launch_nonthin<T, NR, 32 / NR>(ctx, S, run, rp, col, val, rhs, scale, x, nrhs, bar);
+                    break;
                 case 1: rc = launch_nonthin<T, NR, 1>(ctx, S, run, rp, col, val, rhs, scale, x, nrhs, bar); break;
                 case 2: rc = launch_nonthin<T, NR, 2>(ctx, S, run, rp, col, val, rhs, scale, x, nrhs, bar); break;
                 case 4: rc = launch_nonthin<T, NR, 4>(ctx, S, run, rp, col, val, rhs, scale, x, nrhs, bar); break;

@@ -148,7 +148,7 @@ rw_status tune_t(rw_context* ctx, const TuneTarget& X, int nrhs, const T* av, co
     const rw_options saved = ctx->opt;
     // candidate list: the sync-free solve; the level schedule with entry
     // slices 32/NR, 16/NR, 8/NR (>= 1), 1 or 2 blocks per SM, cluster runs off
-    // or for levels of up to 256 rows
+    // or for levels of up to 256 rows; vector rows with 1 or 2 blocks per SM
     std::vector<int> slices;
     for (int es = 32 / nr; es >= 1 && (int)slices.size() < 3; es /= 2) slices.push_back(es);
     float bp = 1e30f, bs = 1e30f;
@@ -159,6 +159,8 @@ rw_status tune_t(rw_context* ctx, const TuneTarget& X, int nrhs, const T* av, co
     for (int es : slices)
         for (int bps : {1, 2})
             for (int cw : {0, 256}) cands.push_back(Candidate{es, bps, cw, 0, 0});
+    for (int bps : {1, 2}) cands.push_back(Candidate{-1, bps, 0, 0, 0});  // vector rows
+    cands.push_back(Candidate{-1, 1, 0, 0, 1});                            // sync-free, vector rows
     for (const Candidate& c : cands) {
         ctx->opt.solve_mode = c.solve_mode;
         ctx->opt.wide_slices = c.wide_slices;

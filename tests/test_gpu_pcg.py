@@ -293,7 +293,7 @@ def test_autotune_installs_options_and_caches(P, ctx, tmp_path):
     cache = str(tmp_path / "tune.jsonl")
     chosen, ms = P.rw_autotune(c2, dA, F, b.shape[1], P.RW_FP64, cache)
     assert ms[0] > 0 and ms[1] > 0
-    assert chosen["wide_slices"] >= 1 and chosen["spmv_slices"] >= 1
+    assert (chosen["wide_slices"] >= 1 or chosen["wide_slices"] == -1) and chosen["spmv_slices"] >= 1
     lines = open(cache).read().strip().splitlines()
     assert len(lines) == 1 and '"key":' in lines[0]
     again, ms2 = P.rw_autotune(c2, dA, F, b.shape[1], P.RW_FP64, cache)
@@ -316,16 +316,18 @@ def test_autotune_installs_options_and_caches(P, ctx, tmp_path):
     c2.close()
 
 
-@pytest.mark.parametrize("mode,cw", [(1, 0), (0, 256)])
-def test_precond_modes_match_oracle(P, mode, cw):
-    """The sync-free solve and the cluster runs give the oracle's z (1e-12)."""
+@pytest.mark.parametrize("mode,cw,ws", [(1, 0, 0), (0, 256, 0), (0, 0, -1), (0, 256, -1), (1, 0, -1)])
+def test_precond_modes_match_oracle(P, mode, cw, ws):
+    """The sync-free solve, the cluster runs and the vector rows (wide_slices
+    -1: every lane reads all right-hand sides of its entries; level-scheduled
+    or sync-free) give the oracle's z (1e-12)."""
     rng = np.random.default_rng(30 + mode)
     A = W.make_config(2, scale=0.25)["A"]
-    c2 = P.Context(options=P.rw_options_default(solve_mode=mode, cluster_width=cw))
+    c2 = P.Context(options=P.rw_options_default(solve_mode=mode, cluster_width=cw, wide_slices=ws))
     dA = P.CSR.from_host(A)
     F = P.rw_build_factor(c2, dA, 100, 7, 1e-3)
     ref = oracle.build_factor(A, 100, 7, 1e-3)
-    for nrhs in (1, 4, 16):
+    for nrhs in (1, 3, 4, 16):
         r = rng.standard_normal((A.n, nrhs))
         z = _dev(np.zeros_like(r))
         P.rw_precond_apply(c2, F, _dev(r), z)
@@ -338,5 +340,9 @@ def test_precond_modes_match_oracle(P, mode, cw):
     rc, st, its, rel = P.pcg_solve(c2, dA, F, _dev(b), x, 1e-8, 500)
     xr, itr, rr, _ = oracle.pcg(A, ref, b[:, 0], 1e-8, 500)
     assert its[0] == itr and np.linalg.norm(x.cpu().numpy()[:, 0] - xr) / np.linalg.norm(xr) < 1e-10
+    # FP32 mixed solve on the same schedule reaches the tolerance
+    x32 = _dev(np.zeros_like(b))
+    rc, st, its32, rel32 = P.pcg_solve(c2, dA, F, _dev(b), x32, 1e-6, 500, P.RW_FP32_MIXED)
+    assert rc == 0 and np.all(rel32 < 1e-6)
     F.destroy()
     c2.close()
