@@ -254,12 +254,22 @@ def _walk_roofline(peaks, hops, walks_total, walk_ms, bytes_per_hop=64.0):
             "ms_per_launch": walk_ms}
 
 
-def _solve_roofline(peaks, napply, nnz_y, n, nrhs, tri_ms, vbytes, ybytes):
+def _solve_kernels(opt):
+    """Names of the triangular-solve kernels the tuned options run."""
+    def one(mode):
+        return "k_syncfree_vec" if mode == 1 and opt.get("wide_slices") == -1 else (
+            "k_syncfree" if mode == 1 else "k_thin/k_wide")
+    fwd = one(opt.get("solve_mode", 0))
+    bwd = one(opt.get("solve_mode_bwd", -1) if opt.get("solve_mode_bwd", -1) >= 0 else opt.get("solve_mode", 0))
+    return f"{fwd} (forward) + {bwd} (backward)"
+
+
+def _solve_roofline(peaks, napply, nnz_y, n, nrhs, tri_ms, vbytes, ybytes, kernels="triangular solves"):
     # per application of the preconditioner the factor (Y and Y^T) and the
     # vectors (read and written per solve) must be touched once
     tri_bytes = napply * (2 * ybytes * nnz_y + 2 * 3 * vbytes * nrhs * n)
     achieved = tri_bytes / (tri_ms * 1e-3) / 1e9 if tri_ms > 0 else 0.0
-    return {"kernel": "k_thin/k_wide (triangular solves)", "bound": "hbm", "achieved": achieved,
+    return {"kernel": kernels, "bound": "hbm", "achieved": achieved,
             "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
             "traffic": None, "ms_per_step": tri_ms,
             "note": "latency-bound: dependency DAG depth x dependent memory round trips"}
@@ -358,7 +368,8 @@ def run_gpu_single(args, P, torch, dev, stream, ws, rank, local):
     napply = statistics.mean(max(i["iters"]) for i in infos)
     tri_ms = statistics.mean(i["bwd_ms"] + i["fwd_ms"] for i in infos)
     solve_roof = _solve_roofline(peaks, napply, infos[-1]["nnz"], A.n, nrhs, tri_ms,
-                                 4.0 if mixed else 8.0, 8.0 if mixed else 12.0)
+                                 4.0 if mixed else 8.0, 8.0 if mixed else 12.0,
+                                 _solve_kernels(tuned))
     dominant = solve_roof if tri_ms > walk_ms else walk_roof
     line = _base_line(args, ws, ms, "f32-mixed" if mixed else "f64",
                       {"workload": W.CONFIGS[args.workload]["name"], "n": A.n, "nnz": A.nnz,

@@ -111,6 +111,7 @@ typedef struct {
                                 scanned block's successor words with its thresholds (fewer
                                 dependent loads), 0 = read only the chosen block's (fewer bytes),
                                 -1 = 1 when the walk tables fit in 3/4 of L2 (default -1) */
+    int32_t solve_mode_bwd;  /* solve_mode of the backward (Y^T) solve; -1 = as solve_mode (default) */
 } rw_options;
 
 typedef struct rw_context rw_context;

@@ -63,7 +63,7 @@ class rw_options_t(ctypes.Structure):
                 ("timing", _i32), ("solve_blocks_per_sm", _i32), ("graphs", _i32),
                 ("wide_slices", _i32), ("spmv_slices", _i32), ("cluster_width", _i32),
                 ("cluster_size", _i32), ("solve_mode", _i32), ("reuse", _i32),
-                ("walk_fuse", _i32)]
+                ("walk_fuse", _i32), ("solve_mode_bwd", _i32)]
 
 
 class rw_factor_desc_t(ctypes.Structure):
@@ -651,7 +651,7 @@ def pcg_solve_batch(ctx, B, bs, xs, tol, max_iter, prec=RW_FP64):
 # Schedule autotuner
 # ---------------------------------------------------------------------------
 
-_TUNED = ("solve_mode", "wide_slices", "solve_blocks_per_sm", "cluster_width", "spmv_slices")
+_TUNED = ("solve_mode", "solve_mode_bwd", "wide_slices", "solve_blocks_per_sm", "cluster_width", "spmv_slices")
 
 
 def _tune_result(ctx, opt, ms):

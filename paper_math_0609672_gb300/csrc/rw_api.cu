@@ -144,6 +144,7 @@ void rw_options_default(rw_options* opt) {
     opt->timing = 1;
     opt->graphs = 1;
     opt->walk_fuse = -1;
+    opt->solve_mode_bwd = -1;
 }
 
 const char* rw_status_string(rw_status s) {

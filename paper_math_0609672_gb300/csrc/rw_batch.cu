@@ -442,7 +442,7 @@ rw_status pcg_batch_t(rw_context* ctx, rw_batch* B, const double* const* d_b, do
     if ((rc = check_launch("batch pcg init"))) return rc;
     auto precond = [&]() -> rw_status {
         rw_status r2 = solve_runs<T>(ctx, B->bwd_sched, B->yt_rp, B->yt_col, ytv, tv_bwd, r, nullptr, w,
-                                     nrhs, B->bar);
+                                     nrhs, B->bar, true);
         if (r2) return r2;
         return solve_runs<T>(ctx, B->fwd_sched, B->y_rp, B->y_col, yv, tv_fwd, w, dv, z, nrhs, B->bar);
     };

@@ -245,10 +245,11 @@ rw_status build_schedule(rw_context* ctx, int32_t n, const int64_t* rp, const in
 // (at offset 0) and the external sums of a thin run (from byte 256 on).
 constexpr int64_t kSolveWorkspaceBytes = 256 + (int64_t)4096 * 16 * 8;
 
+// backward: the Y^T solve (rw_options.solve_mode_bwd may choose its mode).
 template <typename T>
 rw_status solve_runs(rw_context* ctx, const SolveSchedule& S, const int64_t* rp, const int32_t* col,
                      const T* val, const T* tval, const T* rhs, const T* scale, T* x, int nrhs,
-                     unsigned* bar);
+                     unsigned* bar, bool backward = false);
 
 // ---- solve path (rw_solve.cu) ----------------------------------------------
 

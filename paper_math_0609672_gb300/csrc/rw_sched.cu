@@ -673,10 +673,14 @@ struct RowVec {
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                T w[NR];
-                xload(P, c[u], w);
+                // padding slots past the row's end read nothing: x of column 0
+                // may still be unset (0 * NaN would poison the sum)
+                if (q + u * 32 < R0.e) {
+                    T w[NR];
+                    xload(P, c[u], w);
 #pragma unroll
-                for (int j = 0; j < NR; ++j) acc[j] += y[u] * w[j];
+                    for (int j = 0; j < NR; ++j) acc[j] += y[u] * w[j];
+                }
             }
         }
         const T sum = halving_sum<T, NR>(acc, lane);
@@ -1172,11 +1176,11 @@ static rw_status launch_nonthin(rw_context* ctx, const SolveSchedule& S, const S
 template <typename T, int NR>
 static rw_status solve_runs_nr(rw_context* ctx, const SolveSchedule& S, const int64_t* rp,
                                const int32_t* col, const T* val, const T* tval, const T* rhs,
-                               const T* scale, T* x, int nrhs, unsigned* bar) {
+                               const T* scale, T* x, int nrhs, unsigned* bar, int mode) {
     cudaStream_t s = ctx->stream;
     T* ext = reinterpret_cast<T*>(bar + 64);  // the factor's solve workspace (see build_factor)
     rw_status rc;
-    if (ctx->opt.solve_mode == 1) {
+    if (mode == 1) {
         if (S.n == 0) return RW_OK;
         // vector rows while one entry's right-hand sides fit in 32 bytes of registers
         if constexpr (NR * sizeof(T) <= 32) {
@@ -1235,23 +1239,24 @@ static rw_status solve_runs_nr(rw_context* ctx, const SolveSchedule& S, const in
 template <typename T>
 rw_status solve_runs(rw_context* ctx, const SolveSchedule& S, const int64_t* rp, const int32_t* col,
                      const T* val, const T* tval, const T* rhs, const T* scale, T* x, int nrhs,
-                     unsigned* bar) {
+                     unsigned* bar, bool backward) {
+    const int mode = backward && ctx->opt.solve_mode_bwd >= 0 ? ctx->opt.solve_mode_bwd : ctx->opt.solve_mode;
     int nr = 1;
     while (nr < nrhs) nr <<= 1;
     switch (nr) {
-        case 1: return solve_runs_nr<T, 1>(ctx, S, rp, col, val, tval, rhs, scale, x, nrhs, bar);
-        case 2: return solve_runs_nr<T, 2>(ctx, S, rp, col, val, tval, rhs, scale, x, nrhs, bar);
-        case 4: return solve_runs_nr<T, 4>(ctx, S, rp, col, val, tval, rhs, scale, x, nrhs, bar);
-        case 8: return solve_runs_nr<T, 8>(ctx, S, rp, col, val, tval, rhs, scale, x, nrhs, bar);
-        default: return solve_runs_nr<T, 16>(ctx, S, rp, col, val, tval, rhs, scale, x, nrhs, bar);
+        case 1: return solve_runs_nr<T, 1>(ctx, S, rp, col, val, tval, rhs, scale, x, nrhs, bar, mode);
+        case 2: return solve_runs_nr<T, 2>(ctx, S, rp, col, val, tval, rhs, scale, x, nrhs, bar, mode);
+        case 4: return solve_runs_nr<T, 4>(ctx, S, rp, col, val, tval, rhs, scale, x, nrhs, bar, mode);
+        case 8: return solve_runs_nr<T, 8>(ctx, S, rp, col, val, tval, rhs, scale, x, nrhs, bar, mode);
+        default: return solve_runs_nr<T, 16>(ctx, S, rp, col, val, tval, rhs, scale, x, nrhs, bar, mode);
     }
 }
 
 template rw_status solve_runs<double>(rw_context*, const SolveSchedule&, const int64_t*,
                                       const int32_t*, const double*, const double*, const double*,
-                                      const double*, double*, int, unsigned*);
+                                      const double*, double*, int, unsigned*, bool);
 template rw_status solve_runs<float>(rw_context*, const SolveSchedule&, const int64_t*,
                                      const int32_t*, const float*, const float*, const float*,
-                                     const float*, float*, int, unsigned*);
+                                     const float*, float*, int, unsigned*, bool);
 
 }  // namespace rw

@@ -411,7 +411,7 @@ static rw_status precond_t(rw_context* ctx, const FactorView& F, const T* yv, co
                            const T* d, const T* r, T* w, T* z, int nrhs, SolveTimes* tm = nullptr) {
     if (tm && tm->on) cudaEventRecord(ctx->ev[5], ctx->stream);
     rw_status rc = solve_runs<T>(ctx, *F.bwd_sched, F.yt_rp, F.yt_col, ytv,
-                                 thin_values<T>(*F.bwd_sched), r, nullptr, w, nrhs, F.bar);
+                                 thin_values<T>(*F.bwd_sched), r, nullptr, w, nrhs, F.bar, true);
     if (rc) return rc;
     if (tm && tm->on) cudaEventRecord(ctx->ev[6], ctx->stream);
     rc = solve_runs<T>(ctx, *F.fwd_sched, F.y_rp, F.y_col, yv, thin_values<T>(*F.fwd_sched), w, d,

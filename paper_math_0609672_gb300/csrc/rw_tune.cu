@@ -25,6 +25,7 @@ namespace {
 
 struct Candidate {
     int wide_slices, solve_blocks_per_sm, cluster_width, spmv_slices, solve_mode;
+    int solve_mode_bwd = -1;  // -1: as solve_mode
 };
 
 std::string shape_key(const rw_context* ctx, const TuneTarget& T, int nrhs) {
@@ -66,7 +67,7 @@ bool cache_lookup(const char* path, const std::string& key, Candidate* c) {
         Candidate t{};
         if (json_int(line, "wide_slices", &t.wide_slices) && json_int(line, "solve_blocks_per_sm", &t.solve_blocks_per_sm) &&
             json_int(line, "cluster_width", &t.cluster_width) && json_int(line, "spmv_slices", &t.spmv_slices) &&
-            json_int(line, "solve_mode", &t.solve_mode)) {
+            json_int(line, "solve_mode", &t.solve_mode) && json_int(line, "solve_mode_bwd", &t.solve_mode_bwd)) {
             *c = t;  // the last matching line wins
             found = true;
         }
@@ -80,9 +81,9 @@ void cache_store(const char* path, const std::string& key, const Candidate& c, f
     FILE* f = fopen(path, "a");
     if (!f) return;
     fprintf(f,
-            "{\"key\":\"%s\",\"solve_mode\":%d,\"wide_slices\":%d,\"solve_blocks_per_sm\":%d,\"cluster_width\":%d,"
+            "{\"key\":\"%s\",\"solve_mode\":%d,\"solve_mode_bwd\":%d,\"wide_slices\":%d,\"solve_blocks_per_sm\":%d,\"cluster_width\":%d,"
             "\"spmv_slices\":%d,\"precond_ms\":%.4f,\"spmv_ms\":%.4f}\n",
-            key.c_str(), c.solve_mode, c.wide_slices, c.solve_blocks_per_sm, c.cluster_width, c.spmv_slices, ms_pre,
+            key.c_str(), c.solve_mode, c.solve_mode_bwd, c.wide_slices, c.solve_blocks_per_sm, c.cluster_width, c.spmv_slices, ms_pre,
             ms_spmv);
     fclose(f);
 }
@@ -93,7 +94,7 @@ rw_status time_precond(rw_context* ctx, const TuneTarget& X, const T* yv, const 
     cudaStream_t s = ctx->stream;
     rw_status rc;
     auto once = [&]() -> rw_status {
-        rw_status r2 = solve_runs<T>(ctx, *X.bwd, X.yt_rp, X.yt_col, ytv, tvb, r, nullptr, w, nrhs, X.bar);
+        rw_status r2 = solve_runs<T>(ctx, *X.bwd, X.yt_rp, X.yt_col, ytv, tvb, r, nullptr, w, nrhs, X.bar, true);
         if (r2) return r2;
         return solve_runs<T>(ctx, *X.fwd, X.y_rp, X.y_col, yv, tvf, w, dv, z, nrhs, X.bar);
     };
@@ -161,8 +162,11 @@ rw_status tune_t(rw_context* ctx, const TuneTarget& X, int nrhs, const T* av, co
             for (int cw : {0, 256}) cands.push_back(Candidate{es, bps, cw, 0, 0});
     for (int bps : {1, 2}) cands.push_back(Candidate{-1, bps, 0, 0, 0});  // vector rows
     cands.push_back(Candidate{-1, 1, 0, 0, 1});                            // sync-free, vector rows
+    cands.push_back(Candidate{-1, 1, 0, 0, 1, 0});  // sync-free forward, level-scheduled backward
+    cands.push_back(Candidate{-1, 1, 0, 0, 0, 1});  // level-scheduled forward, sync-free backward
     for (const Candidate& c : cands) {
         ctx->opt.solve_mode = c.solve_mode;
+        ctx->opt.solve_mode_bwd = c.solve_mode_bwd;
         ctx->opt.wide_slices = c.wide_slices;
         ctx->opt.solve_blocks_per_sm = c.solve_blocks_per_sm;
         ctx->opt.cluster_width = c.cluster_width;
@@ -174,6 +178,7 @@ rw_status tune_t(rw_context* ctx, const TuneTarget& X, int nrhs, const T* av, co
         if (ms < bp) {
             bp = ms;
             b.solve_mode = c.solve_mode;
+            b.solve_mode_bwd = c.solve_mode_bwd;
             b.wide_slices = c.wide_slices;
             b.solve_blocks_per_sm = c.solve_blocks_per_sm;
             b.cluster_width = c.cluster_width;
@@ -218,6 +223,7 @@ rw_status autotune(rw_context* ctx, const TuneTarget& X, int nrhs, rw_precision 
         cache_store(cache, key, c, ms_pre, ms_spmv);
     }
     ctx->opt.solve_mode = c.solve_mode;
+    ctx->opt.solve_mode_bwd = c.solve_mode_bwd;
     ctx->opt.wide_slices = c.wide_slices;
     ctx->opt.solve_blocks_per_sm = c.solve_blocks_per_sm;
     ctx->opt.cluster_width = c.cluster_width;

@@ -316,14 +316,17 @@ def test_autotune_installs_options_and_caches(P, ctx, tmp_path):
     c2.close()
 
 
-@pytest.mark.parametrize("mode,cw,ws", [(1, 0, 0), (0, 256, 0), (0, 0, -1), (0, 256, -1), (1, 0, -1)])
-def test_precond_modes_match_oracle(P, mode, cw, ws):
+@pytest.mark.parametrize("mode,cw,ws,bwd", [(1, 0, 0, -1), (0, 256, 0, -1), (0, 0, -1, -1), (0, 256, -1, -1),
+                                            (1, 0, -1, -1), (1, 0, -1, 0), (0, 0, -1, 1)])
+def test_precond_modes_match_oracle(P, mode, cw, ws, bwd):
     """The sync-free solve, the cluster runs and the vector rows (wide_slices
     -1: every lane reads all right-hand sides of its entries; level-scheduled
-    or sync-free) give the oracle's z (1e-12)."""
+    or sync-free, also with the backward solve in the other mode) give the
+    oracle's z (1e-12)."""
     rng = np.random.default_rng(30 + mode)
     A = W.make_config(2, scale=0.25)["A"]
-    c2 = P.Context(options=P.rw_options_default(solve_mode=mode, cluster_width=cw, wide_slices=ws))
+    c2 = P.Context(options=P.rw_options_default(solve_mode=mode, cluster_width=cw, wide_slices=ws,
+                                                solve_mode_bwd=bwd))
     dA = P.CSR.from_host(A)
     F = P.rw_build_factor(c2, dA, 100, 7, 1e-3)
     ref = oracle.build_factor(A, 100, 7, 1e-3)
@@ -346,3 +349,27 @@ def test_precond_modes_match_oracle(P, mode, cw, ws):
     assert rc == 0 and np.all(rel32 < 1e-6)
     F.destroy()
     c2.close()
+
+
+def test_vector_rows_with_long_dependency_lists(P):
+    """Rows with more than the 128 prefetched entries (here rows of Y^T, up to
+    several hundred) take the batched remainder loop of the vector rows; in
+    the backward solve column 0 is computed last, so a padding slot that read
+    its x would poison the sum.  Every mode must give the oracle's z."""
+    rng = np.random.default_rng(41)
+    A = W.make_config(2, scale=0.5)["A"]
+    ref = oracle.build_factor(A, 100, 7, 1e-3)
+    assert np.bincount(ref["col"], minlength=A.n).max() > 128
+    dA = P.CSR.from_host(A)
+    r = rng.standard_normal((A.n, 4))
+    zr = [oracle.precond_apply(ref, r[:, j]) for j in (0, 3)]
+    for mode, bwd in ((0, -1), (1, -1), (1, 0), (0, 1)):
+        c2 = P.Context(options=P.rw_options_default(solve_mode=mode, solve_mode_bwd=bwd, wide_slices=-1))
+        F = P.rw_build_factor(c2, dA, 100, 7, 1e-3)
+        z = _dev(np.zeros_like(r))
+        P.rw_precond_apply(c2, F, _dev(r), z)
+        zg = z.cpu().numpy()
+        for zj, j in zip(zr, (0, 3)):
+            assert np.linalg.norm(zg[:, j] - zj) / np.linalg.norm(zj) < 1e-12, (mode, bwd, j)
+        F.destroy()
+        c2.close()
