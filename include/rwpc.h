@@ -100,7 +100,8 @@ typedef struct {
                                 one thread-block cluster with hardware barriers; 0 = never */
     int32_t cluster_size;    /* CTAs of that cluster (2..16; 0 = 16) */
     int32_t solve_mode;      /* triangular solves: 0 = level schedule (thin / wide / cluster runs),
-                                1 = sync-free (each row waits only for its own dependencies) */
+                                1 = sync-free (each row waits only for its own dependencies),
+                                2 = hybrid (thin runs on one block, the other runs sync-free) */
     int32_t reuse;           /* 1: walk reuse (Algorithm 2 of Sec. 5.3) in single-matrix builds:
                                 every simulated walk also counts, for each later node k' it
                                 passes, the legal sub-walk from k' (k' its least node until it

@@ -1032,9 +1032,13 @@ __global__ void k_fill_pending_sched(T* x, int64_t cnt) {
         x[i] = pending_value(T(0));
 }
 
+// Positions [pos_begin, pos_end) of the level order, sync-free; the rows of
+// the range must hold the pending marker (fill = true marks the whole vector
+// first) and every dependency outside the range must be final.
 template <typename T, int NR, bool VEC>
 static rw_status solve_syncfree(rw_context* ctx, const SolveSchedule& S, const int64_t* rp, const int32_t* col,
-                                const T* val, const T* rhs, const T* scale, T* x, int nrhs) {
+                                const T* val, const T* rhs, const T* scale, T* x, int nrhs,
+                                int64_t pos_begin, int64_t pos_end, bool fill) {
     cudaStream_t s = ctx->stream;
     const void* kern;
     if constexpr (VEC) kern = (const void*)k_syncfree_vec<T, NR>;
@@ -1044,16 +1048,19 @@ static rw_status solve_syncfree(rw_context* ctx, const SolveSchedule& S, const i
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 512, 0);
         if (per_sm < 1) per_sm = 1;
     }
-    const int64_t cnt = (int64_t)S.n * nrhs;
-    RW_COUNT_LAUNCH();
-    k_fill_pending_sched<T><<<grid_for(cnt, 256, ctx->num_sms * 8), 256, 0, s>>>(x, cnt);
-    rw_status rc = check_launch("pending fill");
-    if (rc) return rc;
+    if (fill) {
+        const int64_t cnt = (int64_t)S.n * nrhs;
+        RW_COUNT_LAUNCH();
+        k_fill_pending_sched<T><<<grid_for(cnt, 256, ctx->num_sms * 8), 256, 0, s>>>(x, cnt);
+        rw_status rc = check_launch("pending fill");
+        if (rc) return rc;
+    }
+    const int64_t rows = pos_end - pos_begin;
     int64_t blocks = (int64_t)std::min(per_sm, 2) * ctx->num_sms;
-    const int64_t need = ((int64_t)S.n + 15) / 16;
+    const int64_t need = (rows + 15) / 16;
     if (blocks > need) blocks = need;
     if (blocks < 1) blocks = 1;
-    FreeParams<T> P{S.n, S.order, rp, col, val, rhs, scale, x, nrhs, ctx->d_status};
+    FreeParams<T> P{rows, S.order + pos_begin, rp, col, val, rhs, scale, x, nrhs, ctx->d_status};
     void* args[] = {(void*)&P};
     RW_COUNT_LAUNCH();
     return check_cuda(cudaLaunchCooperativeKernel(kern, dim3((unsigned)blocks), dim3(512), args, 0, s),
@@ -1184,9 +1191,20 @@ static rw_status solve_runs_nr(rw_context* ctx, const SolveSchedule& S, const in
         if (S.n == 0) return RW_OK;
         // vector rows while one entry's right-hand sides fit in 32 bytes of registers
         if constexpr (NR * sizeof(T) <= 32) {
-            if (ctx->opt.wide_slices < 0) return solve_syncfree<T, NR, true>(ctx, S, rp, col, val, rhs, scale, x, nrhs);
+            if (ctx->opt.wide_slices < 0)
+                return solve_syncfree<T, NR, true>(ctx, S, rp, col, val, rhs, scale, x, nrhs, 0, S.n, true);
         }
-        return solve_syncfree<T, NR, false>(ctx, S, rp, col, val, rhs, scale, x, nrhs);
+        return solve_syncfree<T, NR, false>(ctx, S, rp, col, val, rhs, scale, x, nrhs, 0, S.n, true);
+    }
+    // mode 2 (hybrid): thin runs as in the level schedule, every other run
+    // sync-free over its own positions; the whole vector is marked pending
+    // once, before the first run (a run reads only rows of earlier runs,
+    // final by then, and its own rows)
+    if (mode == 2 && S.n > 0) {
+        const int64_t cnt = (int64_t)S.n * nrhs;
+        RW_COUNT_LAUNCH();
+        k_fill_pending_sched<T><<<grid_for(cnt, 256, ctx->num_sms * 8), 256, 0, s>>>(x, cnt);
+        if ((rc = check_launch("pending fill"))) return rc;
     }
     static bool attr = false;
     if (!attr) {
@@ -1214,6 +1232,18 @@ static rw_status solve_runs_nr(rw_context* ctx, const SolveSchedule& S, const in
             RW_COUNT_LAUNCH();
             k_thin<T, NR><<<1, kThinThreads, smem, s>>>(P);
             if ((rc = check_launch("thin-run solve"))) return rc;
+        } else if (mode == 2) {
+            if constexpr (NR * sizeof(T) <= 32) {
+                rc = ctx->opt.wide_slices < 0
+                         ? solve_syncfree<T, NR, true>(ctx, S, rp, col, val, rhs, scale, x, nrhs, run.pos_begin,
+                                                       run.pos_end, false)
+                         : solve_syncfree<T, NR, false>(ctx, S, rp, col, val, rhs, scale, x, nrhs, run.pos_begin,
+                                                        run.pos_end, false);
+            } else {
+                rc = solve_syncfree<T, NR, false>(ctx, S, rp, col, val, rhs, scale, x, nrhs, run.pos_begin,
+                                                  run.pos_end, false);
+            }
+            if (rc) return rc;
         } else {
             switch (es) {
                 case 0:

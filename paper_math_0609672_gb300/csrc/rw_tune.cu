@@ -164,6 +164,8 @@ rw_status tune_t(rw_context* ctx, const TuneTarget& X, int nrhs, const T* av, co
     cands.push_back(Candidate{-1, 1, 0, 0, 1});                            // sync-free, vector rows
     cands.push_back(Candidate{-1, 1, 0, 0, 1, 0});  // sync-free forward, level-scheduled backward
     cands.push_back(Candidate{-1, 1, 0, 0, 0, 1});  // level-scheduled forward, sync-free backward
+    cands.push_back(Candidate{-1, 1, 0, 0, 2});     // hybrid runs (thin: one block; wide: sync-free)
+    cands.push_back(Candidate{-1, 1, 0, 0, 1, 2});  // sync-free forward, hybrid backward
     for (const Candidate& c : cands) {
         ctx->opt.solve_mode = c.solve_mode;
         ctx->opt.solve_mode_bwd = c.solve_mode_bwd;

@@ -317,12 +317,13 @@ def test_autotune_installs_options_and_caches(P, ctx, tmp_path):
 
 
 @pytest.mark.parametrize("mode,cw,ws,bwd", [(1, 0, 0, -1), (0, 256, 0, -1), (0, 0, -1, -1), (0, 256, -1, -1),
-                                            (1, 0, -1, -1), (1, 0, -1, 0), (0, 0, -1, 1)])
+                                            (1, 0, -1, -1), (1, 0, -1, 0), (0, 0, -1, 1), (2, 0, -1, -1),
+                                            (2, 0, 0, -1), (1, 0, -1, 2)])
 def test_precond_modes_match_oracle(P, mode, cw, ws, bwd):
     """The sync-free solve, the cluster runs and the vector rows (wide_slices
-    -1: every lane reads all right-hand sides of its entries; level-scheduled
-    or sync-free, also with the backward solve in the other mode) give the
-    oracle's z (1e-12)."""
+    -1: every lane reads all right-hand sides of its entries; level-scheduled,
+    sync-free or hybrid, also with the backward solve in another mode) give
+    the oracle's z (1e-12)."""
     rng = np.random.default_rng(30 + mode)
     A = W.make_config(2, scale=0.25)["A"]
     c2 = P.Context(options=P.rw_options_default(solve_mode=mode, cluster_width=cw, wide_slices=ws,
@@ -363,7 +364,7 @@ def test_vector_rows_with_long_dependency_lists(P):
     dA = P.CSR.from_host(A)
     r = rng.standard_normal((A.n, 4))
     zr = [oracle.precond_apply(ref, r[:, j]) for j in (0, 3)]
-    for mode, bwd in ((0, -1), (1, -1), (1, 0), (0, 1)):
+    for mode, bwd in ((0, -1), (1, -1), (1, 0), (0, 1), (2, -1), (1, 2)):
         c2 = P.Context(options=P.rw_options_default(solve_mode=mode, solve_mode_bwd=bwd, wide_slices=-1))
         F = P.rw_build_factor(c2, dA, 100, 7, 1e-3)
         z = _dev(np.zeros_like(r))
