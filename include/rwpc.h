@@ -113,6 +113,8 @@ typedef struct {
                                 dependent loads), 0 = read only the chosen block's (fewer bytes),
                                 -1 = 1 when the walk tables fit in 3/4 of L2 (default -1) */
     int32_t solve_mode_bwd;  /* solve_mode of the backward (Y^T) solve; -1 = as solve_mode (default) */
+    int32_t thin_levels;     /* factor build: levels per thin run at most (0 = no cap; default 128);
+                                dependencies on earlier runs are summed by the whole grid */
 } rw_options;
 
 typedef struct rw_context rw_context;

@@ -63,7 +63,8 @@ class rw_options_t(ctypes.Structure):
                 ("timing", _i32), ("solve_blocks_per_sm", _i32), ("graphs", _i32),
                 ("wide_slices", _i32), ("spmv_slices", _i32), ("cluster_width", _i32),
                 ("cluster_size", _i32), ("solve_mode", _i32), ("reuse", _i32),
-                ("walk_fuse", _i32), ("solve_mode_bwd", _i32)]
+                ("walk_fuse", _i32), ("solve_mode_bwd", _i32),
+                ("thin_levels", _i32)]
 
 
 class rw_factor_desc_t(ctypes.Structure):

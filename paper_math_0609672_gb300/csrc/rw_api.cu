@@ -145,6 +145,7 @@ void rw_options_default(rw_options* opt) {
     opt->graphs = 1;
     opt->walk_fuse = -1;
     opt->solve_mode_bwd = -1;
+    opt->thin_levels = 128;
 }
 
 const char* rw_status_string(rw_status s) {

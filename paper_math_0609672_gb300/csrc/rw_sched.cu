@@ -119,6 +119,7 @@ rw_status build_schedule(rw_context* ctx, int32_t n, const int64_t* rp, const in
                          Pool& scratch) {
     cudaStream_t s = ctx->stream;
     rw_status rc;
+    const int thin_levels = ctx->opt.thin_levels;
     S.n = n;
     S.depth = depth;
     S.order = order;
@@ -140,6 +141,10 @@ rw_status build_schedule(rw_context* ctx, int32_t n, const int64_t* rp, const in
             const bool t = w <= kThinWidth;
             if (t != thin) break;
             if (thin && S.lptr_h[l + 1] - run.pos_begin > kThinMaxRows) break;
+            // a cap on a thin run's levels turns the dependencies on earlier
+            // levels into external ones, summed by the whole grid beforehand
+            // (the one block of the run then does less FP64 arithmetic per level)
+            if (thin && thin_levels > 0 && l - run.lev_begin >= thin_levels) break;
             ++l;
         }
         run.lev_end = l;
