@@ -269,11 +269,9 @@ rw_status rw::complete_factor(rw_context* ctx, rw_factor* F, const FactorOut& fo
     F->fwd_order = alloc_n<int32_t>(F->pool, n);
     F->bwd_order = alloc_n<int32_t>(F->pool, n);
     if (!F->fwd_order || !F->bwd_order) return RW_ERR_ALLOC;
-    if ((rc = compute_levels(ctx, n, fo.y_rp, fo.y_col, false, F->fwd_order, &d.fwd_levels,
-                             &fwd_lptr, F->pool, scratch)))
-        return rc;
-    if ((rc = compute_levels(ctx, n, yt_rp, yt_col, true, F->bwd_order, &d.bwd_levels, &bwd_lptr,
-                             F->pool, scratch)))
+    if ((rc = compute_levels_pair(ctx, n, LevelDag{fo.y_rp, fo.y_col, false, F->fwd_order, &d.fwd_levels, &fwd_lptr},
+                                  LevelDag{yt_rp, yt_col, true, F->bwd_order, &d.bwd_levels, &bwd_lptr}, F->pool,
+                                  scratch)))
         return rc;
     if (timing) cudaEventRecord(ctx->ev[13], s);
     if (ctx->opt.store_fp32) {

@@ -789,10 +789,10 @@ rw_status rw_batch_create(rw_context* ctx, int32_t nmat, const rw_csr* As, const
     }
     int64_t* fwd_lptr = nullptr;
     int64_t* bwd_lptr = nullptr;
-    if ((rc = compute_levels(ctx, (int32_t)N, B->y_rp, B->y_col, false, B->fwd_order, &B->fwd_depth, &fwd_lptr,
-                             P, sc)) ||
-        (rc = compute_levels(ctx, (int32_t)N, B->yt_rp, B->yt_col, true, B->bwd_order, &B->bwd_depth, &bwd_lptr,
-                             P, sc)) ||
+    if ((rc = compute_levels_pair(ctx, (int32_t)N,
+                                  LevelDag{B->y_rp, B->y_col, false, B->fwd_order, &B->fwd_depth, &fwd_lptr},
+                                  LevelDag{B->yt_rp, B->yt_col, true, B->bwd_order, &B->bwd_depth, &bwd_lptr}, P,
+                                  sc)) ||
         (rc = build_schedule(ctx, (int32_t)N, B->y_rp, B->y_col, B->y_val, B->y_val32, B->fwd_order, fwd_lptr,
                              B->fwd_depth, B->fwd_sched, P, sc)) ||
         (rc = build_schedule(ctx, (int32_t)N, B->yt_rp, B->yt_col, B->yt_val, B->yt_val32, B->bwd_order, bwd_lptr,

@@ -171,9 +171,11 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned epoch, De
 
 // Sums of NR per-lane values over the warp (NR a power of two, <= 16).  Each
 // step hands half of the still-carried values to the partner lane, so NR = 4
-// costs 7 shuffles instead of 4 x 5.  Lane j < NR receives the total of value j.
+// costs 7 shuffles instead of 4 x 5.  warp_sums_spread leaves the total of
+// value j in lanes j * 32/NR ... j * 32/NR + 32/NR - 1; warp_sums moves it to
+// lane j (j < NR).
 template <typename T, int NR>
-__device__ __forceinline__ T warp_sums(T (&v)[NR]) {
+__device__ __forceinline__ T warp_sums_spread(T (&v)[NR]) {
     const unsigned lane = lane_id();
     int cnt = NR;
 #pragma unroll
@@ -194,8 +196,14 @@ __device__ __forceinline__ T warp_sums(T (&v)[NR]) {
             v[0] += __shfl_xor_sync(kFull, v[0], o);
         }
     }
+    return v[0];
+}
+
+template <typename T, int NR>
+__device__ __forceinline__ T warp_sums(T (&v)[NR]) {
+    const T s = warp_sums_spread<T, NR>(v);
     constexpr int shift = NR >= 16 ? 1 : NR >= 8 ? 2 : NR >= 4 ? 3 : NR >= 2 ? 4 : 5;
-    return __shfl_sync(kFull, v[0], ((int)lane << shift) & 31);
+    return __shfl_sync(kFull, s, ((int)lane_id() << shift) & 31);
 }
 
 template <typename T>

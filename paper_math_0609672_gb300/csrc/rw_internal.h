@@ -211,9 +211,17 @@ rw_status transpose_factor(rw_context* ctx, int32_t n, const FactorOut& fo, int6
 // Level order of a triangular solve: rows sorted by level of the dependency
 // DAG of the strict triangular CSR (rp, col); descending = upper triangular.
 // *lptr_out (allocated from keep) receives the depth + 1 level boundaries.
-rw_status compute_levels(rw_context* ctx, int32_t n, const int64_t* rp, const int32_t* col,
-                         bool descending, int32_t* order, int32_t* depth, int64_t** lptr_out,
-                         Pool& keep, Pool& scratch);
+struct LevelDag {
+    const int64_t* rp;
+    const int32_t* col;
+    bool descending;
+    int32_t* order;       // [n] out
+    int32_t* depth;       // out
+    int64_t** lptr_out;   // out
+};
+// The forward (Y) and backward (Y^T) DAGs in one launch.
+rw_status compute_levels_pair(rw_context* ctx, int32_t n, const LevelDag& fwd, const LevelDag& bwd, Pool& keep,
+                              Pool& scratch);
 
 // Schedule of one triangular solve (see rw_sched.cu).
 struct SolveRun {

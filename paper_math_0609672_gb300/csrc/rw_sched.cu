@@ -573,36 +573,8 @@ struct RowGroup {
 // in one vector load, so each entry's column and value are loaded once (not
 // once per right-hand side) and 4 entries per lane prefetched cover rows of
 // up to 128 entries: a long row costs one round of x loads like a short one.
-// The NR partial sums are reduced by halving: at each of the first log2(NR)
-// butterfly steps a lane keeps half of its sums and adds its partner's half,
-// then plain butterfly steps; lane j * 32 / NR ends with the sum of
-// right-hand side j.
-template <typename T, int NR>
-__device__ __forceinline__ T halving_sum(T (&a)[NR], int lane) {
-    int cnt = NR;
-    int off = 16;
-#pragma unroll
-    for (int st = 0; st < 5; ++st) {
-        if (cnt > 1) {
-            const bool upper = (lane & off) != 0;
-            const int h = cnt / 2;
-#pragma unroll
-            for (int i = 0; i < NR / 2; ++i) {
-                if (i < h) {
-                    const T send = upper ? a[i] : a[i + h];
-                    const T keep = upper ? a[i + h] : a[i];
-                    a[i] = keep + __shfl_xor_sync(kFull, send, off);
-                }
-            }
-            cnt = h;
-        } else {
-            a[0] += __shfl_xor_sync(kFull, a[0], off);
-        }
-        off >>= 1;
-    }
-    return a[0];
-}
-
+// The NR partial sums are reduced by the halving butterfly of warp_sums;
+// lane j * 32 / NR ends with the sum of right-hand side j.
 template <typename T, int NR>
 struct RowVec {
     static constexpr int G = 32;
@@ -688,7 +660,7 @@ struct RowVec {
                 }
             }
         }
-        const T sum = halving_sum<T, NR>(acc, lane);
+        const T sum = warp_sums_spread<T, NR>(acc);
         constexpr int span = 32 / NR;
         const int j = lane / span;
         if (lane % span == 0 && j < P.nrhs) {
@@ -1025,7 +997,7 @@ __global__ void __launch_bounds__(512, 1) k_syncfree_vec(const FreeParams<T> P) 
                 for (int j = 0; j < NR; ++j) acc[j] += y[u] * w[u][j];
             }
         }
-        const T sum = halving_sum<T, NR>(acc, lane);
+        const T sum = warp_sums_spread<T, NR>(acc);
         if (owner) st_relaxed(P.x + (size_t)cur.row * P.nrhs + jo, cur.b - sum);
     }
 }
