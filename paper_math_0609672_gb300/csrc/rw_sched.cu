@@ -29,6 +29,7 @@ constexpr int kThinWidth = 32;       // rows per level in a thin run (one warp e
 constexpr int kThinThreads = 1024;   // the block of a thin run: 32 warps
 constexpr int kThinMaxRows = 4096;   // rows per thin run (shared memory)
 constexpr size_t kThinSmemBudget = 200 * 1024;
+constexpr int kHybridThinLevels = 64;  // hybrid schedule: shorter thin runs join the sync-free launches
 static_assert(256 + (int64_t)kThinMaxRows * 16 * 8 <= kSolveWorkspaceBytes, "solve workspace");
 
 // ---------------------------------------------------------------------------
@@ -1173,10 +1174,12 @@ static rw_status solve_runs_nr(rw_context* ctx, const SolveSchedule& S, const in
         }
         return solve_syncfree<T, NR, false>(ctx, S, rp, col, val, rhs, scale, x, nrhs, 0, S.n, true);
     }
-    // mode 2 (hybrid): thin runs as in the level schedule, every other run
-    // sync-free over its own positions; the whole vector is marked pending
-    // once, before the first run (a run reads only rows of earlier runs,
-    // final by then, and its own rows)
+    // mode 2 (hybrid): thin runs of at least kHybridThinLevels levels as in the
+    // level schedule; everything between them (wide runs and short thin runs,
+    // contiguous positions) as one sync-free launch each, so short runs cost no
+    // launch of their own.  The whole vector is marked pending once, before
+    // the first run (a launch reads only rows of earlier launches, final by
+    // then, and its own rows).
     if (mode == 2 && S.n > 0) {
         const int64_t cnt = (int64_t)S.n * nrhs;
         RW_COUNT_LAUNCH();
@@ -1190,6 +1193,20 @@ static rw_status solve_runs_nr(rw_context* ctx, const SolveSchedule& S, const in
         attr = true;
     }
     const int es = lane_slices(ctx->opt.wide_slices, NR);
+    int64_t free_b = 0, free_e = 0;  // hybrid: positions waiting for one sync-free launch
+    auto flush_free = [&]() -> rw_status {
+        if (free_e <= free_b) return RW_OK;
+        rw_status r2;
+        if constexpr (NR * sizeof(T) <= 32) {
+            r2 = ctx->opt.wide_slices < 0
+                     ? solve_syncfree<T, NR, true>(ctx, S, rp, col, val, rhs, scale, x, nrhs, free_b, free_e, false)
+                     : solve_syncfree<T, NR, false>(ctx, S, rp, col, val, rhs, scale, x, nrhs, free_b, free_e, false);
+        } else {
+            r2 = solve_syncfree<T, NR, false>(ctx, S, rp, col, val, rhs, scale, x, nrhs, free_b, free_e, false);
+        }
+        free_b = free_e = 0;
+        return r2;
+    };
     for (const SolveRun& run : S.runs) {
         const int64_t rows = run.pos_end - run.pos_begin;
         if (rows == 0) continue;
@@ -1198,7 +1215,14 @@ static rw_status solve_runs_nr(rw_context* ctx, const SolveSchedule& S, const in
         const size_t staged = smem + (size_t)run.in_entries * (sizeof(T) + 4);
         const bool stage = run.thin && staged <= kThinSmemBudget + 16 * 1024;
         if (stage) smem = staged;
-        if (run.thin && smem <= kThinSmemBudget + 16 * 1024 && rows <= kThinMaxRows) {
+        const bool thin_ok = run.thin && smem <= kThinSmemBudget + 16 * 1024 && rows <= kThinMaxRows;
+        if (mode == 2 && !(thin_ok && nlev >= kHybridThinLevels)) {
+            if (free_e <= free_b) free_b = run.pos_begin;
+            free_e = run.pos_end;
+            continue;
+        }
+        if (mode == 2 && (rc = flush_free())) return rc;
+        if (thin_ok) {
             const int eb = grid_for(rows * 32, 256, ctx->num_sms * 4);
             RW_COUNT_LAUNCH();
             k_thin_ext<T, NR><<<eb, 256, 0, s>>>(run.pos_begin, run.pos_end, S.tptr, S.tnin, S.tidx,
@@ -1209,18 +1233,6 @@ static rw_status solve_runs_nr(rw_context* ctx, const SolveSchedule& S, const in
             RW_COUNT_LAUNCH();
             k_thin<T, NR><<<1, kThinThreads, smem, s>>>(P);
             if ((rc = check_launch("thin-run solve"))) return rc;
-        } else if (mode == 2) {
-            if constexpr (NR * sizeof(T) <= 32) {
-                rc = ctx->opt.wide_slices < 0
-                         ? solve_syncfree<T, NR, true>(ctx, S, rp, col, val, rhs, scale, x, nrhs, run.pos_begin,
-                                                       run.pos_end, false)
-                         : solve_syncfree<T, NR, false>(ctx, S, rp, col, val, rhs, scale, x, nrhs, run.pos_begin,
-                                                        run.pos_end, false);
-            } else {
-                rc = solve_syncfree<T, NR, false>(ctx, S, rp, col, val, rhs, scale, x, nrhs, run.pos_begin,
-                                                  run.pos_end, false);
-            }
-            if (rc) return rc;
         } else {
             switch (es) {
                 case 0:
@@ -1240,6 +1252,7 @@ static rw_status solve_runs_nr(rw_context* ctx, const SolveSchedule& S, const in
             if (rc) return rc;
         }
     }
+    if (mode == 2 && (rc = flush_free())) return rc;
     return RW_OK;
 }
 
