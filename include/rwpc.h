@@ -456,6 +456,28 @@ rw_status rw_adaptive_budget(rw_context* ctx, const rw_csr* A, uint64_t seed, do
                              uint32_t min_walks, uint32_t max_walks, int32_t max_rounds, uint32_t* d_budget,
                              int32_t* h_rounds);
 
+/* Nonsymmetric matrices (Sec. 7.1).  The walk game needs only diagonal
+ * dominance by rows, so the game on A and the game on A^T (A dominant by rows
+ * and by columns, negative off-diagonals) give two factors: with F_A built on
+ * A and F_AT on A^T, A ~= Y_AT^T diag(D) Y_A (Y_A ~ the rev-LDU's U part of
+ * the paper's Eq. y2, Y_AT^T its L part by Eq. y3, D from the game on A).
+ * rw_csr_transpose writes B = A^T (device arrays of the caller: row_ptr [n+1],
+ * col and val [nnz]; columns ascending in each row); synchronous.
+ * rw_precond_apply_ldu applies z = (Y_AT^T D Y_A)^-1 r (backward solve with
+ * Y_AT^T, scaling by 1/D, forward solve with Y_A), nrhs <= 16, node-major, with
+ * the context's solve schedule options.
+ * bicgstab_solve solves A x = b (one right-hand side, FP64) by BiCGSTAB with
+ * that preconditioner on the right, from x = 0, until the true residual
+ * ||b - A x|| < tol ||b||; stats: iterations, true relative residual, time.
+ * Errors: RW_ERR_ARG (sizes or factors that do not match), RW_ERR_NO_CONVERGENCE
+ * (max_iter reached; x holds the last iterate), RW_ERR_BREAKDOWN (a BiCGSTAB
+ * scalar became zero), RW_ERR_ALLOC, RW_ERR_CUDA. */
+rw_status rw_csr_transpose(rw_context* ctx, const rw_csr* A, int32_t* d_row_ptr, int32_t* d_col, double* d_val);
+rw_status rw_precond_apply_ldu(rw_context* ctx, const rw_factor* F_A, const rw_factor* F_AT, const double* d_r,
+                               double* d_z, int32_t nrhs);
+rw_status bicgstab_solve(rw_context* ctx, const rw_csr* A, const rw_factor* F_A, const rw_factor* F_AT,
+                         const double* d_b, double* d_x, double tol, int32_t max_iter, rw_pcg_stats* stats);
+
 const char* rw_status_string(rw_status s);
 const char* rw_last_error(void);
 

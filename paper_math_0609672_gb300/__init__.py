@@ -31,7 +31,7 @@ __all__ = [
     "rw_last_error", "RW_FP64", "RW_FP32_MIXED",
     "Mlp", "rw_row_features", "rw_pilot_stats", "rw_mlp_create", "rw_mlp_predict",
     "rw_mlp_gradient", "rw_mlp_train", "rw_budget_normalize", "rw_budget_predict",
-    "rw_adaptive_budget",
+    "rw_adaptive_budget", "rw_csr_transpose", "rw_precond_apply_ldu", "bicgstab_solve",
     "RW_NUM_FEATURES", "RW_FEATURE_STRIDE", "RW_MLP_PARAMS",
     "Batch", "rw_batch_create", "pcg_solve_batch", "rw_autotune", "rw_batch_autotune",
     "rw_factor_save", "rw_factor_load", "rw_sha256", "rw_random_permutation", "rw_permute_csr",
@@ -155,6 +155,9 @@ def load():
         "rw_budget_normalize": [vp, P(rw_csr_t), vp, _f64, _u32, vp],
         "rw_budget_predict": [vp, P(rw_csr_t), vp, _f64, _u32, vp],
         "rw_adaptive_budget": [vp, P(rw_csr_t), _u64, _f64, _f64, _u32, _u32, _i32, vp, P(_i32)],
+        "rw_csr_transpose": [vp, P(rw_csr_t), vp, vp, vp],
+        "rw_precond_apply_ldu": [vp, vp, vp, vp, vp, _i32],
+        "bicgstab_solve": [vp, P(rw_csr_t), vp, vp, vp, vp, _f64, _i32, P(rw_pcg_stats_t)],
         "rw_batch_create": [vp, _i32, P(rw_csr_t), P(vp), P(vp)],
         "rw_batch_info": [vp, P(_i32), P(ctypes.c_int64), P(_i32), P(_i32)],
         "pcg_solve_batch": [vp, vp, P(vp), P(vp), _i32, _f64, _i32, ctypes.c_int, P(rw_pcg_stats_t), vp, vp],
@@ -423,6 +426,37 @@ def pcg_solve(ctx, A, F, b, x, tol, max_iter, prec=RW_FP64):
     if rc not in (RW_OK, -5):
         raise RwError(rc, "pcg_solve")
     return rc, st, its, rel
+
+
+def rw_csr_transpose(ctx, A):
+    """A^T of a device CSR as a new device CSR (columns ascending)."""
+    import torch
+    dev = A.rowptr.device
+    rp = torch.empty(A.n + 1, dtype=torch.int32, device=dev)
+    col = torch.empty(A.nnz, dtype=torch.int32, device=dev)
+    val = torch.empty(A.nnz, dtype=torch.float64, device=dev)
+    _check(load().rw_csr_transpose(ctx.handle, ctypes.byref(A.c), _ptr(rp), _ptr(col), _ptr(val)),
+           "rw_csr_transpose")
+    return CSR(rp, col, val)
+
+
+def rw_precond_apply_ldu(ctx, F_A, F_AT, r, z):
+    """z = (Y_AT^T D Y_A)^-1 r with the factors of the games on A and A^T."""
+    nrhs = 1 if r.dim() == 1 else r.shape[1]
+    _check(load().rw_precond_apply_ldu(ctx.handle, F_A.handle, F_AT.handle, _c_void_p(r.data_ptr()),
+                                       _c_void_p(z.data_ptr()), nrhs), "rw_precond_apply_ldu")
+
+
+def bicgstab_solve(ctx, A, F_A, F_AT, b, x, tol, max_iter):
+    """BiCGSTAB for a nonsymmetric A with the two-game preconditioner; b, x:
+    CUDA float64 tensors [n].  Returns (status, stats); raises on errors other
+    than RW_ERR_NO_CONVERGENCE."""
+    st = rw_pcg_stats_t()
+    rc = load().bicgstab_solve(ctx.handle, ctypes.byref(A.c), F_A.handle, F_AT.handle, _c_void_p(b.data_ptr()),
+                               _c_void_p(x.data_ptr()), float(tol), int(max_iter), ctypes.byref(st))
+    if rc not in (RW_OK, -5):
+        raise RwError(rc, "bicgstab_solve")
+    return rc, st
 
 
 def pcg_solve_batched(ctx, As, Fs, bs, xs, tol, max_iter, prec=RW_FP64):

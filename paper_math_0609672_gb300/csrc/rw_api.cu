@@ -644,6 +644,78 @@ static FactorView view_of(const rw_factor* F) {
     return v;
 }
 
+// The two-game factor of Sec. 7.1: forward data (Y, its schedule, D) from the
+// game on A, backward data (Y^T and its schedule) from the game on A^T.
+static rw_status ldu_view(const rw_factor* FA, const rw_factor* FAT, FactorView* v) {
+    if (!FA || !FAT || FA->desc.n != FAT->desc.n) {
+        set_error("two-game factor: factors missing or of different sizes");
+        return RW_ERR_ARG;
+    }
+    *v = view_of(FA);
+    const FactorView t = view_of(FAT);
+    v->yt_rp = t.yt_rp;
+    v->yt_col = t.yt_col;
+    v->yt_val = t.yt_val;
+    v->yt_val32 = t.yt_val32;
+    v->bwd_order = t.bwd_order;
+    v->bwd_sched = t.bwd_sched;
+    return RW_OK;
+}
+
+rw_status rw_csr_transpose(rw_context* ctx, const rw_csr* A, int32_t* d_row_ptr, int32_t* d_col, double* d_val) {
+    if (!ctx || !d_row_ptr || !d_col || !d_val) {
+        set_error("rw_csr_transpose: bad arguments");
+        return RW_ERR_ARG;
+    }
+    rw_status rc = check_csr(A);
+    if (rc) return rc;
+    Pool sc(ctx);
+    rc = csr_transpose(ctx, A, d_row_ptr, d_col, d_val, sc);
+    sc.release_all();
+    if (rc) return rc;
+    return check_cuda(cudaStreamSynchronize(ctx->stream), "sync");
+}
+
+rw_status rw_precond_apply_ldu(rw_context* ctx, const rw_factor* F_A, const rw_factor* F_AT, const double* d_r,
+                               double* d_z, int32_t nrhs) {
+    if (!ctx || !d_r || !d_z || nrhs < 1 || nrhs > 16) {
+        set_error("rw_precond_apply_ldu: bad arguments");
+        return RW_ERR_ARG;
+    }
+    FactorView v;
+    rw_status rc = ldu_view(F_A, F_AT, &v);
+    if (rc) return rc;
+    if (v.n == 0) return RW_OK;
+    if ((rc = reset_status(ctx))) return rc;
+    Pool sc(ctx);
+    rc = precond_fp64(ctx, v, d_r, d_z, nrhs, sc);
+    sc.release_all();
+    cudaStreamSynchronize(ctx->stream);
+    return rc;
+}
+
+rw_status bicgstab_solve(rw_context* ctx, const rw_csr* A, const rw_factor* F_A, const rw_factor* F_AT,
+                         const double* d_b, double* d_x, double tol, int32_t max_iter, rw_pcg_stats* stats) {
+    if (!ctx || !d_b || !d_x || !(tol >= 0.0) || max_iter < 0) {
+        set_error("bicgstab_solve: bad arguments");
+        return RW_ERR_ARG;
+    }
+    rw_status rc = check_csr(A);
+    if (rc) return rc;
+    FactorView v;
+    if ((rc = ldu_view(F_A, F_AT, &v))) return rc;
+    if (v.n != A->n) {
+        set_error("bicgstab_solve: matrix and factors do not match");
+        return RW_ERR_ARG;
+    }
+    if ((rc = reset_status(ctx))) return rc;
+    if (A->n == 0) {
+        if (stats) memset(stats, 0, sizeof(*stats));
+        return RW_OK;
+    }
+    return bicgstab_run(ctx, A, v, d_b, d_x, tol, max_iter, stats);
+}
+
 }  // extern "C"
 
 namespace rw {

@@ -680,6 +680,16 @@ __global__ void k_transpose_gather(int64_t nnz, const uint32_t* __restrict__ pos
     }
 }
 
+__global__ void k_transpose_pairs32(int32_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                    uint32_t* keys, uint32_t* vals, int32_t* row_of) {
+    for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+        for (int32_t p = rp[k]; p < rp[k + 1]; ++p) {
+            keys[p] = (uint32_t)col[p];
+            vals[p] = (uint32_t)p;
+            row_of[p] = k;
+        }
+}
+
 rw_status radix_sort_pairs(rw_context* ctx, uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, int64_t cnt,
                            int bits, Pool& scratch, uint32_t** ko, uint32_t** vo) {
     cudaStream_t s = ctx->stream;
@@ -739,6 +749,42 @@ rw_status transpose_factor(rw_context* ctx, int32_t n, const FactorOut& fo, int6
     RW_COUNT_LAUNCH();
     k_transpose_gather<<<grid_for(nnz, 256, ctx->num_sms * 8), 256, 0, s>>>(nnz, v0, row_of,
                                                                             fo.y_val, yt_col, yt_val);
+    return check_launch("transpose gather");
+}
+
+// A^T of a CSR matrix (int32 row pointers): entries sorted by column with a
+// stable radix sort, so each row of the result lists its columns (the rows of
+// A) in ascending order.
+rw_status csr_transpose(rw_context* ctx, const rw_csr* A, int32_t* rp, int32_t* col, double* val, Pool& scratch) {
+    cudaStream_t s = ctx->stream;
+    const int32_t n = A->n;
+    const int64_t nnz = A->nnz;
+    rw_status rc;
+    uint32_t* cnt = alloc_n<uint32_t>(scratch, n + 1);
+    if (!cnt) return RW_ERR_ALLOC;
+    if ((rc = check_cuda(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * (size_t)(n + 1), s), "memset"))) return rc;
+    if (nnz > 0) {
+        RW_COUNT_LAUNCH();
+        k_col_counts<<<grid_for(nnz, 256, ctx->num_sms * 8), 256, 0, s>>>(nnz, A->col, cnt);
+        if ((rc = check_launch("transpose counts"))) return rc;
+    }
+    // nnz < 2^31, so the prefix sums fit the int32 row pointers
+    if ((rc = check_cuda(scan_u32(cnt, reinterpret_cast<uint32_t*>(rp), n, s, scratch), "scan"))) return rc;
+    if (nnz == 0) return RW_OK;
+    uint32_t* k0 = alloc_n<uint32_t>(scratch, nnz);
+    uint32_t* v0 = alloc_n<uint32_t>(scratch, nnz);
+    uint32_t* k1 = alloc_n<uint32_t>(scratch, nnz);
+    uint32_t* v1 = alloc_n<uint32_t>(scratch, nnz);
+    int32_t* row_of = alloc_n<int32_t>(scratch, nnz);
+    if (!k0 || !v0 || !k1 || !v1 || !row_of) return RW_ERR_ALLOC;
+    RW_COUNT_LAUNCH();
+    k_transpose_pairs32<<<grid_for(n, 256, ctx->num_sms * 8), 256, 0, s>>>(n, A->row_ptr, A->col, k0, v0, row_of);
+    if ((rc = check_launch("transpose pairs"))) return rc;
+    int bits = 1;
+    while (bits < 31 && ((int64_t)1 << bits) < n) ++bits;
+    if ((rc = radix_sort_pairs(ctx, k0, v0, k1, v1, nnz, bits, scratch, &k0, &v0))) return rc;
+    RW_COUNT_LAUNCH();
+    k_transpose_gather<<<grid_for(nnz, 256, ctx->num_sms * 8), 256, 0, s>>>(nnz, v0, row_of, A->val, col, val);
     return check_launch("transpose gather");
 }
 

@@ -293,6 +293,12 @@ rw_status precond_fp64(rw_context* ctx, const FactorView& F, const double* r, do
 rw_status pcg_run(rw_context* ctx, const rw_csr* A, const FactorView& F, const double* b,
                   double* x, int nrhs, double tol, int max_iter, rw_precision prec,
                   rw_pcg_stats* stats, int32_t* h_iters, double* h_relres);
+// BiCGSTAB (right preconditioning, one right-hand side, FP64) with the
+// preconditioner of view F (see rw_solve.cu).
+rw_status bicgstab_run(rw_context* ctx, const rw_csr* A, const FactorView& F, const double* b, double* x, double tol,
+                       int max_iter, rw_pcg_stats* stats);
+// B = A^T as a CSR with ascending columns (row_ptr [n+1], col and val [nnz]).
+rw_status csr_transpose(rw_context* ctx, const rw_csr* A, int32_t* rp, int32_t* col, double* val, Pool& scratch);
 
 // y = A x (node-major, nrhs <= 16) for T = double or float.
 template <typename T>

@@ -633,6 +633,177 @@ rw_status pcg_run(rw_context* ctx, const rw_csr* A, const FactorView& F, const d
 
 
 // ---------------------------------------------------------------------------
+// BiCGSTAB with right preconditioning (van der Vorst's method) for a
+// nonsymmetric A, one right-hand side, FP64.  The preconditioner is the
+// two-game factor of Sec. 7.1 (M = Y_{A^T}^T D Y_A): the view's forward data
+// come from the game on A, its backward data from the game on A^T, and it is
+// applied by the same backward and forward solves as in PCG.  Dot products:
+// per-block sums on the device, added in a fixed order by one warp, so every
+// run takes the same iterations.  Convergence is decided on the true residual
+// ||b - A x|| < tol ||b||, recomputed whenever the recursive one passes (and
+// then replacing it).
+// ---------------------------------------------------------------------------
+__global__ void k_lin3(int64_t n, double* out, const double* a, double ca, const double* b, double cb,
+                       const double* c, double cc) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double v = ca * a[i];
+        if (b) v += cb * b[i];
+        if (c) v += cc * c[i];
+        out[i] = v;
+    }
+}
+
+// One warp adds the block sums of right-hand side 0 in a fixed order.
+__global__ void k_sum_parts(const double* __restrict__ part, int nblocks, double* out) {
+    double t = 0.0;
+    for (int b = (int)lane_id(); b < nblocks; b += 32) t += part[(size_t)b * 16];
+    t = warp_sum(t);
+    if (lane_id() == 0) *out = t;
+}
+
+rw_status bicgstab_run(rw_context* ctx, const rw_csr* A, const FactorView& F, const double* b, double* x, double tol,
+                       int max_iter, rw_pcg_stats* stats) {
+    cudaStream_t s = ctx->stream;
+    const int32_t n = A->n;
+    const int64_t launches0 = g_launches;
+    Pool sc(ctx);
+    double* r = alloc_n<double>(sc, n);
+    double* rh = alloc_n<double>(sc, n);
+    double* pv = alloc_n<double>(sc, n);
+    double* ph = alloc_n<double>(sc, n);
+    double* v = alloc_n<double>(sc, n);
+    double* sv = alloc_n<double>(sc, n);
+    double* sh = alloc_n<double>(sc, n);
+    double* t = alloc_n<double>(sc, n);
+    double* w = alloc_n<double>(sc, n);
+    double* part = alloc_n<double>(sc, (int64_t)kDotParts * 16);
+    double* dres = alloc_n<double>(sc, 1);
+    if (!r || !rh || !pv || !ph || !v || !sv || !sh || !t || !w || !part || !dres) return RW_ERR_ALLOC;
+    double* hd = static_cast<double*>(ctx->h_small);
+    const int vb = grid_for(n, 256, kDotParts);
+    const int gb = grid_for(n, 256, ctx->num_sms * 8);
+    rw_status rc;
+    auto dot = [&](const double* a, const double* c, double* out) -> rw_status {
+        RW_COUNT_LAUNCH();
+        k_dot<double, double><<<vb, 256, 0, s>>>(a, c, n, 1, part);
+        RW_COUNT_LAUNCH();
+        k_sum_parts<<<1, 32, 0, s>>>(part, vb, dres);
+        rw_status r2;
+        if ((r2 = check_launch("bicgstab dot")) ||
+            (r2 = check_cuda(cudaMemcpyAsync(hd, dres, sizeof(double), cudaMemcpyDeviceToHost, s), "copy")) ||
+            (r2 = check_cuda(cudaStreamSynchronize(s), "sync")))
+            return r2;
+        *out = hd[0];
+        return RW_OK;
+    };
+    auto lin3 = [&](double* out, const double* a, double ca, const double* bb, double cb, const double* c,
+                    double cc) -> rw_status {
+        RW_COUNT_LAUNCH();
+        k_lin3<<<gb, 256, 0, s>>>(n, out, a, ca, bb, cb, c, cc);
+        return check_launch("bicgstab update");
+    };
+    auto apply_m = [&](const double* in, double* out) -> rw_status {
+        rw_status r2 = precond_t<double>(ctx, F, F.y_val, F.yt_val, F.d, in, w, out, 1);
+        return r2 ? r2 : check_launch("bicgstab preconditioner");
+    };
+    auto spmv = [&](const double* in, double* out) -> rw_status {
+        return launch_spmv<double, double>(ctx, n, A->row_ptr, A->col, A->val, in, out, 1, nullptr);
+    };
+    cudaEventRecord(ctx->ev[8], s);
+    double bb = 0.0;
+    if ((rc = check_cuda(cudaMemsetAsync(x, 0, sizeof(double) * (size_t)n, s), "memset")) ||
+        (rc = check_cuda(cudaMemsetAsync(pv, 0, sizeof(double) * (size_t)n, s), "memset")) ||
+        (rc = check_cuda(cudaMemsetAsync(v, 0, sizeof(double) * (size_t)n, s), "memset")) ||
+        (rc = lin3(r, b, 1.0, nullptr, 0.0, nullptr, 0.0)) || (rc = lin3(rh, b, 1.0, nullptr, 0.0, nullptr, 0.0)) ||
+        (rc = dot(b, b, &bb)))
+        return rc;
+    if (!std::isfinite(bb)) {
+        set_error("bicgstab: right-hand side holds a non-finite value");
+        return RW_ERR_ARG;
+    }
+    const double bnorm = std::sqrt(bb);
+    double rho_old = 1.0, alpha = 1.0, omega = 1.0, relres = bnorm > 0.0 ? 1.0 : 0.0;
+    int it = 0;
+    bool done = bnorm == 0.0, broke = false;
+    // the true residual b - A x into r; returns its relative norm
+    auto true_residual = [&](double* rel) -> rw_status {
+        rw_status r2;
+        double rr = 0.0;
+        if ((r2 = spmv(x, t)) || (r2 = lin3(r, b, 1.0, t, -1.0, nullptr, 0.0)) || (r2 = dot(r, r, &rr))) return r2;
+        *rel = std::sqrt(rr) / bnorm;
+        return RW_OK;
+    };
+    while (!done && it < max_iter) {
+        ++it;
+        double rho = 0.0, rv = 0.0;
+        if ((rc = dot(rh, r, &rho))) return rc;
+        if (rho == 0.0 || !std::isfinite(rho)) {
+            broke = true;
+            break;
+        }
+        const double beta = (rho / rho_old) * (alpha / omega);
+        if ((rc = lin3(pv, r, 1.0, pv, beta, v, -beta * omega)) || (rc = apply_m(pv, ph)) || (rc = spmv(ph, v)) ||
+            (rc = dot(rh, v, &rv)))
+            return rc;
+        if (rv == 0.0 || !std::isfinite(rv)) {
+            broke = true;
+            break;
+        }
+        alpha = rho / rv;
+        double ss = 0.0;
+        if ((rc = lin3(sv, r, 1.0, v, -alpha, nullptr, 0.0)) || (rc = dot(sv, sv, &ss))) return rc;
+        if (std::sqrt(ss) < tol * bnorm) {
+            if ((rc = lin3(x, x, 1.0, ph, alpha, nullptr, 0.0)) || (rc = true_residual(&relres))) return rc;
+            if (relres < tol) {
+                done = true;
+                break;
+            }
+            rho_old = rho;  // continue from the replaced residual
+            omega = 1.0;
+            continue;
+        }
+        double ts = 0.0, tt = 0.0;
+        if ((rc = apply_m(sv, sh)) || (rc = spmv(sh, t)) || (rc = dot(t, sv, &ts)) || (rc = dot(t, t, &tt))) return rc;
+        if (tt == 0.0 || !std::isfinite(tt)) {
+            broke = true;
+            break;
+        }
+        omega = ts / tt;
+        double rr = 0.0;
+        if ((rc = lin3(x, x, 1.0, ph, alpha, sh, omega)) || (rc = lin3(r, sv, 1.0, t, -omega, nullptr, 0.0)) ||
+            (rc = dot(r, r, &rr)))
+            return rc;
+        relres = std::sqrt(rr) / bnorm;
+        if (relres < tol) {
+            if ((rc = true_residual(&relres))) return rc;
+            if (relres < tol) done = true;
+        }
+        if (omega == 0.0) {
+            broke = !done;
+            break;
+        }
+        rho_old = rho;
+    }
+    if (!done && bnorm > 0.0 && (rc = true_residual(&relres))) return rc;
+    cudaEventRecord(ctx->ev[9], s);
+    if ((rc = read_status(ctx, "bicgstab"))) return rc;
+    if (stats) {
+        memset(stats, 0, sizeof(*stats));
+        stats->iterations = it;
+        stats->rel_residual = relres;
+        cudaEventElapsedTime(&stats->solve_ms, ctx->ev[8], ctx->ev[9]);
+        stats->kernel_launches = g_launches - launches0;
+    }
+    if (done) return RW_OK;
+    if (broke) {
+        set_error("bicgstab: breakdown after %d iterations (relative residual %.3e)", it, relres);
+        return RW_ERR_BREAKDOWN;
+    }
+    set_error("bicgstab: %d iterations without reaching the tolerance (relative residual %.3e)", it, relres);
+    return RW_ERR_NO_CONVERGENCE;
+}
+
+// ---------------------------------------------------------------------------
 // Preconditioner application without allocation.
 //
 // Some callers cannot allocate device memory while they apply the

@@ -203,6 +203,49 @@ def laplace3d_dirichlet(m):
     return assemble(n, ei, ej, np.ones(ei.size), 6.0 - deg)
 
 
+def asym_grid(shape, rng, skew=0.6, glo=0.1, ghi=10.0, excess_frac_hi=1e-3, permute=True):
+    """Nonsymmetric grid matrix (2D 5-point or 3D 7-point by len(shape)) for
+    the two-game factor of Sec. 7.1: edge e = (i, j) with conductance g_e
+    log-U[glo, ghi] and skew s_e ~ U[-skew, skew] gives A_ij = -g_e (1 + s_e),
+    A_ji = -g_e (1 - s_e); the diagonal is max(row sum, column sum) of the
+    off-diagonal magnitudes times (1 + U[0, excess_frac_hi]), so A is
+    diagonally dominant by rows (the game on A) and by columns (the game on
+    A^T).  With `permute`, a seeded random symmetric ordering."""
+    offs = [tuple(1 if d == k else 0 for d in range(len(shape))) for k in range(len(shape))]
+    ei, ej = _grid_edges(tuple(shape), offs)
+    n = int(np.prod(shape))
+    g = _loguniform(rng, glo, ghi, ei.size)
+    sk = rng.uniform(-skew, skew, ei.size)
+    if permute:
+        ei, ej = relabel(n, ei, ej, rng.permutation(n))
+    rows = np.concatenate([ei, ej])
+    cols = np.concatenate([ej, ei])
+    off = np.concatenate([-g * (1.0 + sk), -g * (1.0 - sk)])
+    rsum = np.bincount(rows, weights=-off, minlength=n)
+    csum = np.bincount(cols, weights=-off, minlength=n)
+    dom = np.maximum(rsum, csum)
+    diag = dom * (1.0 + rng.uniform(0.0, excess_frac_hi, n))
+    r = np.concatenate([rows, np.arange(n)])
+    c = np.concatenate([cols, np.arange(n)])
+    v = np.concatenate([off, diag])
+    order = np.lexsort((c, r))
+    r, c, v = r[order], c[order], v[order]
+    rowptr = np.zeros(n + 1, np.int64)
+    np.add.at(rowptr, r + 1, 1)
+    rowptr = np.cumsum(rowptr)
+    return CSR(n, rowptr.astype(np.int32), c.astype(np.int32), v.astype(np.float64))
+
+
+def transpose(A):
+    """A^T of a host CSR (columns ascending)."""
+    rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+    order = np.lexsort((rows, A.col))
+    r, c, v = A.col[order], rows[order], A.val[order]
+    rowptr = np.zeros(A.n + 1, np.int64)
+    np.add.at(rowptr, r + 1, 1)
+    return CSR(A.n, np.cumsum(rowptr).astype(np.int32), c.astype(np.int32), v.copy())
+
+
 def grid2d_longrange(nx, ny, rng, n_long=2, glo=0.01, ghi=1.0, boundary_excess=1.0,
                      permute=True):
     """2D 5-point unit grid plus `n_long` random long-range edges per row.
