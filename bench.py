@@ -33,6 +33,10 @@ Other workloads (--workload N):
      implementation), the walks per row of each grid set so that the factor
      size C is Table 1's; value = seconds for the six builds and solves, with
      C, I, M2 per matrix beside the paper's.
+  7  a nonsymmetric 64^3 7-point grid (skewed conductances, dominant by rows
+     and columns): GPU transpose, the factors of the walk games on A and on
+     A^T (Sec. 7.1), BiCGSTAB with the two-game preconditioner to 1e-6; beside
+     it the factor of A alone as the preconditioner.
 
 Timing: W warm-up steps, then K steps, each bracketed by CUDA events on the
 library's stream, with an L2 flush (a 512 MB write) between steps outside
@@ -755,6 +759,71 @@ def run_gpu_table1(args, P, torch, dev, stream, ws, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_gpu_asym(args, P, torch, dev, stream, ws, rank, local):
+    """Workload 7: a nonsymmetric matrix (Sec. 7.1).  A step transposes A on the
+    GPU, builds the factors of the games on A and on A^T and solves A x = b by
+    BiCGSTAB with the two-game preconditioner to 1e-6.  The one-game arm uses
+    the factor of A alone (Y_A^T D Y_A) as the preconditioner."""
+    cfg = W.make_config(7, scale=args.scale)
+    A, b = cfg["A"], cfg["b"]
+    walks, seed, drop, tol = cfg["walks"], cfg["walk_seed"], cfg["drop_tol"], cfg["tol"]
+    ctx = P.Context(stream=stream)
+    dA = P.CSR.from_host(A, device=dev)
+    db = torch.as_tensor(b, device=dev)
+    dx = torch.zeros_like(db)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    F0 = P.rw_build_factor(ctx, dA, walks, seed, drop)
+    tuned, _ = P.rw_autotune(ctx, dA, F0, 1, P.RW_FP64)
+    F0.destroy()
+
+    def step(two=True):
+        ev[0].record(stream)
+        FA = P.rw_build_factor(ctx, dA, walks, seed, drop)
+        FAT = FA
+        if two:
+            dAT = P.rw_csr_transpose(ctx, dA)
+            FAT = P.rw_build_factor(ctx, dAT, walks, seed + 1, drop)
+        ev[1].record(stream)
+        rc, st = P.bicgstab_solve(ctx, dA, FA, FAT, db, dx, tol, 2000)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        info = dict(build_ms=ev[0].elapsed_time(ev[1]), solve_ms=ev[1].elapsed_time(ev[2]), iters=int(st.iterations),
+                    rel=float(st.rel_residual), rc=rc, hops=int(FA.desc.total_hops) + (int(FAT.desc.total_hops) if two else 0),
+                    nnz=int(FA.desc.nnz) + (int(FAT.desc.nnz) if two else 0),
+                    launches=int(FA.desc.kernel_launches) + (int(FAT.desc.kernel_launches) if two else 0)
+                    + int(st.kernel_launches))
+        if two:
+            FAT.destroy()
+        FA.destroy()
+        return info
+
+    timer = Timer(torch, dev, stream)
+    ms, infos, clk = timer.run(step, args.steps, args.warmup, ws, local)
+    ms1, infos1, _ = timer.run(lambda: step(False), args.steps, args.warmup, ws, local)
+    _, ms = aggregate(0, ms, ws)
+    _, ms1 = aggregate(0, ms1, ws)
+    ctx.close()
+    if rank != 0:
+        return
+    I, I1 = infos[-1], infos1[-1]
+    name = W.CONFIGS[7]["name"] + ("" if args.scale == 1.0 else f" (edge scale {args.scale})")
+    line = _base_line(args, ws, ms, "f64",
+                      {"workload": name, "n": A.n, "nnz": A.nnz, "walks_per_row": walks, "drop_tol": drop,
+                       "nrhs": 1, "tol": tol, "solver": "BiCGSTAB, right preconditioner Y_AT^T D Y_A",
+                       "l2": "flushed between steps (512 MB write)", "parallelism": f"replicas x{ws}"})
+    line.update({
+        "value": ms * 1e-3, "unit": "s to 1e-6 (transpose + two builds + BiCGSTAB)", "higher_is_better": False,
+        "two_games": {"build_s": statistics.mean(i["build_ms"] for i in infos) * 1e-3,
+                      "solve_s": statistics.mean(i["solve_ms"] for i in infos) * 1e-3, "iterations": I["iters"],
+                      "rel_residual": I["rel"], "factor_nnz": I["nnz"], "hops": I["hops"]},
+        "one_game": {"s": ms1 * 1e-3, "build_s": statistics.mean(i["build_ms"] for i in infos1) * 1e-3,
+                     "solve_s": statistics.mean(i["solve_ms"] for i in infos1) * 1e-3, "iterations": I1["iters"],
+                     "rel_residual": I1["rel"], "form": "factor of A only: Y_A^T D Y_A"},
+        "clocks": clk, "gpu_launches": I["launches"], "autotuned": tuned,
+    })
+    print(json.dumps(line), flush=True)
+
+
 def run_gpu(args):
     import torch
     import paper_math_0609672_gb300 as P
@@ -768,6 +837,8 @@ def run_gpu(args):
         run_gpu_batched(args, P, torch, dev, stream, ws, rank, local)
     elif args.workload == 6:
         run_gpu_table1(args, P, torch, dev, stream, ws, rank, local)
+    elif args.workload == 7:
+        run_gpu_asym(args, P, torch, dev, stream, ws, rank, local)
     else:
         run_gpu_learned(args, P, torch, dev, stream, ws, rank, local)
 
@@ -778,7 +849,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", type=int, default=2, choices=[2, 3, 4, 5, 6])
+    ap.add_argument("--workload", type=int, default=2, choices=[2, 3, 4, 5, 6, 7])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nmat", type=int, default=None, help="workload 4: number of matrices (default 256)")
     ap.add_argument("--scale", type=float, default=1.0, help="workloads 5, 6: grid edge scale (default 1)")

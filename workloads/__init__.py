@@ -367,6 +367,8 @@ CONFIGS = {
             tol=1e-6, nrhs=1, precision="fp32", gen_seed=4, walk_seed=4),
     6: dict(name="laplace3d-7pt-dirichlet-50^3..100^3", walks=20, drop_tol=None, tol=1e-6, nrhs=1,
             precision="fp64", gen_seed=5, walk_seed=5, edges=(50, 60, 70, 80, 90, 100)),
+    7: dict(name="asym-grid3d-7pt-64^3-logU[0.1,10]-skew0.6", walks=300, drop_tol=1e-3, tol=1e-6, nrhs=1,
+            precision="fp64", gen_seed=6, walk_seed=6),
 }
 
 
@@ -377,7 +379,7 @@ def _rngs(seed):
 
 
 def make_config(i, scale=1.0, nmat=None):
-    """Inputs for workload i (1..6).
+    """Inputs for workload i (1..7).
 
     Returns dict(A=CSR or list of CSR, b=array or list, plus the settings of
     CONFIGS[i]).  `scale` < 1 shrinks the grid edge lengths (for quick tests);
@@ -410,6 +412,10 @@ def make_config(i, scale=1.0, nmat=None):
         m = max(4, int(round(128 * scale)))
         A = grid3d(m, m, m, 27, rng_a, excess_frac=1e-4)
         b = rhs(A.n, 1, rng_b)
+    elif i == 7:
+        m = max(4, int(round(64 * scale)))
+        A = asym_grid((m, m, m), rng_a, skew=0.6)
+        b = rhs(A.n, 1, rng_b)[:, 0]
     elif i == 6:
         cfg["edges"] = tuple(max(4, int(round(e * scale))) for e in cfg["edges"])
         A = [laplace3d_dirichlet(e) for e in cfg["edges"]]
