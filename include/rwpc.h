@@ -94,14 +94,15 @@ typedef struct {
     int32_t wide_slices;     /* wide-level solves: entry slices per row (lanes per row = slices x
                                 right-hand sides, power of two <= 32); 0 = one row per warp;
                                 -1 = vector rows: one row per warp, each lane reads all
-                                right-hand sides of its entries */
+                                right-hand sides of its entries (default -1) */
     int32_t spmv_slices;     /* SpMV: entry slices per row, as wide_slices; 0 = one row per warp */
     int32_t cluster_width;   /* levels of at most this many rows (above the thin-run width) run on
                                 one thread-block cluster with hardware barriers; 0 = never */
     int32_t cluster_size;    /* CTAs of that cluster (2..16; 0 = 16) */
     int32_t solve_mode;      /* triangular solves: 0 = level schedule (thin / wide / cluster runs),
                                 1 = sync-free (each row waits only for its own dependencies),
-                                2 = hybrid (thin runs on one block, the other runs sync-free) */
+                                2 = hybrid (thin runs on one block, the other runs sync-free;
+                                default 2) */
     int32_t reuse;           /* 1: walk reuse (Algorithm 2 of Sec. 5.3) in single-matrix builds:
                                 every simulated walk also counts, for each later node k' it
                                 passes, the legal sub-walk from k' (k' its least node until it

@@ -144,6 +144,8 @@ void rw_options_default(rw_options* opt) {
     opt->timing = 1;
     opt->graphs = 1;
     opt->walk_fuse = -1;
+    opt->solve_mode = 2;
+    opt->wide_slices = -1;
     opt->solve_mode_bwd = -1;
     opt->thin_levels = 128;
 }
