@@ -116,6 +116,9 @@ typedef struct {
     int32_t solve_mode_bwd;  /* solve_mode of the backward (Y^T) solve; -1 = as solve_mode (default) */
     int32_t thin_levels;     /* factor build: levels per thin run at most (0 = no cap; default 128);
                                 dependencies on earlier runs are summed by the whole grid */
+    int32_t thin_cluster;    /* thin runs on a thread-block cluster of this many CTAs (2..16, reduced to
+                                what the device can place), x replicated in each CTA's shared memory;
+                                0 or 1 = one block (default 0) */
 } rw_options;
 
 typedef struct rw_context rw_context;

@@ -21,6 +21,8 @@
 // timing.
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "rw_internal.h"
 
 namespace rw {
@@ -310,10 +312,18 @@ __device__ __forceinline__ void load_slot(const T* p, T (&v)[NR]) {
     }
 }
 
-template <typename T, int NR>
+// CL: the run is solved by a thread-block cluster instead of one block.  Every
+// CTA keeps the whole run's x values in its shared memory; row q of a level
+// belongs to CTA q mod csize (warp q / csize), which writes the new value into
+// every CTA's copy through distributed shared memory; a cluster barrier ends
+// each level.  The level's FP64 work is thereby spread over csize SMs.
+template <typename T, int NR, bool CL>
 __global__ void __launch_bounds__(kThinThreads) k_thin(const ThinParams<T> P) {
     constexpr int U = 6;
     extern __shared__ __align__(16) unsigned char smem[];
+    namespace cg = cooperative_groups;
+    const unsigned crank = CL ? cg::this_cluster().block_rank() : 0u;
+    const unsigned csz = CL ? cg::this_cluster().num_blocks() : 1u;
     const int rows = (int)(P.pos_end - P.pos_begin);
     const int nlev = P.lev_end - P.lev_begin;
     T* xs = reinterpret_cast<T*>(smem);                                    // [rows][NR]
@@ -408,12 +418,15 @@ __global__ void __launch_bounds__(kThinThreads) k_thin(const ThinParams<T> P) {
         __syncthreads();
     }
 
+    // every CTA's copy is initialised before any row value is written into it
+    if constexpr (CL) cg::this_cluster().sync();
     // phase 2: the levels in order; in each level warp w takes rows w, w+32, ...
+    // (with a cluster: slot q = warp * csize + rank of the level)
     auto fetch = [&](int li, RowRegs<T, U>& R) {
         R.slot = -1;
         R.n = 0;
         if (li < nlev) {
-            const int sl = lstart[li] + warp;
+            const int sl = lstart[li] + warp * (int)csz + (int)crank;
             if (sl < lstart[li + 1]) {
                 R.slot = sl;
                 R.e0 = eoff[sl];
@@ -431,7 +444,12 @@ __global__ void __launch_bounds__(kThinThreads) k_thin(const ThinParams<T> P) {
     auto finish = [&](int slot, T mine) {
         if (lane < P.nrhs && lane < NR) {
             const T v = xs[(size_t)slot * NR + lane] - mine;
-            xs[(size_t)slot * NR + lane] = v;
+            if constexpr (CL) {
+                for (unsigned r = 0; r < csz; ++r)
+                    cg::this_cluster().map_shared_rank(xs, r)[(size_t)slot * NR + lane] = v;
+            } else {
+                xs[(size_t)slot * NR + lane] = v;
+            }
             __stcg(P.x + (size_t)rowid[slot] * P.nrhs + lane, v);
         }
     };
@@ -461,7 +479,9 @@ __global__ void __launch_bounds__(kThinThreads) k_thin(const ThinParams<T> P) {
             }
             finish(r0.slot, warp_sums<T, NR>(acc));
         }
-        __syncthreads();
+        // the cluster barrier also keeps every CTA alive until the last remote write
+        if constexpr (CL) cg::this_cluster().sync();
+        else __syncthreads();
         r0 = r1;
     }
 }
@@ -1158,6 +1178,42 @@ static rw_status launch_nonthin(rw_context* ctx, const SolveSchedule& S, const S
     return RW_OK;
 }
 
+// CTAs of a thin run's cluster (rw_options.thin_cluster, a power of two
+// <= 16), reduced to the largest size the device can place with this shared
+// memory; 1 = one block.
+template <typename T, int NR>
+static int thin_cluster_size(rw_context* ctx, size_t smem) {
+    int want = ctx->opt.thin_cluster;
+    if (want < 2) return 1;
+    if (want > 16) want = 16;
+    int c = 1;
+    while (c * 2 <= want) c *= 2;
+    static int placeable[17][2] = {};  // per size: 0 unknown, 1 yes, -1 no (by smem above or below 128 KB)
+    const int big = smem > 128 * 1024 ? 1 : 0;
+    while (c > 1) {
+        if (placeable[c][big] == 0) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3((unsigned)c);
+            cfg.blockDim = dim3(kThinThreads);
+            cfg.dynamicSmemBytes = big ? kThinSmemBudget + 16 * 1024 : 128 * 1024;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = (unsigned)c;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            int nc = 0;
+            placeable[c][big] =
+                (cudaOccupancyMaxActiveClusters(&nc, k_thin<T, NR, true>, &cfg) == cudaSuccess && nc >= 1) ? 1 : -1;
+            cudaGetLastError();
+        }
+        if (placeable[c][big] > 0) return c;
+        c >>= 1;
+    }
+    return 1;
+}
+
 template <typename T, int NR>
 static rw_status solve_runs_nr(rw_context* ctx, const SolveSchedule& S, const int64_t* rp,
                                const int32_t* col, const T* val, const T* tval, const T* rhs,
@@ -1188,8 +1244,11 @@ static rw_status solve_runs_nr(rw_context* ctx, const SolveSchedule& S, const in
     }
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_thin<T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_thin<T, NR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kThinSmemBudget + 16 * 1024);
+        cudaFuncSetAttribute(k_thin<T, NR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kThinSmemBudget + 16 * 1024);
+        cudaFuncSetAttribute(k_thin<T, NR, true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         attr = true;
     }
     const int es = lane_slices(ctx->opt.wide_slices, NR);
@@ -1213,7 +1272,8 @@ static rw_status solve_runs_nr(rw_context* ctx, const SolveSchedule& S, const in
         const int nlev = run.lev_end - run.lev_begin;
         size_t smem = thin_stage_offset<T, NR>((int)rows, nlev);
         const size_t staged = smem + (size_t)run.in_entries * (sizeof(T) + 4);
-        const bool stage = run.thin && staged <= kThinSmemBudget + 16 * 1024;
+        const int tc = thin_cluster_size<T, NR>(ctx, smem);  // 1: one block
+        const bool stage = run.thin && tc == 1 && staged <= kThinSmemBudget + 16 * 1024;
         if (stage) smem = staged;
         const bool thin_ok = run.thin && smem <= kThinSmemBudget + 16 * 1024 && rows <= kThinMaxRows;
         if (mode == 2 && !(thin_ok && nlev >= kHybridThinLevels)) {
@@ -1231,7 +1291,24 @@ static rw_status solve_runs_nr(rw_context* ctx, const SolveSchedule& S, const in
                             S.tptr, S.tnin, S.tidx, tval, ext, rhs, scale, x, nrhs, stage ? 1 : 0,
                             (int)run.in_entries};
             RW_COUNT_LAUNCH();
-            k_thin<T, NR><<<1, kThinThreads, smem, s>>>(P);
+            if (tc > 1) {
+                cudaLaunchConfig_t cfg = {};
+                cfg.gridDim = dim3((unsigned)tc);
+                cfg.blockDim = dim3(kThinThreads);
+                cfg.dynamicSmemBytes = smem;
+                cfg.stream = s;
+                cudaLaunchAttribute at[1];
+                at[0].id = cudaLaunchAttributeClusterDimension;
+                at[0].val.clusterDim.x = (unsigned)tc;
+                at[0].val.clusterDim.y = 1;
+                at[0].val.clusterDim.z = 1;
+                cfg.attrs = at;
+                cfg.numAttrs = 1;
+                if ((rc = check_cuda(cudaLaunchKernelEx(&cfg, k_thin<T, NR, true>, P), "thin-run cluster solve")))
+                    return rc;
+            } else {
+                k_thin<T, NR, false><<<1, kThinThreads, smem, s>>>(P);
+            }
             if ((rc = check_launch("thin-run solve"))) return rc;
         } else {
             switch (es) {

@@ -26,6 +26,7 @@ namespace {
 struct Candidate {
     int wide_slices, solve_blocks_per_sm, cluster_width, spmv_slices, solve_mode;
     int solve_mode_bwd = -1;  // -1: as solve_mode
+    int thin_cluster = 0;
 };
 
 std::string shape_key(const rw_context* ctx, const TuneTarget& T, int nrhs) {
@@ -67,7 +68,8 @@ bool cache_lookup(const char* path, const std::string& key, Candidate* c) {
         Candidate t{};
         if (json_int(line, "wide_slices", &t.wide_slices) && json_int(line, "solve_blocks_per_sm", &t.solve_blocks_per_sm) &&
             json_int(line, "cluster_width", &t.cluster_width) && json_int(line, "spmv_slices", &t.spmv_slices) &&
-            json_int(line, "solve_mode", &t.solve_mode) && json_int(line, "solve_mode_bwd", &t.solve_mode_bwd)) {
+            json_int(line, "solve_mode", &t.solve_mode) && json_int(line, "solve_mode_bwd", &t.solve_mode_bwd) &&
+            json_int(line, "thin_cluster", &t.thin_cluster)) {
             *c = t;  // the last matching line wins
             found = true;
         }
@@ -81,9 +83,9 @@ void cache_store(const char* path, const std::string& key, const Candidate& c, f
     FILE* f = fopen(path, "a");
     if (!f) return;
     fprintf(f,
-            "{\"key\":\"%s\",\"solve_mode\":%d,\"solve_mode_bwd\":%d,\"wide_slices\":%d,\"solve_blocks_per_sm\":%d,\"cluster_width\":%d,"
+            "{\"key\":\"%s\",\"solve_mode\":%d,\"solve_mode_bwd\":%d,\"thin_cluster\":%d,\"wide_slices\":%d,\"solve_blocks_per_sm\":%d,\"cluster_width\":%d,"
             "\"spmv_slices\":%d,\"precond_ms\":%.4f,\"spmv_ms\":%.4f}\n",
-            key.c_str(), c.solve_mode, c.solve_mode_bwd, c.wide_slices, c.solve_blocks_per_sm, c.cluster_width, c.spmv_slices, ms_pre,
+            key.c_str(), c.solve_mode, c.solve_mode_bwd, c.thin_cluster, c.wide_slices, c.solve_blocks_per_sm, c.cluster_width, c.spmv_slices, ms_pre,
             ms_spmv);
     fclose(f);
 }
@@ -166,9 +168,15 @@ rw_status tune_t(rw_context* ctx, const TuneTarget& X, int nrhs, const T* av, co
     cands.push_back(Candidate{-1, 1, 0, 0, 0, 1});  // level-scheduled forward, sync-free backward
     cands.push_back(Candidate{-1, 1, 0, 0, 2});     // hybrid runs (thin: one block; wide: sync-free)
     cands.push_back(Candidate{-1, 1, 0, 0, 1, 2});  // sync-free forward, hybrid backward
+    for (int tc : {4, 8}) {                          // hybrid with thin runs on clusters
+        Candidate c{-1, 1, 0, 0, 2};
+        c.thin_cluster = tc;
+        cands.push_back(c);
+    }
     for (const Candidate& c : cands) {
         ctx->opt.solve_mode = c.solve_mode;
         ctx->opt.solve_mode_bwd = c.solve_mode_bwd;
+        ctx->opt.thin_cluster = c.thin_cluster;
         ctx->opt.wide_slices = c.wide_slices;
         ctx->opt.solve_blocks_per_sm = c.solve_blocks_per_sm;
         ctx->opt.cluster_width = c.cluster_width;
@@ -181,6 +189,7 @@ rw_status tune_t(rw_context* ctx, const TuneTarget& X, int nrhs, const T* av, co
             bp = ms;
             b.solve_mode = c.solve_mode;
             b.solve_mode_bwd = c.solve_mode_bwd;
+            b.thin_cluster = c.thin_cluster;
             b.wide_slices = c.wide_slices;
             b.solve_blocks_per_sm = c.solve_blocks_per_sm;
             b.cluster_width = c.cluster_width;
@@ -226,6 +235,7 @@ rw_status autotune(rw_context* ctx, const TuneTarget& X, int nrhs, rw_precision 
     }
     ctx->opt.solve_mode = c.solve_mode;
     ctx->opt.solve_mode_bwd = c.solve_mode_bwd;
+    ctx->opt.thin_cluster = c.thin_cluster;
     ctx->opt.wide_slices = c.wide_slices;
     ctx->opt.solve_blocks_per_sm = c.solve_blocks_per_sm;
     ctx->opt.cluster_width = c.cluster_width;

@@ -316,18 +316,19 @@ def test_autotune_installs_options_and_caches(P, ctx, tmp_path):
     c2.close()
 
 
-@pytest.mark.parametrize("mode,cw,ws,bwd", [(1, 0, 0, -1), (0, 256, 0, -1), (0, 0, -1, -1), (0, 256, -1, -1),
-                                            (1, 0, -1, -1), (1, 0, -1, 0), (0, 0, -1, 1), (2, 0, -1, -1),
-                                            (2, 0, 0, -1), (1, 0, -1, 2)])
-def test_precond_modes_match_oracle(P, mode, cw, ws, bwd):
+@pytest.mark.parametrize("mode,cw,ws,bwd,tc", [(1, 0, 0, -1, 0), (0, 256, 0, -1, 0), (0, 0, -1, -1, 0),
+                                               (0, 256, -1, -1, 0), (1, 0, -1, -1, 0), (1, 0, -1, 0, 0),
+                                               (0, 0, -1, 1, 0), (2, 0, -1, -1, 0), (2, 0, 0, -1, 0),
+                                               (1, 0, -1, 2, 0), (2, 0, -1, -1, 8), (0, 0, 8, -1, 4)])
+def test_precond_modes_match_oracle(P, mode, cw, ws, bwd, tc):
     """The sync-free solve, the cluster runs and the vector rows (wide_slices
     -1: every lane reads all right-hand sides of its entries; level-scheduled,
-    sync-free or hybrid, also with the backward solve in another mode) give
-    the oracle's z (1e-12)."""
+    sync-free or hybrid, also with the backward solve in another mode, thin
+    runs on one block or on a cluster) give the oracle's z (1e-12)."""
     rng = np.random.default_rng(30 + mode)
     A = W.make_config(2, scale=0.25)["A"]
     c2 = P.Context(options=P.rw_options_default(solve_mode=mode, cluster_width=cw, wide_slices=ws,
-                                                solve_mode_bwd=bwd))
+                                                solve_mode_bwd=bwd, thin_cluster=tc))
     dA = P.CSR.from_host(A)
     F = P.rw_build_factor(c2, dA, 100, 7, 1e-3)
     ref = oracle.build_factor(A, 100, 7, 1e-3)
@@ -364,8 +365,9 @@ def test_vector_rows_with_long_dependency_lists(P):
     dA = P.CSR.from_host(A)
     r = rng.standard_normal((A.n, 4))
     zr = [oracle.precond_apply(ref, r[:, j]) for j in (0, 3)]
-    for mode, bwd in ((0, -1), (1, -1), (1, 0), (0, 1), (2, -1), (1, 2)):
-        c2 = P.Context(options=P.rw_options_default(solve_mode=mode, solve_mode_bwd=bwd, wide_slices=-1))
+    for mode, bwd, tc in ((0, -1, 0), (1, -1, 0), (1, 0, 0), (0, 1, 0), (2, -1, 0), (1, 2, 0), (2, -1, 8)):
+        c2 = P.Context(options=P.rw_options_default(solve_mode=mode, solve_mode_bwd=bwd, wide_slices=-1,
+                                                    thin_cluster=tc))
         F = P.rw_build_factor(c2, dA, 100, 7, 1e-3)
         z = _dev(np.zeros_like(r))
         P.rw_precond_apply(c2, F, _dev(r), z)
