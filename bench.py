@@ -527,7 +527,7 @@ def run_gpu_learned(args, P, torch, dev, stream, ws, rank, local):
     db = torch.as_tensor(b, device=dev)
     dx = torch.zeros_like(db)
     budget = torch.zeros(A.n, dtype=torch.int32, device=dev)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     # schedule autotuning of each path on its own factor (untimed)
     P.rw_budget_predict(ctx, dA, M, 300.0, 20, budget)
     F0 = P.rw_build_factor_budget(ctx, dA, budget, seed, drop)
@@ -562,6 +562,7 @@ def run_gpu_learned(args, P, torch, dev, stream, ws, rank, local):
     def adaptive():
         ev[0].record(stream)
         rounds = P.rw_adaptive_budget(ctx, dA, seed, args.adapt_delta, z99, 20, 65535, 12, budget)
+        ev[3].record(stream)
         F = P.rw_build_factor_budget(ctx, dA, budget, seed, drop)
         ev[1].record(stream)
         B = P.Batch(ctx, [dA], [F])
@@ -571,7 +572,8 @@ def run_gpu_learned(args, P, torch, dev, stream, ws, rank, local):
         d = F.desc
         info = dict(hops=int(d.total_hops), walks=int(d.total_walks), nnz=int(d.nnz),
                     build_ms=ev[0].elapsed_time(ev[1]), pcg_ms=ev[1].elapsed_time(ev[2]),
-                    iters=int(its.max()), rel=float(rel.max()), rc=rc, rounds=rounds)
+                    count_ms=ev[0].elapsed_time(ev[3]), iters=int(its.max()), rel=float(rel.max()), rc=rc,
+                    rounds=rounds)
         B.destroy()
         F.destroy()
         return info
@@ -603,6 +605,7 @@ def run_gpu_learned(args, P, torch, dev, stream, ws, rank, local):
         Ad = inf_a[-1]
         adapt = {"delta": args.adapt_delta, "alpha": 0.99, "min_walks": 20, "s": ms_a * 1e-3,
                  "build_s": statistics.mean(i["build_ms"] for i in inf_a) * 1e-3,
+                 "count_s": statistics.mean(i["count_ms"] for i in inf_a) * 1e-3,
                  "pcg_s": statistics.mean(i["pcg_ms"] for i in inf_a) * 1e-3, "iterations": Ad["iters"],
                  "rel_residual": Ad["rel"], "factor_nnz": Ad["nnz"], "walks": Ad["walks"], "hops": Ad["hops"],
                  "rounds": Ad["rounds"],

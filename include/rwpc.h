@@ -89,7 +89,9 @@ typedef struct {
     int32_t refine_every;    /* FP32 PCG: true-residual replacement period (default 50) */
     int32_t walk_blocks_per_sm; /* 0 = from the occupancy calculator */
     int32_t timing;          /* 1: record per-phase device times (default 1) */
-    int32_t solve_blocks_per_sm; /* wide-level solves: 512-thread blocks per SM (0 = 1) */
+    int32_t solve_blocks_per_sm; /* wide-level solves and the sync-free parts with vector rows:
+                                    512-thread blocks per SM (0 = 1; 2 = a register-capped
+                                    sync-free kernel, two blocks resident per SM) */
     int32_t graphs;          /* 1: batched PCG replays each iteration from a CUDA graph (default 1) */
     int32_t wide_slices;     /* wide-level solves: entry slices per row (lanes per row = slices x
                                 right-hand sides, power of two <= 32); 0 = one row per warp;
@@ -119,6 +121,9 @@ typedef struct {
     int32_t thin_cluster;    /* thin runs on a thread-block cluster of this many CTAs (2..16, reduced to
                                 what the device can place), x replicated in each CTA's shared memory;
                                 0 or 1 = one block (default 0) */
+    int32_t adapt_ahead;     /* rw_adaptive_budget: walks a row runs past its next decision point T, in
+                                percent of T (default 100; 0 = exactly up to T); changes only the
+                                time, never the counts */
 } rw_options;
 
 typedef struct rw_context rw_context;
@@ -441,18 +446,21 @@ rw_status rw_budget_predict(rw_context* ctx, const rw_csr* A, const rw_mlp* M, d
 /* Adaptive walk counts of Sec. 5.1 (Eq. lengthdelta).  The paper keeps
  * adding walks from row k until Delta Xi' sqrt(M_k) / sigma > z, where Xi' and
  * sigma are the mean and sample standard deviation of the row's walk lengths
- * and z = Q^-1((1 - alpha)/2) for confidence alpha.  All rows advance together
- * in rounds: round 1 runs min_walks factor walks per walk row; after each
- * round a row failing Delta^2 Xi'^2 M > z^2 sigma^2 (with M < max_walks) grows
- * to max(M + 1, ceil(z^2 sigma^2 / (Delta^2 Xi'^2))), capped at max_walks, and
- * the next round runs walks M, M+1, ... of those rows only; at most max_rounds
- * rounds.  Walks are the factor walks (walk kind 0) of matrix index 0 with
+ * and z = Q^-1((1 - alpha)/2) for confidence alpha.  Each walk row is first
+ * decided after min_walks factor walks; a row failing Delta^2 Xi'^2 M > z^2
+ * sigma^2 (with M < max_walks) grows to max(M + 1, ceil(z^2 sigma^2 /
+ * (Delta^2 Xi'^2))), capped at max_walks, and is decided again with that many
+ * walks; at most max_rounds decisions per row.  The GPU runs the rows in launch
+ * rounds that run rw_options.adapt_ahead percent of a row's next decision
+ * point past it, so one round can hold several decisions of a row; walks past
+ * the final count are discarded.  Walks are the factor walks (walk kind 0) of matrix index 0 with
  * `seed`, so rw_build_factor_budget(seed, d_budget) afterwards consists of
  * exactly the walks that fixed the counts.  Length sums are exact 64-bit
  * integers and the test is FP64 with each operation rounded once, so the
  * counts are deterministic.
  *   d_budget [n] device uint32, written: M_k for walk rows, 0 for the others.
- *   h_rounds host, optional: rounds run.
+ *   h_rounds host, optional: the most decisions any row took (the rounds of
+ *   a schedule that decides every row once per round).
  * Errors: RW_ERR_ARG (delta, z <= 0; min_walks < 2; max_walks < min_walks or
  * > 65535; max_rounds < 1), RW_ERR_NOT_RMATRIX, RW_ERR_WALK_CAP (a walk hit
  * rw_options.max_steps), RW_ERR_ALLOC, RW_ERR_CUDA.  Synchronous. */

@@ -64,7 +64,7 @@ class rw_options_t(ctypes.Structure):
                 ("wide_slices", _i32), ("spmv_slices", _i32), ("cluster_width", _i32),
                 ("cluster_size", _i32), ("solve_mode", _i32), ("reuse", _i32),
                 ("walk_fuse", _i32), ("solve_mode_bwd", _i32),
-                ("thin_levels", _i32), ("thin_cluster", _i32)]
+                ("thin_levels", _i32), ("thin_cluster", _i32), ("adapt_ahead", _i32)]
 
 
 class rw_factor_desc_t(ctypes.Structure):

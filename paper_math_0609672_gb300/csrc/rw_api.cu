@@ -148,6 +148,7 @@ void rw_options_default(rw_options* opt) {
     opt->wide_slices = -1;
     opt->solve_mode_bwd = -1;
     opt->thin_levels = 128;
+    opt->adapt_ahead = 100;
 }
 
 const char* rw_status_string(rw_status s) {

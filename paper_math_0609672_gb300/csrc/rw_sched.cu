@@ -920,8 +920,10 @@ __device__ __forceinline__ bool any_pending(const T (&v)[NR], int nrhs) {
     return pend;
 }
 
-template <typename T, int NR>
-__global__ void __launch_bounds__(512, 1) k_syncfree_vec(const FreeParams<T> P) {
+// MINB = 2 caps the registers so that two 512-thread blocks share an SM:
+// twice the rows in flight, at the cost of some spilled prefetch state.
+template <typename T, int NR, int MINB>
+__global__ void __launch_bounds__(512, MINB) k_syncfree_vec(const FreeParams<T> P) {
     const int lane = (int)lane_id();
     constexpr int span = 32 / NR;
     const int jo = lane / span;  // the right-hand side this lane stores
@@ -1038,10 +1040,12 @@ static rw_status solve_syncfree(rw_context* ctx, const SolveSchedule& S, const i
                                 const T* val, const T* rhs, const T* scale, T* x, int nrhs,
                                 int64_t pos_begin, int64_t pos_end, bool fill) {
     cudaStream_t s = ctx->stream;
+    const int two = VEC && ctx->opt.solve_blocks_per_sm >= 2 ? 1 : 0;
     const void* kern;
-    if constexpr (VEC) kern = (const void*)k_syncfree_vec<T, NR>;
+    if constexpr (VEC) kern = two ? (const void*)k_syncfree_vec<T, NR, 2> : (const void*)k_syncfree_vec<T, NR, 1>;
     else kern = (const void*)k_syncfree<T, NR>;
-    static int per_sm = -1;
+    static int per_sm_of[2] = {-1, -1};
+    int& per_sm = per_sm_of[two];
     if (per_sm < 0) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 512, 0);
         if (per_sm < 1) per_sm = 1;

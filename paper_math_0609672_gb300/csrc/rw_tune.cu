@@ -167,6 +167,7 @@ rw_status tune_t(rw_context* ctx, const TuneTarget& X, int nrhs, const T* av, co
     cands.push_back(Candidate{-1, 1, 0, 0, 1, 0});  // sync-free forward, level-scheduled backward
     cands.push_back(Candidate{-1, 1, 0, 0, 0, 1});  // level-scheduled forward, sync-free backward
     cands.push_back(Candidate{-1, 1, 0, 0, 2});     // hybrid runs (thin: one block; wide: sync-free)
+    cands.push_back(Candidate{-1, 2, 0, 0, 2});     // hybrid, sync-free parts with two blocks per SM
     cands.push_back(Candidate{-1, 1, 0, 0, 1, 2});  // sync-free forward, hybrid backward
     for (int tc : {4, 8}) {                          // hybrid with thin runs on clusters
         Candidate c{-1, 1, 0, 0, 2};

@@ -91,3 +91,18 @@ def test_rejects_bad_arguments(P, ctx):
         with pytest.raises(P.RwError) as e:
             _budget(P, ctx, A, 1, delta, z, mn, mx, rounds)
         assert e.value.code == -1
+
+
+@pytest.mark.parametrize("ahead", [0, 25, 400])
+def test_run_ahead_changes_no_count(P, ahead):
+    """How far the launch rounds run past a row's next decision point
+    (rw_options.adapt_ahead) changes the time only: counts and the decision
+    count stay the oracle's."""
+    c = P.Context(options=P.rw_options_default(adapt_ahead=ahead))
+    try:
+        for i, (A, delta, z, mn, mx, rounds) in enumerate(_cases()[:3]):
+            got, r = _budget(P, c, A, 60 + i, delta, z, mn, mx, rounds)
+            ref, rr = oracle.adaptive_budget(A, 60 + i, delta, z, min_walks=mn, max_walks=mx, max_rounds=rounds)
+            assert r == rr and np.array_equal(got, ref), (ahead, i)
+    finally:
+        c.close()
