@@ -144,6 +144,7 @@ __device__ __forceinline__ bool wait_gives_up(unsigned& spins, unsigned* timeout
 __device__ __forceinline__ void atom_add_release(unsigned* p, unsigned v) {
     unsigned old;
     asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    (void)old;
 }
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
     unsigned v;
