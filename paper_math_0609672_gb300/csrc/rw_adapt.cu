@@ -16,13 +16,12 @@
 //
 // The GPU runs the rows in launch rounds, each running ahead of the row's next
 // decision point T: walks A, A+1, ... up to T + (adapt_ahead % of T), capped,
-// A being the walks run so far.  One warp per row then replays the decisions in walk order over
-// the new lengths, as many as the walks run allow, so a row whose estimate
-// moves by a few walks is decided again in the same round.  Walks beyond the
-// final count are discarded; the counts and the decision count are those of
-// the one-decision-per-round schedule.
+// A being the walks run so far.  One warp per row then replays the decisions
+// in walk order over the new lengths, as many as the walks run allow, so a row
+// whose estimate moves by a few walks is decided again in the same round.
+// Walks beyond the final count are discarded; the counts and the decision
+// count are those of the one-decision-per-round schedule.
 #include <cmath>
-#include <vector>
 
 #include "rw_internal.h"
 
