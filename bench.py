@@ -261,8 +261,8 @@ def _walk_roofline(peaks, hops, walks_total, walk_ms, bytes_per_hop=64.0):
 def _solve_kernels(opt):
     """Names of the triangular-solve kernels the tuned options run."""
     def one(mode):
-        return "k_syncfree_vec" if mode == 1 and opt.get("wide_slices") == -1 else (
-            "k_syncfree" if mode == 1 else "k_thin/k_wide")
+        free = "k_syncfree_vec" if opt.get("wide_slices") == -1 else "k_syncfree"
+        return free if mode == 1 else f"k_thin/{free}" if mode == 2 else "k_thin/k_wide"
     fwd = one(opt.get("solve_mode", 0))
     bwd = one(opt.get("solve_mode_bwd", -1) if opt.get("solve_mode_bwd", -1) >= 0 else opt.get("solve_mode", 0))
     return f"{fwd} (forward) + {bwd} (backward)"
@@ -350,6 +350,8 @@ def run_gpu_single(args, P, torch, dev, stream, ws, rank, local):
         F.destroy()
     e2e = statistics.mean(e2e_ms)
 
+    # the two latencies that bound the solves' dependency chains (untimed)
+    handoff_ns, l2_ns = P.rw_probe_latency(ctx, 20000)
     extra = {}
     if mixed:
         # the same factor solved in FP64 (untimed comparison run): error of the
@@ -374,6 +376,14 @@ def run_gpu_single(args, P, torch, dev, stream, ws, rank, local):
     solve_roof = _solve_roofline(peaks, napply, infos[-1]["nnz"], A.n, nrhs, tri_ms,
                                  4.0 if mixed else 8.0, 8.0 if mixed else 12.0,
                                  _solve_kernels(tuned))
+    # latency view of the solves: each level of a solve waits for at least one
+    # value stored by another SM, so one SM-to-SM hand-off per level is a floor
+    nlev = infos[-1]["fwd"] + infos[-1]["bwd"]
+    per_level_us = tri_ms * 1e3 / (napply * nlev) if napply and nlev else 0.0
+    solve_roof["latency"] = {"per_level_us": per_level_us, "handoff_us": handoff_ns * 1e-3,
+                             "l2_load_us": l2_ns * 1e-3, "levels_per_application": nlev,
+                             "applications": napply,
+                             "frac": handoff_ns * 1e-3 / per_level_us if per_level_us > 0 else None}
     dominant = solve_roof if tri_ms > walk_ms else walk_roof
     line = _base_line(args, ws, ms, "f32-mixed" if mixed else "f64",
                       {"workload": W.CONFIGS[args.workload]["name"], "n": A.n, "nnz": A.nnz,

@@ -317,6 +317,17 @@ rw_status rw_autotune(rw_context* ctx, const rw_csr* A, const rw_factor* F, int3
 rw_status rw_batch_autotune(rw_context* ctx, const rw_batch* B, int32_t nrhs, rw_precision prec,
                             const char* cache_path, rw_options* out, float* h_ms);
 
+/* The two latencies that bound a triangular solve's dependency chain (each
+ * level waits for a value stored by another SM): *h_l2_ns, one dependent
+ * L2-hit load (a relaxed load chasing a 256 KB cyclic permutation, `iters`
+ * steps, one thread); *h_handoff_ns, one SM-to-SM hand-off through L2 (two
+ * blocks on distinct SMs pass a counter with relaxed stores and polls, `iters`
+ * round trips each, averaged over partner SMs 1, n/4, n/2 and n-1 of block 0).
+ * Measurement only: nothing else in the library depends on it.  Synchronous.
+ * Errors: RW_ERR_ARG (iters outside [1, 2^20], null outputs), RW_ERR_TIMEOUT (a
+ * bounded poll gave up), RW_ERR_ALLOC, RW_ERR_CUDA. */
+rw_status rw_probe_latency(rw_context* ctx, int32_t iters, double* h_handoff_ns, double* h_l2_ns);
+
 /* z = (Y^T diag(D) Y)^-1 r for nrhs node-major right-hand sides (FP64): the
  * preconditioner application inside pcg_solve (backward solve with Y^T,
  * scaling by 1/D, forward solve with Y). */

@@ -33,7 +33,7 @@ __all__ = [
     "rw_mlp_gradient", "rw_mlp_train", "rw_budget_normalize", "rw_budget_predict",
     "rw_adaptive_budget", "rw_csr_transpose", "rw_precond_apply_ldu", "bicgstab_solve",
     "RW_NUM_FEATURES", "RW_FEATURE_STRIDE", "RW_MLP_PARAMS",
-    "Batch", "rw_batch_create", "pcg_solve_batch", "rw_autotune", "rw_batch_autotune",
+    "Batch", "rw_batch_create", "pcg_solve_batch", "rw_autotune", "rw_batch_autotune", "rw_probe_latency",
     "rw_factor_save", "rw_factor_load", "rw_sha256", "rw_random_permutation", "rw_permute_csr",
 ]
 
@@ -163,6 +163,7 @@ def load():
         "pcg_solve_batch": [vp, vp, P(vp), P(vp), _i32, _f64, _i32, ctypes.c_int, P(rw_pcg_stats_t), vp, vp],
         "rw_autotune": [vp, P(rw_csr_t), vp, _i32, ctypes.c_int, ctypes.c_char_p, P(rw_options_t), vp],
         "rw_batch_autotune": [vp, vp, _i32, ctypes.c_int, ctypes.c_char_p, P(rw_options_t), vp],
+        "rw_probe_latency": [vp, _i32, P(_f64), P(_f64)],
         "rw_factor_save": [vp, ctypes.c_char_p],
         "rw_factor_load": [vp, ctypes.c_char_p, P(vp)],
         "rw_random_permutation": [vp, _i32, _u64, vp],
@@ -707,6 +708,14 @@ def rw_autotune(ctx, A, F, nrhs, prec=RW_FP64, cache_path=None):
                               cache_path.encode() if cache_path else None, ctypes.byref(opt),
                               ms.ctypes.data_as(_c_void_p)), "rw_autotune")
     return _tune_result(ctx, opt, ms)
+
+
+def rw_probe_latency(ctx, iters=20000):
+    """(SM-to-SM hand-off through L2 in ns, dependent L2-hit load in ns): the two
+    latencies that bound a triangular solve's dependency chain."""
+    h, l2 = _f64(0.0), _f64(0.0)
+    _check(load().rw_probe_latency(ctx.handle, int(iters), ctypes.byref(h), ctypes.byref(l2)), "rw_probe_latency")
+    return float(h.value), float(l2.value)
 
 
 def rw_batch_autotune(ctx, B, nrhs, prec=RW_FP64, cache_path=None):

@@ -38,7 +38,7 @@ std::string shape_key(const rw_context* ctx, const TuneTarget& T, int nrhs) {
     const double per_row = T.n > 0 ? (double)T.nnz_y / T.n : 0.0;
     const int lg_per_row = (int)std::lround(std::log2(std::max(1.0, per_row)) * 2.0);
     const int lg_depth = (int)std::lround(std::log2(std::max(1, T.depth)) * 2.0);
-    char buf[256];
+    char buf[512];
     snprintf(buf, sizeof buf, "%s|sm%d|n2^%d|ypr%d|depth%d|nrhs%d", prop.name, prop.multiProcessorCount, lg_n,
              lg_per_row, lg_depth, nr);
     for (char* p = buf; *p; ++p)
@@ -248,11 +248,123 @@ rw_status autotune(rw_context* ctx, const TuneTarget& X, int nrhs, rw_precision 
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Latency probes.  A triangular solve is a chain through L2: a row's value is
+// stored by one SM and picked up by the polling load of another, so the two
+// latencies that bound it are a dependent L2-hit load and an SM-to-SM hand-off
+// through L2 (a relaxed store seen by a relaxed poll).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void st_relaxed_u32(unsigned* p, unsigned v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// One thread follows `steps` dependent relaxed loads through a cyclic
+// permutation that stays in L2.
+__global__ void k_probe_chase(const unsigned* next, int steps, unsigned* sink, unsigned long long* ns) {
+    unsigned idx = 0;
+    for (int i = 0; i < 256; ++i) idx = ld_relaxed_u32(next + idx);
+    const unsigned long long t0 = global_ns();
+    for (int i = 0; i < steps; ++i) idx = ld_relaxed_u32(next + idx);
+    ns[0] = global_ns() - t0;
+    sink[0] = idx;
+}
+
+// Blocks 0 and `partner` (distinct SMs: the dynamic shared memory admits one
+// block per SM) pass a counter back and forth `iters` times; every wait is
+// bounded and sets the timeout flag when it gives up.
+__global__ void k_probe_pingpong(unsigned* flags, int partner, int iters, unsigned long long* ns, DevStatus* st) {
+    extern __shared__ unsigned probe_pad[];
+    const int b = (int)blockIdx.x;
+    if (threadIdx.x != 0 || (b != 0 && b != partner)) return;
+    probe_pad[0] = (unsigned)b;
+    const bool first = b == 0;
+    unsigned* mine = flags + (first ? 0 : 32);
+    const unsigned* theirs = flags + (first ? 32 : 0);
+    const unsigned long long t0 = global_ns();
+    for (int i = 1; i <= iters; ++i) {
+        if (first) st_relaxed_u32(mine, (unsigned)i);
+        unsigned spins = 0;
+        while (ld_relaxed_u32(theirs) != (unsigned)i)
+            if (wait_gives_up(spins, &st->timeout)) return;
+        if (!first) st_relaxed_u32(mine, (unsigned)i);
+    }
+    if (first) ns[0] = global_ns() - t0;
+}
+
 }  // namespace rw
 
 using namespace rw;
 
 extern "C" {
+
+rw_status rw_probe_latency(rw_context* ctx, int32_t iters, double* h_handoff_ns, double* h_l2_ns) {
+    if (!ctx || iters < 1 || iters > (1 << 20) || !h_handoff_ns || !h_l2_ns) {
+        set_error("rw_probe_latency: bad arguments (1 <= iters <= 2^20, both outputs)");
+        return RW_ERR_ARG;
+    }
+    cudaStream_t s = ctx->stream;
+    rw_status rc;
+    if ((rc = reset_status(ctx))) return rc;
+    Pool sc(ctx);
+    constexpr unsigned kChase = 1u << 16;  // 256 KB: L2-resident
+    unsigned* next = alloc_n<unsigned>(sc, kChase);
+    unsigned* flags = alloc_n<unsigned>(sc, 64);
+    unsigned long long* ns = alloc_n<unsigned long long>(sc, 8);
+    if (!next || !flags || !ns) return RW_ERR_ALLOC;
+    // one cycle through all entries (Sattolo's shuffle, fixed LCG)
+    std::vector<unsigned> perm(kChase);
+    for (unsigned i = 0; i < kChase; ++i) perm[i] = i;
+    uint64_t lcg = 0x9E3779B97F4A7C15ull;
+    for (unsigned i = kChase - 1; i > 0; --i) {
+        lcg = lcg * 6364136223846793005ull + 1442695040888963407ull;
+        const unsigned j = (unsigned)((lcg >> 33) % i);
+        std::swap(perm[i], perm[j]);
+    }
+    if ((rc = check_cuda(cudaMemcpyAsync(next, perm.data(), sizeof(unsigned) * kChase, cudaMemcpyHostToDevice, s),
+                         "copy")))
+        return rc;
+    RW_COUNT_LAUNCH();
+    k_probe_chase<<<1, 1, 0, s>>>(next, iters, flags + 48, ns);
+    if ((rc = check_launch("latency probe"))) return rc;
+    const int smem = 120 * 1024;
+    if ((rc = check_cuda(cudaFuncSetAttribute(k_probe_pingpong, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
+                         "attribute")))
+        return rc;
+    const int nsm = ctx->num_sms;
+    int partners[4] = {1, nsm / 4, nsm / 2, nsm - 1};
+    int np = 0;
+    for (int i = 0; i < 4; ++i) {
+        bool dup = partners[i] < 1 || partners[i] >= nsm;
+        for (int j = 0; j < np; ++j) dup = dup || partners[j] == partners[i];
+        if (!dup) partners[np++] = partners[i];
+    }
+    for (int i = 0; i < np; ++i) {
+        if ((rc = check_cuda(cudaMemsetAsync(flags, 0, sizeof(unsigned) * 48, s), "memset"))) return rc;
+        unsigned long long* out = ns + 1 + i;
+        int partner = partners[i], it = iters;
+        DevStatus* st = ctx->d_status;
+        void* args[] = {(void*)&flags, (void*)&partner, (void*)&it, (void*)&out, (void*)&st};
+        RW_COUNT_LAUNCH();
+        if ((rc = check_cuda(cudaLaunchCooperativeKernel((const void*)k_probe_pingpong, dim3((unsigned)nsm), dim3(32),
+                                                         args, (size_t)smem, s),
+                             "latency probe")))
+            return rc;
+    }
+    unsigned long long h[8] = {0};
+    if ((rc = check_cuda(cudaMemcpyAsync(h, ns, sizeof(h), cudaMemcpyDeviceToHost, s), "copy")) ||
+        (rc = read_status(ctx, "latency probe")))
+        return rc;
+    *h_l2_ns = (double)h[0] / iters;
+    double sum = 0.0;
+    for (int i = 0; i < np; ++i) sum += (double)h[1 + i] / (2.0 * iters);
+    *h_handoff_ns = np ? sum / np : 0.0;
+    return RW_OK;
+}
 
 rw_status rw_autotune(rw_context* ctx, const rw_csr* A, const rw_factor* F, int32_t nrhs, rw_precision prec,
                       const char* cache_path, rw_options* out, float* h_ms) {

@@ -378,3 +378,13 @@ def test_vector_rows_with_long_dependency_lists(P):
             assert np.linalg.norm(zg[:, j] - zj) / np.linalg.norm(zj) < 1e-12, (mode, bwd, j)
         F.destroy()
         c2.close()
+
+
+def test_latency_probe(P, ctx):
+    """The hand-off and L2-load latencies come back positive and in a plausible
+    range; bad arguments are rejected."""
+    h, l2 = P.rw_probe_latency(ctx, 2000)
+    assert 20.0 < l2 < 5000.0 and 50.0 < h < 20000.0, (h, l2)
+    with pytest.raises(P.RwError) as e:
+        P.rw_probe_latency(ctx, 0)
+    assert e.value.code == -1
