@@ -182,6 +182,7 @@ rw_status rw_adaptive_budget(rw_context* ctx, const rw_csr* A, uint64_t seed, do
     unsigned long long* hops = alloc_n<unsigned long long>(sc, 1);
     if (!R.A || !R.T || !R.M || !R.D || !R.S1 || !R.S2 || !inc || !flags || !hops) return RW_ERR_ALLOC;
     if ((rc = check_cuda(cudaMemsetAsync(R.A, 0, sizeof(uint32_t) * (size_t)nw, s), "memset")) ||
+        (rc = check_cuda(cudaMemsetAsync(R.M, 0, sizeof(uint32_t) * (size_t)nw, s), "memset")) ||
         (rc = check_cuda(cudaMemsetAsync(R.D, 0, sizeof(uint32_t) * (size_t)nw, s), "memset")) ||
         (rc = check_cuda(cudaMemsetAsync(R.S1, 0, sizeof(unsigned long long) * (size_t)nw, s), "memset")) ||
         (rc = check_cuda(cudaMemsetAsync(R.S2, 0, sizeof(unsigned long long) * (size_t)nw, s), "memset")) ||
@@ -195,6 +196,7 @@ rw_status rw_adaptive_budget(rw_context* ctx, const rw_csr* A, uint64_t seed, do
     if ((rc = check_launch("adaptive start"))) return rc;
     const double d2 = delta * delta, z2 = z * z;
     unsigned* hp = static_cast<unsigned*>(ctx->h_small);
+    hp[0] = hp[1] = 0u;
     // Every launch round reaches each pending row's decision point at least
     // once, so max_rounds launch rounds decide every row.
     for (int32_t round = 0; round < max_rounds; ++round) {
