@@ -124,6 +124,9 @@ typedef struct {
     int32_t adapt_ahead;     /* rw_adaptive_budget: walks a row runs past its next decision point T, in
                                 percent of T (default 100; 0 = exactly up to T); changes only the
                                 time, never the counts */
+    int32_t thin_flags;      /* thin runs on one block: 1 = each row flags its slot in shared memory
+                                when done and readers wait on the flags of their entries (no barrier
+                                per level); 0 = one block barrier per level (default 0) */
 } rw_options;
 
 typedef struct rw_context rw_context;

@@ -64,7 +64,8 @@ class rw_options_t(ctypes.Structure):
                 ("wide_slices", _i32), ("spmv_slices", _i32), ("cluster_width", _i32),
                 ("cluster_size", _i32), ("solve_mode", _i32), ("reuse", _i32),
                 ("walk_fuse", _i32), ("solve_mode_bwd", _i32),
-                ("thin_levels", _i32), ("thin_cluster", _i32), ("adapt_ahead", _i32)]
+                ("thin_levels", _i32), ("thin_cluster", _i32), ("adapt_ahead", _i32),
+                ("thin_flags", _i32)]
 
 
 class rw_factor_desc_t(ctypes.Structure):
@@ -688,7 +689,7 @@ def pcg_solve_batch(ctx, B, bs, xs, tol, max_iter, prec=RW_FP64):
 # ---------------------------------------------------------------------------
 
 _TUNED = ("solve_mode", "solve_mode_bwd", "wide_slices", "solve_blocks_per_sm", "cluster_width", "spmv_slices",
-          "thin_cluster")
+          "thin_cluster", "thin_flags")
 
 
 def _tune_result(ctx, opt, ms):

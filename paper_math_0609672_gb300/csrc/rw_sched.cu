@@ -265,15 +265,17 @@ struct ThinParams {
     int nrhs;
     int stage;  // 1: copy the run's in-run entries to shared memory first
     int stage_entries;
+    int flags;  // 1: per-row ready flags in shared memory instead of a barrier per level
+    DevStatus* st;
 };
 
 // Shared memory of a thin run: x values [rows][NR], row ids, entry offsets and
-// counts, level starts, staged-entry offsets; then (staged) the in-run values
-// and their slot indices.
+// counts, level starts, staged-entry offsets, ready flags; then (staged) the
+// in-run values and their slot indices.
 template <typename T, int NR>
 __host__ __device__ __forceinline__ size_t thin_stage_offset(int rows, int nlev) {
     const size_t base = (size_t)rows * NR * sizeof(T) + (size_t)rows * 12 + (size_t)(nlev + 1) * 4 +
-                        (size_t)(rows + 1) * 4;
+                        (size_t)(rows + 1) * 4 + (size_t)rows * 4;
     return (base + 15) & ~(size_t)15;
 }
 
@@ -338,6 +340,7 @@ __global__ void __launch_bounds__(kThinThreads) k_thin(const ThinParams<T> P) {
     const int32_t* tidx = P.tidx + run_e0;
     const T* tval = P.tval + run_e0;
     int32_t* soff = lstart + nlev + 1;  // [rows + 1] staged: first entry of each slot
+    volatile int32_t* ready = soff + rows + 1;  // [rows] flags mode: slot finished
 
     for (int i = threadIdx.x; i <= nlev; i += blockDim.x)
         lstart[i] = (int32_t)(P.lptr[P.lev_begin + i] - P.pos_begin);
@@ -346,6 +349,7 @@ __global__ void __launch_bounds__(kThinThreads) k_thin(const ThinParams<T> P) {
         const int64_t pos = P.pos_begin + slot;
         const int32_t row = P.order[pos];
         rowid[slot] = row;
+        ready[slot] = 0;
         eoff[slot] = (int32_t)(P.tptr[pos] - run_e0);
         ecnt[slot] = P.tnin[pos];
         for (int j = 0; j < P.nrhs && j < NR; ++j) {
@@ -453,6 +457,27 @@ __global__ void __launch_bounds__(kThinThreads) k_thin(const ThinParams<T> P) {
             __stcg(P.x + (size_t)rowid[slot] * P.nrhs + lane, v);
         }
     };
+    // flags mode: a lane reads an in-run value only once its slot is flagged
+    // (bounded wait; the warp holding the lowest unfinished slot always has its
+    // dependencies, so the run progresses without a barrier per level)
+    // (after one wait gives up, the others of the block give up at once)
+    const bool flags = !CL && P.flags != 0;
+    __shared__ int gave_up;
+    if (threadIdx.x == 0) gave_up = 0;
+    __syncthreads();
+    auto wait_slot = [&](int32_t sl) {
+        if (!flags) return;
+        unsigned spins = 0;
+        while (ready[sl] == 0) {
+            if (*(volatile int*)&gave_up) break;
+            if (++spins > kSpinLimit) {
+                *(volatile int*)&gave_up = 1;
+                atomicAdd(&P.st->timeout, 1u);
+                break;
+            }
+        }
+        __threadfence_block();
+    };
     RowRegs<T, U> r0, r1;
     fetch(0, r0);
     for (int li = 0; li < nlev; ++li) {
@@ -464,6 +489,7 @@ __global__ void __launch_bounds__(kThinThreads) k_thin(const ThinParams<T> P) {
 #pragma unroll
             for (int u = 0; u < U; ++u)
                 if (r0.s[u] >= 0) {
+                    wait_slot(r0.s[u]);
                     T v[NR];
                     load_slot<T, NR>(xs + (size_t)r0.s[u] * NR, v);
 #pragma unroll
@@ -472,16 +498,22 @@ __global__ void __launch_bounds__(kThinThreads) k_thin(const ThinParams<T> P) {
             for (int k = lane + 32 * U; k < r0.n; k += 32) {  // rows longer than 32*U
                 const int32_t sl = tidx[r0.e0 + k];
                 const T y = tval[r0.e0 + k];
+                wait_slot(sl);
                 T v[NR];
                 load_slot<T, NR>(xs + (size_t)sl * NR, v);
 #pragma unroll
                 for (int j = 0; j < NR; ++j) acc[j] += y * v[j];
             }
             finish(r0.slot, warp_sums<T, NR>(acc));
+            if (flags) {
+                __syncwarp();
+                __threadfence_block();
+                if (lane == 0) ready[r0.slot] = 1;
+            }
         }
         // the cluster barrier also keeps every CTA alive until the last remote write
         if constexpr (CL) cg::this_cluster().sync();
-        else __syncthreads();
+        else if (!flags) __syncthreads();
         r0 = r1;
     }
 }
@@ -1293,7 +1325,7 @@ static rw_status solve_runs_nr(rw_context* ctx, const SolveSchedule& S, const in
                                                   tval, x, nrhs, ext);
             ThinParams<T> P{run.pos_begin, run.pos_end, run.lev_begin, run.lev_end, S.lptr, S.order,
                             S.tptr, S.tnin, S.tidx, tval, ext, rhs, scale, x, nrhs, stage ? 1 : 0,
-                            (int)run.in_entries};
+                            (int)run.in_entries, ctx->opt.thin_flags ? 1 : 0, ctx->d_status};
             RW_COUNT_LAUNCH();
             if (tc > 1) {
                 cudaLaunchConfig_t cfg = {};
