@@ -61,7 +61,7 @@ __device__ __forceinline__ uint32_t adapt_ahead(uint32_t t, uint32_t pct, uint32
     return a > max_walks ? max_walks : (uint32_t)a;
 }
 
-// One warp per walk row: consumes this round's lengths (walks A .. A+cnt-1 in
+// One warp per walk row: consumes this launch round's lengths (walks A .. A+cnt-1 in
 // rec[wbase[r] ..]) in walk order, deciding at every decision point reached;
 // sets the row's next request in inc[node] and counts the rows still pending.
 __global__ void k_adapt_chain(int32_t nw, const int4* __restrict__ wrow, const int64_t* __restrict__ wbase,
@@ -200,7 +200,7 @@ rw_status rw_adaptive_budget(rw_context* ctx, const rw_csr* A, uint64_t seed, do
     // Every launch round reaches each pending row's decision point at least
     // once, so max_rounds launch rounds decide every row.
     for (int32_t round = 0; round < max_rounds; ++round) {
-        Pool rp(ctx);  // this round's walk space and records
+        Pool rp(ctx);  // this launch round's walk space and records
         WalkSpace ws;
         if ((rc = build_walk_space(ctx, T, 0, inc, ws, rp, true))) return rc;
         if (ws.total == 0) break;
