@@ -371,6 +371,11 @@ def run_gpu_single(args, P, torch, dev, stream, ws, rank, local):
         return
     peaks, peak_kind = _peaks()
     walk_roof = _walk_roofline(peaks, hops, infos[-1]["walks"], walk_ms)
+    if args.workload == 2:
+        # DRAM bytes read + written by one k_walk launch of this workload in an
+        # ncu capture (55.6 MB read, 840.3 MB written: the records; the tables
+        # stay in L2); to be retaken whenever the walk kernel changes
+        walk_roof["traffic"] = 895.9e6
     napply = statistics.mean(max(i["iters"]) for i in infos)
     tri_ms = statistics.mean(i["bwd_ms"] + i["fwd_ms"] for i in infos)
     solve_roof = _solve_roofline(peaks, napply, infos[-1]["nnz"], A.n, nrhs, tri_ms,
