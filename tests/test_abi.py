@@ -69,3 +69,35 @@ def test_sha256_matches_hashlib():
     for size in (0, 1, 55, 56, 63, 64, 65, 119, 120, 1000, 100000):
         data = rng.integers(0, 256, size, dtype=np.uint8).tobytes()
         assert P.rw_sha256(data) == hashlib.sha256(data).digest(), size
+
+
+def documented_option_defaults():
+    """(field, default) for every rw_options field whose comment in
+    include/rwpc.h states its default."""
+    src = open(os.path.join(ROOT, "include", "rwpc.h")).read()
+    body = src[src.index("typedef struct {\n    uint64_t max_steps;"):src.index("} rw_options;")]
+    fields = re.split(r"\n(?=    (?:int32_t|uint64_t) )", body)
+    out = {}
+    for f in fields:
+        m = re.match(r"\s*(?:int32_t|uint64_t)\s+(\w+);(.*)", f, flags=re.S)
+        if not m:
+            continue
+        name, comment = m.group(1), " ".join(m.group(2).split())
+        d = re.search(r"default (-?\d+)(?: << (\d+))?", comment)
+        if d:
+            out[name] = int(d.group(1)) << int(d.group(2) or 0)
+            continue
+        d = re.search(r"(-?\d+) = [^()]*\(default\)", comment)
+        if d:
+            out[name] = int(d.group(1))
+    return out
+
+
+def test_option_defaults_match_the_header(lib_path):
+    import paper_math_0609672_gb300 as P
+    P.load()
+    doc = documented_option_defaults()
+    assert len(doc) >= 15, sorted(doc)
+    o = P.rw_options_default()
+    got = {k: getattr(o, k) for k in doc}
+    assert got == doc
