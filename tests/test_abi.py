@@ -101,3 +101,34 @@ def test_option_defaults_match_the_header(lib_path):
     o = P.rw_options_default()
     got = {k: getattr(o, k) for k in doc}
     assert got == doc
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every ctypes structure of the binding has the C struct's size and each
+    field's offset (a C program built from include/rwpc.h prints them)."""
+    import ctypes
+    import shutil
+    import paper_math_0609672_gb300 as P
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    pairs = [("rw_csr", P.rw_csr_t), ("rw_options", P.rw_options_t), ("rw_factor_desc", P.rw_factor_desc_t),
+             ("rw_pcg_stats", P.rw_pcg_stats_t)]
+    lines = ['#include <stdio.h>', '#include "rwpc.h"', "int main(void) {"]
+    for cname, py in pairs:
+        lines.append(f'    printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f in py._fields_:
+            lines.append(f'    printf("{cname} {f[0]} %zu\\n", offsetof({cname}, {f[0]}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        a, b, v = line.split()
+        got[(a, b)] = int(v)
+    for cname, py in pairs:
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f in py._fields_:
+            assert got[(cname, f[0])] == getattr(py, f[0]).offset, (cname, f[0])
