@@ -3,7 +3,9 @@ only: on a row whose walk lengths have a closed-form law the counts settle
 where z^2 Var / (Delta^2 mean^2) puts them and scale as Delta^-2; the counts
 replay, round by round, from the lengths of the factor walks that
 build_factor runs with them (so the adaptive walks are the factor walks);
-and the bounds (min, max, rounds, rows without walks) hold."""
+the bounds (min, max, rounds, rows without walks) hold; and a schedule that
+runs walks past each decision point and replays the decisions in walk order
+(the GPU's launch rounds) reaches the same counts in fewer rounds."""
 import math
 
 import numpy as np
@@ -112,3 +114,64 @@ def test_rejects_bad_arguments():
         args.update(kw)
         with pytest.raises(oracle.OracleError):
             oracle.adaptive_budget(A, 1, **args)
+
+
+def _run_ahead_schedule(lengths, min_walks, max_walks, max_rounds, d2, z2, ahead):
+    """Host model of the GPU's launch rounds for one row (test only): each
+    round runs the row's walks up to `ahead` percent past its next decision
+    point and replays the decisions in walk order over the lengths run.
+    Returns (count, decisions, launch rounds)."""
+    a = s1 = s2 = d = 0
+    t = min_walks
+    launches = 0
+    while True:
+        a1 = min(max_walks, t + t * ahead // 100)
+        launches += 1
+        while True:
+            if a == t:
+                d += 1
+                nt = 0
+                if 1 < t < max_walks:
+                    mean = s1 / t
+                    var = (s2 - s1 * mean) / (t - 1.0)
+                    lhs = d2 * (mean * mean) * t
+                    rhs = z2 * var
+                    if not lhs > rhs:
+                        need = rhs / (d2 * (mean * mean))
+                        nt = max_walks if need >= max_walks else math.ceil(need)
+                        nt = max(nt, t + 1)
+                if nt == 0 or d >= max_rounds:
+                    return t, d, launches
+                t = nt
+                continue
+            if a == a1:
+                break
+            e = min(t, a1)
+            seg = lengths[a:e].astype(np.uint64)
+            s1 += int(seg.sum())
+            s2 += int((seg * seg).sum())
+            a = e
+
+
+@pytest.mark.parametrize("ahead", [0, 30, 100, 400])
+def test_run_ahead_rounds_give_the_oracle_counts(ahead):
+    """Running walks past a row's next decision point and replaying the
+    decisions in walk order (the GPU's launch rounds) gives the counts and the
+    decision count of one decision per round: the walk lengths come from the
+    oracle's factor walks, the counts from the oracle's adaptive rule."""
+    rng = np.random.default_rng(77)
+    A = W.grid3d(5, 4, 4, 27, rng, excess_frac=1e-3)
+    delta, z, mn, mx, rounds = 0.15, 2.576, 8, 300, 10
+    ref, rr = oracle.adaptive_budget(A, 5, delta, z, min_walks=mn, max_walks=mx, max_rounds=rounds)
+    F = oracle.build_factor(A, mx, 5, 0.0, records=True)
+    wr = F["walk_rows"]
+    dmax, launches = 0, 0
+    for i, k in enumerate(wr):
+        lengths = F["rec_len"][i * mx:(i + 1) * mx]
+        cnt, dec, lr = _run_ahead_schedule(lengths, mn, mx, rounds, delta * delta, z * z, ahead)
+        assert cnt == ref[k], (k, cnt, ref[k])
+        dmax, launches = max(dmax, dec), max(launches, lr)
+    assert dmax == rr
+    assert launches <= rr
+    if ahead == 0:
+        assert launches == rr
