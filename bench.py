@@ -170,7 +170,8 @@ def cpu_oracle_sample(A, walks, seed, drop, label, target_s=12.0, rng_seed=2024)
         chunk = min(chunk * 2, 8192)
     return {"value": hops / t_used, "unit": "hops/s", "cores": 1, "kind": "oracle",
             "sample": f"{done_rows} random walk rows of {label} x {walks} walks "
-                      f"({hops} hops) in {t_used:.1f} s, single thread, factor rows only"}
+                      f"({hops} hops) in {t_used:.1f} s, single thread, factor rows only",
+            "seconds": t_used}
 
 
 def _oracle_sample_for(workload, cfg, target_s, rng_seed):
@@ -200,7 +201,8 @@ def run_reference(args):
     v = statistics.mean(r["value"] for r in vals)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "hops/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": 1e3 * statistics.mean(r["seconds"] for r in vals),
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": W.CONFIGS[args.workload]["name"]},
             "cpu_baseline": {"value": v, "unit": "hops/s", "cores": 1, "kind": "oracle",
