@@ -175,6 +175,28 @@ def test_full_size_c2_sampled_rows(P, ctx):
     assert t["total_hops"] > 0
 
 
+@pytest.mark.parametrize("workload,nsample", [(3, 60), (5, 40)])
+def test_full_size_sampled_rows(P, ctx, workload, nsample):
+    """Workloads 3 (n = 10^6, 200 walks/row) and 5 (128^3 27-point grid,
+    uniform 300 walks/row: the plain arm's build) at full size on the GPU;
+    the oracle recomputes a seeded sample of rows bit for bit."""
+    cfg = W.make_config(workload)
+    A = cfg["A"]
+    t = gpu_factor(P, ctx, A, cfg["walks"], cfg["walk_seed"], cfg["drop_tol"])
+    rng = np.random.default_rng(7 + workload)
+    rows = np.unique(np.concatenate([rng.choice(A.n, nsample, replace=False), [0, A.n - 1]]))
+    ref = oracle.build_factor(A, cfg["walks"], cfg["walk_seed"], cfg["drop_tol"], rows=rows)
+    for k in rows:
+        a, b = t["y_row_ptr"][k], t["y_row_ptr"][k + 1]
+        c, d = ref["rowptr"][k], ref["rowptr"][k + 1]
+        assert np.array_equal(t["y_col"][a:b], ref["col"][c:d]), k
+        assert np.array_equal(t["y_val"][a:b].view(np.int64), ref["val"][c:d].view(np.int64)), k
+        assert t["d"][k].view(np.int64) == ref["D"][k].view(np.int64), k
+        assert t["walks"][k] == ref["M"][k] and t["visits"][k] == ref["J"][k] and t["ground"][k] == ref["G"][k]
+    assert np.all(t["d"] > 0) and np.all(np.abs(t["y_val"]) >= cfg["drop_tol"])
+    assert np.all(t["walks"][oracle.walk_rows(A)] == cfg["walks"])
+
+
 def test_transpose_and_levels(P, ctx):
     import scipy.sparse as sp
     A = W.make_config(2, scale=0.25)["A"]
