@@ -141,10 +141,10 @@ __device__ __forceinline__ bool wait_gives_up(unsigned& spins, unsigned* timeout
 // preceding __syncthreads) and polls with acquire loads, so a barrier costs
 // about two L2 round trips and no reset.  Every wait is bounded; returns false
 // when it gave up (the timeout flag is then set).
-__device__ __forceinline__ void atom_add_release(unsigned* p, unsigned v) {
+__device__ __forceinline__ unsigned atom_add_release(unsigned* p, unsigned v) {
     unsigned old;
     asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-    (void)old;
+    return old;
 }
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
     unsigned v;

@@ -482,7 +482,7 @@ __global__ void __launch_bounds__(256) k_feat_moments(int64_t n, const float* __
     }
 }
 
-__global__ void k_exp_weights(int64_t n, const float* __restrict__ pred, float* __restrict__ w) {
+__global__ void k_exp_weights(int64_t n, const float* pred, float* w) {  // may run in place
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
          k += (int64_t)gridDim.x * blockDim.x)
         w[k] = expf(fminf(fmaxf(pred[k], -60.f), 60.f));

@@ -335,7 +335,6 @@ __global__ void __launch_bounds__(kThinThreads) k_thin(const ThinParams<T> P) {
     int32_t* lstart = ecnt + rows;                                         // [nlev + 1] slots
     const int lane = (int)lane_id();
     const int warp = threadIdx.x >> 5;
-    const int nwarps = blockDim.x >> 5;
     const int64_t run_e0 = P.tptr[P.pos_begin];
     const int32_t* tidx = P.tidx + run_e0;
     const T* tval = P.tval + run_e0;
