@@ -55,7 +55,9 @@ typedef enum {
     RW_ERR_BREAKDOWN = -6,      /* PCG found p.Ap <= 0 */
     RW_ERR_CUDA = -7,           /* a CUDA runtime call failed */
     RW_ERR_TIMEOUT = -8,        /* a bounded device-side wait gave up */
-    RW_ERR_CAPACITY = -9        /* a row has more than 2^29 possible end points (merge table limit) */
+    RW_ERR_CAPACITY = -9        /* a fixed-size table is too small: a row has more than 2^29 possible
+                                   end points (merge table limit), or n * nrhs exceeds the 2^20-entry
+                                   scratch array of rw_precond_apply_static */
 } rw_status;
 
 typedef enum { RW_FP64 = 0, RW_FP32_MIXED = 1 } rw_precision;
@@ -111,10 +113,6 @@ typedef struct {
                                 ends below k' or at ground; one-step sub-walks excluded; walks of
                                 one start row never overlap).  Y, D and the counters then hold
                                 all these walks (default 0) */
-    int32_t walk_fuse;       /* walk kernel, nodes of more than 7 neighbours: 1 = read each
-                                scanned block's successor words with its thresholds (fewer
-                                dependent loads), 0 = read only the chosen block's (fewer bytes),
-                                -1 = 1 when the walk tables fit in 3/4 of L2 (default -1) */
     int32_t solve_mode_bwd;  /* solve_mode of the backward (Y^T) solve; -1 = as solve_mode (default) */
     int32_t thin_levels;     /* factor build: levels per thin run at most (0 = no cap; default 128);
                                 dependencies on earlier runs are summed by the whole grid */
@@ -127,6 +125,11 @@ typedef struct {
     int32_t thin_flags;      /* thin runs on one block: 1 = each row flags its slot in shared memory
                                 when done and readers wait on the flags of their entries (no barrier
                                 per level); 0 = one block barrier per level (default 0) */
+    int32_t spin_limit;      /* polls of one device-side wait (level computation, solve hand-offs,
+                                grid and cluster barriers, the latency probe) before it gives up and
+                                the call returns RW_ERR_TIMEOUT; 0 = 2^20 (about a second at L2
+                                latency; default 0).  A small value makes waits give up early: for
+                                testing the timeout path, never for results */
 } rw_options;
 
 typedef struct rw_context rw_context;
@@ -331,9 +334,27 @@ rw_status rw_batch_autotune(rw_context* ctx, const rw_batch* B, int32_t nrhs, rw
  * bounded poll gave up), RW_ERR_ALLOC, RW_ERR_CUDA. */
 rw_status rw_probe_latency(rw_context* ctx, int32_t iters, double* h_handoff_ns, double* h_l2_ns);
 
+/* Random-gather throughput of the device memory level that holds a buffer of
+ * buffer_bytes (the L2 for a buffer well inside it, HBM for a larger one):
+ * threads load aligned units of access_bytes (32, 64 or 128) from uniformly
+ * random units of the buffer, four independent loads in flight per thread,
+ * about 2^28 units per launch; *h_gbs receives the accessed bytes per second
+ * (GB/s) of the second of two launches.  This is the ceiling of a kernel
+ * whose reads are random sectors, such as the walk kernel's table reads.
+ * Measurement only; the buffer is allocated through the context and freed
+ * before the call returns.  Synchronous.  Errors: RW_ERR_ARG (buffer outside
+ * [1 MiB, 128 GiB], another access size, null output), RW_ERR_ALLOC,
+ * RW_ERR_CUDA. */
+rw_status rw_probe_gather(rw_context* ctx, uint64_t buffer_bytes, int32_t access_bytes, double* h_gbs);
+
 /* z = (Y^T diag(D) Y)^-1 r for nrhs node-major right-hand sides (FP64): the
  * preconditioner application inside pcg_solve (backward solve with Y^T,
- * scaling by 1/D, forward solve with Y). */
+ * scaling by 1/D, forward solve with Y).
+ * Concurrency: every solve on a factor (this call, rw_precond_apply_static,
+ * pcg_solve, rw_precond_apply_ldu, bicgstab_solve) uses the factor's own solve
+ * workspace (grid-barrier words and thin-run sums), so two of them on the same
+ * factor must not overlap on the GPU (different streams or threads); calls on
+ * different factors may. */
 rw_status rw_precond_apply(rw_context* ctx, const rw_factor* F, const double* d_r, double* d_z,
                            int32_t nrhs);
 
@@ -347,11 +368,13 @@ rw_status rw_precond_apply(rw_context* ctx, const rw_factor* F, const double* d_
  * 2^20 doubles (8 MiB) that every GPU loading the library holds until the
  * process exits.  n * nrhs must not exceed 2^20 (RW_ERR_CAPACITY otherwise).
  * The first call on a device looks up that array's device address (with the
- * device current); make that first call before any stream capture.  All calls
- * share the one array, which keeps the previous call's contents (this call
- * re-initialises what it reads), so calls that overlap on the GPU -- on
- * different streams or from different threads -- race and must not be issued.
- * The current device must be the context's device. */
+ * device current); make that first call before any stream capture.  Every
+ * call synchronises the context stream before it returns (it reads back the
+ * device status).  All calls share the one array, which keeps the previous
+ * call's contents (this call re-initialises what it reads), so calls that
+ * overlap on the GPU -- on different streams or from different threads -- race
+ * and must not be issued; the factor's solve workspace is shared as for
+ * rw_precond_apply.  The current device must be the context's device. */
 rw_status rw_precond_apply_static(rw_context* ctx, const rw_factor* F, const double* d_r,
                                   double* d_z, int32_t nrhs);
 

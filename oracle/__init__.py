@@ -50,7 +50,7 @@ def build(force=False):
         return _LIB
     tmp = _LIB + f".{os.getpid()}.tmp"
     subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-                           "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+                           "-fPIC", "-shared", "-pthread", "-o", tmp, _SRC, "-lm"])
     os.replace(tmp, _LIB)
     return _LIB
 
@@ -77,6 +77,11 @@ def _load():
                                      ctypes.c_uint64, ctypes.c_int32, i32p, ctypes.c_int32,
                                      i32p, u32p, u32p, ctypes.c_int64, P(ctypes.c_void_p)]
     lib.orc_factor_build.restype = ctypes.c_int
+    lib.orc_factor_build_mt.argtypes = [ctypes.c_int32, i32p, i32p, f64p, u32p, ctypes.c_uint64,
+                                        ctypes.c_uint32, ctypes.c_uint32, ctypes.c_double,
+                                        ctypes.c_uint64, i32p, ctypes.c_int32, ctypes.c_int32,
+                                        P(ctypes.c_void_p)]
+    lib.orc_factor_build_mt.restype = ctypes.c_int
     lib.orc_factor_nnz.argtypes = [ctypes.c_void_p]
     lib.orc_factor_nnz.restype = ctypes.c_int64
     lib.orc_factor_get.argtypes = [ctypes.c_void_p, i64p, i32p, f64p, f64p, u64p, u64p, u64p, u64p]
@@ -138,7 +143,7 @@ def walk_rows(A):
 
 
 def build_factor(A, walks, seed, drop_tol, matrix_index=0, tag=0, max_steps=1 << 24,
-                 reuse=False, records=False, rows=None):
+                 reuse=False, records=False, rows=None, threads=1):
     """Factor A ~= Y^T diag(D) Y from walks.
 
     walks: int (uniform budget) or uint32 array [n] of per-row budgets.
@@ -146,7 +151,9 @@ def build_factor(A, walks, seed, drop_tol, matrix_index=0, tag=0, max_steps=1 <<
     M, J, G (walks, visits to the start row, ground ends) and hops, and with
     ``records=True`` the per-walk records (end, returns, length) in walk order.
     ``rows``: optional subset of rows to compute (the rows are independent);
-    the other rows come back empty with D = 0.
+    the other rows come back empty with D = 0.  ``threads`` > 1 runs the rows
+    of the plain build (no reuse, no records) on that many host threads
+    (``orc_factor_build_mt``; the same factor bit for bit).
     """
     lib = _load()
     n = A.n
@@ -168,15 +175,24 @@ def build_factor(A, walks, seed, drop_tol, matrix_index=0, tag=0, max_steps=1 <<
         rec_ret = np.zeros(max(1, cap), dtype=np.uint32)
         rec_len = np.zeros(max(1, cap), dtype=np.uint32)
     h = ctypes.c_void_p()
-    rc = lib.orc_factor_build(
-        n, _ptr(A.rowptr, ctypes.c_int32), _ptr(A.col, ctypes.c_int32),
-        _ptr(A.val, ctypes.c_double), _ptr(budget, ctypes.c_uint32), seed, matrix_index, tag,
-        float(drop_tol), int(max_steps), 1 if reuse else 0,
-        _ptr(sel, ctypes.c_int32) if sel is not None else None,
-        0 if sel is None else int(sel.size),
-        _ptr(rec_end, ctypes.c_int32) if records else None,
-        _ptr(rec_ret, ctypes.c_uint32) if records else None,
-        _ptr(rec_len, ctypes.c_uint32) if records else None, cap, ctypes.byref(h))
+    if threads > 1:
+        if reuse or records:
+            raise ValueError("the multi-threaded build has no reuse and no records")
+        rc = lib.orc_factor_build_mt(
+            n, _ptr(A.rowptr, ctypes.c_int32), _ptr(A.col, ctypes.c_int32),
+            _ptr(A.val, ctypes.c_double), _ptr(budget, ctypes.c_uint32), seed, matrix_index, tag,
+            float(drop_tol), int(max_steps), _ptr(sel, ctypes.c_int32) if sel is not None else None,
+            0 if sel is None else int(sel.size), int(threads), ctypes.byref(h))
+    else:
+        rc = lib.orc_factor_build(
+            n, _ptr(A.rowptr, ctypes.c_int32), _ptr(A.col, ctypes.c_int32),
+            _ptr(A.val, ctypes.c_double), _ptr(budget, ctypes.c_uint32), seed, matrix_index, tag,
+            float(drop_tol), int(max_steps), 1 if reuse else 0,
+            _ptr(sel, ctypes.c_int32) if sel is not None else None,
+            0 if sel is None else int(sel.size),
+            _ptr(rec_end, ctypes.c_int32) if records else None,
+            _ptr(rec_ret, ctypes.c_uint32) if records else None,
+            _ptr(rec_len, ctypes.c_uint32) if records else None, cap, ctypes.byref(h))
     if rc:
         raise OracleError(rc, "oracle factor build")
     try:

@@ -13,6 +13,8 @@
 #include "rw_oracle.h"
 
 #include <math.h>
+#include <pthread.h>
+#include <stdatomic.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -558,6 +560,166 @@ fail:
     free(cnt); free(list); tables_free(&t);
     orc_factor_free(f);
     return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The same build on several host threads.  Rows are independent (Sec. 4: each */
+/* row of Y uses only "rows 0..k-1 are homes"), so chunks of consecutive rows  */
+/* go to threads in any order; every row runs exactly the walks and the        */
+/* emission of the single-thread loop above, and the chunks are concatenated   */
+/* in row order afterwards.  The result therefore does not depend on the       */
+/* thread count.  Mode 0 only, no per-walk records.                            */
+/* ------------------------------------------------------------------------ */
+enum { kMtChunkRows = 256 }; /* largest chunk; fewer rows per chunk for short row lists */
+
+typedef struct {
+    const tables* t;
+    const int32_t *rowptr, *col;
+    const double* val;
+    const uint32_t* budget;
+    uint64_t seed, max_steps;
+    uint32_t mi, tag;
+    double drop_tol;
+    const int32_t* rows;   /* ascending row list (NULL: all rows) */
+    int32_t nlist;         /* rows in the list (n when rows == NULL) */
+    int64_t nchunks, chunk_rows;
+    orc_factor* f;         /* shared per-row arrays D, M, J, G, hops */
+    orc_factor* chunk;     /* [nchunks] per-chunk Y entries */
+    int64_t* rownnz;       /* [n] entries kept per row */
+    atomic_llong next;
+    atomic_int err;
+} mt_job;
+
+static void* mt_worker(void* arg) {
+    mt_job* J = (mt_job*)arg;
+    const int32_t n = J->f->n;
+    uint64_t* cnt = (uint64_t*)calloc((size_t)(n > 0 ? n : 1), sizeof(uint64_t));
+    int32_t* list = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1) * 2);
+    if (!cnt || !list) {
+        atomic_store(&J->err, -4);
+        free(cnt); free(list);
+        return NULL;
+    }
+    for (;;) {
+        if (atomic_load(&J->err)) break;
+        const int64_t c = atomic_fetch_add(&J->next, 1);
+        if (c >= J->nchunks) break;
+        orc_factor* fc = &J->chunk[c];
+        const int64_t s0 = c * J->chunk_rows;
+        const int64_t s1 = s0 + J->chunk_rows < J->nlist ? s0 + J->chunk_rows : J->nlist;
+        for (int64_t s = s0; s < s1; ++s) {
+            const int32_t k = J->rows ? J->rows[s] : (int32_t)s;
+            int32_t nlist = 0;
+            if (J->t->up0[k] >= 0) {
+                for (uint32_t w = 0; w < J->budget[k]; ++w) {
+                    int32_t end = -1;
+                    uint32_t ret = 0;
+                    uint64_t h = 0;
+                    int rc = one_walk(J->t, J->seed, J->mi, J->tag, k, w, J->max_steps, &end, &ret,
+                                      &h, NULL, 0, NULL);
+                    if (rc) { atomic_store(&J->err, rc); goto out; }
+                    fc->M[k] += 1;
+                    fc->J[k] += 1 + (uint64_t)ret;
+                    fc->hops[k] += h;
+                    if (end < 0) fc->G[k] += 1;
+                    else {
+                        if (cnt[end] == 0) list[nlist++] = end;
+                        cnt[end] += 1;
+                    }
+                }
+            }
+            const int64_t before = fc->nnz;
+            int rc = emit_row(fc, J->rowptr, J->col, J->val, J->t, k, cnt, list, nlist, J->drop_tol);
+            if (rc) { atomic_store(&J->err, rc); goto out; }
+            J->rownnz[k] = fc->nnz - before;
+        }
+    }
+out:
+    free(cnt); free(list);
+    return NULL;
+}
+
+int orc_factor_build_mt(int32_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                        const uint32_t* budget, uint64_t seed, uint32_t matrix_index, uint32_t tag,
+                        double drop_tol, uint64_t max_steps, const int32_t* rows, int32_t nrows,
+                        int32_t nthreads, orc_factor** out) {
+    *out = NULL;
+    if (n < 0 || max_steps < 1 || !(drop_tol >= 0.0) || nthreads < 1 || nthreads > 1024) return -1;
+    for (int32_t s = 1; rows && s < nrows; ++s)
+        if (rows[s] <= rows[s - 1]) return -1;
+    for (int32_t s = 0; rows && s < nrows; ++s)
+        if (rows[s] < 0 || rows[s] >= n) return -1;
+    int rc = orc_validate(n, rowptr, col, val);
+    if (rc) return rc;
+    tables t;
+    if ((rc = tables_build(n, rowptr, col, val, &t))) return rc;
+    for (int32_t k = 0; k < n; ++k)
+        if (t.up0[k] >= 0 && budget[k] < 1) { tables_free(&t); return -1; }
+    const size_t nn = (size_t)(n > 0 ? n : 1);
+    orc_factor* f = (orc_factor*)calloc(1, sizeof(orc_factor));
+    mt_job J;
+    memset(&J, 0, sizeof(J));
+    pthread_t* th = NULL;
+    int started = 0;
+    if (!f) { tables_free(&t); return -4; }
+    f->n = n;
+    f->rowptr = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+    f->D = (double*)calloc(nn, sizeof(double));
+    f->M = (uint64_t*)calloc(nn, sizeof(uint64_t));
+    f->J = (uint64_t*)calloc(nn, sizeof(uint64_t));
+    f->G = (uint64_t*)calloc(nn, sizeof(uint64_t));
+    f->hops = (uint64_t*)calloc(nn, sizeof(uint64_t));
+    J.nlist = rows ? nrows : n;
+    /* about 16 chunks per thread, at most kMtChunkRows rows each */
+    J.chunk_rows = (int64_t)J.nlist / ((int64_t)nthreads * 16);
+    if (J.chunk_rows < 1) J.chunk_rows = 1;
+    if (J.chunk_rows > kMtChunkRows) J.chunk_rows = kMtChunkRows;
+    J.nchunks = ((int64_t)J.nlist + J.chunk_rows - 1) / J.chunk_rows;
+    J.chunk = (orc_factor*)calloc((size_t)(J.nchunks > 0 ? J.nchunks : 1), sizeof(orc_factor));
+    J.rownnz = (int64_t*)calloc(nn, sizeof(int64_t));
+    th = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)nthreads);
+    if (!f->rowptr || !f->D || !f->M || !f->J || !f->G || !f->hops || !J.chunk || !J.rownnz || !th) {
+        rc = -4;
+        goto done;
+    }
+    for (int64_t c = 0; c < J.nchunks; ++c) {
+        J.chunk[c].n = n;
+        J.chunk[c].D = f->D; J.chunk[c].M = f->M; J.chunk[c].J = f->J;
+        J.chunk[c].G = f->G; J.chunk[c].hops = f->hops;
+    }
+    J.t = &t; J.rowptr = rowptr; J.col = col; J.val = val; J.budget = budget;
+    J.seed = seed; J.max_steps = max_steps; J.mi = matrix_index; J.tag = tag;
+    J.drop_tol = drop_tol; J.rows = rows; J.f = f;
+    atomic_init(&J.next, 0);
+    atomic_init(&J.err, 0);
+    for (; started < nthreads; ++started)
+        if (pthread_create(&th[started], NULL, mt_worker, &J) != 0) break;
+    if (started == 0) mt_worker(&J);
+    for (int i = 0; i < started; ++i) pthread_join(th[i], NULL);
+    if ((rc = atomic_load(&J.err))) goto done;
+    /* row pointers, then the chunks' entries in row order */
+    for (int32_t k = 0; k < n; ++k) f->rowptr[k + 1] = f->rowptr[k] + J.rownnz[k];
+    f->nnz = f->rowptr[n];
+    f->cap = f->nnz > 0 ? f->nnz : 1;
+    f->col = (int32_t*)malloc(sizeof(int32_t) * (size_t)f->cap);
+    f->val = (double*)malloc(sizeof(double) * (size_t)f->cap);
+    if (!f->col || !f->val) { rc = -4; goto done; }
+    {
+        int64_t o = 0;
+        for (int64_t c = 0; c < J.nchunks; ++c) {
+            if (J.chunk[c].nnz == 0) continue;
+            memcpy(f->col + o, J.chunk[c].col, sizeof(int32_t) * (size_t)J.chunk[c].nnz);
+            memcpy(f->val + o, J.chunk[c].val, sizeof(double) * (size_t)J.chunk[c].nnz);
+            o += J.chunk[c].nnz;
+        }
+    }
+done:
+    for (int64_t c = 0; J.chunk && c < J.nchunks; ++c) { free(J.chunk[c].col); free(J.chunk[c].val); }
+    free(J.chunk); free(J.rownnz); free(th);
+    tables_free(&t);
+    if (rc) { orc_factor_free(f); return rc; }
+    *out = f;
+    return 0;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -1,11 +1,13 @@
 /*
  * rw_oracle.h -- CPU oracle for the random-walk incomplete LDL^T preconditioner.
  *
- * TEST INFRASTRUCTURE, NOT PRODUCT CODE.  This is a plain, slow, single-threaded
- * restatement of the method of Qian & Sapatnekar, "Stochastic Preconditioning for
- * Iterative Linear Equation Solvers", used only by the tests, by the smoke check
- * and by the CPU-baseline leg of the benchmark.  It shares no code with the CUDA
- * library and must never be linked into it.
+ * TEST INFRASTRUCTURE, NOT PRODUCT CODE.  This is a plain, slow restatement of
+ * the method of Qian & Sapatnekar, "Stochastic Preconditioning for Iterative
+ * Linear Equation Solvers", used only by the tests, by the smoke check and by
+ * the CPU-baseline leg of the benchmark.  Everything is single-threaded except
+ * orc_factor_build_mt, which runs the rows of the plain build on several host
+ * threads (for timing on all cores and for full-size parity inputs).  It shares
+ * no code with the CUDA library and must never be linked into it.
  *
  * Index convention: 0-based.  Walks started at row k treat rows 0..k-1 as homes
  * (Sec. 2.2.1) plus the virtual ground reached through the diagonal excess
@@ -60,6 +62,13 @@ int orc_factor_build(int32_t n, const int32_t* rowptr, const int32_t* col, const
                      const int32_t* rows, int32_t nrows,
                      int32_t* rec_end, uint32_t* rec_ret, uint32_t* rec_len, int64_t rec_cap,
                      orc_factor** out);
+/* orc_factor_build (mode 0, no records) on nthreads host threads: rows are
+ * independent (Sec. 4), so chunks of rows run concurrently and are joined in
+ * row order; the factor equals the single-thread build bit for bit. */
+int orc_factor_build_mt(int32_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                        const uint32_t* budget, uint64_t seed, uint32_t matrix_index, uint32_t tag,
+                        double drop_tol, uint64_t max_steps, const int32_t* rows, int32_t nrows,
+                        int32_t nthreads, orc_factor** out);
 int64_t orc_factor_nnz(const orc_factor* f);
 void orc_factor_get(const orc_factor* f, int64_t* rowptr, int32_t* col, double* val, double* D,
                     uint64_t* M, uint64_t* J, uint64_t* G, uint64_t* hops);

@@ -34,6 +34,7 @@ __all__ = [
     "rw_adaptive_budget", "rw_csr_transpose", "rw_precond_apply_ldu", "bicgstab_solve",
     "RW_NUM_FEATURES", "RW_FEATURE_STRIDE", "RW_MLP_PARAMS",
     "Batch", "rw_batch_create", "pcg_solve_batch", "rw_autotune", "rw_batch_autotune", "rw_probe_latency",
+    "rw_probe_gather",
     "rw_factor_save", "rw_factor_load", "rw_sha256", "rw_random_permutation", "rw_permute_csr",
 ]
 
@@ -63,9 +64,9 @@ class rw_options_t(ctypes.Structure):
                 ("timing", _i32), ("solve_blocks_per_sm", _i32), ("graphs", _i32),
                 ("wide_slices", _i32), ("spmv_slices", _i32), ("cluster_width", _i32),
                 ("cluster_size", _i32), ("solve_mode", _i32), ("reuse", _i32),
-                ("walk_fuse", _i32), ("solve_mode_bwd", _i32),
+                ("solve_mode_bwd", _i32),
                 ("thin_levels", _i32), ("thin_cluster", _i32), ("adapt_ahead", _i32),
-                ("thin_flags", _i32)]
+                ("thin_flags", _i32), ("spin_limit", _i32)]
 
 
 class rw_factor_desc_t(ctypes.Structure):
@@ -165,6 +166,7 @@ def load():
         "rw_autotune": [vp, P(rw_csr_t), vp, _i32, ctypes.c_int, ctypes.c_char_p, P(rw_options_t), vp],
         "rw_batch_autotune": [vp, vp, _i32, ctypes.c_int, ctypes.c_char_p, P(rw_options_t), vp],
         "rw_probe_latency": [vp, _i32, P(_f64), P(_f64)],
+        "rw_probe_gather": [vp, _u64, _i32, P(_f64)],
         "rw_factor_save": [vp, ctypes.c_char_p],
         "rw_factor_load": [vp, ctypes.c_char_p, P(vp)],
         "rw_random_permutation": [vp, _i32, _u64, vp],
@@ -717,6 +719,15 @@ def rw_probe_latency(ctx, iters=20000):
     h, l2 = _f64(0.0), _f64(0.0)
     _check(load().rw_probe_latency(ctx.handle, int(iters), ctypes.byref(h), ctypes.byref(l2)), "rw_probe_latency")
     return float(h.value), float(l2.value)
+
+
+def rw_probe_gather(ctx, buffer_bytes, access_bytes=32):
+    """Random-gather throughput (GB/s of accessed bytes) over a device buffer
+    of buffer_bytes, in aligned units of access_bytes (32, 64 or 128)."""
+    g = _f64(0.0)
+    _check(load().rw_probe_gather(ctx.handle, int(buffer_bytes), int(access_bytes), ctypes.byref(g)),
+           "rw_probe_gather")
+    return float(g.value)
 
 
 def rw_batch_autotune(ctx, B, nrhs, prec=RW_FP64, cache_path=None):

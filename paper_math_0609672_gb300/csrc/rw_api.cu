@@ -5,6 +5,9 @@
 #include <cstdio>
 #include <cstring>
 
+#include <mutex>
+#include <set>
+#include <tuple>
 #include <vector>
 
 #include "rw_internal.h"
@@ -30,9 +33,21 @@ rw_status check_cuda(cudaError_t e, const char* what) {
 
 rw_status check_launch(const char* what) { return check_cuda(cudaGetLastError(), what); }
 
+rw_status set_kernel_attr_once(int device, const void* func, cudaFuncAttribute attr, int value) {
+    static std::mutex mu;
+    static std::set<std::tuple<int, const void*, int, int>> done;
+    std::lock_guard<std::mutex> lock(mu);
+    const auto key = std::make_tuple(device, func, (int)attr, value);
+    if (done.count(key)) return RW_OK;
+    rw_status rc = check_cuda(cudaFuncSetAttribute(func, attr, value), "kernel attribute");
+    if (rc == RW_OK) done.insert(key);
+    return rc;
+}
+
 rw_status reset_status(rw_context* ctx) {
     DevStatus init{};
     init.bad_row = UINT_MAX;
+    init.spin_limit = ctx->opt.spin_limit > 0 ? (unsigned)ctx->opt.spin_limit : kSpinLimit;
     *ctx->h_status = init;
     return check_cuda(cudaMemcpyAsync(ctx->d_status, ctx->h_status, sizeof(DevStatus),
                                       cudaMemcpyHostToDevice, ctx->stream),
@@ -143,7 +158,6 @@ void rw_options_default(rw_options* opt) {
     opt->walk_blocks_per_sm = 0;
     opt->timing = 1;
     opt->graphs = 1;
-    opt->walk_fuse = -1;
     opt->solve_mode = 2;
     opt->wide_slices = -1;
     opt->solve_mode_bwd = -1;

@@ -302,7 +302,7 @@ __global__ void k_seg_gather_b(int32_t N, int nrhs, const int32_t* __restrict__ 
         const double* src = bs[m] + (size_t)(i - row0[m]) * nrhs;
         for (int j = 0; j < nrhs; ++j) {
             const double v = src[j];
-            if (!isfinite(v)) atomicAdd(&st->pad[0], 1u);
+            if (!isfinite(v)) atomicAdd(&st->nonfinite, 1u);
             b[(size_t)i * nrhs + j] = v;
             r[(size_t)i * nrhs + j] = (T)v;
             x[(size_t)i * nrhs + j] = 0.0;
@@ -455,7 +455,7 @@ rw_status pcg_batch_t(rw_context* ctx, rw_batch* B, const double* const* d_b, do
     k_copy_vec<T><<<vb, 256, 0, s>>>(z, p, cnt);
     if ((rc = check_launch("batch pcg start"))) return rc;
     if ((rc = read_status(ctx, "batch pcg start"))) return rc;
-    if (ctx->h_status->pad[0]) {
+    if (ctx->h_status->nonfinite) {
         set_error("pcg: right-hand side holds a non-finite value");
         return RW_ERR_ARG;
     }

@@ -17,7 +17,8 @@ struct DevStatus {
     unsigned int timeout;      // bounded waits that gave up
     unsigned int bad_budget;   // walk rows with a zero budget
     unsigned int breakdown;    // PCG p.Ap <= 0
-    unsigned int pad[2];
+    unsigned int nonfinite;    // non-finite right-hand-side entries
+    unsigned int spin_limit;   // polls of one bounded wait before it gives up (set by the host)
 };
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
@@ -111,10 +112,11 @@ __device__ __forceinline__ bool is_pending(double v) {
 }
 __device__ __forceinline__ bool is_pending(float v) { return __float_as_int(v) == 0x7FA0C0DE; }
 
-// Upper bound on polls of one device-side wait before it gives up (about a
-// second at L2 latency).  Once any wait gives up, the others see the timeout
-// flag within kAbortPoll polls and give up too, so a failing solve ends after
-// about one wait limit in total.
+// Default upper bound on polls of one device-side wait before it gives up
+// (about a second at L2 latency; rw_options.spin_limit overrides it, and the
+// host passes the value in DevStatus::spin_limit).  Once any wait gives up, the
+// others see the timeout flag within kAbortPoll polls and give up too, so a
+// failing solve ends after about one wait limit in total.
 constexpr unsigned kSpinLimit = 1u << 20;
 constexpr unsigned kAbortPoll = 1024;
 
@@ -124,10 +126,11 @@ __device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
     return v;
 }
 
-// One poll step of a bounded wait: returns true when the wait must give up.
-__device__ __forceinline__ bool wait_gives_up(unsigned& spins, unsigned* timeout_flag) {
+// One poll step of a bounded wait of at most `limit` polls: returns true when
+// the wait must give up.
+__device__ __forceinline__ bool wait_gives_up(unsigned& spins, unsigned limit, unsigned* timeout_flag) {
     ++spins;
-    if (spins > kSpinLimit) {
+    if (spins > limit) {
         atomicAdd(timeout_flag, 1u);
         return true;
     }
@@ -157,10 +160,11 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned epoch, De
     if (threadIdx.x == 0) {
         give_up = 0;
         const unsigned target = epoch * gridDim.x;
+        const unsigned limit = st->spin_limit;
         atom_add_release(count, 1u);
         unsigned spins = 0;
         while (ld_acquire_u32(count) < target) {
-            if (wait_gives_up(spins, &st->timeout)) {
+            if (wait_gives_up(spins, limit, &st->timeout)) {
                 give_up = 1;
                 break;
             }

@@ -477,15 +477,9 @@ rw_status emit_factor(rw_context* ctx, const rw_csr* A, const Tables& T, const W
     if (ms_merge) cudaEventRecord(ctx->ev[2], s);
     if (nw > 0) {
         const size_t sm_small = (size_t)kMergeWarps * (1 << kLog2SmallHash) * 8;
-        static bool attr_small = false;
-        if (!attr_small) {
-            if ((rc = check_cuda(cudaFuncSetAttribute(k_merge_small,
-                                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                      (int)sm_small),
-                                 "smem attribute")))
-                return rc;
-            attr_small = true;
-        }
+        if ((rc = set_kernel_attr_once(ctx->device, (const void*)k_merge_small,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_small)))
+            return rc;
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_merge_small, 32 * kMergeWarps,
                                                       sm_small);
@@ -501,15 +495,9 @@ rw_status emit_factor(rw_context* ctx, const rw_csr* A, const Tables& T, const W
         const int32_t nbig = h32[0];
         if (nbig > 0) {
             const size_t sm_big = (size_t)(1 << kLog2BigHash) * 8;
-            static bool attr_big = false;
-            if (!attr_big) {
-                if ((rc = check_cuda(cudaFuncSetAttribute(k_merge_big,
-                                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                          (int)sm_big),
-                                     "smem attribute")))
-                    return rc;
-                attr_big = true;
-            }
+            if ((rc = set_kernel_attr_once(ctx->device, (const void*)k_merge_big,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_big)))
+                return rc;
             RW_COUNT_LAUNCH();
             k_merge_big<<<grid_for(nbig, 1, ctx->num_sms), 256, sm_big, s>>>(P, nbig);
             if ((rc = check_launch("merge (block tables)"))) return rc;

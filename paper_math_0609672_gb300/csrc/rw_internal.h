@@ -78,25 +78,28 @@ inline int grid_for(int64_t work, int block, int max_blocks) {
 // ---- build path (rw_tables.cu, rw_walk.cu, rw_emit.cu, rw_levels.cu) -------
 
 // Walk tables of one matrix, in the layout read by the walk kernel.
-//  tab:   per node ceil((1 + deg) / 8) blocks of 16 uint32 words (64 bytes).
-//         Slot j of a node's slot sequence (slot 0 = header, slot s + 1 =
-//         successor s in ascending column order) lives in block j / 8 at
-//         word j % 8 (threshold; the header slot holds deg) and word
-//         8 + j % 8 (the successor word: the index of that successor's first
-//         block, bit 31 set when the successor has more than one block; 0
-//         for the header and padding).  A hop to a node of one block reads
-//         that block: the thresholds and the successor words arrive together.
-//  bnode: [blocks] the node each block belongs to.
-//  fthr:  per walk row a block [updeg, lowdeg, ft_0 .. ft_{updeg-1}, pad].
-// First-block indices increase with the node index, so the walk compares
-// block indices instead of node indices (home: below the start row's block,
-// return: equal to it).  Padding thresholds are 0xFFFFFFFF.
+//  tab:   per node ng = ceil((1 + deg) / 4) group sectors of 8 uint32 words
+//         (32 bytes), preceded by one summary sector when ng > 2.  Slot j of
+//         a node's slot sequence (slot 0 = header, slot s + 1 = successor s in
+//         ascending column order) lives in group j / 4: word j % 4 holds its
+//         threshold (0 for the header slot: always passed) and word 4 + j % 4
+//         its successor word (the index of that successor's first sector, bit
+//         31 set when the successor has a summary sector; deg for the header
+//         slot, 0 for padding).  The summary sector holds deg in word 0 and,
+//         in words 1..7, the threshold of the last slot of groups 0..6
+//         (0xFFFFFFFF past the last).  A hop reads the summary, then the one
+//         group that holds the drawn successor; a node of at most two groups
+//         (deg <= 7) has no summary and its second group is read only when
+//         the draw passes the first.  Random DRAM reads are limited per
+//         sector, so a hop costs two sectors at most (except nodes of more
+//         than 27 neighbours, whose groups past 6 are scanned in turn).
+//  bnode: [sectors] the node each sector belongs to.
 struct Tables {
     int32_t n = 0;
     uint32_t* tab = nullptr;
     int32_t* bnode = nullptr;
     uint32_t* fthr = nullptr;
-    uint32_t* toff = nullptr;     // [n+1] first block of each node (64-byte blocks)
+    uint32_t* toff = nullptr;     // [n+1] first sector of each node (32-byte sectors)
     uint32_t* foff8 = nullptr;    // [n+1] first-step blocks (32-byte blocks)
     int32_t* deg = nullptr;       // [n] off-diagonal count
     int32_t* lowdeg = nullptr;    // [n] entries with column < row
@@ -107,7 +110,7 @@ struct Tables {
     int32_t n_walk_rows = 0;
     int4* wrow = nullptr;         // [n_walk_rows] {k, foff8_k, toff_k, lowdeg_k}
     int32_t* walk_rows = nullptr; // [n_walk_rows] k ascending
-    uint64_t blocks = 0, first_words = 0;
+    uint64_t sectors = 0, first_words = 0;
 };
 
 rw_status build_tables(rw_context* ctx, const rw_csr* A, Tables& T, Pool& pool);
@@ -155,7 +158,7 @@ struct WalkBatch {
     int64_t total = 0;
 };
 
-inline uint64_t table_bytes(const Tables& T) { return T.blocks * 64u; }
+inline uint64_t table_bytes(const Tables& T) { return T.sectors * 32u; }
 
 inline MatWalk mat_walk(const Tables& T, uint64_t seed, uint32_t matrix_index, uint32_t kind) {
     return MatWalk{T.tab, T.bnode, T.fthr, (uint32_t)seed, (uint32_t)(seed >> 32),
@@ -342,6 +345,10 @@ rw_status batch_tune_target(const rw_batch* B, TuneTarget* X);
 // Launch-and-check helper: returns RW_ERR_CUDA with a message on failure.
 rw_status check_cuda(cudaError_t e, const char* what);
 rw_status check_launch(const char* what);
+// Kernel attributes (dynamic shared-memory limit, non-portable cluster sizes)
+// belong to each device's context: set `attr` of `func` to `value` once per
+// device (thread-safe; later calls on the same device return at once).
+rw_status set_kernel_attr_once(int device, const void* func, cudaFuncAttribute attr, int value);
 rw_status read_status(rw_context* ctx, const char* what);  // syncs, maps device flags
 rw_status reset_status(rw_context* ctx);
 

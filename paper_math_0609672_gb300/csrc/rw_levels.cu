@@ -41,6 +41,7 @@ __global__ void __launch_bounds__(256) k_levels(int32_t n, const LevelJob J0, co
     const int64_t* __restrict__ rp = J.rp;
     const int32_t* __restrict__ col = J.col;
     int* lev = J.lev;
+    const unsigned limit = st->spin_limit;
     int my_max = -1;
     for (int64_t pos = gw; pos < n; pos += nw) {
         const int32_t row = J.descending ? n - 1 - (int32_t)pos : (int32_t)pos;
@@ -51,7 +52,7 @@ __global__ void __launch_bounds__(256) k_levels(int32_t n, const LevelJob J0, co
             int v = ld_relaxed(&lev[c]);
             unsigned spins = 0;
             while (v < 0) {
-                if (wait_gives_up(spins, &st->timeout)) {
+                if (wait_gives_up(spins, limit, &st->timeout)) {
                     v = 0;
                     break;
                 }

@@ -464,12 +464,13 @@ __global__ void __launch_bounds__(kThinThreads) k_thin(const ThinParams<T> P) {
     __shared__ int gave_up;
     if (threadIdx.x == 0) gave_up = 0;
     __syncthreads();
+    const unsigned spin_limit = P.st->spin_limit;
     auto wait_slot = [&](int32_t sl) {
         if (!flags) return;
         unsigned spins = 0;
         while (ready[sl] == 0) {
             if (*(volatile int*)&gave_up) break;
-            if (++spins > kSpinLimit) {
+            if (++spins > spin_limit) {
                 *(volatile int*)&gave_up = 1;
                 atomicAdd(&P.st->timeout, 1u);
                 break;
@@ -847,6 +848,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_syncfree(const 
     const bool jok = j < P.nrhs;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const unsigned spin_limit = P.st->spin_limit;
     struct Pre {
         int32_t row;
         int64_t s, e;
@@ -878,7 +880,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_syncfree(const 
     auto wait_value = [&](const T* src, T v) -> T {
         unsigned spins = 0;
         while (is_pending(v)) {
-            if (wait_gives_up(spins, &P.st->timeout)) return T(0);
+            if (wait_gives_up(spins, spin_limit, &P.st->timeout)) return T(0);
             if (spins > 4) __nanosleep(64);
             v = ld_relaxed(src);
         }
@@ -961,6 +963,7 @@ __global__ void __launch_bounds__(512, MINB) k_syncfree_vec(const FreeParams<T> 
     const bool owner = (lane % span) == 0 && jo < P.nrhs;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const unsigned spin_limit = P.st->spin_limit;
     struct Pre {
         int32_t row;
         int64_t s, e;
@@ -991,7 +994,7 @@ __global__ void __launch_bounds__(512, MINB) k_syncfree_vec(const FreeParams<T> 
     auto wait_vec = [&](int32_t c, T (&v)[NR]) {
         unsigned spins = 0;
         while (any_pending<T, NR>(v, P.nrhs)) {
-            if (wait_gives_up(spins, &P.st->timeout)) {
+            if (wait_gives_up(spins, spin_limit, &P.st->timeout)) {
 #pragma unroll
                 for (int j = 0; j < NR; ++j) v[j] = T(0);
                 return;
@@ -1152,11 +1155,9 @@ static rw_status launch_cluster(rw_context* ctx, const SolveSchedule& S, int32_t
     if constexpr (NR * ES > 32) {
         return RW_ERR_ARG;
     } else {
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(k_cluster<T, NR, ES>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-            attr = true;
-        }
+        rw_status arc = set_kernel_attr_once(ctx->device, (const void*)k_cluster<T, NR, ES>,
+                                             cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (arc) return arc;
         WideParams<T> P{lev_begin, lev_end, S.lptr, S.order, rp, col, val, rhs, scale, x, nrhs, bar, ctx->d_status};
         cudaLaunchConfig_t cfg = {};
         cfg.blockDim = dim3(NR >= 8 ? 512u : 1024u);
@@ -1277,15 +1278,13 @@ static rw_status solve_runs_nr(rw_context* ctx, const SolveSchedule& S, const in
         k_fill_pending_sched<T><<<grid_for(cnt, 256, ctx->num_sms * 8), 256, 0, s>>>(x, cnt);
         if ((rc = check_launch("pending fill"))) return rc;
     }
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_thin<T, NR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kThinSmemBudget + 16 * 1024);
-        cudaFuncSetAttribute(k_thin<T, NR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kThinSmemBudget + 16 * 1024);
-        cudaFuncSetAttribute(k_thin<T, NR, true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        attr = true;
-    }
+    if ((rc = set_kernel_attr_once(ctx->device, (const void*)k_thin<T, NR, false>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kThinSmemBudget + 16 * 1024)) ||
+        (rc = set_kernel_attr_once(ctx->device, (const void*)k_thin<T, NR, true>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kThinSmemBudget + 16 * 1024)) ||
+        (rc = set_kernel_attr_once(ctx->device, (const void*)k_thin<T, NR, true>,
+                                   cudaFuncAttributeNonPortableClusterSizeAllowed, 1)))
+        return rc;
     const int es = lane_slices(ctx->opt.wide_slices, NR);
     int64_t free_b = 0, free_e = 0;  // hybrid: positions waiting for one sync-free launch
     auto flush_free = [&]() -> rw_status {

@@ -317,7 +317,7 @@ __global__ void k_convert(const Tin* in, Tout* out, int64_t cnt) {
 __global__ void k_check_finite(const double* v, int64_t cnt, DevStatus* st) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
          i += (int64_t)gridDim.x * blockDim.x)
-        if (!isfinite(v[i])) atomicAdd(&st->pad[0], 1u);
+        if (!isfinite(v[i])) atomicAdd(&st->nonfinite, 1u);
 }
 
 // ---------------------------------------------------------------------------
@@ -506,7 +506,7 @@ static rw_status pcg_t(rw_context* ctx, const rw_csr* A, const FactorView& F, co
     if ((rc = check_cuda(cudaMemcpyAsync(hS, S, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s), "copy")))
         return rc;
     if ((rc = read_status(ctx, "pcg start"))) return rc;
-    if (ctx->d_status && static_cast<rw::DevStatus*>(ctx->h_status)->pad[0]) {
+    if (ctx->d_status && ctx->h_status->nonfinite) {
         set_error("pcg: right-hand side holds a non-finite value");
         return RW_ERR_ARG;
     }

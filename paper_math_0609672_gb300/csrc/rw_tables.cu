@@ -161,31 +161,36 @@ __global__ void k_row_info(int32_t n, int64_t nnz, const int32_t* __restrict__ r
         deg[l] = d;
         lowdeg[l] = lo;
         dpos[l] = dp;
-        blk_full[l] = (uint32_t)(1 + d + 7) / 8u;
+        // groups of four slots, ceil((1 + deg) / 4), plus a summary sector when there are more than two
+        const uint32_t ng = (uint32_t)(1 + d + 3) / 4u;
+        blk_full[l] = ng + (ng > 2u ? 1u : 0u);
         blk_first[l] = up > 0 ? (uint32_t)(2 + up + 7) / 8u : 0u;
         walk_flag[l] = up > 0 ? 1u : 0u;
     }
 }
 
-// Thresholds and successor block indices.  One thread per row; the sums run
+// Thresholds and successor sector indices.  One thread per row; the sums run
 // sequentially over the row in ascending column order, each addition and
 // division rounded once (the same order the sampling rule is defined in).
 __global__ void k_fill_tables(int32_t n, const int32_t* __restrict__ rp,
                               const int32_t* __restrict__ col, const double* __restrict__ val,
                               const int32_t* __restrict__ deg, const int32_t* __restrict__ lowdeg,
                               const int32_t* __restrict__ dpos, const uint32_t* __restrict__ toff,
-                              const uint32_t* __restrict__ foff8, uint32_t* tab, int32_t* bnode,
+                              const uint32_t* __restrict__ foff8, uint32_t* tab, int32_t* snode,
                               uint32_t* fthr, double* S, double* diag) {
     for (int32_t l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x) {
         const int32_t s = rp[l], e = rp[l + 1], dp = dpos[l], d = deg[l], lo = lowdeg[l];
         const double dg = val[dp];
         diag[l] = dg;
-        const uint64_t b0 = toff[l], b1 = toff[l + 1];
-        for (uint64_t b = b0; b < b1; ++b) bnode[b] = l;
-        // slot j: threshold at word 16 * (b0 + j / 8) + j % 8, successor at + 8
-        auto word = [&](uint64_t j) -> uint32_t* { return tab + (b0 + j / 8u) * 16u + (j % 8u); };
-        *word(0) = (uint32_t)d;
-        word(0)[8] = 0u;
+        const uint64_t s0 = toff[l], s1 = toff[l + 1];
+        for (uint64_t q = s0; q < s1; ++q) snode[q] = l;
+        // a node of more than two groups starts with its summary sector
+        const uint64_t ng = ((uint64_t)d + 4u) / 4u;
+        const uint64_t g0 = s0 + (ng > 2u ? 1u : 0u);
+        // slot j: threshold at word 8 * (g0 + j / 4) + j % 4, successor word at + 4
+        auto word = [&](uint64_t j) -> uint32_t* { return tab + (g0 + j / 4u) * 8u + (j % 4u); };
+        *word(0) = 0u;                 // the header slot: always passed
+        word(0)[4] = (uint32_t)d;      // slot 0 has no successor: its word holds deg
         double c = 0.0;
         uint64_t j = 1;
         for (int32_t p = s; p < e; ++p) {
@@ -194,13 +199,20 @@ __global__ void k_fill_tables(int32_t n, const int32_t* __restrict__ rp,
             uint32_t* w = word(j);
             w[0] = cumulative_threshold(c, dg);
             const int32_t jc = col[p];
-            w[8] = toff[jc] | (toff[jc + 1] - toff[jc] > 1u ? 0x80000000u : 0u);  // flag: several blocks
+            const uint32_t ngc = (uint32_t)(deg[jc] + 4) / 4u;
+            w[4] = toff[jc] | (ngc > 2u ? 0x80000000u : 0u);  // flag: the successor has a summary sector
             ++j;
         }
-        for (; j < (b1 - b0) * 8u; ++j) {
+        for (; j < ng * 4u; ++j) {
             uint32_t* w = word(j);
             w[0] = 0xFFFFFFFFu;
-            w[8] = 0u;
+            w[4] = 0u;
+        }
+        if (ng > 2u) {
+            // summary: deg, then the threshold of the last slot of groups 0..6
+            uint32_t* sw = tab + s0 * 8u;
+            sw[0] = (uint32_t)d;
+            for (uint64_t g = 0; g < 7u; ++g) sw[1 + g] = g < ng ? *word(4u * g + 3u) : 0xFFFFFFFFu;
         }
         const int32_t up = d - lo;
         double cu = 0.0;
@@ -268,15 +280,15 @@ rw_status build_tables(rw_context* ctx, const rw_csr* A, Tables& T, Pool& pool) 
                          "copy")))
         return rc;
     if ((rc = read_status(ctx, "matrix validation"))) return rc;
-    T.blocks = hs[0];
-    if (T.blocks >= 0x80000000ull) {
-        set_error("walk tables: %llu blocks exceed the 2^31 block-index range", (unsigned long long)T.blocks);
+    T.sectors = hs[0];
+    if (T.sectors >= 0x80000000ull) {
+        set_error("walk tables: %llu sectors exceed the 2^31 sector-index range", (unsigned long long)T.sectors);
         return RW_ERR_CAPACITY;
     }
     T.first_words = (uint64_t)hs[1] * 8u;
     T.n_walk_rows = (int32_t)hs[2];
-    T.tab = alloc_n<uint32_t>(pool, (int64_t)T.blocks * 16);
-    T.bnode = alloc_n<int32_t>(pool, (int64_t)T.blocks);
+    T.tab = alloc_n<uint32_t>(pool, (int64_t)T.sectors * 8);
+    T.bnode = alloc_n<int32_t>(pool, (int64_t)T.sectors);
     T.fthr = alloc_n<uint32_t>(pool, (int64_t)T.first_words);
     T.wrow = alloc_n<int4>(pool, T.n_walk_rows);
     T.walk_rows = alloc_n<int32_t>(pool, T.n_walk_rows);

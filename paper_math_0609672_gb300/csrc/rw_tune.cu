@@ -294,15 +294,54 @@ __global__ void k_probe_pingpong(unsigned* flags, int partner, int iters, unsign
     const bool first = b == 0;
     unsigned* mine = flags + (first ? 0 : 32);
     const unsigned* theirs = flags + (first ? 32 : 0);
+    const unsigned limit = st->spin_limit;
     const unsigned long long t0 = global_ns();
     for (int i = 1; i <= iters; ++i) {
         if (first) st_relaxed_u32(mine, (unsigned)i);
         unsigned spins = 0;
         while (ld_relaxed_u32(theirs) != (unsigned)i)
-            if (wait_gives_up(spins, &st->timeout)) return;
+            if (wait_gives_up(spins, limit, &st->timeout)) return;
         if (!first) st_relaxed_u32(mine, (unsigned)i);
     }
     if (first) ns[0] = global_ns() - t0;
+}
+
+// Random-gather throughput: every thread runs kGatherStreams independent
+// address streams (a 64-bit LCG each) and per step loads one aligned unit of
+// W * 32 bytes from a random unit of the buffer per stream, folding the words
+// into a checksum so that no load is dead.  The loads of a step are
+// independent, so kGatherStreams of them are in flight per thread.
+constexpr int kGatherStreams = 4;
+
+__device__ __forceinline__ void ld_gather8(const uint32_t* p, uint4& lo, uint4& hi) {
+    asm volatile("ld.global.nc.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(lo.x), "=r"(lo.y), "=r"(lo.z), "=r"(lo.w), "=r"(hi.x), "=r"(hi.y), "=r"(hi.z), "=r"(hi.w)
+                 : "l"(p));
+}
+
+template <int W>
+__global__ void __launch_bounds__(256) k_probe_gather(const uint32_t* __restrict__ buf, uint64_t nunits, int steps,
+                                                      unsigned* sink) {
+    uint64_t st[kGatherStreams];
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+#pragma unroll
+    for (int c = 0; c < kGatherStreams; ++c) st[c] = (tid * kGatherStreams + c) * 0x9E3779B97F4A7C15ull + 1u;
+    uint32_t acc = 0;
+    for (int i = 0; i < steps; ++i) {
+#pragma unroll
+        for (int c = 0; c < kGatherStreams; ++c) {
+            st[c] = st[c] * 6364136223846793005ull + 1442695040888963407ull;
+            const uint64_t unit = ((st[c] >> 32) * nunits) >> 32;  // < nunits
+            const uint32_t* p = buf + unit * (uint64_t)(W * 8);
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                uint4 a, b;
+                ld_gather8(p + 8 * w, a, b);
+                acc ^= a.x ^ a.y ^ a.z ^ a.w ^ b.x ^ b.y ^ b.z ^ b.w;
+            }
+        }
+    }
+    if (acc == 0x9E3779B9u) atomicAdd(sink, 1u);
 }
 
 }  // namespace rw
@@ -310,6 +349,50 @@ __global__ void k_probe_pingpong(unsigned* flags, int partner, int iters, unsign
 using namespace rw;
 
 extern "C" {
+
+rw_status rw_probe_gather(rw_context* ctx, uint64_t buffer_bytes, int32_t access_bytes, double* h_gbs) {
+    if (!ctx || !h_gbs || buffer_bytes < ((uint64_t)1 << 20) || buffer_bytes > ((uint64_t)1 << 37) ||
+        (access_bytes != 32 && access_bytes != 64 && access_bytes != 128)) {
+        set_error("rw_probe_gather: bad arguments (buffer 1 MiB .. 128 GiB, access 32, 64 or 128 bytes)");
+        return RW_ERR_ARG;
+    }
+    cudaStream_t s = ctx->stream;
+    rw_status rc;
+    if ((rc = reset_status(ctx))) return rc;
+    Pool sc(ctx);
+    const uint64_t nunits = buffer_bytes / (uint64_t)access_bytes;
+    uint32_t* buf = static_cast<uint32_t*>(sc.get((size_t)(nunits * (uint64_t)access_bytes)));
+    unsigned* sink = alloc_n<unsigned>(sc, 1);
+    if (!buf || !sink) return RW_ERR_ALLOC;
+    if ((rc = check_cuda(cudaMemsetAsync(buf, 0x5A, (size_t)(nunits * (uint64_t)access_bytes), s), "memset")))
+        return rc;
+    const void* fn = access_bytes == 32 ? (const void*)k_probe_gather<1>
+                     : access_bytes == 64 ? (const void*)k_probe_gather<2> : (const void*)k_probe_gather<4>;
+    int per_sm = 0;
+    if ((rc = check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0), "occupancy")))
+        return rc;
+    if (per_sm < 1) per_sm = 1;
+    const unsigned blocks = (unsigned)(per_sm * ctx->num_sms);
+    const uint64_t threads = (uint64_t)blocks * 256u;
+    // about 2^28 accessed units per launch
+    int steps = (int)(((uint64_t)1 << 28) / (threads * kGatherStreams));
+    if (steps < 16) steps = 16;
+    float ms = 0.f;
+    for (int rep = 0; rep < 2; ++rep) {  // the first launch warms the caches and the TLB
+        cudaEventRecord(ctx->ev[0], s);
+        RW_COUNT_LAUNCH();
+        if (access_bytes == 32) k_probe_gather<1><<<blocks, 256, 0, s>>>(buf, nunits, steps, sink);
+        else if (access_bytes == 64) k_probe_gather<2><<<blocks, 256, 0, s>>>(buf, nunits, steps, sink);
+        else k_probe_gather<4><<<blocks, 256, 0, s>>>(buf, nunits, steps, sink);
+        if ((rc = check_launch("gather probe"))) return rc;
+        cudaEventRecord(ctx->ev[1], s);
+        if ((rc = check_cuda(cudaEventSynchronize(ctx->ev[1]), "gather probe"))) return rc;
+        cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]);
+    }
+    const double bytes = (double)threads * (double)steps * kGatherStreams * (double)access_bytes;
+    *h_gbs = ms > 0.f ? bytes / ((double)ms * 1e-3) / 1e9 : 0.0;
+    return read_status(ctx, "gather probe");
+}
 
 rw_status rw_probe_latency(rw_context* ctx, int32_t iters, double* h_handoff_ns, double* h_l2_ns) {
     if (!ctx || iters < 1 || iters > (1 << 20) || !h_handoff_ns || !h_l2_ns) {

@@ -4,12 +4,16 @@
 // Persistent kernel, one warp lane per walk.  A warp claims kWalkChunk walk
 // indices at a time from a global cursor; a lane whose walk ends takes the next
 // index of the warp's pool, so the warp stays full although walk lengths vary
-// by orders of magnitude.  A hop reads one 64-byte block of the current node
-// (the whole node for degree <= 7): its thresholds and, beside them, the
-// first-block index of every successor, so the next node is known when the
-// block arrives -- one dependent memory access per hop.  The walk works in
-// block indices (they increase with the node index); the end node's index is
-// looked up once, when the walk ends.
+// by orders of magnitude.  The tables hold each node's transitions in 32-byte
+// group sectors of four thresholds and the four successors' sector indices
+// beside them, so the next node is known when the group arrives.  A hop to a
+// node of degree <= 3 reads one sector, to a node of degree <= 7 one or two
+// (the second only when the draw passes the first group), to a node of higher
+// degree two: its summary sector (the last threshold of each group), then
+// the one group that holds the drawn successor.  Random reads from HBM are
+// limited per sector, not per byte, so the kernel is bound by sectors per
+// hop.  The walk works in sector indices (they increase with the node
+// index); the end node's index is looked up once, when the walk ends.
 //
 // Walk w of row k (rows 0..k-1 are homes, ground absorbs):
 //   step 1: draw 0 picks an upper neighbour j > k with probability
@@ -19,7 +23,7 @@
 //   the walk ends at a node < k (home) or at ground; each visit to k counts a
 //   return.  Draw s is word (s mod 4) of Philox(s/4, w, k, tag).
 // Output: one record per walk, {end node (-1 ground, -2 step cap), returns or
-// length}; the kernel writes a home end as its first-block index and
+// length}; the kernel writes a home end as its first-sector index and
 // k_rec_nodes converts it after the launch.
 #include "rw_internal.h"
 
@@ -39,7 +43,6 @@ struct WalkParams {
     DevStatus* st;
     uint64_t max_steps;
     int record_lengths;
-    int fuse_multi;                     // read successor words with every scanned block
     MatWalk m0;                         // the matrix of a single-matrix launch
 };
 
@@ -55,74 +58,78 @@ __device__ __forceinline__ uint4 ld_nc4(const uint32_t* p) {
     return __ldg(reinterpret_cast<const uint4*>(p));
 }
 
-constexpr uint32_t kMultiFlag = 0x80000000u;  // successor word: node of more than one block
-constexpr uint32_t kBlockMask = 0x7FFFFFFFu;
+constexpr uint32_t kSumFlag = 0x80000000u;    // successor word: node with a summary sector
+constexpr uint32_t kSectorMask = 0x7FFFFFFFu;
 
-// 32 bytes (eight words) in one load; p must be 32-byte aligned (blocks are
-// 64-byte aligned, their threshold and successor halves 32-byte aligned).
+// 32 bytes (eight words) in one load; p must be 32-byte aligned (sectors are).
 __device__ __forceinline__ void ld_nc8(const uint32_t* p, uint4& lo, uint4& hi) {
     asm("ld.global.nc.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
         : "=r"(lo.x), "=r"(lo.y), "=r"(lo.z), "=r"(lo.w), "=r"(hi.x), "=r"(hi.y), "=r"(hi.z), "=r"(hi.w)
         : "l"(p));
 }
 
-// Word j (0..7) of the eight words {c, d}.
-__device__ __forceinline__ uint32_t pick8(const uint4 c, const uint4 d, uint32_t j) {
-    const uint32_t lo = (j & 2u) ? ((j & 1u) ? c.w : c.z) : ((j & 1u) ? c.y : c.x);
-    const uint32_t hi = (j & 2u) ? ((j & 1u) ? d.w : d.z) : ((j & 1u) ? d.y : d.x);
-    return (j & 4u) ? hi : lo;
+// Word j (0..3) of the four words c.
+__device__ __forceinline__ uint32_t pick4(const uint4 c, uint32_t j) {
+    return (j & 2u) ? ((j & 1u) ? c.w : c.z) : ((j & 1u) ? c.y : c.x);
 }
 
-// One transition from the node of successor word cw (first-block index, bit
-// 31 set when the node has more than 7 neighbours), with draw u: the least
-// successor m whose threshold exceeds u, ground if none.  Returns that
-// successor's word; *ground is set when the walk is absorbed.
-// `together`: the successor half of each scanned block is read with its
-// threshold half (one round trip per block, 64 bytes); otherwise the
-// threshold halves are scanned and only the chosen successor word is read
-// afterwards (36 bytes for a node of one block, a second round trip).  The
-// first suits a lane whose latency is exposed (few walks left in flight), the
-// second a kernel limited by the bytes the L1 delivers.
-__device__ __forceinline__ uint32_t hop_block(const uint32_t* __restrict__ tab, uint32_t cw, uint32_t u,
-                                              bool together, bool* ground) {
-    const uint32_t* blk = tab + (size_t)(cw & kBlockMask) * 16u;
-    uint4 a, b, c = make_uint4(0u, 0u, 0u, 0u), d = c;
-    ld_nc8(blk, a, b);
-    if (together) ld_nc8(blk + 8, c, d);
-    const uint32_t deg = a.x;
-    uint32_t m = (uint32_t)(a.y <= u) + (uint32_t)(a.z <= u) + (uint32_t)(a.w <= u) + (uint32_t)(b.x <= u) +
-                 (uint32_t)(b.y <= u) + (uint32_t)(b.z <= u) + (uint32_t)(b.w <= u);
-    uint32_t bi = 0;
-    if (m == 7u && deg > 7u) {
-        for (bi = 1;; ++bi) {
-            const uint32_t* nb = blk + 16u * bi;
-            uint4 t0, t1;
-            ld_nc8(nb, t0, t1);
-            if (together) ld_nc8(nb + 8, c, d);
-            const uint32_t cnt = count_le8(t0, t1, u);
-            m += cnt;
-            if (cnt < 8u || m >= deg) break;
+// Thresholds t <= u among the four words of a group.
+__device__ __forceinline__ uint32_t count_le4(const uint4 t, uint32_t u) {
+    return (uint32_t)(t.x <= u) + (uint32_t)(t.y <= u) + (uint32_t)(t.z <= u) + (uint32_t)(t.w <= u);
+}
+
+// One transition from the node of successor word cw (first-sector index, bit
+// 31 set when the node has a summary sector), with draw u: the least slot j
+// whose threshold exceeds u (thresholds do not decrease along the slots, the
+// header slot counts as passed), i.e. successor j - 1, ground if j > deg.
+// Returns that successor's word; *ground is set when the walk is absorbed.
+__device__ __forceinline__ uint32_t hop_sector(const uint32_t* __restrict__ tab, uint32_t cw, uint32_t u,
+                                               bool* ground) {
+    const uint32_t* sec = tab + (size_t)(cw & kSectorMask) * 8u;
+    uint4 t, w;
+    ld_nc8(sec, t, w);
+    uint32_t deg, j = 0xFFFFFFFFu, nw = 0u;
+    if (cw & kSumFlag) {
+        // summary: deg, the last threshold of groups 0..6
+        deg = t.x;
+        const uint32_t ng = (deg + 4u) >> 2;
+        uint32_t g = (uint32_t)(t.y <= u) + (uint32_t)(t.z <= u) + (uint32_t)(t.w <= u) + count_le4(w, u);
+        for (; g < ng; ++g) {  // one iteration unless the node has more than seven groups
+            ld_nc8(sec + 8u * (g + 1u), t, w);
+            if (g == 0u) t.x = 0u;
+            const uint32_t c = count_le4(t, u);
+            if (c < 4u) {
+                j = 4u * g + c;
+                nw = pick4(w, c);
+                break;
+            }
+        }
+    } else {
+        // group 0 (slot 0's successor word holds deg); group 1 only when u passes group 0
+        deg = w.x;
+        const uint32_t c0 = count_le4(t, u);
+        if (c0 < 4u) {
+            j = c0;
+            nw = pick4(w, c0);
+        } else if (deg >= 4u) {
+            ld_nc8(sec + 8u, t, w);
+            const uint32_t c1 = count_le4(t, u);
+            j = 4u + c1;
+            nw = c1 < 4u ? pick4(w, c1) : 0u;
         }
     }
-    *ground = m >= deg;
-    const uint32_t j = (m + 1u) & 7u;
-    if (together) return pick8(c, d, j);
-    return m < deg ? __ldg(blk + 16u * bi + 8u + j) : 0u;
+    *ground = j > deg;
+    return *ground ? 0u : nw;
 }
 
-// Whether a hop from successor word cw reads successor words together with
-// thresholds: always in the tail of the launch (the warp has no walks left to
-// claim); for nodes of several blocks also when the tables fit in L2.
-__device__ __forceinline__ bool read_together(uint32_t cw, bool tail, int fuse_multi) {
-    return tail || (fuse_multi != 0 && (cw & kMultiFlag) != 0u);
-}
-
-// First step of a walk from the row with first block kb, lower degree lo:
-// the successor word of successor lo + m.
+// First step of a walk from the row with first sector kb, lower degree lo and
+// upper degree up: the successor word of successor lo + m (the row's groups
+// start after its summary sector when it has one).
 __device__ __forceinline__ uint32_t first_successor(const uint32_t* __restrict__ tab, uint32_t kb, uint32_t lo,
-                                                    uint32_t m) {
+                                                    uint32_t up, uint32_t m) {
     const uint32_t slot = lo + m + 1u;
-    return __ldg(tab + ((size_t)kb + (slot >> 3)) * 16u + 8u + (slot & 7u));
+    const uint32_t g0 = kb + (((lo + up + 4u) >> 2) > 2u ? 1u : 0u);
+    return __ldg(tab + ((size_t)g0 + (slot >> 2)) * 8u + 4u + (slot & 3u));
 }
 
 template <bool MULTI>
@@ -207,7 +214,7 @@ __global__ void __launch_bounds__(256) k_walk(const WalkParams P) {
                 }
                 if (m > up - 1u) m = up - 1u;
                 kb = (uint32_t)info.z;
-                coff = first_successor(tab, kb, (uint32_t)info.w, m);
+                coff = first_successor(tab, kb, (uint32_t)info.w, up, m);
                 h = 1;
                 ret = 0;
                 active = true;
@@ -236,13 +243,13 @@ __global__ void __launch_bounds__(256) k_walk(const WalkParams P) {
                 const uint32_t u = q == 0u ? rnd.v0 : q == 1u ? rnd.v1 : q == 2u ? rnd.v2 : rnd.v3;
                 ++h;
                 bool ground;
-                const uint32_t nw = hop_block(tab, coff, u, read_together(coff, exhausted, P.fuse_multi), &ground);
-                const uint32_t nb = nw & kBlockMask;
+                const uint32_t nw = hop_sector(tab, coff, u, &ground);
+                const uint32_t nb = nw & kSectorMask;
                 if (ground) {
                     end = -1;
                     done = true;
                 } else if (nb < kb) {
-                    end = (int32_t)nb;  // home, as its first-block index (k_rec_nodes converts it)
+                    end = (int32_t)nb;  // home, as its first-sector index (k_rec_nodes converts it)
                     done = true;
                 } else {
                     ret += (nb == kb) ? 1u : 0u;
@@ -264,15 +271,7 @@ __global__ void __launch_bounds__(256) k_walk(const WalkParams P) {
     }
 }
 
-// Successor words with every scanned block of a node of several blocks when
-// the walk tables fit well inside L2 (rw_options.walk_fuse: 1 always, 0 never,
-// -1 by size).
-static int fuse_multi_blocks(rw_context* ctx, uint64_t table_bytes) {
-    if (ctx->opt.walk_fuse >= 0) return ctx->opt.walk_fuse ? 1 : 0;
-    return table_bytes * 4u <= (uint64_t)ctx->l2_bytes * 3u ? 1 : 0;
-}
-
-// The walk kernels write a home end as its first-block index; this pass turns
+// The walk kernels write a home end as its first-sector index; this pass turns
 // it into the node index (one warp per walk row; ground -1 and the step-cap
 // mark -2 stay).  Keeping the lookup out of the walk saves a dependent load at
 // the end of every walk.
@@ -331,7 +330,6 @@ rw_status run_walks(rw_context* ctx, const WalkBatch& wb, const WalkLaunch& wl, 
     P.st = ctx->d_status;
     P.max_steps = wl.max_steps;
     P.record_lengths = wl.record_lengths;
-    P.fuse_multi = fuse_multi_blocks(ctx, wb.table_bytes);
     P.m0 = wb.m0;
     int per_sm = ctx->opt.walk_blocks_per_sm;
     if (per_sm <= 0) {
@@ -373,11 +371,11 @@ rw_status run_walks(rw_context* ctx, const WalkBatch& wb, const WalkLaunch& wl, 
 // Sub-walks of one start row never overlap (a start is popped before the same
 // node can be pushed again), as the paper requires.  Finished sub-walks go to
 // the warp's shared-memory stage and from there, in bulk, to the global
-// extra-record arrays {start, end or -1, returns}, both as first-block indices
+// extra-record arrays {start, end or -1, returns}, both as first-sector indices
 // (they order like the nodes; the bucketing turns them into node indices).
 struct ReuseParams {
-    int32_t* xnode;  // first-block index of the start node
-    int32_t* xend;   // first-block index of the end node, -1 ground
+    int32_t* xnode;  // first-sector index of the start node
+    int32_t* xend;   // first-sector index of the end node, -1 ground
     uint32_t* xret;
     unsigned long long* xcount;  // records produced (may exceed xcap: then none past xcap is written)
     int64_t xcap;
@@ -476,11 +474,11 @@ __global__ void __launch_bounds__(256) k_walk_reuse(const WalkParams P, const Re
                 }
                 if (m > up - 1u) m = up - 1u;
                 kb = (uint32_t)info.z;
-                coff = first_successor(tab, kb, (uint32_t)info.w, m);
+                coff = first_successor(tab, kb, (uint32_t)info.w, up, m);
                 h = 1;
                 ret = 0;
                 depth = 1;  // the first step's upper neighbour starts the stack
-                top = coff & kBlockMask;
+                top = coff & kSectorMask;
                 top_ret = 0;
                 fresh = true;
                 active = true;
@@ -497,7 +495,7 @@ __global__ void __launch_bounds__(256) k_walk_reuse(const WalkParams P, const Re
         // outcome: 0 idle, 1 moved to node `to`, 2 ended at `to` (home, or -1 ground),
         // 3 stopped (step cap or stack overflow)
         int outcome = 0;
-        int32_t to = 0;        // first-block index of the next node (-1: ground)
+        int32_t to = 0;        // first-sector index of the next node (-1: ground)
         uint32_t to_word = 0;  // its successor word
         if (active) {
             if (h >= P.max_steps ||
@@ -511,8 +509,8 @@ __global__ void __launch_bounds__(256) k_walk_reuse(const WalkParams P, const Re
                 const uint32_t u = q == 0u ? rnd.v0 : q == 1u ? rnd.v1 : q == 2u ? rnd.v2 : rnd.v3;
                 ++h;
                 bool ground;
-                to_word = hop_block(tab, coff, u, read_together(coff, exhausted, P.fuse_multi), &ground);
-                const uint32_t nb = to_word & kBlockMask;
+                to_word = hop_sector(tab, coff, u, &ground);
+                const uint32_t nb = to_word & kSectorMask;
                 if (ground) {
                     outcome = 2;
                     to = -1;
@@ -646,7 +644,6 @@ rw_status run_walks_reuse(rw_context* ctx, const WalkBatch& wb, const WalkLaunch
     P.st = ctx->d_status;
     P.max_steps = wl.max_steps;
     P.record_lengths = 0;
-    P.fuse_multi = fuse_multi_blocks(ctx, wb.table_bytes);
     P.m0 = wb.m0;
     int64_t cap = (int64_t)(ctx->reuse_ratio * (double)wb.total) + (1 << 16);
     int stack = 64;

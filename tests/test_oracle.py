@@ -487,3 +487,26 @@ def test_table1_grids():
     assert np.allclose(d, d.T) and np.all(np.linalg.eigvalsh(d) > 0)
     cfg = W.make_config(6, scale=0.1)
     assert [a.n for a in cfg["A"]] == [e ** 3 for e in cfg["edges"]] and cfg["edges"] == (5, 6, 7, 8, 9, 10)
+
+
+def test_multithreaded_build_equals_single_thread():
+    """Rows are independent (Sec. 4): the oracle's build on several host
+    threads gives the single-thread factor bit for bit, for every thread
+    count, for uniform and per-row budgets and for a subset of rows."""
+    rng = np.random.default_rng(11)
+    cases = [(W.make_config(1)["A"], 200), (W.make_config(2, scale=0.2)["A"], 60),
+             (W.random_rmatrix(70, rng), 40)]
+    for A, walks in cases:
+        budget = rng.integers(1, walks, A.n).astype(np.uint32)
+        for wk in (walks, budget):
+            ref = oracle.build_factor(A, wk, 9, 1e-3)
+            for threads in (2, 3, 8):
+                got = oracle.build_factor(A, wk, 9, 1e-3, threads=threads)
+                for key in ("rowptr", "col", "val", "D", "M", "J", "G", "hops"):
+                    assert np.array_equal(ref[key], got[key]), (A.n, threads, key)
+    A = W.make_config(1)["A"]
+    rows = np.array([0, 5, 31, 500, 1000, 1023])
+    ref = oracle.build_factor(A, 100, 3, 1e-3, rows=rows)
+    got = oracle.build_factor(A, 100, 3, 1e-3, rows=rows, threads=4)
+    for key in ("rowptr", "col", "val", "D", "M", "J", "G", "hops"):
+        assert np.array_equal(ref[key], got[key]), key
