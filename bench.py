@@ -1,16 +1,28 @@
 """Benchmark: random-walk factor construction + PCG on one GB300.
 
-Default workload (2): 3D 7-point grid 64^3 (n = 262,144), conductances
-log-uniform in [0.1, 10], diagonal excess U[0, 1e-3] * row sum, seeded random
-symmetric ordering, 500 walks per row, drop tolerance 1e-3, 4 right-hand sides
-~ N(0,1), PCG to 1e-6 true relative residual in FP64.  Synthetic, seeded
-inputs.  One step = the whole hot path on one batch: build the factor
-(rw_build_factor: tables, walks, merge, emission, transpose, levels) and solve
-the 4 right-hand sides (pcg_solve), then release the factor.  The headline
-value is walk-hops per second of step time (hops of the build / step time);
-factor-build seconds and PCG seconds are reported beside it.
+Default workload (5), the configuration the headline metric is quoted on:
+3D 27-point grid 128^3 (n = 2,097,152, 55.7 M stored entries), conductances
+log-uniform in [0.1, 10], diagonal excess 1e-4 * row sum, seeded random
+symmetric ordering, drop tolerance 1e-3, one right-hand side ~ N(0,1), PCG to
+1e-6 true relative residual.  Synthetic, seeded inputs.  Two forms of the
+same step (build the factor, solve) are timed on the same matrix:
+  learned  the walk budget predicted by the network (12 -> 64 -> 64 -> 1,
+           trained untimed beforehand on pilot-walk labels of 50 seeded 64^3
+           instances of the same distribution, mean 300 walks per row, at
+           least 20), factor build, FP32 PCG (FP64 dots / alpha / beta / x,
+           residual replacement every 50 iterations) on the batched engine;
+  plain    300 walks on every row, FP64 PCG.
+value = seconds of the learned form (build + solve); the plain form's
+seconds, both forms' walk-hops/s, build and PCG seconds, iterations and
+factor sizes are reported beside it.  A third arm sets the walk counts by the
+adaptive rule of Sec. 5.1 (--adapt-delta; 0 skips it).  `e2e` times the
+learned form through the C ABI with host buffers: the copy of A and b from
+pinned host memory to the GPU and the copy of x back are inside each step.
 
 Other workloads (--workload N):
+  2  3D 7-point grid 64^3 (n = 262,144), conductances log-uniform in
+     [0.1, 10], excess U[0, 1e-3] * row sum, 500 walks per row, 4 right-hand
+     sides, FP64 PCG to 1e-6; value = walk-hops per second of step time.
   3  2D 1000^2 grid + 2 long-range edges per row (n = 1e6), 200 walks, factor
      stored FP32, PCG FP32 (FP64 dots / alpha / beta / x, residual replacement
      every 50 iterations) to 1e-6; the FP32 solution's error against the FP64
@@ -19,15 +31,6 @@ Other workloads (--workload N):
      16 right-hand sides each, 200 walks: one walk launch for all matrices
      (rw_build_factor_batched), one block-diagonal PCG with the iteration
      replayed from a CUDA graph (rw_batch_create + pcg_solve_batch).
-  5  3D 27-point grid 128^3 (n = 2,097,152), excess 1e-4 * row sum: learned
-     budget (network trained on pilot-walk labels of seeded 64^3 instances of
-     the same distribution, mean 300, min 20; default label: the relative
-     variance of the visits to the start row per unit walk cost) + FP32 PCG
-     on the batched engine, against the plain form (uniform 300 walks, FP64
-     PCG); value = seconds to 1e-6 (build + solve) of the learned form.  A
-     third arm sets the walk counts by the adaptive rule of Sec. 5.1
-     (margin --adapt-delta, confidence 99 %, at least 20 walks) and solves on
-     the same engine as the learned form.
   6  the paper's Table 1 grids: 7-point Dirichlet Laplacians 50^3 .. 100^3,
      random order, b = 1, walk reuse (Sec. 5.3), no dropping (as the paper's
      implementation), the walks per row of each grid set so that the factor
@@ -45,8 +48,13 @@ region.  Under torchrun each rank runs its own replica (the factor build and
 the solves of independent matrices do not exchange data); value = all ranks'
 work / max-over-ranks time.
 
---impl reference times the CPU oracle on a bounded row sample of the same
-workload (the oracle is the baseline: a plain single-threaded C program).
+--impl reference times the CPU oracle on a bounded sample of the same
+workload (the oracle is the baseline: a plain C program; its factor build
+runs on all host cores).  For workload 5 it reports the estimated seconds of
+the plain form (uniform 300 walks, FP64 PCG) on the full matrix: build time
+from a row sample stratified by row index, PCG time from the oracle's
+per-iteration cost on the full matrix and its iteration count on a 32^3
+instance of the same distribution.
 """
 from __future__ import annotations
 
@@ -182,14 +190,143 @@ def _oracle_sample_for(workload, cfg, target_s, rng_seed):
     if workload == 6:
         return cpu_oracle_sample(cfg["A"][0], cfg["walks"], cfg["walk_seed"], 1e-3,
                                  "the 50^3 Dirichlet grid (m1)", target_s, rng_seed)
-    walks = 300 if workload == 5 else cfg["walks"]
-    return cpu_oracle_sample(cfg["A"], walks, cfg["walk_seed"], cfg["drop_tol"],
+    return cpu_oracle_sample(cfg["A"], cfg["walks"], cfg["walk_seed"], cfg["drop_tol"],
                              f"the {W.CONFIGS[workload]['name']} workload", target_s, rng_seed)
+
+
+class OracleEstimate:
+    """Seconds the CPU oracle needs for the plain form of workload 5 (uniform
+    walks, FP64 PCG to tol) on the full matrix, estimated from bounded samples.
+
+    Build: rows are independent (Sec. 4), and a row's cost falls steeply with
+    its index (rows early in the order have few homes, so their walks are
+    long), so rows are sampled uniformly within strata of the row index
+    [0, 64), [64, 256), ... (factor 4), the sample is built by the oracle on
+    all host cores, and each stratum's hops and factor entries are scaled by
+    its size over its sample size.  Estimated build seconds = the oracle's
+    fixed cost (validation and tables, timed with no rows) + the sample's
+    remaining time x estimated hops / sample hops.
+    PCG: seconds per iteration = the oracle's time for two extra iterations on
+    the full matrix with a one-walk-per-row factor, per multiplication of the
+    paper's count M1 = 2C + E + 4N (Sec. 6), times the estimated M1 of the
+    full factor; iterations = the oracle's count to tol on a 32^3 instance of
+    the same distribution (full factor, same walks)."""
+
+    def __init__(self, A, b, walks, seed, drop, tol, small, threads=None):
+        import oracle
+        self.oracle = oracle
+        self.A, self.b, self.walks, self.seed, self.drop, self.tol = A, b, walks, seed, drop, tol
+        self.threads = threads or os.cpu_count() or 1
+        self.m = 16
+        n = A.n
+        edges = [0]
+        e = 64
+        while e < n:
+            edges.append(e)
+            e *= 4
+        edges.append(n)
+        self.strata = [(a, b_) for a, b_ in zip(edges[:-1], edges[1:]) if b_ > a]
+        t0 = time.perf_counter()
+        oracle.build_factor(A, walks, seed, drop, rows=np.zeros(0, np.int32), threads=self.threads)
+        self.t_fixed = time.perf_counter() - t0
+        # PCG: per-iteration cost on the full matrix, iterations on the small instance
+        F1 = oracle.build_factor(A, 1, seed, drop, threads=self.threads)
+        t0 = time.perf_counter()
+        oracle.pcg(A, F1, b, 0.0, 1)
+        t1 = time.perf_counter()
+        oracle.pcg(A, F1, b, 0.0, 3)
+        t2 = time.perf_counter()
+        m1_one = 2 * (F1["nnz"] + n) + A.nnz + 4 * n
+        self.sec_per_mult = max(0.0, (t2 - t1) - (t1 - t0)) / 2.0 / m1_one
+        As, bs = small
+        Fs = oracle.build_factor(As, walks, seed, drop, threads=self.threads)
+        _, self.iters_small, _, _ = oracle.pcg(As, Fs, bs, tol, 3000)
+
+    def step(self, rng, target_s):
+        """One sample; returns (estimated seconds, details)."""
+        oracle = self.oracle
+        A = self.A
+        picks = []
+        sizes = []
+        for a, b_ in self.strata:
+            k = min(b_ - a, self.m)
+            picks.append(np.sort(rng.choice(np.arange(a, b_), size=k, replace=False)))
+            sizes.append((b_ - a, k))
+        rows = np.concatenate(picks).astype(np.int32)
+        t0 = time.perf_counter()
+        F = oracle.build_factor(A, self.walks, self.seed, self.drop, rows=rows, threads=self.threads)
+        t_s = time.perf_counter() - t0
+        rownnz = np.diff(F["rowptr"])
+        H_est = C_est = 0.0
+        H_s = 0
+        for (N, k), pk in zip(sizes, picks):
+            h = int(F["hops"][pk].sum())
+            H_s += h
+            H_est += N / k * h
+            C_est += N / k * float(rownnz[pk].sum())
+        t_walk = max(t_s - self.t_fixed, 1e-9)
+        build_s = self.t_fixed + t_walk * (H_est / max(H_s, 1))
+        m1 = 2 * (C_est + A.n) + A.nnz + 4 * A.n
+        pcg_s = self.iters_small * self.sec_per_mult * m1
+        # the next sample sized for about target_s of walk time
+        self.m = int(min(4096, max(4, round(self.m * target_s / t_walk))))
+        return build_s + pcg_s, dict(build_s=build_s, pcg_s=pcg_s, rows=int(rows.size), hops=H_s,
+                                     hops_est=H_est, factor_entries_est=C_est, sample_s=t_s)
+
+    def describe(self, d):
+        return (f"{d['rows']} rows stratified by row index ({len(self.strata)} strata, factor 4), "
+                f"{self.walks} walks each ({d['hops']} hops) built by the oracle on {self.threads} host "
+                f"threads in {d['sample_s']:.1f} s; scaled to {d['hops_est']:.3e} hops (build "
+                f"{d['build_s']:.0f} s) and {d['factor_entries_est']:.3e} factor entries; PCG "
+                f"{self.iters_small} iterations (oracle, 32^3 instance) x "
+                f"{self.sec_per_mult * 1e9:.3f} ns per multiplication of M1 on the full matrix "
+                f"({d['pcg_s']:.1f} s)")
+
+
+def _small_instance():
+    cfg = W.make_config(5, scale=0.25)
+    return cfg["A"], cfg["b"][:, 0]
+
+
+def oracle_baseline_c5(cfg, target_s=10.0, seed=2024):
+    """The oracle's estimated seconds for workload 5's plain form (one bounded
+    sample after calibration), as the bench line's cpu_baseline."""
+    est = OracleEstimate(cfg["A"], cfg["b"][:, 0], cfg["walks"], cfg["walk_seed"], cfg["drop_tol"],
+                         cfg["tol"], _small_instance())
+    rng = np.random.default_rng(seed)
+    est.step(rng, target_s)            # sizes the sample
+    v, d = est.step(rng, target_s)
+    return {"value": v, "unit": "s to 1e-6 (build + solve)", "cores": est.threads, "kind": "oracle",
+            "form": "plain: uniform 300 walks + FP64 PCG", "sample": est.describe(d)}
 
 
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
+        return
+    if args.workload == 5:
+        cfg = W.make_config(5, scale=args.scale)
+        est = OracleEstimate(cfg["A"], cfg["b"][:, 0], cfg["walks"], cfg["walk_seed"], cfg["drop_tol"],
+                             cfg["tol"], _small_instance())
+        target = max(2.0, 60.0 / max(1, args.warmup + args.steps))
+        rng = np.random.default_rng(100)
+        vals = []
+        for i in range(args.warmup + args.steps):
+            v, d = est.step(rng, target)
+            if i >= args.warmup:
+                vals.append((v, d))
+        v = statistics.mean(x for x, _ in vals)
+        unit = "s to 1e-6 (build + solve)"
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": unit,
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * statistics.mean(d["sample_s"] for _, d in vals),
+                "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": {"workload": W.CONFIGS[5]["name"], "form": "plain: uniform 300 walks + FP64 PCG"},
+                "cpu_baseline": {"value": v, "unit": unit, "cores": est.threads, "kind": "oracle",
+                                 "sample": est.describe(vals[-1][1])},
+                "e2e": {"value": v, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
         return
     cfg = W.make_config(args.workload)
     vals = []
@@ -249,15 +386,43 @@ class Timer:
         return ms, infos, clk
 
 
-def _walk_roofline(peaks, hops, walks_total, walk_ms, bytes_per_hop=64.0):
-    # algorithmic bytes of the walk kernel: per hop the threshold sectors of
-    # the current node and one sector for the chosen successor; per walk one
-    # 8-byte record
-    alg_bytes = bytes_per_hop * hops + 8.0 * walks_total
-    achieved = alg_bytes / (walk_ms * 1e-3) / 1e9 if walk_ms > 0 else 0.0
-    return {"kernel": "k_walk", "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
-            "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-            "ms_per_launch": walk_ms}
+def _tables_bytes(A):
+    """Bytes of the walk tables of A (group sectors plus summary sectors)."""
+    deg = np.diff(A.rowptr).astype(np.int64) - 1
+    ng = (deg + 4) // 4
+    return int(((ng + (ng > 2)) * 32).sum())
+
+
+def _walk_roofline(P, ctx, peaks, peak_kind, As, hops, walk_ms, l2_bytes, tag):
+    """Roofline of the walk kernel: algorithmic bytes per hop (stationary-
+    weighted over the matrices) x hops / kernel time, against the measured
+    HBM copy peak, or against the L2 random-sector gather peak (measured live)
+    when the tables fit in three quarters of the L2.  Traffic comes from the
+    profile of this workload while the walk sources are unchanged."""
+    As = As if isinstance(As, list) else [As]
+    num = den = 0.0
+    for A in As:
+        deg = np.diff(A.rowptr).astype(np.int64) - 1
+        rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+        diag = A.val[A.col == rows]
+        num += float((diag * 32.0 * (2 + np.ceil(4.0 * (deg + 1) / 32.0))).sum())
+        den += float(diag.sum())
+    bph = num / den
+    tb = sum(_tables_bytes(A) for A in As)
+    achieved = bph * hops / (walk_ms * 1e-3) / 1e9 if walk_ms > 0 else 0.0
+    gather_l2 = P.rw_probe_gather(ctx, 32 << 20, 32)
+    gather_tab = P.rw_probe_gather(ctx, max(tb, 1 << 20), 32)
+    tph, tsrc = _walk_traffic_per_hop(tag)
+    if tb * 4 <= l2_bytes * 3:
+        bound, peak, pk = "l2", gather_l2, "measured live: random 32-byte gathers over an L2-resident buffer"
+    else:
+        bound, peak, pk = "hbm", peaks["hbm_gbs"], peak_kind
+    return {"kernel": "k_walk", "bound": bound, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak if peak else None, "traffic": tph * hops if tph else None,
+            "traffic_source": tsrc, "bytes_per_hop": bph, "hops_per_launch": hops, "ms_per_launch": walk_ms,
+            "peak_kind": pk, "tables_bytes": tb,
+            "gather": {"tables_random_sector_gbs": gather_tab, "l2_random_sector_gbs": gather_l2,
+                       "dram_gbs": (tph * hops / (walk_ms * 1e-3) / 1e9) if tph else None}}
 
 
 def _solve_kernels(opt):
@@ -368,16 +533,13 @@ def run_gpu_single(args, P, torch, dev, stream, ws, rank, local):
                                  "rel_residual_fp32": rel32.tolist(), "rel_residual_fp64": rel64.tolist(),
                                  "pcg_s_fp32": st32.solve_ms * 1e-3, "pcg_s_fp64": st64.solve_ms * 1e-3}
         F.destroy()
+    peaks, peak_kind = _peaks()
+    walk_roof = _walk_roofline(P, ctx, peaks, peak_kind, A, hops, walk_ms,
+                               torch.cuda.get_device_properties(dev).L2_cache_size,
+                               {2: "grid3d7pt_64cube", 3: "grid2d_1000sq_longrange"}[args.workload])
     ctx.close()
     if rank != 0:
         return
-    peaks, peak_kind = _peaks()
-    walk_roof = _walk_roofline(peaks, hops, infos[-1]["walks"], walk_ms)
-    if args.workload == 2:
-        # DRAM bytes read + written by one k_walk launch of this workload in an
-        # ncu capture (55.6 MB read, 840.3 MB written: the records; the tables
-        # stay in L2); to be retaken whenever the walk kernel changes
-        walk_roof["traffic"] = 895.9e6
     napply = statistics.mean(max(i["iters"]) for i in infos)
     tri_ms = statistics.mean(i["bwd_ms"] + i["fwd_ms"] for i in infos)
     solve_roof = _solve_roofline(peaks, napply, infos[-1]["nnz"], A.n, nrhs, tri_ms,
@@ -406,8 +568,8 @@ def run_gpu_single(args, P, torch, dev, stream, ws, rank, local):
         "phase_ms": {k: round(v, 3) for k, v in zip(
             ["tables", "walk", "merge", "emit", "transpose", "levels", "fp32", "build_total"],
             infos[-1]["phase"])},
-        "roofline": dict(dominant, peak_kind=peak_kind),
-        "roofline_walk": dict(walk_roof, peak_kind=peak_kind),
+        "roofline": dominant if dominant is walk_roof else dict(dominant, peak_kind=peak_kind),
+        "roofline_walk": walk_roof,
         "solve_phase_ms": {"spmv": infos[-1]["spmv_ms"], "bwd": infos[-1]["bwd_ms"],
                            "fwd": infos[-1]["fwd_ms"]},
         "clocks": clk,
@@ -470,11 +632,12 @@ def run_gpu_batched(args, P, torch, dev, stream, ws, rank, local):
     hops = statistics.mean(i["hops"] for i in infos)
     all_hops, ms = aggregate(hops, ms, ws)
     last = infos[-1]
+    peaks, peak_kind = _peaks()
+    walk_roof = _walk_roofline(P, ctx, peaks, peak_kind, As, hops, last["walk_ms"],
+                               torch.cuda.get_device_properties(dev).L2_cache_size, "rgg256")
     ctx.close()
     if rank != 0:
         return
-    peaks, peak_kind = _peaks()
-    walk_roof = _walk_roofline(peaks, hops, last["walks"], last["walk_ms"], 96.0)
     line = _base_line(args, ws, ms, "f64",
                       {"workload": W.CONFIGS[4]["name"], "nmat": nmat, "n_total": sum(A.n for A in As),
                        "nnz_total": sum(A.nnz for A in As), "walks_per_row": walks, "drop_tol": drop,
@@ -489,7 +652,7 @@ def run_gpu_batched(args, P, torch, dev, stream, ws, rank, local):
         "walk_kernel_hops_per_s": hops / (last["walk_ms"] * 1e-3) if last["walk_ms"] > 0 else None,
         "pcg_iterations": {"max": int(its.max()), "median": float(np.median(its)), "min": int(its.min())},
         "pcg_rel_residual_max": last["rel"], "factor_nnz_total": last["nnz"], "batch": last["info"],
-        "roofline": dict(walk_roof, peak_kind=peak_kind),
+        "roofline": walk_roof,
         "clocks": clk,
         "gpu_launches": last["launches"],
         "autotuned": {"options": tuned, "precond_ms": tuned_ms[0], "spmv_ms": tuned_ms[1]},
@@ -501,8 +664,8 @@ def run_gpu_batched(args, P, torch, dev, stream, ws, rank, local):
 
 def train_budget_model(P, torch, ctx, dev, ninst, edge, epochs, pilot_walks=64, quantity=0):
     """Features and pilot-walk labels (quantity 0: walk lengths, 1: visits to
-    the start row) of `ninst` training instances (seeds 100 + j), then Adam
-    training; returns the model and a summary."""
+    the start row, 2: visits per unit walk cost) of `ninst` training instances
+    (seeds 100 + j), then Adam training; returns the model and a summary."""
     feats, labels, masks = [], [], []
     t0 = time.time()
     for j in range(ninst):
@@ -525,10 +688,60 @@ def train_budget_model(P, torch, ctx, dev, ninst, edge, epochs, pilot_walks=64, 
     torch.cuda.synchronize()
     t_train = time.time() - t0
     yv = Y[Mk > 0]
-    return M, {"instances": ninst, "edge": edge, "rows": int(yv.numel()), "epochs": epochs,
-               "pilot_walks": pilot_walks, "label": ["walk length", "visits to the start row", "visits per unit walk cost"][quantity], "data_s": t_data, "train_s": t_train,
+    return M, {"instances": ninst, "edge": edge, "seeds": f"{100}..{100 + ninst - 1}", "rows": int(yv.numel()),
+               "epochs": epochs, "batch": 4096, "lr": 2e-3, "train_seed": 1, "init_seed": 0,
+               "pilot_walks": pilot_walks, "pilot_seeds": f"{1000}..{1000 + ninst - 1}",
+               "label": ["walk length", "visits to the start row", "visits per unit walk cost"][quantity],
+               "data_s": t_data, "train_s": t_train,
                "loss_first": float(losses[0]), "loss_last": float(losses[-1]),
                "label_var": float(yv.var()), "r2": 1.0 - float(losses[-1]) / float(yv.var())}
+
+
+def walk_bytes_per_hop(A):
+    """Algorithmic bytes of one hop (SURVEY-style count, per node l): a row
+    header sector, the threshold sectors the sampling rule must see
+    (ceil(4 (deg_l + 1) / 32)) and one successor sector, 32 bytes each --
+    96 B for 5- and 7-point nodes, 192 B for interior 27-point nodes, 128 B at
+    degree 8.  Averaged with the stationary weights of the walk (proportional
+    to A_ll for a chain with transition probabilities -A_lj / A_ll on an
+    undirected graph)."""
+    deg = np.diff(A.rowptr).astype(np.int64) - 1
+    rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+    diag = A.val[A.col == rows]
+    b = 32.0 * (2 + np.ceil(4.0 * (deg + 1) / 32.0))
+    return float((diag * b).sum() / diag.sum())
+
+
+def _source_digest(files):
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+# Walk-kernel DRAM traffic per hop from an ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum of one launch divided by its hops), and the digest of
+# the sources the kernel was built from when it was taken; the line reports
+# traffic only while the sources are unchanged.
+WALK_SOURCES = ["paper_math_0609672_gb300/csrc/rw_walk.cu", "paper_math_0609672_gb300/csrc/rw_tables.cu",
+                "paper_math_0609672_gb300/csrc/rw_common.cuh"]
+
+
+def _walk_traffic_per_hop(tag):
+    """(DRAM bytes per hop, profile file) from profiles/k_walk_<tag>.md when
+    its source digest matches the current walk sources, else (None, None)."""
+    import re
+    path = os.path.join(ROOT, "profiles", f"k_walk_{tag}.md")
+    if not os.path.exists(path):
+        return None, None
+    txt = open(path).read()
+    m = re.search(r"source digest:\s*([0-9a-f]{16})", txt)
+    t = re.search(r"DRAM bytes per hop:\s*([0-9.]+)", txt)
+    if m and t and m.group(1) == _source_digest(WALK_SOURCES):
+        return float(t.group(1)), os.path.relpath(path, ROOT)
+    return None, None
 
 
 def run_gpu_learned(args, P, torch, dev, stream, ws, rank, local):
@@ -569,6 +782,7 @@ def run_gpu_learned(args, P, torch, dev, stream, ws, rank, local):
         info = dict(hops=int(d.total_hops), walks=int(d.total_walks), nnz=int(d.nnz),
                     build_ms=ev[0].elapsed_time(ev[1]), pcg_ms=ev[1].elapsed_time(ev[2]),
                     iters=int(its.max()), rel=float(rel.max()), rc=rc, walk_ms=d.phase_ms[1],
+                    phase=list(d.phase_ms), levels=[d.fwd_levels, d.bwd_levels],
                     launches=int(d.kernel_launches) + int(st[0].kernel_launches))
         B.destroy()
         F.destroy()
@@ -627,40 +841,85 @@ def run_gpu_learned(args, P, torch, dev, stream, ws, rank, local):
                  "rel_residual": Ad["rel"], "factor_nnz": Ad["nnz"], "walks": Ad["walks"], "hops": Ad["hops"],
                  "rounds": Ad["rounds"],
                  "form": "Sec. 5.1 counts (walks run twice: rounds, then build) + FP32 PCG (batched engine)"}
+
+    # end to end through the C ABI with host buffers: the learned form with the
+    # H2D copy of A and b from pinned memory and the D2H copy of x in every step
+    hA = [torch.as_tensor(a).pin_memory() for a in (A.rowptr, A.col, A.val)]
+    hb = torch.as_tensor(b).pin_memory()
+    hx = torch.empty_like(hb).pin_memory()
+    dA2 = [torch.empty_like(t, device=dev) for t in hA]
+    db2 = torch.empty_like(hb, device=dev)
+    dx2 = torch.empty_like(hb, device=dev)
+    A2 = P.CSR(*dA2)
+    h2d = sum(t.numel() * t.element_size() for t in hA) + hb.numel() * hb.element_size()
+    d2h = hx.numel() * hx.element_size()
+    e2e_ms = []
+    for i in range(args.warmup + args.steps):
+        timer.flush.fill_(float(i))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for d_, h_ in zip(dA2, hA):
+            d_.copy_(h_, non_blocking=True)
+        db2.copy_(hb, non_blocking=True)
+        P.rw_budget_predict(ctx, A2, M, 300.0, 20, budget)
+        F = P.rw_build_factor_budget(ctx, A2, budget, seed, drop)
+        B = P.Batch(ctx, [A2], [F])
+        P.pcg_solve_batch(ctx, B, [db2], [dx2], tol, 3000, P.RW_FP32_MIXED)
+        hx.copy_(dx2, non_blocking=True)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        B.destroy()
+        F.destroy()
+    e2e = statistics.mean(e2e_ms)
+    _, e2e = aggregate(0, e2e, ws)
+    peaks, peak_kind = _peaks()
+    L, Pn = inf_l[-1], inf_p[-1]
+    walk_ms = statistics.mean(i["walk_ms"] for i in inf_l)
+    walk_roof = _walk_roofline(P, ctx, peaks, peak_kind, A, L["hops"], walk_ms,
+                               torch.cuda.get_device_properties(dev).L2_cache_size, "grid3d27pt_128cube")
     M.destroy()
     ctx.close()
     ctxp.close()
     if rank != 0:
         return
-    peaks, peak_kind = _peaks()
-    L, Pn = inf_l[-1], inf_p[-1]
-    walk_roof = _walk_roofline(peaks, L["hops"], L["walks"], L["walk_ms"], 192.0)
     name = W.CONFIGS[5]["name"] + ("" if args.scale == 1.0 else f" (edge scale {args.scale})")
     line = _base_line(args, ws, ms_l, "f32-mixed",
                       {"workload": name, "n": A.n, "nnz": A.nnz, "mean_budget": 300, "min_budget": 20,
                        "drop_tol": drop, "nrhs": 1, "pcg_tol": tol,
                        "learned": "predict + build + FP32 PCG (batched engine, graphs)",
-                       "plain": "uniform 300 + FP64 PCG", "l2": "flushed between steps (512 MB write)",
+                       "plain": "uniform 300 + FP64 PCG", "training": "untimed, before the timed steps",
+                       "l2": "flushed between steps (512 MB write)",
                        "parallelism": f"replicas x{ws}"})
+
+    def arm(infos, last):
+        b_s = statistics.mean(i["build_ms"] for i in infos) * 1e-3
+        w_ms = statistics.mean(i["walk_ms"] for i in infos)
+        return {"build_s": b_s, "pcg_s": statistics.mean(i["pcg_ms"] for i in infos) * 1e-3,
+                "walk_kernel_ms": w_ms, "walk_hops_per_s": last["hops"] / (w_ms * 1e-3),
+                "build_hops_per_s": last["hops"] / b_s, "iterations": last["iters"],
+                "rel_residual": last["rel"], "factor_nnz": last["nnz"], "walks": last["walks"],
+                "hops": last["hops"]}
+
     line.update({
         "value": ms_l * 1e-3, "unit": "s to 1e-6 (build + solve)", "higher_is_better": False,
         "plain_s": ms_p * 1e-3, "speedup_vs_plain": ms_p / ms_l,
-        "learned": {"build_s": statistics.mean(i["build_ms"] for i in inf_l) * 1e-3,
-                    "pcg_s": statistics.mean(i["pcg_ms"] for i in inf_l) * 1e-3, "iterations": L["iters"],
-                    "rel_residual": L["rel"], "factor_nnz": L["nnz"], "walks": L["walks"], "hops": L["hops"]},
-        "plain": {"build_s": statistics.mean(i["build_ms"] for i in inf_p) * 1e-3,
-                  "pcg_s": statistics.mean(i["pcg_ms"] for i in inf_p) * 1e-3, "iterations": Pn["iters"],
-                  "rel_residual": Pn["rel"], "factor_nnz": Pn["nnz"], "walks": Pn["walks"], "hops": Pn["hops"]},
+        "learned": dict(arm(inf_l, L), phase_ms={k: round(v, 3) for k, v in zip(
+            ["tables", "walk", "merge", "emit", "transpose", "levels", "fp32", "build_total"], L["phase"])},
+            levels=L["levels"]),
+        "plain": arm(inf_p, Pn),
         "adaptive": adapt,
         "training": train,
         "autotuned": {"learned": tuned_l, "plain": tuned_p},
-        "walk_kernel_hops_per_s": L["hops"] / (L["walk_ms"] * 1e-3) if L["walk_ms"] > 0 else None,
-        "roofline": dict(walk_roof, peak_kind=peak_kind),
+        "roofline": walk_roof,
         "clocks": clk, "clocks_plain": clk_p,
+        "e2e": {"value": e2e * 1e-3, "unit": "s to 1e-6 (build + solve)", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e,
+                "form": "learned, through the C ABI from pinned host buffers"},
         "gpu_launches": L["launches"],
     })
     if not args.no_cpu_baseline and ws == 1:
-        line["cpu_baseline"] = _oracle_sample_for(5, cfg, 12.0, 2024)
+        line["cpu_baseline"] = oracle_baseline_c5(cfg)
     print(json.dumps(line), flush=True)
 
 
@@ -869,10 +1128,10 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", type=int, default=2, choices=[2, 3, 4, 5, 6, 7])
+    ap.add_argument("--workload", type=int, default=5, choices=[2, 3, 4, 5, 6, 7])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nmat", type=int, default=None, help="workload 4: number of matrices (default 256)")
-    ap.add_argument("--scale", type=float, default=1.0, help="workloads 5, 6: grid edge scale (default 1)")
+    ap.add_argument("--scale", type=float, default=1.0, help="workloads 5, 6, 7: grid edge scale (default 1)")
     ap.add_argument("--walks", type=int, default=0,
                     help="workload 6: walks per row (default: the count that gives Table 1's factor size)")
     ap.add_argument("--no-reuse", action="store_true", help="workload 6: no walk reuse")
