@@ -260,10 +260,13 @@ class Context:
 
     stream: a torch.cuda.Stream (default: the current stream).  With
     torch_allocator=True the library allocates its storage through PyTorch's
-    caching allocator; otherwise through cudaMallocAsync on the stream.
+    caching allocator; with allocator=(alloc, free) through the two Python
+    callables alloc(nbytes, stream_ptr) -> device pointer (int; 0 or None on
+    failure) and free(ptr, nbytes, stream_ptr); otherwise through
+    cudaMallocAsync on the stream.
     """
 
-    def __init__(self, stream=None, options=None, torch_allocator=False):
+    def __init__(self, stream=None, options=None, torch_allocator=False, allocator=None):
         import torch
         lib = load()
         self.stream = stream or torch.cuda.current_stream()
@@ -285,6 +288,18 @@ class Context:
                 torch.cuda.caching_allocator_delete(ptr)
 
             af, ff = ALLOC_FN(_alloc), FREE_FN(_free)
+            self._keep += [af, ff]
+        elif allocator is not None:
+            user_alloc, user_free = allocator
+
+            def _alloc2(user, size, stream_ptr):
+                p = user_alloc(int(size), int(stream_ptr or 0))
+                return int(p) if p else None
+
+            def _free2(user, ptr, size, stream_ptr):
+                user_free(int(ptr), int(size), int(stream_ptr or 0))
+
+            af, ff = ALLOC_FN(_alloc2), FREE_FN(_free2)
             self._keep += [af, ff]
         else:
             af, ff = ALLOC_FN(), FREE_FN()

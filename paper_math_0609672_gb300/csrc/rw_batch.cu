@@ -91,37 +91,103 @@ struct BatchState {
 enum { kFlagActive = 0, kFlagCheck, kFlagBroke, kFlagIter, kFlagMaxIter, kFlagWords = 8 };
 
 // Per-chunk partial dot products a.b per right-hand side: part[c * 16 + j].
-// One block per chunk; thread t takes rows t, t + 256, ...; fixed-order sums.
-template <typename TA, typename TB>
+// One block per chunk; thread t takes rows t, t + 256, ...; fixed-order sums
+// (FP64 products and sums).  NR: the right-hand sides rounded up to a power
+// of two, so that only those accumulators are reduced.
+template <typename TA, typename TB, int NR>
 __global__ void __launch_bounds__(256) k_seg_dot(const TA* __restrict__ a, const TB* __restrict__ b,
                                                  int nrhs, const int32_t* __restrict__ chunk_row0,
                                                  double* __restrict__ part) {
-    __shared__ double sm[8][kMaxRhs];
+    __shared__ double sm[8][NR];
     const int32_t r0 = chunk_row0[blockIdx.x], r1 = chunk_row0[blockIdx.x + 1];
-    double acc[kMaxRhs];
+    double acc[NR];
 #pragma unroll
-    for (int j = 0; j < kMaxRhs; ++j) acc[j] = 0.0;
+    for (int j = 0; j < NR; ++j) acc[j] = 0.0;
     for (int32_t i = r0 + (int32_t)threadIdx.x; i < r1; i += blockDim.x)
 #pragma unroll
-        for (int j = 0; j < kMaxRhs; ++j)
+        for (int j = 0; j < NR; ++j)
             if (j < nrhs) acc[j] += (double)a[(size_t)i * nrhs + j] * (double)b[(size_t)i * nrhs + j];
 #pragma unroll
-    for (int j = 0; j < kMaxRhs; ++j) acc[j] = warp_sum(acc[j]);
+    for (int j = 0; j < NR; ++j) acc[j] = warp_sum(acc[j]);
     if (lane_id() == 0)
 #pragma unroll
-        for (int j = 0; j < kMaxRhs; ++j) sm[threadIdx.x >> 5][j] = acc[j];
+        for (int j = 0; j < NR; ++j) sm[threadIdx.x >> 5][j] = acc[j];
     __syncthreads();
     if (threadIdx.x < kMaxRhs) {
         double s = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sm[w][threadIdx.x];
+        if ((int)threadIdx.x < NR)
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sm[w][threadIdx.x];
         part[(size_t)blockIdx.x * kMaxRhs + threadIdx.x] = s;
     }
 }
 
+template <typename TA, typename TB>
+static void seg_dot(int nch, cudaStream_t s, const TA* a, const TB* b, int nrhs, const int32_t* chunk_row0,
+                    double* part) {
+    RW_COUNT_LAUNCH();
+    if (nrhs == 1) k_seg_dot<TA, TB, 1><<<nch, 256, 0, s>>>(a, b, nrhs, chunk_row0, part);
+    else if (nrhs == 2) k_seg_dot<TA, TB, 2><<<nch, 256, 0, s>>>(a, b, nrhs, chunk_row0, part);
+    else if (nrhs <= 4) k_seg_dot<TA, TB, 4><<<nch, 256, 0, s>>>(a, b, nrhs, chunk_row0, part);
+    else if (nrhs <= 8) k_seg_dot<TA, TB, 8><<<nch, 256, 0, s>>>(a, b, nrhs, chunk_row0, part);
+    else k_seg_dot<TA, TB, 16><<<nch, 256, 0, s>>>(a, b, nrhs, chunk_row0, part);
+}
+
 enum BatchOp { kBOpBnorm = 0, kBOpRho0, kBOpAlpha, kBOpResid, kBOpTrue, kBOpBeta, kBOpReport };
 
+// The step of Algorithm 1 for system sys given the sum v of its chunks.
+__device__ __forceinline__ void seg_step(const BatchState& S, int sys, double v, int op, int it, double tol,
+                                         int& broke) {
+    switch (op) {
+        case kBOpBnorm:
+            S.bnorm2[sys] = v;
+            S.active[sys] = v > 0.0;
+            S.iters[sys] = 0;
+            S.check[sys] = 0;
+            break;
+        case kBOpRho0:
+            S.rho[sys] = v;
+            break;
+        case kBOpAlpha:
+            if (S.active[sys]) {
+                if (!(v > 0.0)) {
+                    broke = 1;
+                    S.active[sys] = 0;
+                    S.alpha[sys] = 0.0;
+                } else {
+                    S.alpha[sys] = S.rho[sys] / v;
+                }
+            } else {
+                S.alpha[sys] = 0.0;
+            }
+            break;
+        case kBOpResid:
+            S.rr[sys] = v;
+            S.check[sys] = S.active[sys] && (sqrt(v) < tol * sqrt(S.bnorm2[sys]));
+            break;
+        case kBOpTrue:
+            S.tt[sys] = v;
+            if (S.check[sys] && sqrt(v) < tol * sqrt(S.bnorm2[sys])) {
+                S.active[sys] = 0;
+                S.iters[sys] = it;
+            }
+            S.check[sys] = 0;
+            break;
+        case kBOpBeta:
+            S.beta[sys] = S.active[sys] ? v / S.rho[sys] : 0.0;
+            S.rho[sys] = v;
+            break;
+        case kBOpReport:
+            S.tt[sys] = v;
+            break;
+    }
+}
+
 // One block of 1024 threads over all systems s = m * nrhs + j: sums the
-// chunks of matrix m in order and applies the step of Algorithm 1.
+// chunks of matrix m in a fixed order and applies the step of Algorithm 1.
+// WIDE (matrices of more than 64 chunks): a warp per system, lane l summing
+// chunks l, l + 32, ... before a fixed-order warp reduction; otherwise a
+// thread per system summing its chunks in order.
+template <bool WIDE>
 __global__ void __launch_bounds__(1024) k_seg_scalars(BatchState S, const double* __restrict__ part,
                                                       const int32_t* __restrict__ seg_chunk0, int nmat,
                                                       int nrhs, int op, double tol) {
@@ -141,55 +207,29 @@ __global__ void __launch_bounds__(1024) k_seg_scalars(BatchState S, const double
     const int nsys = nmat * nrhs;
     int any_act = 0, any_chk = 0, broke = 0;
     if (!s_skip) {
-        for (int sys = threadIdx.x; sys < nsys; sys += blockDim.x) {
-            const int m = sys / nrhs, j = sys - m * nrhs;
-            double v = 0.0;
-            for (int32_t c = seg_chunk0[m]; c < seg_chunk0[m + 1]; ++c) v += part[(size_t)c * kMaxRhs + j];
-            switch (op) {
-                case kBOpBnorm:
-                    S.bnorm2[sys] = v;
-                    S.active[sys] = v > 0.0;
-                    S.iters[sys] = 0;
-                    S.check[sys] = 0;
-                    break;
-                case kBOpRho0:
-                    S.rho[sys] = v;
-                    break;
-                case kBOpAlpha:
-                    if (S.active[sys]) {
-                        if (!(v > 0.0)) {
-                            broke = 1;
-                            S.active[sys] = 0;
-                            S.alpha[sys] = 0.0;
-                        } else {
-                            S.alpha[sys] = S.rho[sys] / v;
-                        }
-                    } else {
-                        S.alpha[sys] = 0.0;
-                    }
-                    break;
-                case kBOpResid:
-                    S.rr[sys] = v;
-                    S.check[sys] = S.active[sys] && (sqrt(v) < tol * sqrt(S.bnorm2[sys]));
-                    break;
-                case kBOpTrue:
-                    S.tt[sys] = v;
-                    if (S.check[sys] && sqrt(v) < tol * sqrt(S.bnorm2[sys])) {
-                        S.active[sys] = 0;
-                        S.iters[sys] = it;
-                    }
-                    S.check[sys] = 0;
-                    break;
-                case kBOpBeta:
-                    S.beta[sys] = S.active[sys] ? v / S.rho[sys] : 0.0;
-                    S.rho[sys] = v;
-                    break;
-                case kBOpReport:
-                    S.tt[sys] = v;
-                    break;
+        if (WIDE) {
+            const int lane = (int)lane_id(), warp = (int)(threadIdx.x >> 5);
+            for (int sys = warp; sys < nsys; sys += (int)(blockDim.x >> 5)) {
+                const int m = sys / nrhs, j = sys - m * nrhs;
+                double v = 0.0;
+                for (int32_t c = seg_chunk0[m] + lane; c < seg_chunk0[m + 1]; c += 32)
+                    v += part[(size_t)c * kMaxRhs + j];
+                v = warp_sum(v);
+                if (lane == 0) {
+                    seg_step(S, sys, v, op, it, tol, broke);
+                    any_act |= S.active[sys];
+                    any_chk |= S.check[sys];
+                }
             }
-            any_act |= S.active[sys];
-            any_chk |= S.check[sys];
+        } else {
+            for (int sys = threadIdx.x; sys < nsys; sys += blockDim.x) {
+                const int m = sys / nrhs, j = sys - m * nrhs;
+                double v = 0.0;
+                for (int32_t c = seg_chunk0[m]; c < seg_chunk0[m + 1]; ++c) v += part[(size_t)c * kMaxRhs + j];
+                seg_step(S, sys, v, op, it, tol, broke);
+                any_act |= S.active[sys];
+                any_chk |= S.check[sys];
+            }
         }
     } else if (op == kBOpAlpha) {
         // past max_iter: every step is a no-op
@@ -206,6 +246,13 @@ __global__ void __launch_bounds__(1024) k_seg_scalars(BatchState S, const double
             S.flags[kFlagCheck] = any_chk;
         }
     }
+}
+
+static void seg_scalars(bool wide, cudaStream_t s, const BatchState& S, const double* part,
+                        const int32_t* seg_chunk0, int nmat, int nrhs, int op, double tol) {
+    RW_COUNT_LAUNCH();
+    if (wide) k_seg_scalars<true><<<1, 1024, 0, s>>>(S, part, seg_chunk0, nmat, nrhs, op, tol);
+    else k_seg_scalars<false><<<1, 1024, 0, s>>>(S, part, seg_chunk0, nmat, nrhs, op, tol);
 }
 
 // x += alpha p (x FP64), r -= alpha q, per system.
@@ -345,6 +392,7 @@ struct rw_batch {
     int32_t nchunks = 0;
     int32_t* chunk_row0 = nullptr;  // [nchunks + 1]
     int32_t* seg_chunk0 = nullptr;  // [nmat + 1]
+    int32_t max_seg_chunks = 0;     // chunks of the largest matrix
     // combined A (FP64 and FP32 values)
     int32_t* a_rp = nullptr;
     int32_t* a_col = nullptr;
@@ -428,6 +476,7 @@ rw_status pcg_batch_t(rw_context* ctx, rw_batch* B, const double* const* d_b, do
         return rc;
     const int vb = grid_for(N, 256, ctx->num_sms * 8);
     const int nch = B->nchunks;
+    const bool wide = B->max_seg_chunks > 64;
     const int refine = ctx->opt.refine_every > 0 ? ctx->opt.refine_every : 50;
     const bool timing = ctx->opt.timing != 0;
     const int64_t l0 = g_launches;
@@ -435,10 +484,8 @@ rw_status pcg_batch_t(rw_context* ctx, rw_batch* B, const double* const* d_b, do
     // start: r = b, x = 0, ||b||, z = M^-1 r, rho = r.z, p = z
     RW_COUNT_LAUNCH();
     k_seg_gather_b<T><<<vb, 256, 0, s>>>(N, nrhs, B->rowseg, B->row0, bptr, b, r, x, ctx->d_status);
-    RW_COUNT_LAUNCH();
-    k_seg_dot<double, double><<<nch, 256, 0, s>>>(b, b, nrhs, B->chunk_row0, part);
-    RW_COUNT_LAUNCH();
-    k_seg_scalars<<<1, 1024, 0, s>>>(S, part, B->seg_chunk0, nmat, nrhs, kBOpBnorm, tol);
+    seg_dot<double, double>(nch, s, b, b, nrhs, B->chunk_row0, part);
+    seg_scalars(wide, s, S, part, B->seg_chunk0, nmat, nrhs, kBOpBnorm, tol);
     if ((rc = check_launch("batch pcg init"))) return rc;
     auto precond = [&]() -> rw_status {
         rw_status r2 = solve_runs<T>(ctx, B->bwd_sched, B->yt_rp, B->yt_col, ytv, tv_bwd, r, nullptr, w,
@@ -447,10 +494,8 @@ rw_status pcg_batch_t(rw_context* ctx, rw_batch* B, const double* const* d_b, do
         return solve_runs<T>(ctx, B->fwd_sched, B->y_rp, B->y_col, yv, tv_fwd, w, dv, z, nrhs, B->bar);
     };
     if ((rc = precond())) return rc;
-    RW_COUNT_LAUNCH();
-    k_seg_dot<T, T><<<nch, 256, 0, s>>>(r, z, nrhs, B->chunk_row0, part);
-    RW_COUNT_LAUNCH();
-    k_seg_scalars<<<1, 1024, 0, s>>>(S, part, B->seg_chunk0, nmat, nrhs, kBOpRho0, tol);
+    seg_dot<T, T>(nch, s, r, z, nrhs, B->chunk_row0, part);
+    seg_scalars(wide, s, S, part, B->seg_chunk0, nmat, nrhs, kBOpRho0, tol);
     RW_COUNT_LAUNCH();
     k_copy_vec<T><<<vb, 256, 0, s>>>(z, p, cnt);
     if ((rc = check_launch("batch pcg start"))) return rc;
@@ -464,31 +509,24 @@ rw_status pcg_batch_t(rw_context* ctx, rw_batch* B, const double* const* d_b, do
     auto iteration = [&]() -> rw_status {
         rw_status r2;
         if ((r2 = spmv_launch<T>(ctx, N, B->a_rp, B->a_col, Aval, p, q, nrhs))) return r2;
-        RW_COUNT_LAUNCH();
-        k_seg_dot<T, T><<<nch, 256, 0, s>>>(p, q, nrhs, B->chunk_row0, part);
-        RW_COUNT_LAUNCH();
-        k_seg_scalars<<<1, 1024, 0, s>>>(S, part, B->seg_chunk0, nmat, nrhs, kBOpAlpha, tol);
+        seg_dot<T, T>(nch, s, p, q, nrhs, B->chunk_row0, part);
+        seg_scalars(wide, s, S, part, B->seg_chunk0, nmat, nrhs, kBOpAlpha, tol);
         RW_COUNT_LAUNCH();
         k_seg_update_xr<T><<<vb, 256, 0, s>>>(N, nrhs, B->rowseg, S.alpha, x, r, p, q);
-        RW_COUNT_LAUNCH();
-        k_seg_dot<T, T><<<nch, 256, 0, s>>>(r, r, nrhs, B->chunk_row0, part);
+        seg_dot<T, T>(nch, s, r, r, nrhs, B->chunk_row0, part);
         if (mixed) {
             RW_COUNT_LAUNCH();
             k_seg_true_resid<T><<<nch, 256, 0, s>>>(B->a_rp, B->a_col, B->a_val, b, x, nrhs, B->chunk_row0,
                                                     r, part, S.flags, kTrueRefine, refine);
         }
-        RW_COUNT_LAUNCH();
-        k_seg_scalars<<<1, 1024, 0, s>>>(S, part, B->seg_chunk0, nmat, nrhs, kBOpResid, tol);
+        seg_scalars(wide, s, S, part, B->seg_chunk0, nmat, nrhs, kBOpResid, tol);
         RW_COUNT_LAUNCH();
         k_seg_true_resid<T><<<nch, 256, 0, s>>>(B->a_rp, B->a_col, B->a_val, b, x, nrhs, B->chunk_row0,
                                                 r, part, S.flags, kTrueCheck, refine);
-        RW_COUNT_LAUNCH();
-        k_seg_scalars<<<1, 1024, 0, s>>>(S, part, B->seg_chunk0, nmat, nrhs, kBOpTrue, tol);
+        seg_scalars(wide, s, S, part, B->seg_chunk0, nmat, nrhs, kBOpTrue, tol);
         if ((r2 = precond())) return r2;
-        RW_COUNT_LAUNCH();
-        k_seg_dot<T, T><<<nch, 256, 0, s>>>(r, z, nrhs, B->chunk_row0, part);
-        RW_COUNT_LAUNCH();
-        k_seg_scalars<<<1, 1024, 0, s>>>(S, part, B->seg_chunk0, nmat, nrhs, kBOpBeta, tol);
+        seg_dot<T, T>(nch, s, r, z, nrhs, B->chunk_row0, part);
+        seg_scalars(wide, s, S, part, B->seg_chunk0, nmat, nrhs, kBOpBeta, tol);
         RW_COUNT_LAUNCH();
         k_seg_update_p<T><<<vb, 256, 0, s>>>(N, nrhs, B->rowseg, S.beta, z, p);
         return check_launch("batch pcg step");
@@ -546,8 +584,7 @@ rw_status pcg_batch_t(rw_context* ctx, rw_batch* B, const double* const* d_b, do
     RW_COUNT_LAUNCH();
     k_seg_true_resid<T><<<nch, 256, 0, s>>>(B->a_rp, B->a_col, B->a_val, b, x, nrhs, B->chunk_row0, r, part,
                                             S.flags, kTrueAlways, refine);
-    RW_COUNT_LAUNCH();
-    k_seg_scalars<<<1, 1024, 0, s>>>(S, part, B->seg_chunk0, nmat, nrhs, kBOpReport, tol);
+    seg_scalars(wide, s, S, part, B->seg_chunk0, nmat, nrhs, kBOpReport, tol);
     RW_COUNT_LAUNCH();
     k_seg_scatter_x<<<vb, 256, 0, s>>>(N, nrhs, B->rowseg, B->row0, x, xptr);
     if ((rc = check_launch("batch pcg report"))) return rc;
@@ -652,6 +689,7 @@ rw_status rw_batch_create(rw_context* ctx, int32_t nmat, const rw_csr* As, const
         for (int64_t c = 0; c < n; c += kChunkRows) chunk_row0.push_back((int32_t)c);
         seg_chunk0[1] = (int32_t)chunk_row0.size();
         B->nchunks = (int32_t)chunk_row0.size();
+        B->max_seg_chunks = B->nchunks;
         chunk_row0.push_back(n);
         Pool& P = B->pool;
         B->row0 = alloc_n<int32_t>(P, 2);
@@ -719,6 +757,8 @@ rw_status rw_batch_create(rw_context* ctx, int32_t nmat, const rw_csr* As, const
     B->row0_h[nmat] = (int32_t)r0;
     seg_chunk0[nmat] = (int32_t)chunk_row0.size();
     B->nchunks = (int32_t)chunk_row0.size();
+    for (int32_t m = 0; m < nmat; ++m)
+        B->max_seg_chunks = std::max(B->max_seg_chunks, seg_chunk0[m + 1] - seg_chunk0[m]);
     chunk_row0.push_back((int32_t)r0);
     Pool& P = B->pool;
     B->row0 = alloc_n<int32_t>(P, nmat + 1);

@@ -11,7 +11,9 @@
 // are dropped (post-processing drop, footnote of Sec. 4).  Rows without an
 // upper neighbour are exact: Y_ki = A_ki / A_kk, D_kk = A_kk.
 #include <algorithm>
+#include <climits>
 #include <utility>
+#include <vector>
 
 #include "rw_internal.h"
 
@@ -244,31 +246,60 @@ __device__ void merge_row(const MergeParams& P, int32_t r, int* keys, uint32_t* 
     team_bitonic<TEAM>(keys, vals, Pw);
 
     const double akk = P.diag[k];
-    const double a = __ddiv_rn(P.S[k], akk);
     const int64_t walks = row_walks(P, r);
     const double Mk = (double)walks;
     const int64_t tb = P.tbase[r];
+    // The row's quotients in one warp-wide FP64 division (each lane one IEEE
+    // quotient; the FP64 pipe is narrow, so the per-row divisions are packed):
+    // lane 0: a = S_k / A_kk; lanes 1..8: h / M' for the small counts h almost
+    // every end point has; lanes 9..31: A_ki / A_kk for the first 23 lower
+    // neighbours (in column order).  Rarer quotients are divided where needed.
+    constexpr int kQuotSmall = 8, kQuotNbr = 9;
+    const int nlow = dp - rs;
+    const int ql = (int)lane_id();
+    double qnum = 1.0, qden = 1.0;
+    if (ql == 0) {
+        qnum = P.S[k];
+        qden = akk;
+    } else if (ql <= kQuotSmall) {
+        qnum = (double)ql;
+        qden = Mk;
+    } else if (ql - kQuotNbr < nlow) {
+        qnum = P.val[rs + ql - kQuotNbr];
+        qden = akk;
+    }
+    const double quot = __ddiv_rn(qnum, qden);
+    const double a = __shfl_sync(kFull, quot, 0);
     int kept = 0;
+    int nbr_before = 0;  // lower neighbours among the keys of earlier chunks
     for (int base = 0; base < u; base += TEAM) {
         const int s = base + t;
         bool keep = false;
         int key = 0;
         double y = 0.0;
+        const uint32_t v = s < u ? vals[s] : 1u;
+        const uint32_t hcount = v & kCountMask;
+        // the keys are sorted, and so are the row's lower entries (CSR positions
+        // rs .. dp - 1): the i-th key flagged as a neighbour is entry rs + i
+        const bool nb = s < u && (v & kNbrFlag) != 0u;
+        int nb_tot;
+        const int nb_rank = nbr_before + team_prefix<TEAM>(nb, &nb_tot, wsm);
+        nbr_before += nb_tot;
+        double ratio = __shfl_sync(kFull, quot, (int)(1u + ((hcount - 1u) & 7u)));
+        double d = __shfl_sync(kFull, quot, kQuotNbr + (nb_rank < 32 - kQuotNbr ? nb_rank : 0));
+        const bool div_ratio = s < u && hcount > (uint32_t)kQuotSmall;
+        const bool div_d = nb && nb_rank >= 32 - kQuotNbr;
+        if (__any_sync(kFull, div_ratio || div_d)) {
+            if (div_ratio) ratio = __ddiv_rn((double)hcount, Mk);
+            if (div_d) d = __ddiv_rn(P.val[rs + nb_rank], akk);
+        }
+        if (hcount == 0u) ratio = 0.0;  // a neighbour no walk ended at
         if (s < u) {
             key = keys[s];
-            const uint32_t v = vals[s];
-            double d = 0.0;
-            if (v & kNbrFlag) {
-                int lo = rs, hi = dp - 1;  // binary search of the column among the lower entries
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (P.col[mid] < key) lo = mid + 1;
-                    else hi = mid;
-                }
-                d = __ddiv_rn(P.val[lo], akk);
-            }
-            const double ratio = __ddiv_rn((double)(v & kCountMask), Mk);
-            y = __dadd_rn(d, __dmul_rn(a, ratio));
+            // y = A_ki/A_kk + a * H'/M' (a non-neighbour's first term is +0 and
+            // the product is non-zero, so the sum is the product itself)
+            const double prod = __dmul_rn(a, ratio);
+            y = nb ? __dadd_rn(d, prod) : prod;
             keep = fabs(y) >= P.drop_tol;
         }
         int tot;
@@ -639,16 +670,226 @@ __global__ void __launch_bounds__(kRadixThreads)
     }
 }
 
-// keys = column, vals = position of the entry in Y (row order).
-__global__ void k_transpose_pairs(int32_t n, const int64_t* __restrict__ rp,
-                                  const int32_t* __restrict__ col, uint32_t* keys, uint32_t* vals,
-                                  int32_t* row_of) {
-    for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
-        for (int64_t p = rp[k]; p < rp[k + 1]; ++p) {
-            keys[p] = (uint32_t)col[p];
-            vals[p] = (uint32_t)p;
-            row_of[p] = k;
+// ---------------------------------------------------------------------------
+// Transpose of the factor: every entry (k, c) of Y goes to row c of Y^T at a
+// position taken with an atomic counter of that row (one warp per row of Y,
+// reads coalesced, one 16-byte record {k, Y_kc} written per entry); then each
+// row of Y^T is sorted by k while it is copied into the column and value
+// arrays, so the result lists the rows of Y in ascending order -- the same
+// arrays a stable sort by column gives.  Rows of at most 32 entries are sorted
+// in the registers of one warp, rows of at most kSortWarp entries by one warp
+// in its shared memory, rows of at most kSortSmem entries by one block in
+// shared memory, longer rows by one block through a global scratch copy
+// (bitonic networks throughout; the keys of a row are distinct).
+// ---------------------------------------------------------------------------
+constexpr int kSortWarp = 1024;
+constexpr int kSortSmem = 4096;
+constexpr int kSortWarpsPerBlock = 4;
+
+struct TRec {
+    int32_t k;
+    int32_t pad;
+    double v;
+};
+
+__global__ void k_transpose_place(int32_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                  const double* __restrict__ val, unsigned long long* fill, TRec* tr) {
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int lane = (int)lane_id();
+    for (int64_t k = gw; k < n; k += nw) {
+        const int64_t s = rp[k], e = rp[k + 1];
+        for (int64_t p = s + lane; p < e; p += 32) {
+            const unsigned long long q = atomicAdd(&fill[col[p]], 1ull);
+            TRec r;
+            r.k = (int32_t)k;
+            r.pad = 0;
+            r.v = val[p];
+            tr[q] = r;
         }
+    }
+}
+
+// Rows of at most 32 entries: a bitonic network across the lanes of a warp.
+// Longer rows are listed for the shared-memory sorts (by size class).
+__global__ void k_sort_rows_warp(int32_t n, const int64_t* __restrict__ trp, const TRec* __restrict__ tr,
+                                 int32_t* tcol, double* tval, int32_t* lists, int32_t* counts) {
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int lane = (int)lane_id();
+    for (int64_t c = gw; c < n; c += nw) {
+        const int64_t s = trp[c], L = trp[c + 1] - s;
+        if (L == 0) continue;
+        if (L > 32) {
+            if (lane == 0) {
+                const int cls = L <= kSortWarp ? 0 : L <= kSortSmem ? 1 : 2;
+                lists[(int64_t)cls * n + atomicAdd(&counts[cls], 1)] = (int32_t)c;
+            }
+            continue;
+        }
+        int32_t key = INT32_MAX;
+        double v = 0.0;
+        if (lane < L) {
+            const TRec r = tr[s + lane];
+            key = r.k;
+            v = r.v;
+        }
+#pragma unroll
+        for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                const int32_t ok = __shfl_xor_sync(kFull, key, j);
+                const double ov = __shfl_xor_sync(kFull, v, j);
+                const bool asc = (lane & k) == 0;
+                const bool low = (lane & j) == 0;
+                // the lower lane of a pair keeps the smaller key in an ascending block
+                const bool take = low == asc ? ok < key : ok > key;
+                if (take) {
+                    key = ok;
+                    v = ov;
+                }
+            }
+        }
+        if (lane < L) {
+            tcol[s + lane] = key;
+            tval[s + lane] = v;
+        }
+    }
+}
+
+struct WarpSync {
+    __device__ void operator()() const { __syncwarp(); }
+};
+struct BlockSync {
+    __device__ void operator()() const { __syncthreads(); }
+};
+
+// Bitonic sort of P (a power of two) keys with payloads, in place, by
+// `threads` cooperating threads of index t; sync() separates the stages.
+template <typename Sync>
+__device__ __forceinline__ void bitonic(int32_t* key, double* val, int64_t P, int t, int threads, Sync sync) {
+    for (int64_t k = 2; k <= P; k <<= 1) {
+        for (int64_t j = k >> 1; j > 0; j >>= 1) {
+            for (int64_t i = t; i < P / 2; i += threads) {
+                const int64_t a = 2 * i - (i & (j - 1));  // the lower index of pair i (j a power of two)
+                const int64_t b = a + j;
+                const bool asc = (a & k) == 0;
+                const int32_t ka = key[a], kb = key[b];
+                if ((ka > kb) == asc) {
+                    key[a] = kb;
+                    key[b] = ka;
+                    const double x = val[a];
+                    val[a] = val[b];
+                    val[b] = x;
+                }
+            }
+            sync();
+        }
+    }
+}
+
+// Rows of 33 .. kSortWarp entries: one warp per row, in its shared memory.
+__global__ void __launch_bounds__(32 * kSortWarpsPerBlock) k_sort_rows_wsmem(const int64_t* __restrict__ trp,
+                                                                            const int32_t* __restrict__ rows,
+                                                                            const int32_t* __restrict__ n_rows,
+                                                                            const TRec* __restrict__ tr,
+                                                                            int32_t* tcol, double* tval) {
+    __shared__ int32_t skey[kSortWarpsPerBlock][kSortWarp];
+    __shared__ double sval[kSortWarpsPerBlock][kSortWarp];
+    const int warp = (int)(threadIdx.x >> 5), lane = (int)lane_id();
+    int32_t* key = skey[warp];
+    double* val = sval[warp];
+    const int32_t nr = *n_rows;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = gw; r < nr; r += nw) {
+        const int32_t c = rows[r];
+        const int64_t s = trp[c], L = trp[c + 1] - s;
+        int64_t P = 64;
+        while (P < L) P <<= 1;
+        for (int64_t i = lane; i < P; i += 32) {
+            if (i < L) {
+                const TRec x = tr[s + i];
+                key[i] = x.k;
+                val[i] = x.v;
+            } else {
+                key[i] = INT32_MAX;
+                val[i] = 0.0;
+            }
+        }
+        __syncwarp();
+        bitonic(key, val, P, lane, 32, WarpSync{});
+        for (int64_t i = lane; i < L; i += 32) {
+            tcol[s + i] = key[i];
+            tval[s + i] = val[i];
+        }
+        __syncwarp();
+    }
+}
+
+// Rows of kSortWarp + 1 .. kSortSmem entries: one block per row, in shared memory.
+__global__ void __launch_bounds__(512) k_sort_rows_smem(const int64_t* __restrict__ trp, const int32_t* __restrict__ rows,
+                                                        const int32_t* __restrict__ n_rows,
+                                                        const TRec* __restrict__ tr, int32_t* tcol, double* tval) {
+    __shared__ int32_t skey[kSortSmem];
+    __shared__ double sval[kSortSmem];
+    const int32_t nr = *n_rows;
+    for (int32_t r = blockIdx.x; r < nr; r += gridDim.x) {
+        const int32_t c = rows[r];
+        const int64_t s = trp[c], L = trp[c + 1] - s;
+        int64_t P = 64;
+        while (P < L) P <<= 1;
+        for (int64_t i = threadIdx.x; i < P; i += blockDim.x) {
+            if (i < L) {
+                const TRec x = tr[s + i];
+                skey[i] = x.k;
+                sval[i] = x.v;
+            } else {
+                skey[i] = INT32_MAX;
+                sval[i] = 0.0;
+            }
+        }
+        __syncthreads();
+        bitonic(skey, sval, P, (int)threadIdx.x, (int)blockDim.x, BlockSync{});
+        for (int64_t i = threadIdx.x; i < L; i += blockDim.x) {
+            tcol[s + i] = skey[i];
+            tval[s + i] = sval[i];
+        }
+        __syncthreads();
+    }
+}
+
+// Rows longer than kSortSmem: one block per row over a padded global copy
+// (scratch of 2^ceil(log2 L) entries per row, placed at sbase[r]).
+__global__ void __launch_bounds__(1024) k_sort_rows_global(const int64_t* __restrict__ trp,
+                                                           const int32_t* __restrict__ rows,
+                                                           const int64_t* __restrict__ sbase, int32_t nr,
+                                                           const TRec* __restrict__ tr, int32_t* skey_all,
+                                                           double* sval_all, int32_t* tcol, double* tval) {
+    for (int32_t r = blockIdx.x; r < nr; r += gridDim.x) {
+        const int32_t c = rows[r];
+        const int64_t s = trp[c], L = trp[c + 1] - s;
+        const int64_t P = sbase[r + 1] - sbase[r];
+        int32_t* key = skey_all + sbase[r];
+        double* val = sval_all + sbase[r];
+        for (int64_t i = threadIdx.x; i < P; i += blockDim.x) {
+            if (i < L) {
+                const TRec x = tr[s + i];
+                key[i] = x.k;
+                val[i] = x.v;
+            } else {
+                key[i] = INT32_MAX;
+                val[i] = 0.0;
+            }
+        }
+        __syncthreads();
+        bitonic(key, val, P, (int)threadIdx.x, (int)blockDim.x, BlockSync{});
+        for (int64_t i = threadIdx.x; i < L; i += blockDim.x) {
+            tcol[s + i] = key[i];
+            tval[s + i] = val[i];
+        }
+        __syncthreads();
+    }
 }
 
 __global__ void k_col_counts(int64_t nnz, const int32_t* __restrict__ col, uint32_t* cnt) {
@@ -717,27 +958,67 @@ rw_status transpose_factor(rw_context* ctx, int32_t n, const FactorOut& fo, int6
     }
     if ((rc = check_cuda(scan_u32_to_i64(cnt, yt_rp, n, s, scratch), "scan"))) return rc;
     if (nnz == 0) return RW_OK;
-    if (nnz >= ((int64_t)1 << 32)) {
-        set_error("transpose: factor too large (%lld entries)", (long long)nnz);
-        return RW_ERR_CAPACITY;
+    unsigned long long* fill = alloc_n<unsigned long long>(scratch, n);
+    TRec* tr = alloc_n<TRec>(scratch, nnz);
+    int32_t* lists = alloc_n<int32_t>(scratch, 3 * (int64_t)n);
+    int32_t* counts = alloc_n<int32_t>(scratch, 3);
+    if (!fill || !tr || !lists || !counts) return RW_ERR_ALLOC;
+    if ((rc = check_cuda(cudaMemcpyAsync(fill, yt_rp, sizeof(int64_t) * (size_t)n, cudaMemcpyDeviceToDevice, s),
+                         "copy")) ||
+        (rc = check_cuda(cudaMemsetAsync(counts, 0, 3 * sizeof(int32_t), s), "memset")))
+        return rc;
+    const int wblocks = grid_for((int64_t)n * 32, 256, ctx->num_sms * 16);
+    RW_COUNT_LAUNCH();
+    k_transpose_place<<<wblocks, 256, 0, s>>>(n, fo.y_rp, fo.y_col, fo.y_val, fill, tr);
+    RW_COUNT_LAUNCH();
+    k_sort_rows_warp<<<wblocks, 256, 0, s>>>(n, yt_rp, tr, yt_col, yt_val, lists, counts);
+    RW_COUNT_LAUNCH();
+    k_sort_rows_wsmem<<<ctx->num_sms * 4, 32 * kSortWarpsPerBlock, 0, s>>>(yt_rp, lists, counts, tr, yt_col,
+                                                                            yt_val);
+    RW_COUNT_LAUNCH();
+    k_sort_rows_smem<<<ctx->num_sms * 2, 512, 0, s>>>(yt_rp, lists + n, counts + 1, tr, yt_col, yt_val);
+    if ((rc = check_launch("transpose"))) return rc;
+    // rows longer than the shared-memory sorts (none on most factors)
+    int32_t* h = static_cast<int32_t*>(ctx->h_small);
+    if ((rc = check_cuda(cudaMemcpyAsync(h, counts + 2, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "copy")) ||
+        (rc = check_cuda(cudaStreamSynchronize(s), "sync")))
+        return rc;
+    const int32_t nbig = h[0];
+    if (nbig > 0) {
+        std::vector<int32_t> rows(nbig);
+        std::vector<int64_t> trp((size_t)n + 1);
+        if ((rc = check_cuda(cudaMemcpy(rows.data(), lists + 2 * (int64_t)n, sizeof(int32_t) * nbig,
+                                        cudaMemcpyDeviceToHost),
+                             "copy")) ||
+            (rc = check_cuda(cudaMemcpy(trp.data(), yt_rp, sizeof(int64_t) * ((size_t)n + 1), cudaMemcpyDeviceToHost),
+                             "copy")))
+            return rc;
+        std::sort(rows.begin(), rows.end());
+        std::vector<int64_t> sbase(nbig + 1, 0);
+        for (int32_t r = 0; r < nbig; ++r) {
+            int64_t P = 1;
+            while (P < trp[rows[r] + 1] - trp[rows[r]]) P <<= 1;
+            sbase[r + 1] = sbase[r] + P;
+        }
+        int32_t* d_rows = alloc_n<int32_t>(scratch, nbig);
+        int64_t* d_sbase = alloc_n<int64_t>(scratch, nbig + 1);
+        int32_t* skey = alloc_n<int32_t>(scratch, sbase[nbig]);
+        double* sval = alloc_n<double>(scratch, sbase[nbig]);
+        if (!d_rows || !d_sbase || !skey || !sval) return RW_ERR_ALLOC;
+        if ((rc = check_cuda(cudaMemcpyAsync(d_rows, rows.data(), sizeof(int32_t) * nbig, cudaMemcpyHostToDevice, s),
+                             "copy")) ||
+            (rc = check_cuda(cudaMemcpyAsync(d_sbase, sbase.data(), sizeof(int64_t) * (nbig + 1),
+                                             cudaMemcpyHostToDevice, s),
+                             "copy")))
+            return rc;
+        RW_COUNT_LAUNCH();
+        k_sort_rows_global<<<std::min(nbig, ctx->num_sms * 2), 1024, 0, s>>>(yt_rp, d_rows, d_sbase, nbig, tr, skey,
+                                                                            sval, yt_col, yt_val);
+        if ((rc = check_launch("transpose long rows"))) return rc;
+        // the host copies of rows and sbase are read by the launch: keep them until it is done
+        if ((rc = check_cuda(cudaStreamSynchronize(s), "sync"))) return rc;
     }
-    uint32_t* k0 = alloc_n<uint32_t>(scratch, nnz);
-    uint32_t* v0 = alloc_n<uint32_t>(scratch, nnz);
-    uint32_t* k1 = alloc_n<uint32_t>(scratch, nnz);
-    uint32_t* v1 = alloc_n<uint32_t>(scratch, nnz);
-    int32_t* row_of = alloc_n<int32_t>(scratch, nnz);
-    if (!k0 || !v0 || !k1 || !v1 || !row_of) return RW_ERR_ALLOC;
-    RW_COUNT_LAUNCH();
-    k_transpose_pairs<<<grid_for(n, 256, ctx->num_sms * 8), 256, 0, s>>>(n, fo.y_rp, fo.y_col, k0,
-                                                                          v0, row_of);
-    if ((rc = check_launch("transpose pairs"))) return rc;
-    int bits = 1;
-    while (bits < 31 && ((int64_t)1 << bits) < n) ++bits;
-    if ((rc = radix_sort_pairs(ctx, k0, v0, k1, v1, nnz, bits, scratch, &k0, &v0))) return rc;
-    RW_COUNT_LAUNCH();
-    k_transpose_gather<<<grid_for(nnz, 256, ctx->num_sms * 8), 256, 0, s>>>(nnz, v0, row_of,
-                                                                            fo.y_val, yt_col, yt_val);
-    return check_launch("transpose gather");
+    return RW_OK;
 }
 
 // A^T of a CSR matrix (int32 row pointers): entries sorted by column with a

@@ -78,28 +78,32 @@ inline int grid_for(int64_t work, int block, int max_blocks) {
 // ---- build path (rw_tables.cu, rw_walk.cu, rw_emit.cu, rw_levels.cu) -------
 
 // Walk tables of one matrix, in the layout read by the walk kernel.
-//  tab:   per node ng = ceil((1 + deg) / 4) group sectors of 8 uint32 words
-//         (32 bytes), preceded by one summary sector when ng > 2.  Slot j of
-//         a node's slot sequence (slot 0 = header, slot s + 1 = successor s in
-//         ascending column order) lives in group j / 4: word j % 4 holds its
-//         threshold (0 for the header slot: always passed) and word 4 + j % 4
-//         its successor word (the index of that successor's first sector, bit
-//         31 set when the successor has a summary sector; deg for the header
-//         slot, 0 for padding).  The summary sector holds deg in word 0 and,
-//         in words 1..7, the threshold of the last slot of groups 0..6
-//         (0xFFFFFFFF past the last).  A hop reads the summary, then the one
-//         group that holds the drawn successor; a node of at most two groups
-//         (deg <= 7) has no summary and its second group is read only when
-//         the draw passes the first.  Random DRAM reads are limited per
-//         sector, so a hop costs two sectors at most (except nodes of more
-//         than 27 neighbours, whose groups past 6 are scanned in turn).
-//  bnode: [sectors] the node each sector belongs to.
+//  tab:   32-byte sectors of 8 uint32 words in three regions.  A node's slots
+//         (slot 0 = header, slot s + 1 = successor s in ascending column
+//         order) form ng = ceil((1 + deg) / 4) groups; slot j lives in group
+//         j / 4, word j % 4 its threshold (0 for the header slot: always
+//         passed), word 4 + j % 4 its successor word (the successor's node
+//         index, bit 31 set when that node has a summary; deg for the header
+//         slot, 0 for padding).
+//           sectors [0, 2n): node j's groups at 2j, 2j + 1 when ng <= 2;
+//           sectors [2n, 3n): node j's summary at 2n + j when ng > 2 -- deg in
+//             word 0, in words 1..7 the last threshold of groups 0..6
+//             (0xFFFFFFFF past the last);
+//           sectors [3n, 3n + G): the groups of the nodes with a summary.
+//         The summaries (32 bytes per node, dense) and gbase stay in L2 on
+//         large matrices, so a hop to a node with a summary costs one DRAM
+//         sector (its group) besides two L2 reads issued together; a node of
+//         at most seven neighbours costs one or two sectors of group 0/1.
+//  gbase: [n] the sector of each node's group 0.
+//  fthr:  per walk row a block [updeg, lowdeg, ft_0 .. ft_{updeg-1}, pad].
+// The walk works with node indices throughout (home: below the start row,
+// return: equal to it).  Padding thresholds are 0xFFFFFFFF.
 struct Tables {
     int32_t n = 0;
     uint32_t* tab = nullptr;
-    int32_t* bnode = nullptr;
+    uint32_t* gbase = nullptr;    // [n] sector of each node's group 0
     uint32_t* fthr = nullptr;
-    uint32_t* toff = nullptr;     // [n+1] first sector of each node (32-byte sectors)
+    uint32_t* toff = nullptr;     // [n+1] groups of the nodes with a summary before each node (prefix)
     uint32_t* foff8 = nullptr;    // [n+1] first-step blocks (32-byte blocks)
     int32_t* deg = nullptr;       // [n] off-diagonal count
     int32_t* lowdeg = nullptr;    // [n] entries with column < row
@@ -108,7 +112,7 @@ struct Tables {
     int32_t* diag_pos = nullptr;  // [n] CSR position of the diagonal
     uint32_t* walk_flag = nullptr;    // [n+1] scanned into the walk-row index
     int32_t n_walk_rows = 0;
-    int4* wrow = nullptr;         // [n_walk_rows] {k, foff8_k, toff_k, lowdeg_k}
+    int4* wrow = nullptr;         // [n_walk_rows] {k, foff8_k, gbase_k, lowdeg_k}
     int32_t* walk_rows = nullptr; // [n_walk_rows] k ascending
     uint64_t sectors = 0, first_words = 0;
 };
@@ -138,9 +142,9 @@ struct WalkLaunch {
 // is (matrix_index << 2) | kind (kind 0: factor walks, 1: pilot walks).
 struct MatWalk {
     const uint32_t* tab;
-    const int32_t* bnode;
+    const uint32_t* gbase;
     const uint32_t* fthr;
-    uint32_t key0, key1, tag, pad;
+    uint32_t key0, key1, tag, n;  // n: nodes (the summaries start at sector 2n)
 };
 
 // The walk index space of one launch (one matrix, or several concatenated).
@@ -158,11 +162,11 @@ struct WalkBatch {
     int64_t total = 0;
 };
 
-inline uint64_t table_bytes(const Tables& T) { return T.sectors * 32u; }
+inline uint64_t table_bytes(const Tables& T) { return T.sectors * 32u + (uint64_t)T.n * 4u; }
 
 inline MatWalk mat_walk(const Tables& T, uint64_t seed, uint32_t matrix_index, uint32_t kind) {
-    return MatWalk{T.tab, T.bnode, T.fthr, (uint32_t)seed, (uint32_t)(seed >> 32),
-                   (matrix_index << 2) | (kind & 3u), 0u};
+    return MatWalk{T.tab, T.gbase, T.fthr, (uint32_t)seed, (uint32_t)(seed >> 32),
+                   (matrix_index << 2) | (kind & 3u), (uint32_t)T.n};
 }
 
 rw_status run_walks(rw_context* ctx, const WalkBatch& wb, const WalkLaunch& wl, int2* rec,

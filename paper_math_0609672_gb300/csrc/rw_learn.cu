@@ -32,8 +32,28 @@ namespace rw {
 // 10 log(1 + sum over upper neighbours c of #{entries of row c with column > k})
 // 11 log A_kk
 // ---------------------------------------------------------------------------
+// Per node c: its off-diagonal count and (A_cc + sum_j A_cj) / A_cc, the sum
+// taken in column order (what feature 8 averages over a row's neighbours).
+__global__ void k_node_info(int32_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                            const double* __restrict__ val, int32_t* ndeg, double* exr) {
+    for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        double cd = 0.0, csum = 0.0;
+        for (int32_t q = rp[c]; q < rp[c + 1]; ++q) {
+            if (col[q] == c) cd = val[q];
+            else csum += val[q];
+        }
+        ndeg[c] = rp[c + 1] - rp[c] - 1;
+        exr[c] = (cd + csum) / cd;
+    }
+}
+
+// One thread per row k (FP64).  Feature 8 averages the neighbours' excess
+// ratios and feature 9 their degrees (per-node arrays from k_node_info);
+// feature 10 counts, over the upper neighbours c, the off-diagonal entries of
+// row c with column > k: a binary search of row c's ascending columns.
 __global__ void k_features(int32_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
-                           const double* __restrict__ val, float* __restrict__ feat) {
+                           const double* __restrict__ val, const int32_t* __restrict__ ndeg_of,
+                           const double* __restrict__ exr, float* __restrict__ feat) {
     for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const int32_t s = rp[k], e = rp[k + 1];
         double diag = 0.0, wsum = 0.0, wup = 0.0, wmax = 0.0;
@@ -62,19 +82,19 @@ __global__ void k_features(int32_t n, const int32_t* __restrict__ rp, const int3
             if (c == k) continue;
             const double pr = -val[p] / wsum;
             if (pr > 0.0) ent -= pr * log(pr);
-            const int32_t cs = rp[c], ce = rp[c + 1];
-            double cd = 0.0, csum = 0.0;
-            for (int32_t q = cs; q < ce; ++q) {
-                const int32_t cq = col[q];
-                if (cq == c) {
-                    cd = val[q];
-                } else {
-                    csum += val[q];
-                    if (c > k && cq > k) ++up2;
+            nex += exr[c];
+            ndeg += (double)ndeg_of[c];
+            if (c > k) {
+                // first position of row c with column > k (the diagonal c > k is among them)
+                int32_t a = rp[c], b = rp[c + 1];
+                const int32_t ce = b;
+                while (a < b) {
+                    const int32_t m = (a + b) >> 1;
+                    if (col[m] > k) b = m;
+                    else a = m + 1;
                 }
+                up2 += ce - a - 1;
             }
-            nex += (cd + csum) / cd;
-            ndeg += (double)(ce - cs - 1);
         }
         float* f = feat + (size_t)k * kFeatStride;
         f[0] = (float)log1p((double)deg);
@@ -648,9 +668,16 @@ __global__ void k_norm_final(int32_t n, const uint32_t* __restrict__ frac,
 // Host side
 // ---------------------------------------------------------------------------
 static rw_status features_run(rw_context* ctx, const rw_csr* A, float* feat) {
+    Pool sc(ctx);
+    int32_t* ndeg = alloc_n<int32_t>(sc, A->n);
+    double* exr = alloc_n<double>(sc, A->n);
+    if (!ndeg || !exr) return RW_ERR_ALLOC;
+    RW_COUNT_LAUNCH();
+    k_node_info<<<grid_for(A->n, 256, ctx->num_sms * 8), 256, 0, ctx->stream>>>(A->n, A->row_ptr, A->col, A->val,
+                                                                                 ndeg, exr);
     RW_COUNT_LAUNCH();
     k_features<<<grid_for(A->n, 128, ctx->num_sms * 16), 128, 0, ctx->stream>>>(A->n, A->row_ptr, A->col,
-                                                                                 A->val, feat);
+                                                                                 A->val, ndeg, exr, feat);
     return check_launch("row features");
 }
 

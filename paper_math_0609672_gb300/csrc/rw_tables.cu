@@ -161,32 +161,32 @@ __global__ void k_row_info(int32_t n, int64_t nnz, const int32_t* __restrict__ r
         deg[l] = d;
         lowdeg[l] = lo;
         dpos[l] = dp;
-        // groups of four slots, ceil((1 + deg) / 4), plus a summary sector when there are more than two
+        // groups of four slots, ceil((1 + deg) / 4); a node of more than two
+        // has a summary and its groups in the third region of the tables
         const uint32_t ng = (uint32_t)(1 + d + 3) / 4u;
-        blk_full[l] = ng + (ng > 2u ? 1u : 0u);
+        blk_full[l] = ng > 2u ? ng : 0u;
         blk_first[l] = up > 0 ? (uint32_t)(2 + up + 7) / 8u : 0u;
         walk_flag[l] = up > 0 ? 1u : 0u;
     }
 }
 
-// Thresholds and successor sector indices.  One thread per row; the sums run
+// Thresholds and successor words.  One thread per row; the sums run
 // sequentially over the row in ascending column order, each addition and
 // division rounded once (the same order the sampling rule is defined in).
 __global__ void k_fill_tables(int32_t n, const int32_t* __restrict__ rp,
                               const int32_t* __restrict__ col, const double* __restrict__ val,
                               const int32_t* __restrict__ deg, const int32_t* __restrict__ lowdeg,
                               const int32_t* __restrict__ dpos, const uint32_t* __restrict__ toff,
-                              const uint32_t* __restrict__ foff8, uint32_t* tab, int32_t* snode,
+                              const uint32_t* __restrict__ foff8, uint32_t* tab, uint32_t* gbase,
                               uint32_t* fthr, double* S, double* diag) {
     for (int32_t l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x) {
         const int32_t s = rp[l], e = rp[l + 1], dp = dpos[l], d = deg[l], lo = lowdeg[l];
         const double dg = val[dp];
         diag[l] = dg;
-        const uint64_t s0 = toff[l], s1 = toff[l + 1];
-        for (uint64_t q = s0; q < s1; ++q) snode[q] = l;
-        // a node of more than two groups starts with its summary sector
         const uint64_t ng = ((uint64_t)d + 4u) / 4u;
-        const uint64_t g0 = s0 + (ng > 2u ? 1u : 0u);
+        const bool big = ng > 2u;
+        const uint64_t g0 = big ? 3u * (uint64_t)n + toff[l] : 2u * (uint64_t)l;
+        gbase[l] = (uint32_t)g0;
         // slot j: threshold at word 8 * (g0 + j / 4) + j % 4, successor word at + 4
         auto word = [&](uint64_t j) -> uint32_t* { return tab + (g0 + j / 4u) * 8u + (j % 4u); };
         *word(0) = 0u;                 // the header slot: always passed
@@ -200,7 +200,7 @@ __global__ void k_fill_tables(int32_t n, const int32_t* __restrict__ rp,
             w[0] = cumulative_threshold(c, dg);
             const int32_t jc = col[p];
             const uint32_t ngc = (uint32_t)(deg[jc] + 4) / 4u;
-            w[4] = toff[jc] | (ngc > 2u ? 0x80000000u : 0u);  // flag: the successor has a summary sector
+            w[4] = (uint32_t)jc | (ngc > 2u ? 0x80000000u : 0u);  // flag: the successor has a summary
             ++j;
         }
         for (; j < ng * 4u; ++j) {
@@ -208,9 +208,9 @@ __global__ void k_fill_tables(int32_t n, const int32_t* __restrict__ rp,
             w[0] = 0xFFFFFFFFu;
             w[4] = 0u;
         }
-        if (ng > 2u) {
+        if (big) {
             // summary: deg, then the threshold of the last slot of groups 0..6
-            uint32_t* sw = tab + s0 * 8u;
+            uint32_t* sw = tab + (2u * (uint64_t)n + (uint64_t)l) * 8u;
             sw[0] = (uint32_t)d;
             for (uint64_t g = 0; g < 7u; ++g) sw[1 + g] = g < ng ? *word(4u * g + 3u) : 0xFFFFFFFFu;
         }
@@ -235,12 +235,12 @@ __global__ void k_fill_tables(int32_t n, const int32_t* __restrict__ rp,
 }
 
 __global__ void k_walk_rows(int32_t n, const uint32_t* __restrict__ widx,
-                            const uint32_t* __restrict__ toff, const uint32_t* __restrict__ foff8,
+                            const uint32_t* __restrict__ gbase, const uint32_t* __restrict__ foff8,
                             const int32_t* __restrict__ lowdeg, int4* wrow, int32_t* walk_rows) {
     for (int32_t l = blockIdx.x * blockDim.x + threadIdx.x; l < n; l += gridDim.x * blockDim.x) {
         const uint32_t r = widx[l];
         if (widx[l + 1] != r) {
-            wrow[r] = make_int4(l, (int)foff8[l], (int)toff[l], lowdeg[l]);
+            wrow[r] = make_int4(l, (int)foff8[l], (int)gbase[l], lowdeg[l]);
             walk_rows[r] = l;
         }
     }
@@ -280,7 +280,7 @@ rw_status build_tables(rw_context* ctx, const rw_csr* A, Tables& T, Pool& pool) 
                          "copy")))
         return rc;
     if ((rc = read_status(ctx, "matrix validation"))) return rc;
-    T.sectors = hs[0];
+    T.sectors = 3u * (uint64_t)n + hs[0];
     if (T.sectors >= 0x80000000ull) {
         set_error("walk tables: %llu sectors exceed the 2^31 sector-index range", (unsigned long long)T.sectors);
         return RW_ERR_CAPACITY;
@@ -288,18 +288,18 @@ rw_status build_tables(rw_context* ctx, const rw_csr* A, Tables& T, Pool& pool) 
     T.first_words = (uint64_t)hs[1] * 8u;
     T.n_walk_rows = (int32_t)hs[2];
     T.tab = alloc_n<uint32_t>(pool, (int64_t)T.sectors * 8);
-    T.bnode = alloc_n<int32_t>(pool, (int64_t)T.sectors);
+    T.gbase = alloc_n<uint32_t>(pool, n);
     T.fthr = alloc_n<uint32_t>(pool, (int64_t)T.first_words);
     T.wrow = alloc_n<int4>(pool, T.n_walk_rows);
     T.walk_rows = alloc_n<int32_t>(pool, T.n_walk_rows);
-    if (!T.tab || !T.bnode || !T.fthr || !T.wrow || !T.walk_rows) return RW_ERR_ALLOC;
+    if (!T.tab || !T.gbase || !T.fthr || !T.wrow || !T.walk_rows) return RW_ERR_ALLOC;
     RW_COUNT_LAUNCH();
     k_fill_tables<<<blocks, 256, 0, s>>>(n, A->row_ptr, A->col, A->val, T.deg, T.lowdeg,
-                                         T.diag_pos, T.toff, T.foff8, T.tab, T.bnode, T.fthr, T.S,
+                                         T.diag_pos, T.toff, T.foff8, T.tab, T.gbase, T.fthr, T.S,
                                          T.diag);
     if ((rc = check_launch("fill tables"))) return rc;
     RW_COUNT_LAUNCH();
-    k_walk_rows<<<blocks, 256, 0, s>>>(n, T.walk_flag, T.toff, T.foff8, T.lowdeg, T.wrow,
+    k_walk_rows<<<blocks, 256, 0, s>>>(n, T.walk_flag, T.gbase, T.foff8, T.lowdeg, T.wrow,
                                        T.walk_rows);
     return check_launch("walk rows");
 }

@@ -5,15 +5,14 @@
 // indices at a time from a global cursor; a lane whose walk ends takes the next
 // index of the warp's pool, so the warp stays full although walk lengths vary
 // by orders of magnitude.  The tables hold each node's transitions in 32-byte
-// group sectors of four thresholds and the four successors' sector indices
-// beside them, so the next node is known when the group arrives.  A hop to a
-// node of degree <= 3 reads one sector, to a node of degree <= 7 one or two
-// (the second only when the draw passes the first group), to a node of higher
-// degree two: its summary sector (the last threshold of each group), then
-// the one group that holds the drawn successor.  Random reads from HBM are
-// limited per sector, not per byte, so the kernel is bound by sectors per
-// hop.  The walk works in sector indices (they increase with the node
-// index); the end node's index is looked up once, when the walk ends.
+// group sectors of four thresholds with the four successors' words beside
+// them, so the next node is known when the group arrives.  A hop to a node of
+// degree <= 7 reads its group 0 (and group 1 only when the draw passes group
+// 0); a hop to a node of higher degree reads the node's summary (the last
+// threshold of each group; a dense node-indexed region that stays in L2) and
+// its group base together, then the one group that holds the drawn successor.
+// Random reads from HBM are limited per sector, not per byte, so the kernel is
+// bound by the DRAM sectors per hop: one for 27-point nodes.
 //
 // Walk w of row k (rows 0..k-1 are homes, ground absorbs):
 //   step 1: draw 0 picks an upper neighbour j > k with probability
@@ -23,8 +22,7 @@
 //   the walk ends at a node < k (home) or at ground; each visit to k counts a
 //   return.  Draw s is word (s mod 4) of Philox(s/4, w, k, tag).
 // Output: one record per walk, {end node (-1 ground, -2 step cap), returns or
-// length}; the kernel writes a home end as its first-sector index and
-// k_rec_nodes converts it after the launch.
+// length}.
 #include "rw_internal.h"
 
 namespace rw {
@@ -43,6 +41,7 @@ struct WalkParams {
     DevStatus* st;
     uint64_t max_steps;
     int record_lengths;
+    int cache_hint;                     // tables larger than the L2: evict_last / evict_first policies
     MatWalk m0;                         // the matrix of a single-matrix launch
 };
 
@@ -58,14 +57,43 @@ __device__ __forceinline__ uint4 ld_nc4(const uint32_t* p) {
     return __ldg(reinterpret_cast<const uint4*>(p));
 }
 
-constexpr uint32_t kSumFlag = 0x80000000u;    // successor word: node with a summary sector
-constexpr uint32_t kSectorMask = 0x7FFFFFFFu;
+constexpr uint32_t kSumFlag = 0x80000000u;    // successor word: node with a summary
+constexpr uint32_t kNodeMask = 0x7FFFFFFFu;
 
 // 32 bytes (eight words) in one load; p must be 32-byte aligned (sectors are).
 __device__ __forceinline__ void ld_nc8(const uint32_t* p, uint4& lo, uint4& hi) {
     asm("ld.global.nc.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
         : "=r"(lo.x), "=r"(lo.y), "=r"(lo.z), "=r"(lo.w), "=r"(hi.x), "=r"(hi.y), "=r"(hi.z), "=r"(hi.w)
         : "l"(p));
+}
+
+// The same with an L2 cache-policy operand (createpolicy): evict_last keeps
+// the summaries and group bases in L2 while the group sectors stream through
+// with evict_first, when the tables are larger than the L2.
+__device__ __forceinline__ void ld_nc8_hint(const uint32_t* p, uint4& lo, uint4& hi, uint64_t pol) {
+    asm("ld.global.nc.L2::cache_hint.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8], %9;"
+        : "=r"(lo.x), "=r"(lo.y), "=r"(lo.z), "=r"(lo.w), "=r"(hi.x), "=r"(hi.y), "=r"(hi.z), "=r"(hi.w)
+        : "l"(p), "l"(pol));
+}
+__device__ __forceinline__ uint32_t ld_nc_hint(const uint32_t* p, uint64_t pol) {
+    uint32_t v;
+    asm("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ void st_rec_hint(int2* p, int2 v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.v2.s32 [%0], {%1, %2}, %3;" ::"l"(p), "r"(v.x), "r"(v.y), "l"(pol)
+                 : "memory");
+}
+// Cache policies: keep (evict_last) and stream (evict_first) when `hint`,
+// evict_normal for both otherwise.
+__device__ __forceinline__ void walk_policies(int hint, uint64_t& keep, uint64_t& stream) {
+    if (hint) {
+        asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep));
+        asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(stream));
+    } else {
+        asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(keep));
+        stream = keep;
+    }
 }
 
 // Word j (0..3) of the four words c.
@@ -78,24 +106,27 @@ __device__ __forceinline__ uint32_t count_le4(const uint4 t, uint32_t u) {
     return (uint32_t)(t.x <= u) + (uint32_t)(t.y <= u) + (uint32_t)(t.z <= u) + (uint32_t)(t.w <= u);
 }
 
-// One transition from the node of successor word cw (first-sector index, bit
-// 31 set when the node has a summary sector), with draw u: the least slot j
-// whose threshold exceeds u (thresholds do not decrease along the slots, the
-// header slot counts as passed), i.e. successor j - 1, ground if j > deg.
-// Returns that successor's word; *ground is set when the walk is absorbed.
-__device__ __forceinline__ uint32_t hop_sector(const uint32_t* __restrict__ tab, uint32_t cw, uint32_t u,
-                                               bool* ground) {
-    const uint32_t* sec = tab + (size_t)(cw & kSectorMask) * 8u;
+// One transition from the node of successor word cw (node index, bit 31 set
+// when the node has a summary), with draw u: the least slot j whose threshold
+// exceeds u (thresholds do not decrease along the slots, the header slot
+// counts as passed), i.e. successor j - 1, ground if j > deg.  Returns that
+// successor's word; *ground is set when the walk is absorbed.  n2 = 2n, the
+// first summary sector.
+__device__ __forceinline__ uint32_t hop_node(const uint32_t* __restrict__ tab, const uint32_t* __restrict__ gbase,
+                                             uint32_t n2, uint32_t cw, uint32_t u, bool* ground, uint64_t keep,
+                                             uint64_t stream) {
+    const uint32_t node = cw & kNodeMask;
     uint4 t, w;
-    ld_nc8(sec, t, w);
     uint32_t deg, j = 0xFFFFFFFFu, nw = 0u;
     if (cw & kSumFlag) {
-        // summary: deg, the last threshold of groups 0..6
+        // summary and group base together (both kept in L2)
+        ld_nc8_hint(tab + (size_t)(n2 + node) * 8u, t, w, keep);
+        const uint32_t g0 = ld_nc_hint(gbase + node, keep);
         deg = t.x;
         const uint32_t ng = (deg + 4u) >> 2;
         uint32_t g = (uint32_t)(t.y <= u) + (uint32_t)(t.z <= u) + (uint32_t)(t.w <= u) + count_le4(w, u);
         for (; g < ng; ++g) {  // one iteration unless the node has more than seven groups
-            ld_nc8(sec + 8u * (g + 1u), t, w);
+            ld_nc8_hint(tab + (size_t)(g0 + g) * 8u, t, w, stream);
             if (g == 0u) t.x = 0u;
             const uint32_t c = count_le4(t, u);
             if (c < 4u) {
@@ -106,13 +137,15 @@ __device__ __forceinline__ uint32_t hop_sector(const uint32_t* __restrict__ tab,
         }
     } else {
         // group 0 (slot 0's successor word holds deg); group 1 only when u passes group 0
+        const uint32_t* g = tab + (size_t)node * 16u;
+        ld_nc8(g, t, w);
         deg = w.x;
         const uint32_t c0 = count_le4(t, u);
         if (c0 < 4u) {
             j = c0;
             nw = pick4(w, c0);
         } else if (deg >= 4u) {
-            ld_nc8(sec + 8u, t, w);
+            ld_nc8(g + 8u, t, w);
             const uint32_t c1 = count_le4(t, u);
             j = 4u + c1;
             nw = c1 < 4u ? pick4(w, c1) : 0u;
@@ -122,13 +155,11 @@ __device__ __forceinline__ uint32_t hop_sector(const uint32_t* __restrict__ tab,
     return *ground ? 0u : nw;
 }
 
-// First step of a walk from the row with first sector kb, lower degree lo and
-// upper degree up: the successor word of successor lo + m (the row's groups
-// start after its summary sector when it has one).
-__device__ __forceinline__ uint32_t first_successor(const uint32_t* __restrict__ tab, uint32_t kb, uint32_t lo,
-                                                    uint32_t up, uint32_t m) {
+// First step of a walk from the row whose group 0 is sector g0, lower degree
+// lo: the successor word of successor lo + m.
+__device__ __forceinline__ uint32_t first_successor(const uint32_t* __restrict__ tab, uint32_t g0, uint32_t lo,
+                                                    uint32_t m) {
     const uint32_t slot = lo + m + 1u;
-    const uint32_t g0 = kb + (((lo + up + 4u) >> 2) > 2u ? 1u : 0u);
     return __ldg(tab + ((size_t)g0 + (slot >> 2)) * 8u + 4u + (slot & 3u));
 }
 
@@ -143,14 +174,17 @@ __global__ void __launch_bounds__(256) k_walk(const WalkParams P) {
 
     bool active = false;
     int64_t widx = 0;
-    uint32_t k = 0, kb = 0, w = 0, coff = 0, ret = 0;
+    uint32_t k = 0, w = 0, coff = 0, ret = 0;
     // the walking lane's matrix (fixed for a single-matrix launch)
     const uint32_t* tab = P.m0.tab;
-    uint32_t key0 = P.m0.key0, key1 = P.m0.key1, tag = P.m0.tag;
+    const uint32_t* gbase = P.m0.gbase;
+    uint32_t key0 = P.m0.key0, key1 = P.m0.key1, tag = P.m0.tag, n2 = 2u * P.m0.n;
     uint64_t h = 0;
     Philox4 rnd{0u, 0u, 0u, 0u};
     unsigned long long my_hops = 0;
     int32_t my_m = 0;  // matrix whose hops my_hops holds
+    uint64_t keep, stream;
+    walk_policies(P.cache_hint, keep, stream);
 
     for (;;) {
         // ---- refill idle lanes from the warp's pool of walk indices ----
@@ -189,10 +223,12 @@ __global__ void __launch_bounds__(256) k_walk(const WalkParams P) {
                     }
                     const MatWalk& mw = P.mats[m];
                     tab = mw.tab;
+                    gbase = mw.gbase;
                     fthr = mw.fthr;
                     key0 = mw.key0;
                     key1 = mw.key1;
                     tag = mw.tag;
+                    n2 = 2u * mw.n;
                 }
                 k = (uint32_t)info.x;
                 w = (uint32_t)(widx - P.wbase[r]) + (P.wofs ? P.wofs[r] : 0u);
@@ -213,8 +249,7 @@ __global__ void __launch_bounds__(256) k_walk(const WalkParams P) {
                     }
                 }
                 if (m > up - 1u) m = up - 1u;
-                kb = (uint32_t)info.z;
-                coff = first_successor(tab, kb, (uint32_t)info.w, up, m);
+                coff = first_successor(tab, (uint32_t)info.z, (uint32_t)info.w, m);
                 h = 1;
                 ret = 0;
                 active = true;
@@ -228,36 +263,42 @@ __global__ void __launch_bounds__(256) k_walk(const WalkParams P) {
         if (__ballot_sync(kFull, active) == 0u) break;
 
         // ---- one hop of every active lane ----
+        bool stepping = false;
+        uint32_t u = 0u;
         if (active) {
-            int32_t end = 0;
-            bool done = false;
             if (h >= P.max_steps || ((h & 4095u) == 0u && ld_relaxed_u32(&P.st->walk_cap) != 0u)) {
                 // the step cap, or another walk hit it: stop (the build reports the error)
-                end = -2;
-                done = true;
                 if (h >= P.max_steps) atomicAdd(&P.st->walk_cap, 1u);
+                P.rec[widx] = make_int2(-2, (int32_t)(P.record_lengths ? (uint32_t)h : ret));
+                my_hops += h;
+                active = false;
             } else {
                 const uint32_t sidx = (uint32_t)h;
                 if ((sidx & 3u) == 0u) rnd = philox4x32_10(sidx >> 2, w, k, tag, key0, key1);
                 const uint32_t q = sidx & 3u;
-                const uint32_t u = q == 0u ? rnd.v0 : q == 1u ? rnd.v1 : q == 2u ? rnd.v2 : rnd.v3;
-                ++h;
-                bool ground;
-                const uint32_t nw = hop_sector(tab, coff, u, &ground);
-                const uint32_t nb = nw & kSectorMask;
-                if (ground) {
-                    end = -1;
-                    done = true;
-                } else if (nb < kb) {
-                    end = (int32_t)nb;  // home, as its first-sector index (k_rec_nodes converts it)
-                    done = true;
-                } else {
-                    ret += (nb == kb) ? 1u : 0u;
-                    coff = nw;
-                }
+                u = q == 0u ? rnd.v0 : q == 1u ? rnd.v1 : q == 2u ? rnd.v2 : rnd.v3;
+                stepping = true;
+            }
+        }
+        if (stepping) {
+            int32_t end = 0;
+            bool done = false;
+            ++h;
+            bool ground;
+            const uint32_t nw = hop_node(tab, gbase, n2, coff, u, &ground, keep, stream);
+            const uint32_t nb = nw & kNodeMask;
+            if (ground) {
+                end = -1;
+                done = true;
+            } else if (nb < k) {
+                end = (int32_t)nb;  // home
+                done = true;
+            } else {
+                ret += (nb == k) ? 1u : 0u;
+                coff = nw;
             }
             if (done) {
-                P.rec[widx] = make_int2(end, (int32_t)(P.record_lengths ? (uint32_t)h : ret));
+                st_rec_hint(P.rec + widx, make_int2(end, (int32_t)(P.record_lengths ? (uint32_t)h : ret)), stream);
                 my_hops += h;
                 active = false;
             }
@@ -269,35 +310,6 @@ __global__ void __launch_bounds__(256) k_walk(const WalkParams P) {
         my_hops = warp_sum(my_hops);
         if (lane == 0 && my_hops) atomicAdd(P.hops, my_hops);
     }
-}
-
-// The walk kernels write a home end as its first-sector index; this pass turns
-// it into the node index (one warp per walk row; ground -1 and the step-cap
-// mark -2 stay).  Keeping the lookup out of the walk saves a dependent load at
-// the end of every walk.
-__global__ void k_rec_nodes(int32_t nrows, const int64_t* __restrict__ wbase, const int32_t* __restrict__ wmat,
-                            const MatWalk* __restrict__ mats, const int32_t* __restrict__ bnode0, int2* rec) {
-    const int32_t gw = (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int32_t nwarps = (int32_t)((gridDim.x * blockDim.x) >> 5);
-    for (int32_t r = gw; r < nrows; r += nwarps) {
-        const int32_t* bn = wmat ? mats[wmat[r]].bnode : bnode0;
-        for (int64_t i = wbase[r] + lane_id(); i < wbase[r + 1]; i += 32) {
-            int2 v = rec[i];
-            if (v.x >= 0) {
-                v.x = __ldg(bn + v.x);
-                rec[i] = v;
-            }
-        }
-    }
-}
-
-static rw_status rec_nodes(rw_context* ctx, int32_t nrows, const int64_t* wbase, const int32_t* wmat,
-                           const MatWalk* mats, const int32_t* bnode, int2* rec) {
-    if (nrows <= 0) return RW_OK;
-    RW_COUNT_LAUNCH();
-    k_rec_nodes<<<grid_for((int64_t)nrows * 32, 256, ctx->num_sms * 16), 256, 0, ctx->stream>>>(nrows, wbase, wmat,
-                                                                                                 mats, bnode, rec);
-    return check_launch("walk records");
 }
 
 rw_status run_walks(rw_context* ctx, const WalkBatch& wb, const WalkLaunch& wl, int2* rec,
@@ -330,6 +342,7 @@ rw_status run_walks(rw_context* ctx, const WalkBatch& wb, const WalkLaunch& wl, 
     P.st = ctx->d_status;
     P.max_steps = wl.max_steps;
     P.record_lengths = wl.record_lengths;
+    P.cache_hint = wb.table_bytes * 4u > (uint64_t)ctx->l2_bytes * 3u ? 1 : 0;
     P.m0 = wb.m0;
     int per_sm = ctx->opt.walk_blocks_per_sm;
     if (per_sm <= 0) {
@@ -347,8 +360,6 @@ rw_status run_walks(rw_context* ctx, const WalkBatch& wb, const WalkLaunch& wl, 
     if (multi) k_walk<true><<<(unsigned)blocks, 256, 0, s>>>(P);
     else k_walk<false><<<(unsigned)blocks, 256, 0, s>>>(P);
     if ((rc = check_launch("walk kernel"))) return rc;
-    if ((rc = rec_nodes(ctx, wb.nrows, wb.wbase, multi ? wb.wmat : nullptr, wb.mats, wb.m0.bnode, rec)))
-        return rc;
     if (ms) {
         cudaEventRecord(ctx->ev[1], s);
         cudaEventSynchronize(ctx->ev[1]);
@@ -371,11 +382,10 @@ rw_status run_walks(rw_context* ctx, const WalkBatch& wb, const WalkLaunch& wl, 
 // Sub-walks of one start row never overlap (a start is popped before the same
 // node can be pushed again), as the paper requires.  Finished sub-walks go to
 // the warp's shared-memory stage and from there, in bulk, to the global
-// extra-record arrays {start, end or -1, returns}, both as first-sector indices
-// (they order like the nodes; the bucketing turns them into node indices).
+// extra-record arrays {start node, end node or -1, returns}.
 struct ReuseParams {
-    int32_t* xnode;  // first-sector index of the start node
-    int32_t* xend;   // first-sector index of the end node, -1 ground
+    int32_t* xnode;  // start node
+    int32_t* xend;   // end node, -1 ground
     uint32_t* xret;
     unsigned long long* xcount;  // records produced (may exceed xcap: then none past xcap is written)
     int64_t xcap;
@@ -399,12 +409,15 @@ __global__ void __launch_bounds__(256) k_walk_reuse(const WalkParams P, const Re
 
     bool active = false;
     int64_t widx = 0;
-    uint32_t k = 0, kb = 0, w = 0, coff = 0, ret = 0;
+    uint32_t k = 0, w = 0, coff = 0, ret = 0;
     const uint32_t* tab = P.m0.tab;
-    const uint32_t key0 = P.m0.key0, key1 = P.m0.key1, tag = P.m0.tag;
+    const uint32_t* gbase = P.m0.gbase;
+    const uint32_t key0 = P.m0.key0, key1 = P.m0.key1, tag = P.m0.tag, n2 = 2u * P.m0.n;
     uint64_t h = 0;
     Philox4 rnd{0u, 0u, 0u, 0u};
     unsigned long long my_hops = 0;
+    uint64_t keep, stream;
+    walk_policies(P.cache_hint, keep, stream);
 
     uint2 stk[CAP];      // candidates below the top: {node, returns}
     int32_t depth = 0;   // candidates above k (the top one in registers)
@@ -473,12 +486,11 @@ __global__ void __launch_bounds__(256) k_walk_reuse(const WalkParams P, const Re
                     }
                 }
                 if (m > up - 1u) m = up - 1u;
-                kb = (uint32_t)info.z;
-                coff = first_successor(tab, kb, (uint32_t)info.w, up, m);
+                coff = first_successor(tab, (uint32_t)info.z, (uint32_t)info.w, m);
                 h = 1;
                 ret = 0;
                 depth = 1;  // the first step's upper neighbour starts the stack
-                top = coff & kSectorMask;
+                top = coff & kNodeMask;
                 top_ret = 0;
                 fresh = true;
                 active = true;
@@ -495,7 +507,7 @@ __global__ void __launch_bounds__(256) k_walk_reuse(const WalkParams P, const Re
         // outcome: 0 idle, 1 moved to node `to`, 2 ended at `to` (home, or -1 ground),
         // 3 stopped (step cap or stack overflow)
         int outcome = 0;
-        int32_t to = 0;        // first-sector index of the next node (-1: ground)
+        int32_t to = 0;        // the next node (-1: ground)
         uint32_t to_word = 0;  // its successor word
         if (active) {
             if (h >= P.max_steps ||
@@ -509,14 +521,14 @@ __global__ void __launch_bounds__(256) k_walk_reuse(const WalkParams P, const Re
                 const uint32_t u = q == 0u ? rnd.v0 : q == 1u ? rnd.v1 : q == 2u ? rnd.v2 : rnd.v3;
                 ++h;
                 bool ground;
-                to_word = hop_sector(tab, coff, u, &ground);
-                const uint32_t nb = to_word & kSectorMask;
+                to_word = hop_node(tab, gbase, n2, coff, u, &ground, keep, stream);
+                const uint32_t nb = to_word & kNodeMask;
                 if (ground) {
                     outcome = 2;
                     to = -1;
                 } else {
                     to = (int32_t)nb;
-                    outcome = nb < kb ? 2 : 1;
+                    outcome = nb < k ? 2 : 1;
                 }
             }
         }
@@ -546,7 +558,7 @@ __global__ void __launch_bounds__(256) k_walk_reuse(const WalkParams P, const Re
             }
         }
         if (outcome == 1) {
-            if ((uint32_t)to == kb) {
+            if ((uint32_t)to == k) {
                 ++ret;  // every candidate is above k, so the stack is empty here
                 fresh = false;
             } else if (depth > 0 && (uint32_t)to == top) {
@@ -578,21 +590,20 @@ __global__ void __launch_bounds__(256) k_walk_reuse(const WalkParams P, const Re
 
 // Extra records -> per walk row: counts, then a scatter into row order (the
 // order inside a row is immaterial: the merge only sums them).
-__global__ void k_extra_count(int64_t cnt, const int32_t* __restrict__ xnode, const int32_t* __restrict__ bnode,
-                              const uint32_t* __restrict__ wflag, unsigned long long* rows) {
+__global__ void k_extra_count(int64_t cnt, const int32_t* __restrict__ xnode, const uint32_t* __restrict__ wflag,
+                              unsigned long long* rows) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x)
-        atomicAdd(rows + wflag[bnode[xnode[i]]], 1ull);
+        atomicAdd(rows + wflag[xnode[i]], 1ull);
 }
 
 __global__ void k_extra_scatter(int64_t cnt, const int32_t* __restrict__ xnode, const int32_t* __restrict__ xend,
-                                const uint32_t* __restrict__ xret, const int32_t* __restrict__ bnode,
-                                const uint32_t* __restrict__ wflag, const int64_t* __restrict__ xbase,
-                                unsigned long long* fill, int2* xrec) {
+                                const uint32_t* __restrict__ xret, const uint32_t* __restrict__ wflag,
+                                const int64_t* __restrict__ xbase, unsigned long long* fill, int2* xrec) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t r = wflag[bnode[xnode[i]]];
+        const uint32_t r = wflag[xnode[i]];
         const int64_t p = xbase[r] + (int64_t)atomicAdd(fill + r, 1ull);
         const int32_t e = xend[i];
-        xrec[p] = make_int2(e >= 0 ? bnode[e] : -1, (int32_t)xret[i]);
+        xrec[p] = make_int2(e >= 0 ? e : -1, (int32_t)xret[i]);
     }
 }
 
@@ -644,6 +655,7 @@ rw_status run_walks_reuse(rw_context* ctx, const WalkBatch& wb, const WalkLaunch
     P.st = ctx->d_status;
     P.max_steps = wl.max_steps;
     P.record_lengths = 0;
+    P.cache_hint = wb.table_bytes * 4u > (uint64_t)ctx->l2_bytes * 3u ? 1 : 0;
     P.m0 = wb.m0;
     int64_t cap = (int64_t)(ctx->reuse_ratio * (double)wb.total) + (1 << 16);
     int stack = 64;
@@ -665,7 +677,6 @@ rw_status run_walks_reuse(rw_context* ctx, const WalkBatch& wb, const WalkLaunch
         if (ms) cudaEventRecord(ctx->ev[0], s);
         rc = stack == 64 ? launch_reuse<64>(ctx, P, R) : launch_reuse<1024>(ctx, P, R);
         if (rc) return rc;
-        if ((rc = rec_nodes(ctx, T.n_walk_rows, wb.wbase, nullptr, nullptr, T.bnode, rec))) return rc;
         if (ms) cudaEventRecord(ctx->ev[1], s);
         if ((rc = check_cuda(cudaMemcpyAsync(h64, xcount, 8, cudaMemcpyDeviceToHost, s), "copy")) ||
             (rc = check_cuda(cudaMemcpyAsync(h64 + 1, overflow, 4, cudaMemcpyDeviceToHost, s), "copy")) ||
@@ -712,7 +723,7 @@ rw_status run_walks_reuse(rw_context* ctx, const WalkBatch& wb, const WalkLaunch
     const int g = grid_for(X.count, 256, ctx->num_sms * 16);
     if (X.count > 0) {
         RW_COUNT_LAUNCH();
-        k_extra_count<<<g, 256, 0, s>>>(X.count, X.xnode, T.bnode, T.walk_flag, rows);
+        k_extra_count<<<g, 256, 0, s>>>(X.count, X.xnode, T.walk_flag, rows);
         if ((rc = check_launch("extra counts"))) return rc;
     }
     if ((rc = check_cuda(scan_i64(reinterpret_cast<const int64_t*>(rows), X.xbase, nw, s, pool), "scan")) ||
@@ -720,8 +731,7 @@ rw_status run_walks_reuse(rw_context* ctx, const WalkBatch& wb, const WalkLaunch
         return rc;
     if (X.count > 0) {
         RW_COUNT_LAUNCH();
-        k_extra_scatter<<<g, 256, 0, s>>>(X.count, X.xnode, X.xend, X.xret, T.bnode, T.walk_flag, X.xbase, rows,
-                                          X.xrec);
+        k_extra_scatter<<<g, 256, 0, s>>>(X.count, X.xnode, X.xend, X.xret, T.walk_flag, X.xbase, rows, X.xrec);
         if ((rc = check_launch("extra scatter"))) return rc;
     }
     return RW_OK;

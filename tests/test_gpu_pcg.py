@@ -127,10 +127,17 @@ def test_pcg_fp32_mixed_reaches_tolerance(P, ctx):
     assert true < cfg["tol"]
     x64, it64, rr64, _ = oracle.pcg(A, ref, b[:, 0], cfg["tol"], 1000)
     xm, itm, rrm, _ = oracle.pcg(A, ref, b[:, 0], cfg["tol"], 1000, mixed=True)
+    # the oracle's FP32 mode is the same algorithm rounded in another order:
+    # equal iteration counts and x within 8 sqrt(m) u max|x| element-wise (the
+    # bound of tests/test_gpu_fullsize.py, m the longest row of A, Y and Y^T)
+    m = int(max(np.diff(A.rowptr).max(), np.diff(ref["rowptr"]).max(),
+                np.bincount(ref["col"], minlength=A.n).max()))
+    assert int(its[0]) == itm, (its[0], itm)
+    assert np.abs(xg - xm).max() <= 8.0 * np.sqrt(m) * 2.0 ** -24 * np.abs(xm).max()
+    # the error against the FP64 solution is that of the oracle's FP32 mode
     err = np.linalg.norm(xg - x64) / np.linalg.norm(x64)
-    # both reach ||r|| < 1e-6 ||b||; kappa(A) bounds the solution error
-    assert err < 1e-3, err
-    assert abs(int(its[0]) - itm) <= max(2, itm // 5)
+    errm = np.linalg.norm(xm - x64) / np.linalg.norm(x64)
+    assert err <= max(2.0 * errm, 1e-9), (err, errm)
     F.destroy()
 
 
@@ -238,8 +245,16 @@ def test_batch_fp32_mixed(P, ctx):
         true = np.linalg.norm(bs[m] - A.to_scipy() @ xg, axis=0) / np.linalg.norm(bs[m], axis=0)
         assert np.all(true < 1e-6)
         ref = oracle.build_factor(A, 60, m + 1, 1e-3, matrix_index=m)
-        xr, itr, rr, _ = oracle.pcg(A, ref, bs[m][:, 0], 1e-6, 1000, mixed=True)
-        assert abs(int(its[m, 0]) - itr) <= max(2, itr // 5)
+        mm = int(max(np.diff(A.rowptr).max(), np.diff(ref["rowptr"]).max(),
+                     np.bincount(ref["col"], minlength=A.n).max() if ref["nnz"] else 1))
+        for j in range(bs[m].shape[1]):
+            xr, itr, rr, _ = oracle.pcg(A, ref, bs[m][:, j], 1e-6, 1000, mixed=True)
+            # the batched engine's per-system sums run in another order than
+            # the single solve's: iteration counts within one, x within the
+            # FP32 bound once both stopped at the same count
+            assert abs(int(its[m, j]) - itr) <= 1, (m, j, its[m, j], itr)
+            if int(its[m, j]) == itr:
+                assert np.abs(xg[:, j] - xr).max() <= 8.0 * np.sqrt(mm) * 2.0 ** -24 * np.abs(xr).max()
     for F in Fs:
         F.destroy()
 
