@@ -148,6 +148,7 @@ extern "C" {
 rw_status rw_adaptive_budget(rw_context* ctx, const rw_csr* A, uint64_t seed, double delta, double z,
                              uint32_t min_walks, uint32_t max_walks, int32_t max_rounds, uint32_t* d_budget,
                              int32_t* h_rounds) {
+    NvtxRange nvtx_range("rw_adaptive_budget");
     if (!ctx || !d_budget || !(delta > 0.0) || !(z > 0.0) || min_walks < 2 || max_walks < min_walks ||
         max_walks > 65535u || max_rounds < 1) {
         set_error("rw_adaptive_budget: bad arguments (delta, z > 0; 2 <= min_walks <= max_walks <= 65535; "

@@ -440,6 +440,7 @@ rw_status pcg_batch_t(rw_context* ctx, rw_batch* B, const double* const* d_b, do
                       int nrhs, double tol, int max_iter, rw_pcg_stats* stats, int32_t* h_iters,
                       double* h_relres, const T* Aval, const T* yv, const T* ytv, const T* dv,
                       const T* tv_fwd, const T* tv_bwd, bool mixed, Pool& sc) {
+    NvtxRange nvtx_range("rw_pcg_batch");
     cudaStream_t s = ctx->stream;
     const int32_t N = B->N;
     const int nmat = B->nmat;
@@ -640,6 +641,7 @@ extern "C" {
 
 rw_status rw_batch_create(rw_context* ctx, int32_t nmat, const rw_csr* As, const rw_factor* const* Fs,
                           rw_batch** out) {
+    NvtxRange nvtx_range("rw_batch_create");
     if (!ctx || nmat < 1 || !As || !Fs || !out) {
         set_error("rw_batch_create: bad arguments");
         return RW_ERR_ARG;

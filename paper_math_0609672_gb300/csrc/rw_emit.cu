@@ -441,6 +441,7 @@ __global__ void k_copy_rows(int32_t nw, const int4* __restrict__ wrow,
 rw_status emit_factor(rw_context* ctx, const rw_csr* A, const Tables& T, const WalkSpace& ws,
                       const int2* rec, const Extras* X, double drop_tol, FactorOut& fo, Pool& pool,
                       Pool& scratch, float* ms_merge, float* ms_emit) {
+    NvtxRange nvtx_range("rw_merge_emit");
     cudaStream_t s = ctx->stream;
     const int32_t n = A->n, nw = T.n_walk_rows;
     rw_status rc;
@@ -944,6 +945,7 @@ rw_status radix_sort_pairs(rw_context* ctx, uint32_t* k0, uint32_t* v0, uint32_t
 
 rw_status transpose_factor(rw_context* ctx, int32_t n, const FactorOut& fo, int64_t* yt_rp,
                            int32_t* yt_col, double* yt_val, Pool& scratch) {
+    NvtxRange nvtx_range("rw_transpose");
     cudaStream_t s = ctx->stream;
     const int64_t nnz = fo.nnz;
     rw_status rc;

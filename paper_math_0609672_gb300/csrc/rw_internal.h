@@ -7,6 +7,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "rw_common.cuh"
 #include "rwpc.h"
 
@@ -27,6 +29,17 @@ struct rw_context {
 };
 
 namespace rw {
+
+// NVTX range over a host scope: a profiler attributes the kernels launched
+// inside it to that phase of the library (for example
+// ncu --nvtx --nvtx-include "rw_walk/").  Without a profiler attached the
+// calls return at once.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 constexpr int kFeatures = RW_NUM_FEATURES;
 constexpr int kFeatStride = RW_FEATURE_STRIDE;

@@ -668,6 +668,7 @@ __global__ void k_norm_final(int32_t n, const uint32_t* __restrict__ frac,
 // Host side
 // ---------------------------------------------------------------------------
 static rw_status features_run(rw_context* ctx, const rw_csr* A, float* feat) {
+    NvtxRange nvtx_range("rw_features");
     Pool sc(ctx);
     int32_t* ndeg = alloc_n<int32_t>(sc, A->n);
     double* exr = alloc_n<double>(sc, A->n);
@@ -703,6 +704,7 @@ static rw_status pilot_cost(rw_context* ctx, const rw_csr* A, uint32_t walks, ui
 
 static rw_status pilot_run(rw_context* ctx, const rw_csr* A, uint32_t walks, uint64_t seed, int quantity,
                            float* mean, float* sd, float* label, float* has) {
+    NvtxRange nvtx_range("rw_pilot");
     cudaStream_t s = ctx->stream;
     Pool scratch(ctx);
     Tables T;
@@ -744,6 +746,7 @@ static rw_status pilot_run(rw_context* ctx, const rw_csr* A, uint32_t walks, uin
 
 static rw_status normalize_run(rw_context* ctx, const rw_csr* A, const float* w, double mean_budget,
                                uint32_t min_budget, uint32_t* budget, Pool& sc) {
+    NvtxRange nvtx_range("rw_budget_normalize");
     cudaStream_t s = ctx->stream;
     const int32_t n = A->n;
     const int blocks = grid_for(n, 256, ctx->num_sms * 4);
@@ -1050,6 +1053,7 @@ rw_status rw_mlp_params(rw_mlp* M, float* h_params, float* h_norm, const float* 
 
 rw_status rw_mlp_predict(rw_context* ctx, const rw_mlp* M, const float* d_feat, int64_t nrows,
                          float* d_out) {
+    NvtxRange nvtx_range("rw_mlp_predict");
     if (!ctx || !M || !d_feat || !d_out || nrows < 0) {
         set_error("rw_mlp_predict: bad arguments");
         return RW_ERR_ARG;
@@ -1090,6 +1094,7 @@ rw_status rw_mlp_gradient(rw_context* ctx, rw_mlp* M, const float* d_feat, const
 rw_status rw_mlp_train(rw_context* ctx, rw_mlp* M, const float* d_feat, const float* d_label,
                        const float* d_mask, int64_t nrows, int32_t epochs, int32_t batch, float lr,
                        uint64_t seed, int32_t set_norm, float* h_epoch_loss) {
+    NvtxRange nvtx_range("rw_mlp_train");
     if (!ctx || !M || !d_feat || !d_label || !d_mask || nrows < 1 || epochs < 0 || batch < 16 ||
         !(lr > 0.f) || nrows > 0xFFFFFFFFll) {
         set_error("rw_mlp_train: bad arguments");

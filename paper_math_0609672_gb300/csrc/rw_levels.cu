@@ -103,6 +103,7 @@ static rw_status level_order(rw_context* ctx, int32_t n, const int* lev, int nle
 
 rw_status compute_levels_pair(rw_context* ctx, int32_t n, const LevelDag& fwd, const LevelDag& bwd, Pool& keep,
                               Pool& scratch) {
+    NvtxRange nvtx_range("rw_levels");
     cudaStream_t s = ctx->stream;
     *fwd.depth = 0;
     *bwd.depth = 0;

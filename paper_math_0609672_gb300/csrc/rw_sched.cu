@@ -120,6 +120,7 @@ rw_status build_schedule(rw_context* ctx, int32_t n, const int64_t* rp, const in
                          const double* val, const float* val32, const int32_t* order,
                          const int64_t* lptr_dev, int32_t depth, SolveSchedule& S, Pool& pool,
                          Pool& scratch) {
+    NvtxRange nvtx_range("rw_schedule");
     cudaStream_t s = ctx->stream;
     rw_status rc;
     const int thin_levels = ctx->opt.thin_levels;
@@ -1371,6 +1372,7 @@ template <typename T>
 rw_status solve_runs(rw_context* ctx, const SolveSchedule& S, const int64_t* rp, const int32_t* col,
                      const T* val, const T* tval, const T* rhs, const T* scale, T* x, int nrhs,
                      unsigned* bar, bool backward) {
+    NvtxRange nvtx_range(backward ? "rw_solve_bwd" : "rw_solve_fwd");
     const int mode = backward && ctx->opt.solve_mode_bwd >= 0 ? ctx->opt.solve_mode_bwd : ctx->opt.solve_mode;
     int nr = 1;
     while (nr < nrhs) nr <<= 1;

@@ -376,6 +376,7 @@ static rw_status launch_spmv(rw_context* ctx, int32_t n, const int32_t* rp, cons
 template <typename T>
 rw_status spmv_launch(rw_context* ctx, int32_t n, const int32_t* rp, const int32_t* col, const T* val,
                       const T* x, T* y, int nrhs) {
+    NvtxRange nvtx_range("rw_spmv");
     return launch_spmv<T, T>(ctx, n, rp, col, val, x, y, nrhs, nullptr);
 }
 template rw_status spmv_launch<double>(rw_context*, int32_t, const int32_t*, const int32_t*, const double*,
@@ -409,6 +410,7 @@ const float* thin_values<float>(const SolveSchedule& S) { return S.tval32; }
 template <typename T>
 static rw_status precond_t(rw_context* ctx, const FactorView& F, const T* yv, const T* ytv,
                            const T* d, const T* r, T* w, T* z, int nrhs, SolveTimes* tm = nullptr) {
+    NvtxRange nvtx_range("rw_precond");
     if (tm && tm->on) cudaEventRecord(ctx->ev[5], ctx->stream);
     rw_status rc = solve_runs<T>(ctx, *F.bwd_sched, F.yt_rp, F.yt_col, ytv,
                                  thin_values<T>(*F.bwd_sched), r, nullptr, w, nrhs, F.bar, true);
@@ -464,6 +466,7 @@ static rw_status pcg_t(rw_context* ctx, const rw_csr* A, const FactorView& F, co
                        double* x, int nrhs, double tol, int max_iter, rw_pcg_stats* stats,
                        int32_t* h_iters, double* h_relres, Pool& sc, const T* Aval, const T* yv,
                        const T* ytv, const T* dv, bool mixed) {
+    NvtxRange nvtx_range("rw_pcg");
     cudaStream_t s = ctx->stream;
     const int32_t n = A->n;
     const int64_t cnt = (int64_t)n * nrhs;

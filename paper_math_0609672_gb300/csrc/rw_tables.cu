@@ -247,6 +247,7 @@ __global__ void k_walk_rows(int32_t n, const uint32_t* __restrict__ widx,
 }
 
 rw_status build_tables(rw_context* ctx, const rw_csr* A, Tables& T, Pool& pool) {
+    NvtxRange nvtx_range("rw_tables");
     const int32_t n = A->n;
     cudaStream_t s = ctx->stream;
     T.n = n;

@@ -460,6 +460,7 @@ rw_status rw_probe_latency(rw_context* ctx, int32_t iters, double* h_handoff_ns,
 
 rw_status rw_autotune(rw_context* ctx, const rw_csr* A, const rw_factor* F, int32_t nrhs, rw_precision prec,
                       const char* cache_path, rw_options* out, float* h_ms) {
+    NvtxRange nvtx_range("rw_autotune");
     if (!ctx || !A || !F || nrhs < 1 || nrhs > 16 || (prec != RW_FP64 && prec != RW_FP32_MIXED)) {
         set_error("rw_autotune: bad arguments");
         return RW_ERR_ARG;
@@ -486,6 +487,7 @@ rw_status rw_autotune(rw_context* ctx, const rw_csr* A, const rw_factor* F, int3
 
 rw_status rw_batch_autotune(rw_context* ctx, const rw_batch* B, int32_t nrhs, rw_precision prec,
                             const char* cache_path, rw_options* out, float* h_ms) {
+    NvtxRange nvtx_range("rw_autotune");
     if (!ctx || !B || nrhs < 1 || nrhs > 16 || (prec != RW_FP64 && prec != RW_FP32_MIXED)) {
         set_error("rw_batch_autotune: bad arguments");
         return RW_ERR_ARG;

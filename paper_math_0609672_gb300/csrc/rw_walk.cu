@@ -314,6 +314,7 @@ __global__ void __launch_bounds__(256) k_walk(const WalkParams P) {
 
 rw_status run_walks(rw_context* ctx, const WalkBatch& wb, const WalkLaunch& wl, int2* rec,
                     unsigned long long* d_hops, Pool& pool, float* ms) {
+    NvtxRange nvtx_range("rw_walk");
     cudaStream_t s = ctx->stream;
     unsigned long long* cursor = alloc_n<unsigned long long>(pool, 1);
     if (!cursor) return RW_ERR_ALLOC;
@@ -627,6 +628,7 @@ static rw_status launch_reuse(rw_context* ctx, const WalkParams& P, const ReuseP
 
 rw_status run_walks_reuse(rw_context* ctx, const WalkBatch& wb, const WalkLaunch& wl, const Tables& T, int2* rec,
                           unsigned long long* d_hops, Pool& pool, Pool& xpool, float* ms, Extras& X) {
+    NvtxRange nvtx_range("rw_walk_reuse");
     cudaStream_t s = ctx->stream;
     const int32_t nw = T.n_walk_rows;
     rw_status rc;
