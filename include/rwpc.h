@@ -165,6 +165,10 @@ typedef struct {
     float phase_ms[8];         /* tables, walk, merge, emit, transpose, levels, fp32, total */
     int64_t kernel_launches;   /* kernels launched by the build */
     int64_t extra_walks;       /* walk reuse: sub-walks counted besides the simulated walks */
+    const int32_t* fwd_order;  /* [n] rows of Y z = v by level (level 0 first; any order inside a level) */
+    const int64_t* fwd_level_ptr; /* [fwd_levels+1] level l = fwd_order[ptr[l] .. ptr[l+1]) */
+    const int32_t* bwd_order;  /* the same for Y^T w = r */
+    const int64_t* bwd_level_ptr;
 } rw_factor_desc;
 
 typedef struct {

@@ -78,7 +78,8 @@ class rw_factor_desc_t(ctypes.Structure):
                 ("walk_base", _c_void_p), ("records", _c_void_p), ("n_walk_rows", _i32),
                 ("total_walks", _i64), ("total_hops", _u64), ("fwd_levels", _i32),
                 ("bwd_levels", _i32), ("phase_ms", ctypes.c_float * 8), ("kernel_launches", _i64),
-                ("extra_walks", _i64)]
+                ("extra_walks", _i64), ("fwd_order", _c_void_p), ("fwd_level_ptr", _c_void_p),
+                ("bwd_order", _c_void_p), ("bwd_level_ptr", _c_void_p)]
 
 
 class rw_pcg_stats_t(ctypes.Structure):
@@ -351,6 +352,10 @@ class Factor:
             "walks": _dev_tensor(d.walks, n, "<u4"),
             "visits": _dev_tensor(d.visits, n, "<u8"),
             "ground": _dev_tensor(d.ground, n, "<u4"),
+            "fwd_order": _dev_tensor(d.fwd_order, n, "<i4"),
+            "fwd_level_ptr": _dev_tensor(d.fwd_level_ptr, d.fwd_levels + 1, "<i8"),
+            "bwd_order": _dev_tensor(d.bwd_order, n, "<i4"),
+            "bwd_level_ptr": _dev_tensor(d.bwd_level_ptr, d.bwd_levels + 1, "<i8"),
         }
         if d.y_val32:
             out["y_val32"] = _dev_tensor(d.y_val32, nnz, "<f4")

@@ -291,6 +291,10 @@ rw_status rw::complete_factor(rw_context* ctx, rw_factor* F, const FactorOut& fo
                                   scratch)))
         return rc;
     if (timing) cudaEventRecord(ctx->ev[13], s);
+    d.fwd_order = F->fwd_order;
+    d.fwd_level_ptr = fwd_lptr;
+    d.bwd_order = F->bwd_order;
+    d.bwd_level_ptr = bwd_lptr;
     if (ctx->opt.store_fp32) {
         y32 = alloc_n<float>(F->pool, fo.nnz);
         yt32 = alloc_n<float>(F->pool, fo.nnz);

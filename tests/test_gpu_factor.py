@@ -214,6 +214,38 @@ def test_transpose_and_levels(P, ctx):
                                  n - 1 - Yt.indices)), shape=(n, n))))
     assert t["bwd_levels"] == rev.max() + 1
     assert np.allclose(t["y_val32"], t["y_val"].astype(np.float32), rtol=0, atol=0)
+    # every row's level, not only the depth: the rows of level l are fwd_order[ptr[l] .. ptr[l+1])
+    check_level_order(t["fwd_order"], t["fwd_level_ptr"], levels_of(n, t["y_row_ptr"], t["y_col"]))
+    check_level_order(t["bwd_order"], t["bwd_level_ptr"], rev[::-1])
+
+
+def check_level_order(order, ptr, lev):
+    """order lists every row once, grouped by level as ptr says, and each row's
+    group is its longest-path level lev."""
+    n = lev.size
+    assert ptr.size == lev.max() + 2 and ptr[0] == 0 and ptr[-1] == n
+    assert np.all(np.diff(ptr) > 0)
+    assert np.array_equal(np.sort(order), np.arange(n))
+    got = np.repeat(np.arange(ptr.size - 1), np.diff(ptr))
+    assert np.array_equal(lev[order], got)
+
+
+def test_levels_wide_and_deep(P, ctx):
+    """Level order of the 27-point grid (wide levels, several frontier
+    rounds with thousands of rows) and of a 2D grid with long-range edges."""
+    import scipy.sparse as sp
+    for A in (W.make_config(5, scale=0.125)["A"], W.make_config(3, scale=0.05)["A"]):
+        t = gpu_factor(P, ctx, A, 40, 7, 1e-3)
+        n = A.n
+        lf = levels_of(n, t["y_row_ptr"], t["y_col"])
+        check_level_order(t["fwd_order"], t["fwd_level_ptr"], lf)
+        Y = sp.csr_matrix((t["y_val"], t["y_col"], t["y_row_ptr"]), shape=(n, n))
+        # backward DAG in reversed numbering: row n-1-c depends on n-1-k for every Y_kc
+        R = sp.csr_matrix((np.ones(Y.nnz), (n - 1 - Y.indices, n - 1 - np.repeat(np.arange(n), np.diff(Y.indptr)))),
+                          shape=(n, n))
+        R.sort_indices()
+        lb = levels_of(n, R.indptr, R.indices)[::-1]
+        check_level_order(t["bwd_order"], t["bwd_level_ptr"], lb)
 
 
 def test_edge_cases(P, ctx):
