@@ -130,6 +130,9 @@ typedef struct {
                                 the call returns RW_ERR_TIMEOUT; 0 = 2^20 (about a second at L2
                                 latency; default 0).  A small value makes waits give up early: for
                                 testing the timeout path, never for results */
+    int32_t thin_lanes;      /* thin runs on one block: lanes per row, 8, 16 or 32 (0 = 32);
+                                fewer lanes let one FP64 instruction serve several rows
+                                (default 0) */
 } rw_options;
 
 typedef struct rw_context rw_context;

@@ -66,7 +66,7 @@ class rw_options_t(ctypes.Structure):
                 ("cluster_size", _i32), ("solve_mode", _i32), ("reuse", _i32),
                 ("solve_mode_bwd", _i32),
                 ("thin_levels", _i32), ("thin_cluster", _i32), ("adapt_ahead", _i32),
-                ("thin_flags", _i32), ("spin_limit", _i32)]
+                ("thin_flags", _i32), ("spin_limit", _i32), ("thin_lanes", _i32)]
 
 
 class rw_factor_desc_t(ctypes.Structure):
@@ -711,7 +711,7 @@ def pcg_solve_batch(ctx, B, bs, xs, tol, max_iter, prec=RW_FP64):
 # ---------------------------------------------------------------------------
 
 _TUNED = ("solve_mode", "solve_mode_bwd", "wide_slices", "solve_blocks_per_sm", "cluster_width", "spmv_slices",
-          "thin_cluster", "thin_flags")
+          "thin_cluster", "thin_flags", "thin_lanes")
 
 
 def _tune_result(ctx, opt, ms):

@@ -758,6 +758,87 @@ __global__ void k_sort_rows_warp(int32_t n, const int64_t* __restrict__ trp, con
     }
 }
 
+// Rows of at most 256 entries, one warp per row, keys in registers: entry e
+// of the row becomes the 32-bit key (k << ibits) | e (k < 2^(32-ibits),
+// e < 2^ibits), so sorting the keys alone orders the row by k, and the value
+// of each sorted entry is read back by its index.  Element t * 32 + lane lives
+// in register t of the lane: partners closer than 32 are exchanged by a
+// shuffle, farther ones inside the lane (bitonic network, fully unrolled).
+template <int EPL>
+__device__ __forceinline__ void reg_bitonic(uint32_t (&v)[EPL], int lane) {
+    constexpr int P = 32 * EPL;
+#pragma unroll
+    for (int k = 2; k <= P; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 32) {
+#pragma unroll
+                for (int t = 0; t < EPL; ++t) {
+                    const int t2 = t ^ (j >> 5);
+                    if (t2 > t) {
+                        const bool asc = ((t * 32 + lane) & k) == 0;
+                        const uint32_t a = v[t], b = v[t2];
+                        v[t] = asc ? min(a, b) : max(a, b);
+                        v[t2] = asc ? max(a, b) : min(a, b);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int t = 0; t < EPL; ++t) {
+                    const uint32_t o = __shfl_xor_sync(kFull, v[t], j);
+                    const bool asc = ((t * 32 + lane) & k) == 0;
+                    const bool low = (lane & j) == 0;
+                    v[t] = (low == asc) ? min(v[t], o) : max(v[t], o);
+                }
+            }
+        }
+    }
+}
+
+template <int EPL>
+__device__ __forceinline__ void sort_row_reg(int64_t s, int64_t L, const TRec* __restrict__ tr, int32_t* tcol,
+                                             double* tval, int ibits, int lane) {
+    uint32_t v[EPL];
+#pragma unroll
+    for (int t = 0; t < EPL; ++t) {
+        const int e = t * 32 + lane;
+        v[t] = e < L ? (((uint32_t)tr[s + e].k << ibits) | (uint32_t)e) : 0xFFFFFFFFu;
+    }
+    reg_bitonic<EPL>(v, lane);
+    const uint32_t imask = (1u << ibits) - 1u;
+#pragma unroll
+    for (int t = 0; t < EPL; ++t) {
+        const int e = t * 32 + lane;
+        if (e < L) {
+            tcol[s + e] = (int32_t)(v[t] >> ibits);
+            tval[s + e] = tr[s + (v[t] & imask)].v;
+        }
+    }
+}
+
+// Rows of at most 256 entries sorted in registers (key packing needs
+// n <= 2^(32 - ibits), ibits >= 8); longer rows listed for the shared-memory
+// sorts by size class, as in k_sort_rows_warp.
+__global__ void __launch_bounds__(256) k_sort_rows_reg(int32_t n, const int64_t* __restrict__ trp,
+                                                       const TRec* __restrict__ tr, int32_t* tcol, double* tval,
+                                                       int32_t* lists, int32_t* counts, int ibits) {
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int lane = (int)lane_id();
+    for (int64_t c = gw; c < n; c += nw) {
+        const int64_t s = trp[c], L = trp[c + 1] - s;
+        if (L == 0) continue;
+        if (L <= 32) sort_row_reg<1>(s, L, tr, tcol, tval, ibits, lane);
+        else if (L <= 64) sort_row_reg<2>(s, L, tr, tcol, tval, ibits, lane);
+        else if (L <= 128) sort_row_reg<4>(s, L, tr, tcol, tval, ibits, lane);
+        else if (L <= 256) sort_row_reg<8>(s, L, tr, tcol, tval, ibits, lane);
+        else if (lane == 0) {
+            const int cls = L <= kSortWarp ? 0 : L <= kSortSmem ? 1 : 2;
+            lists[(int64_t)cls * n + atomicAdd(&counts[cls], 1)] = (int32_t)c;
+        }
+    }
+}
+
 struct WarpSync {
     __device__ void operator()() const { __syncwarp(); }
 };
@@ -972,8 +1053,14 @@ rw_status transpose_factor(rw_context* ctx, int32_t n, const FactorOut& fo, int6
     const int wblocks = grid_for((int64_t)n * 32, 256, ctx->num_sms * 16);
     RW_COUNT_LAUNCH();
     k_transpose_place<<<wblocks, 256, 0, s>>>(n, fo.y_rp, fo.y_col, fo.y_val, fill, tr);
+    // packed 32-bit keys (k, entry) when k fits beside 8 or more index bits
+    int kbits = 1;
+    while (kbits < 32 && (1ll << kbits) < (int64_t)n) ++kbits;
     RW_COUNT_LAUNCH();
-    k_sort_rows_warp<<<wblocks, 256, 0, s>>>(n, yt_rp, tr, yt_col, yt_val, lists, counts);
+    if (kbits <= 24)
+        k_sort_rows_reg<<<wblocks, 256, 0, s>>>(n, yt_rp, tr, yt_col, yt_val, lists, counts, 32 - kbits);
+    else
+        k_sort_rows_warp<<<wblocks, 256, 0, s>>>(n, yt_rp, tr, yt_col, yt_val, lists, counts);
     RW_COUNT_LAUNCH();
     k_sort_rows_wsmem<<<ctx->num_sms * 4, 32 * kSortWarpsPerBlock, 0, s>>>(yt_rp, lists, counts, tr, yt_col,
                                                                             yt_val);

@@ -320,9 +320,19 @@ __device__ __forceinline__ void load_slot(const T* p, T (&v)[NR]) {
 // belongs to CTA q mod csize (warp q / csize), which writes the new value into
 // every CTA's copy through distributed shared memory; a cluster barrier ends
 // each level.  The level's FP64 work is thereby spread over csize SMs.
-template <typename T, int NR, bool CL>
+//
+// G: lanes per row (32 / G rows per warp, without clusters).  The run's one SM
+// is bound by its FP64 rate (one warp-wide FP64 instruction per 19 cycles per
+// SM on GB300, whatever the lanes active), and a row of a thin run has few
+// in-run entries, so G = 8 lets each FP64 instruction serve four rows: the
+// entry terms and a three-step reduction per group instead of a five-step one
+// per row.
+template <typename T, int NR, bool CL, int G = 32>
 __global__ void __launch_bounds__(kThinThreads) k_thin(const ThinParams<T> P) {
+    static_assert(G == 32 || !CL, "cluster thin runs take one row per warp");
+    static_assert(NR <= G && (G & (G - 1)) == 0, "lane groups");
     constexpr int U = 6;
+    constexpr int RPW = 32 / G;  // rows per warp
     extern __shared__ __align__(16) unsigned char smem[];
     namespace cg = cooperative_groups;
     const unsigned crank = CL ? cg::this_cluster().block_rank() : 0u;
@@ -336,6 +346,7 @@ __global__ void __launch_bounds__(kThinThreads) k_thin(const ThinParams<T> P) {
     int32_t* lstart = ecnt + rows;                                         // [nlev + 1] slots
     const int lane = (int)lane_id();
     const int warp = threadIdx.x >> 5;
+    const int gl = lane % G, grp = lane / G;  // lane in its group, group in the warp
     const int64_t run_e0 = P.tptr[P.pos_begin];
     const int32_t* tidx = P.tidx + run_e0;
     const T* tval = P.tval + run_e0;
@@ -430,7 +441,7 @@ __global__ void __launch_bounds__(kThinThreads) k_thin(const ThinParams<T> P) {
         R.slot = -1;
         R.n = 0;
         if (li < nlev) {
-            const int sl = lstart[li] + warp * (int)csz + (int)crank;
+            const int sl = lstart[li] + (warp * RPW + grp) * (int)csz + (int)crank;
             if (sl < lstart[li + 1]) {
                 R.slot = sl;
                 R.e0 = eoff[sl];
@@ -439,22 +450,22 @@ __global__ void __launch_bounds__(kThinThreads) k_thin(const ThinParams<T> P) {
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int k = lane + 32 * u;
+            const int k = gl + G * u;
             const bool ok = R.slot >= 0 && k < R.n;
             R.s[u] = ok ? tidx[R.e0 + k] : -1;
             R.y[u] = ok ? tval[R.e0 + k] : T(0);
         }
     };
     auto finish = [&](int slot, T mine) {
-        if (lane < P.nrhs && lane < NR) {
-            const T v = xs[(size_t)slot * NR + lane] - mine;
+        if (slot >= 0 && gl < P.nrhs && gl < NR) {
+            const T v = xs[(size_t)slot * NR + gl] - mine;
             if constexpr (CL) {
                 for (unsigned r = 0; r < csz; ++r)
-                    cg::this_cluster().map_shared_rank(xs, r)[(size_t)slot * NR + lane] = v;
+                    cg::this_cluster().map_shared_rank(xs, r)[(size_t)slot * NR + gl] = v;
             } else {
-                xs[(size_t)slot * NR + lane] = v;
+                xs[(size_t)slot * NR + gl] = v;
             }
-            __stcg(P.x + (size_t)rowid[slot] * P.nrhs + lane, v);
+            __stcg(P.x + (size_t)rowid[slot] * P.nrhs + gl, v);
         }
     };
     // flags mode: a lane reads an in-run value only once its slot is flagged
@@ -483,7 +494,7 @@ __global__ void __launch_bounds__(kThinThreads) k_thin(const ThinParams<T> P) {
     fetch(0, r0);
     for (int li = 0; li < nlev; ++li) {
         fetch(li + 1, r1);  // the next level's entries: in flight while this level computes
-        if (r0.slot >= 0) {
+        if (__any_sync(kFull, r0.slot >= 0)) {  // G = 32: r0.slot is warp-uniform
             T acc[NR];
 #pragma unroll
             for (int j = 0; j < NR; ++j) acc[j] = T(0);
@@ -496,20 +507,22 @@ __global__ void __launch_bounds__(kThinThreads) k_thin(const ThinParams<T> P) {
 #pragma unroll
                     for (int j = 0; j < NR; ++j) acc[j] += r0.y[u] * v[j];
                 }
-            for (int k = lane + 32 * U; k < r0.n; k += 32) {  // rows longer than 32*U
-                const int32_t sl = tidx[r0.e0 + k];
-                const T y = tval[r0.e0 + k];
-                wait_slot(sl);
-                T v[NR];
-                load_slot<T, NR>(xs + (size_t)sl * NR, v);
+            if (r0.slot >= 0) {
+                for (int k = gl + G * U; k < r0.n; k += G) {  // rows longer than G*U
+                    const int32_t sl = tidx[r0.e0 + k];
+                    const T y = tval[r0.e0 + k];
+                    wait_slot(sl);
+                    T v[NR];
+                    load_slot<T, NR>(xs + (size_t)sl * NR, v);
 #pragma unroll
-                for (int j = 0; j < NR; ++j) acc[j] += y * v[j];
+                    for (int j = 0; j < NR; ++j) acc[j] += y * v[j];
+                }
             }
-            finish(r0.slot, warp_sums<T, NR>(acc));
+            finish(r0.slot, group_sums<T, NR, G>(acc));
             if (flags) {
                 __syncwarp();
                 __threadfence_block();
-                if (lane == 0) ready[r0.slot] = 1;
+                if (gl == 0 && r0.slot >= 0) ready[r0.slot] = 1;
             }
         }
         // the cluster barrier also keeps every CTA alive until the last remote write
@@ -1279,7 +1292,17 @@ static rw_status solve_runs_nr(rw_context* ctx, const SolveSchedule& S, const in
         k_fill_pending_sched<T><<<grid_for(cnt, 256, ctx->num_sms * 8), 256, 0, s>>>(x, cnt);
         if ((rc = check_launch("pending fill"))) return rc;
     }
-    if ((rc = set_kernel_attr_once(ctx->device, (const void*)k_thin<T, NR, false>,
+    // one-block thin runs: lanes per row (rw_options.thin_lanes), at least NR
+    int tl = ctx->opt.thin_lanes == 8 || ctx->opt.thin_lanes == 16 ? ctx->opt.thin_lanes : 32;
+    if (tl < NR) tl = 32;
+    const void* thin_kern = (const void*)k_thin<T, NR, false>;
+    if constexpr (NR <= 8) {
+        if (tl == 8) thin_kern = (const void*)k_thin<T, NR, false, 8>;
+    }
+    if constexpr (NR <= 16) {
+        if (tl == 16) thin_kern = (const void*)k_thin<T, NR, false, 16>;
+    }
+    if ((rc = set_kernel_attr_once(ctx->device, thin_kern,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kThinSmemBudget + 16 * 1024)) ||
         (rc = set_kernel_attr_once(ctx->device, (const void*)k_thin<T, NR, true>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kThinSmemBudget + 16 * 1024)) ||
@@ -1342,7 +1365,10 @@ static rw_status solve_runs_nr(rw_context* ctx, const SolveSchedule& S, const in
                 if ((rc = check_cuda(cudaLaunchKernelEx(&cfg, k_thin<T, NR, true>, P), "thin-run cluster solve")))
                     return rc;
             } else {
-                k_thin<T, NR, false><<<1, kThinThreads, smem, s>>>(P);
+                void* args[] = {(void*)&P};
+                if ((rc = check_cuda(cudaLaunchKernel(thin_kern, dim3(1), dim3(kThinThreads), args, smem, s),
+                                     "thin-run solve")))
+                    return rc;
             }
             if ((rc = check_launch("thin-run solve"))) return rc;
         } else {

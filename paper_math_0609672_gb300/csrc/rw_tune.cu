@@ -28,6 +28,7 @@ struct Candidate {
     int solve_mode_bwd = -1;  // -1: as solve_mode
     int thin_cluster = 0;
     int thin_flags = 0;
+    int thin_lanes = 0;
 };
 
 std::string shape_key(const rw_context* ctx, const TuneTarget& T, int nrhs) {
@@ -71,6 +72,7 @@ bool cache_lookup(const char* path, const std::string& key, Candidate* c) {
             json_int(line, "cluster_width", &t.cluster_width) && json_int(line, "spmv_slices", &t.spmv_slices) &&
             json_int(line, "solve_mode", &t.solve_mode) && json_int(line, "solve_mode_bwd", &t.solve_mode_bwd) &&
             json_int(line, "thin_cluster", &t.thin_cluster) && json_int(line, "thin_flags", &t.thin_flags)) {
+            json_int(line, "thin_lanes", &t.thin_lanes);  // absent in older cache lines: 0
             *c = t;  // the last matching line wins
             found = true;
         }
@@ -84,9 +86,9 @@ void cache_store(const char* path, const std::string& key, const Candidate& c, f
     FILE* f = fopen(path, "a");
     if (!f) return;
     fprintf(f,
-            "{\"key\":\"%s\",\"solve_mode\":%d,\"solve_mode_bwd\":%d,\"thin_cluster\":%d,\"thin_flags\":%d,\"wide_slices\":%d,\"solve_blocks_per_sm\":%d,\"cluster_width\":%d,"
+            "{\"key\":\"%s\",\"solve_mode\":%d,\"solve_mode_bwd\":%d,\"thin_cluster\":%d,\"thin_flags\":%d,\"thin_lanes\":%d,\"wide_slices\":%d,\"solve_blocks_per_sm\":%d,\"cluster_width\":%d,"
             "\"spmv_slices\":%d,\"precond_ms\":%.4f,\"spmv_ms\":%.4f}\n",
-            key.c_str(), c.solve_mode, c.solve_mode_bwd, c.thin_cluster, c.thin_flags, c.wide_slices, c.solve_blocks_per_sm, c.cluster_width, c.spmv_slices, ms_pre,
+            key.c_str(), c.solve_mode, c.solve_mode_bwd, c.thin_cluster, c.thin_flags, c.thin_lanes, c.wide_slices, c.solve_blocks_per_sm, c.cluster_width, c.spmv_slices, ms_pre,
             ms_spmv);
     fclose(f);
 }
@@ -180,11 +182,22 @@ rw_status tune_t(rw_context* ctx, const TuneTarget& X, int nrhs, const T* av, co
         c.thin_flags = 1;
         cands.push_back(c);
     }
+    for (int tl : {8, 16}) {                         // hybrid, thin runs with lane groups
+        if (tl < nr) continue;
+        for (int bps : {1, 2})
+            for (int fl : {0, 1}) {
+                Candidate c{-1, bps, 0, 0, 2};
+                c.thin_lanes = tl;
+                c.thin_flags = fl;
+                cands.push_back(c);
+            }
+    }
     for (const Candidate& c : cands) {
         ctx->opt.solve_mode = c.solve_mode;
         ctx->opt.solve_mode_bwd = c.solve_mode_bwd;
         ctx->opt.thin_cluster = c.thin_cluster;
         ctx->opt.thin_flags = c.thin_flags;
+        ctx->opt.thin_lanes = c.thin_lanes;
         ctx->opt.wide_slices = c.wide_slices;
         ctx->opt.solve_blocks_per_sm = c.solve_blocks_per_sm;
         ctx->opt.cluster_width = c.cluster_width;
@@ -199,6 +212,7 @@ rw_status tune_t(rw_context* ctx, const TuneTarget& X, int nrhs, const T* av, co
             b.solve_mode_bwd = c.solve_mode_bwd;
             b.thin_cluster = c.thin_cluster;
             b.thin_flags = c.thin_flags;
+            b.thin_lanes = c.thin_lanes;
             b.wide_slices = c.wide_slices;
             b.solve_blocks_per_sm = c.solve_blocks_per_sm;
             b.cluster_width = c.cluster_width;
@@ -246,6 +260,7 @@ rw_status autotune(rw_context* ctx, const TuneTarget& X, int nrhs, rw_precision 
     ctx->opt.solve_mode_bwd = c.solve_mode_bwd;
     ctx->opt.thin_cluster = c.thin_cluster;
     ctx->opt.thin_flags = c.thin_flags;
+    ctx->opt.thin_lanes = c.thin_lanes;
     ctx->opt.wide_slices = c.wide_slices;
     ctx->opt.solve_blocks_per_sm = c.solve_blocks_per_sm;
     ctx->opt.cluster_width = c.cluster_width;

@@ -331,25 +331,28 @@ def test_autotune_installs_options_and_caches(P, ctx, tmp_path):
     c2.close()
 
 
-@pytest.mark.parametrize("mode,cw,ws,bwd,tc,bps,tf", [(1, 0, 0, -1, 0, 1, 0), (0, 256, 0, -1, 0, 1, 0),
-                                                      (0, 0, -1, -1, 0, 1, 0), (0, 256, -1, -1, 0, 1, 0),
-                                                      (1, 0, -1, -1, 0, 1, 0), (1, 0, -1, 0, 0, 1, 0),
-                                                      (0, 0, -1, 1, 0, 1, 0), (2, 0, -1, -1, 0, 1, 0),
-                                                      (2, 0, 0, -1, 0, 1, 0), (1, 0, -1, 2, 0, 1, 0),
-                                                      (2, 0, -1, -1, 8, 1, 0), (0, 0, 8, -1, 4, 1, 0),
-                                                      (2, 0, -1, -1, 0, 2, 0), (1, 0, -1, -1, 0, 2, 0),
-                                                      (2, 0, -1, -1, 0, 1, 1), (0, 0, 8, -1, 0, 1, 1)])
-def test_precond_modes_match_oracle(P, mode, cw, ws, bwd, tc, bps, tf):
+@pytest.mark.parametrize("mode,cw,ws,bwd,tc,bps,tf,tl", [(1, 0, 0, -1, 0, 1, 0, 0), (0, 256, 0, -1, 0, 1, 0, 0),
+                                                         (0, 0, -1, -1, 0, 1, 0, 0), (0, 256, -1, -1, 0, 1, 0, 0),
+                                                         (1, 0, -1, -1, 0, 1, 0, 0), (1, 0, -1, 0, 0, 1, 0, 0),
+                                                         (0, 0, -1, 1, 0, 1, 0, 0), (2, 0, -1, -1, 0, 1, 0, 0),
+                                                         (2, 0, 0, -1, 0, 1, 0, 0), (1, 0, -1, 2, 0, 1, 0, 0),
+                                                         (2, 0, -1, -1, 8, 1, 0, 0), (0, 0, 8, -1, 4, 1, 0, 0),
+                                                         (2, 0, -1, -1, 0, 2, 0, 0), (1, 0, -1, -1, 0, 2, 0, 0),
+                                                         (2, 0, -1, -1, 0, 1, 1, 0), (0, 0, 8, -1, 0, 1, 1, 0),
+                                                         (2, 0, -1, -1, 0, 1, 0, 8), (2, 0, -1, -1, 0, 1, 1, 8),
+                                                         (0, 0, 8, -1, 0, 1, 0, 16), (2, 0, -1, -1, 0, 2, 1, 16)])
+def test_precond_modes_match_oracle(P, mode, cw, ws, bwd, tc, bps, tf, tl):
     """The sync-free solve, the cluster runs and the vector rows (wide_slices
     -1: every lane reads all right-hand sides of its entries; level-scheduled,
     sync-free or hybrid, also with the backward solve in another mode, thin
     runs on one block or on a cluster, sync-free parts with one or two blocks
-    per SM, thin runs with ready flags) give the oracle's z (1e-12)."""
+    per SM, thin runs with ready flags, thin runs with 8 or 16 lanes per row)
+    give the oracle's z (1e-12)."""
     rng = np.random.default_rng(30 + mode)
     A = W.make_config(2, scale=0.25)["A"]
     c2 = P.Context(options=P.rw_options_default(solve_mode=mode, cluster_width=cw, wide_slices=ws,
                                                 solve_mode_bwd=bwd, thin_cluster=tc, solve_blocks_per_sm=bps,
-                                                thin_flags=tf))
+                                                thin_flags=tf, thin_lanes=tl))
     dA = P.CSR.from_host(A)
     F = P.rw_build_factor(c2, dA, 100, 7, 1e-3)
     ref = oracle.build_factor(A, 100, 7, 1e-3)
@@ -386,9 +389,10 @@ def test_vector_rows_with_long_dependency_lists(P):
     dA = P.CSR.from_host(A)
     r = rng.standard_normal((A.n, 4))
     zr = [oracle.precond_apply(ref, r[:, j]) for j in (0, 3)]
-    for mode, bwd, tc in ((0, -1, 0), (1, -1, 0), (1, 0, 0), (0, 1, 0), (2, -1, 0), (1, 2, 0), (2, -1, 8)):
+    for mode, bwd, tc, tl in ((0, -1, 0, 0), (1, -1, 0, 0), (1, 0, 0, 0), (0, 1, 0, 0), (2, -1, 0, 0), (1, 2, 0, 0),
+                              (2, -1, 8, 0), (2, -1, 0, 8), (0, -1, 0, 16)):
         c2 = P.Context(options=P.rw_options_default(solve_mode=mode, solve_mode_bwd=bwd, wide_slices=-1,
-                                                    thin_cluster=tc))
+                                                    thin_cluster=tc, thin_lanes=tl))
         F = P.rw_build_factor(c2, dA, 100, 7, 1e-3)
         z = _dev(np.zeros_like(r))
         P.rw_precond_apply(c2, F, _dev(r), z)
