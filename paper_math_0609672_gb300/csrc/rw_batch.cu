@@ -492,7 +492,8 @@ rw_status pcg_batch_t(rw_context* ctx, rw_batch* B, const double* const* d_b, do
         rw_status r2 = solve_runs<T>(ctx, B->bwd_sched, B->yt_rp, B->yt_col, ytv, tv_bwd, r, nullptr, w,
                                      nrhs, B->bar, true);
         if (r2) return r2;
-        return solve_runs<T>(ctx, B->fwd_sched, B->y_rp, B->y_col, yv, tv_fwd, w, dv, z, nrhs, B->bar);
+        if ((r2 = apply_inverse_diag<T>(ctx, w, dv, B->fwd_sched.n, nrhs))) return r2;
+        return solve_runs<T>(ctx, B->fwd_sched, B->y_rp, B->y_col, yv, tv_fwd, w, nullptr, z, nrhs, B->bar);
     };
     if ((rc = precond())) return rc;
     seg_dot<T, T>(nch, s, r, z, nrhs, B->chunk_row0, part);

@@ -211,35 +211,6 @@ __device__ __forceinline__ T warp_sums(T (&v)[NR]) {
     return __shfl_sync(kFull, s, ((int)lane_id() << shift) & 31);
 }
 
-// warp_sums over each group of G lanes (G a power of two, NR <= G): value j
-// of a group ends in the group's lane j.  G = 32 is warp_sums.
-template <typename T, int NR, int G>
-__device__ __forceinline__ T group_sums(T (&v)[NR]) {
-    const unsigned lane = lane_id();
-    int cnt = NR;
-#pragma unroll
-    for (int o = G / 2; o >= 1; o >>= 1) {
-        if (cnt > 1) {
-            const int half = cnt / 2;
-            const bool upper = (lane & o) != 0;
-#pragma unroll
-            for (int i = 0; i < NR / 2; ++i) {
-                if (i < half) {
-                    const T send = upper ? v[i] : v[i + half];
-                    const T keep = upper ? v[i + half] : v[i];
-                    v[i] = keep + __shfl_xor_sync(kFull, send, o);
-                }
-            }
-            cnt = half;
-        } else {
-            v[0] += __shfl_xor_sync(kFull, v[0], o);
-        }
-    }
-    constexpr unsigned span = G / NR;  // value j sits in the group's lanes j * span ...
-    const unsigned src = (lane & ~(unsigned)(G - 1)) + (((lane & (G - 1)) * span) & (G - 1));
-    return __shfl_sync(kFull, v[0], src);
-}
-
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll

@@ -313,10 +313,8 @@ __device__ void merge_row(const MergeParams& P, int32_t r, int* keys, uint32_t* 
     jsum = team_sum<TEAM, unsigned long long>(jsum, sm64);
     const unsigned long long g_all = team_sum<TEAM, unsigned long long>(gsum, sm64);
     const unsigned long long c_all = team_sum<TEAM, unsigned long long>(csum, sm64);
-    if (t == 0) {
+    if (t == 0) {  // D_kk follows in k_walk_row_d, 32 rows per FP64 instruction
         const uint64_t Jk = (uint64_t)walks + jsum;
-        const double q = __ddiv_rn((double)Jk, Mk);
-        P.D[k] = __ddiv_rn(akk, __dadd_rn(1.0, __dmul_rn(a, __dadd_rn(1.0, -q))));
         P.M[k] = (uint32_t)walks;
         P.J[k] = Jk;
         P.G[k] = (uint32_t)g_all;
@@ -379,6 +377,25 @@ __global__ void __launch_bounds__(256) k_merge_huge(const MergeParams P, int32_t
         int* keys = base;
         uint32_t* vals = reinterpret_cast<uint32_t*>(base + (size_t(1) << lg));
         merge_row<256, 0>(P, r, keys, vals, wsm, &sm64, lg);
+    }
+}
+
+// D_kk of the walk rows (Eq. newz with Eq. d): D = A_kk / (1 + a (1 - J'/M')),
+// a = S_k / A_kk, one thread per row after the merge has counted J'_k -- the
+// same operations as inside the merge, but each FP64 instruction serves 32
+// rows (GB300 issues one warp-wide FP64 instruction per 19 cycles per SM,
+// whatever the lanes active).
+__global__ void k_walk_row_d(int32_t nw, const int4* __restrict__ wrow, const int64_t* __restrict__ wbase,
+                             const int64_t* __restrict__ xbase, const double* __restrict__ S,
+                             const double* __restrict__ diag, const uint64_t* __restrict__ J, double* D) {
+    for (int32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < nw; r += gridDim.x * blockDim.x) {
+        const int32_t k = wrow[r].x;
+        const int64_t walks = wbase[r + 1] - wbase[r] + (xbase ? xbase[r + 1] - xbase[r] : 0);
+        const double Mk = (double)walks;
+        const double akk = diag[k];
+        const double a = __ddiv_rn(S[k], akk);
+        const double q = __ddiv_rn((double)J[k], Mk);
+        D[k] = __ddiv_rn(akk, __dadd_rn(1.0, __dmul_rn(a, __dadd_rn(1.0, -q))));
     }
 }
 
@@ -556,6 +573,11 @@ rw_status emit_factor(rw_context* ctx, const rw_csr* A, const Tables& T, const W
                 if ((rc = check_launch("merge (global tables)"))) return rc;
             }
         }
+    }
+    if (nw > 0) {
+        RW_COUNT_LAUNCH();
+        k_walk_row_d<<<blocks, 256, 0, s>>>(nw, T.wrow, ws.wbase, X ? X->xbase : nullptr, T.S, T.diag, fo.J, fo.d);
+        if ((rc = check_launch("walk-row diagonal"))) return rc;
     }
     RW_COUNT_LAUNCH();
     k_exact_rows<<<blocks, 256, 0, s>>>(n, T.walk_flag, A->row_ptr, A->col, A->val, T.diag_pos,
@@ -816,26 +838,44 @@ __device__ __forceinline__ void sort_row_reg(int64_t s, int64_t L, const TRec* _
     }
 }
 
-// Rows of at most 256 entries sorted in registers (key packing needs
-// n <= 2^(32 - ibits), ibits >= 8); longer rows listed for the shared-memory
-// sorts by size class, as in k_sort_rows_warp.
-__global__ void __launch_bounds__(256) k_sort_rows_reg(int32_t n, const int64_t* __restrict__ trp,
+// Size classes of the Yt rows (packed-key path): 3..6 = at most 32, 64, 128,
+// 256 entries (register sorts); 0..2 = the shared-memory and global sorts of
+// k_sort_rows_warp.  One thread per row, one atomic per class and warp.
+__global__ void __launch_bounds__(256) k_sort_classify(int32_t n, const int64_t* __restrict__ trp, int32_t* lists,
+                                                       int32_t* counts) {
+    const unsigned lt = lanemask_lt();
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x; b < n; b += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = b + threadIdx.x;
+        int cls = -1;
+        if (c < n) {
+            const int64_t L = trp[c + 1] - trp[c];
+            if (L > 0)
+                cls = L <= 32 ? 3 : L <= 64 ? 4 : L <= 128 ? 5 : L <= 256 ? 6 : L <= kSortWarp ? 0 : L <= kSortSmem ? 1 : 2;
+        }
+        const unsigned same = __match_any_sync(kFull, cls);
+        const int leader = __ffs(same) - 1;
+        int base = 0;
+        if (cls >= 0 && (int)lane_id() == leader) base = atomicAdd(&counts[cls], __popc(same));
+        base = __shfl_sync(kFull, base, leader);
+        if (cls >= 0) lists[(int64_t)cls * n + base + __popc(same & lt)] = (int32_t)c;
+    }
+}
+
+// The rows of one class, one warp per row, sorted in registers.
+template <int EPL>
+__global__ void __launch_bounds__(256) k_sort_rows_reg(const int32_t* __restrict__ rows,
+                                                       const int32_t* __restrict__ n_rows,
+                                                       const int64_t* __restrict__ trp,
                                                        const TRec* __restrict__ tr, int32_t* tcol, double* tval,
-                                                       int32_t* lists, int32_t* counts, int ibits) {
+                                                       int ibits) {
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int lane = (int)lane_id();
-    for (int64_t c = gw; c < n; c += nw) {
+    const int32_t nr = *n_rows;
+    for (int64_t r = gw; r < nr; r += nw) {
+        const int32_t c = rows[r];
         const int64_t s = trp[c], L = trp[c + 1] - s;
-        if (L == 0) continue;
-        if (L <= 32) sort_row_reg<1>(s, L, tr, tcol, tval, ibits, lane);
-        else if (L <= 64) sort_row_reg<2>(s, L, tr, tcol, tval, ibits, lane);
-        else if (L <= 128) sort_row_reg<4>(s, L, tr, tcol, tval, ibits, lane);
-        else if (L <= 256) sort_row_reg<8>(s, L, tr, tcol, tval, ibits, lane);
-        else if (lane == 0) {
-            const int cls = L <= kSortWarp ? 0 : L <= kSortSmem ? 1 : 2;
-            lists[(int64_t)cls * n + atomicAdd(&counts[cls], 1)] = (int32_t)c;
-        }
+        sort_row_reg<EPL>(s, L, tr, tcol, tval, ibits, lane);
     }
 }
 
@@ -1043,12 +1083,12 @@ rw_status transpose_factor(rw_context* ctx, int32_t n, const FactorOut& fo, int6
     if (nnz == 0) return RW_OK;
     unsigned long long* fill = alloc_n<unsigned long long>(scratch, n);
     TRec* tr = alloc_n<TRec>(scratch, nnz);
-    int32_t* lists = alloc_n<int32_t>(scratch, 3 * (int64_t)n);
-    int32_t* counts = alloc_n<int32_t>(scratch, 3);
+    int32_t* lists = alloc_n<int32_t>(scratch, 7 * (int64_t)n);
+    int32_t* counts = alloc_n<int32_t>(scratch, 7);
     if (!fill || !tr || !lists || !counts) return RW_ERR_ALLOC;
     if ((rc = check_cuda(cudaMemcpyAsync(fill, yt_rp, sizeof(int64_t) * (size_t)n, cudaMemcpyDeviceToDevice, s),
                          "copy")) ||
-        (rc = check_cuda(cudaMemsetAsync(counts, 0, 3 * sizeof(int32_t), s), "memset")))
+        (rc = check_cuda(cudaMemsetAsync(counts, 0, 7 * sizeof(int32_t), s), "memset")))
         return rc;
     const int wblocks = grid_for((int64_t)n * 32, 256, ctx->num_sms * 16);
     RW_COUNT_LAUNCH();
@@ -1056,11 +1096,24 @@ rw_status transpose_factor(rw_context* ctx, int32_t n, const FactorOut& fo, int6
     // packed 32-bit keys (k, entry) when k fits beside 8 or more index bits
     int kbits = 1;
     while (kbits < 32 && (1ll << kbits) < (int64_t)n) ++kbits;
-    RW_COUNT_LAUNCH();
-    if (kbits <= 24)
-        k_sort_rows_reg<<<wblocks, 256, 0, s>>>(n, yt_rp, tr, yt_col, yt_val, lists, counts, 32 - kbits);
-    else
+    if (kbits <= 24) {
+        // rows by size class, then one register sort per class (one unrolled
+        // network per kernel)
+        RW_COUNT_LAUNCH();
+        k_sort_classify<<<grid_for(n, 256, ctx->num_sms * 8), 256, 0, s>>>(n, yt_rp, lists, counts);
+        const int rb = ctx->num_sms * 16;
+        RW_COUNT_LAUNCH();
+        k_sort_rows_reg<1><<<rb, 256, 0, s>>>(lists + 3 * (int64_t)n, counts + 3, yt_rp, tr, yt_col, yt_val, 32 - kbits);
+        RW_COUNT_LAUNCH();
+        k_sort_rows_reg<2><<<rb, 256, 0, s>>>(lists + 4 * (int64_t)n, counts + 4, yt_rp, tr, yt_col, yt_val, 32 - kbits);
+        RW_COUNT_LAUNCH();
+        k_sort_rows_reg<4><<<rb, 256, 0, s>>>(lists + 5 * (int64_t)n, counts + 5, yt_rp, tr, yt_col, yt_val, 32 - kbits);
+        RW_COUNT_LAUNCH();
+        k_sort_rows_reg<8><<<rb, 256, 0, s>>>(lists + 6 * (int64_t)n, counts + 6, yt_rp, tr, yt_col, yt_val, 32 - kbits);
+    } else {
+        RW_COUNT_LAUNCH();
         k_sort_rows_warp<<<wblocks, 256, 0, s>>>(n, yt_rp, tr, yt_col, yt_val, lists, counts);
+    }
     RW_COUNT_LAUNCH();
     k_sort_rows_wsmem<<<ctx->num_sms * 4, 32 * kSortWarpsPerBlock, 0, s>>>(yt_rp, lists, counts, tr, yt_col,
                                                                             yt_val);

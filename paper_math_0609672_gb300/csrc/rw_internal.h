@@ -273,6 +273,14 @@ rw_status build_schedule(rw_context* ctx, int32_t n, const int64_t* rp, const in
 // (at offset 0) and the external sums of a thin run (from byte 256 on).
 constexpr int64_t kSolveWorkspaceBytes = 256 + (int64_t)4096 * 16 * 8;
 
+// w <- w / d row by row (w node-major [n][nrhs]), in place: the D^-1 step of
+// the preconditioner between the two solves, so that the forward solve's rows
+// need no division of their own (the FP64 division is a long instruction
+// sequence on GB300's narrow FP64 pipe; here one instruction serves 32 rows).
+// IEEE division as the solve would do it, so results are unchanged.
+template <typename T>
+rw_status apply_inverse_diag(rw_context* ctx, T* w, const T* d, int64_t n, int nrhs);
+
 // backward: the Y^T solve (rw_options.solve_mode_bwd may choose its mode).
 template <typename T>
 rw_status solve_runs(rw_context* ctx, const SolveSchedule& S, const int64_t* rp, const int32_t* col,

@@ -541,47 +541,70 @@ __device__ __forceinline__ unsigned long long sat_add(unsigned long long a, unsi
     return (a >= sat || b >= sat - a) ? sat : a + b;
 }
 
-// out[3 block + {0,1,2}] = {sum of V_k saturated at sat, walk rows, invalid weights}
-__global__ void __launch_bounds__(256) k_norm_total(int32_t n, const int32_t* __restrict__ rp,
-                                                    const int32_t* __restrict__ col,
-                                                    const float* __restrict__ w, double s, double min_b,
-                                                    double cap, unsigned long long sat,
-                                                    unsigned long long* __restrict__ out) {
-    unsigned long long sum = 0, cnt = 0, bad = 0;
+// The walk rows' weights in a row-indexed array (-1 for the other rows), read
+// by every pass of the search instead of the matrix; out[3 block + {0,1,2}] =
+// {0, walk rows, invalid weights}.
+__global__ void __launch_bounds__(256) k_norm_prep(int32_t n, const int32_t* __restrict__ rp,
+                                                   const int32_t* __restrict__ col, const float* __restrict__ w,
+                                                   float* __restrict__ wv, unsigned long long* __restrict__ out) {
+    unsigned long long cnt = 0, bad = 0;
     for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        if (!row_has_upper(rp, col, k)) continue;
-        ++cnt;
-        const float wk = w[k];
-        if (!(wk >= 0.f) || isinf(wk)) {
-            ++bad;
-            continue;
+        float v = -1.0f;
+        if (row_has_upper(rp, col, k)) {
+            ++cnt;
+            v = w[k];
+            if (!(v >= 0.f) || isinf(v)) {
+                ++bad;
+                v = -1.0f;
+            }
         }
-        sum = sat_add(sum, (unsigned long long)quota_fixed(wk, s, min_b, cap), sat);
+        wv[k] = v;
     }
-    __shared__ unsigned long long sm[3][8];
+    __shared__ unsigned long long sm[2][8];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        sum = sat_add(sum, __shfl_xor_sync(kFull, sum, o), sat);
         cnt += __shfl_xor_sync(kFull, cnt, o);
         bad += __shfl_xor_sync(kFull, bad, o);
     }
     const int wid = threadIdx.x >> 5;
     if (lane_id() == 0) {
-        sm[0][wid] = sum;
-        sm[1][wid] = cnt;
-        sm[2][wid] = bad;
+        sm[0][wid] = cnt;
+        sm[1][wid] = bad;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        unsigned long long a = 0, c = 0, b = 0;
+        unsigned long long c = 0, b = 0;
         for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
-            a = sat_add(a, sm[0][i], sat);
-            c += sm[1][i];
-            b += sm[2][i];
+            c += sm[0][i];
+            b += sm[1][i];
         }
-        out[3 * blockIdx.x] = a;
+        out[3 * blockIdx.x] = 0;
         out[3 * blockIdx.x + 1] = c;
         out[3 * blockIdx.x + 2] = b;
+    }
+}
+
+// out[3 block] = sum over the walk rows (wv >= 0) of V_k(s), saturated at sat.
+__global__ void __launch_bounds__(256) k_norm_sum(int32_t n, const float* __restrict__ wv, double s, double min_b,
+                                                  double cap, unsigned long long sat,
+                                                  unsigned long long* __restrict__ out) {
+    unsigned long long sum = 0;
+    for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const float wk = wv[k];
+        if (wk >= 0.f) sum = sat_add(sum, (unsigned long long)quota_fixed(wk, s, min_b, cap), sat);
+    }
+    __shared__ unsigned long long sm[8];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum = sat_add(sum, __shfl_xor_sync(kFull, sum, o), sat);
+    const int wid = threadIdx.x >> 5;
+    if (lane_id() == 0) sm[wid] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long a = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) a = sat_add(a, sm[i], sat);
+        out[3 * blockIdx.x] = a;
+        out[3 * blockIdx.x + 1] = 0;
+        out[3 * blockIdx.x + 2] = 0;
     }
 }
 
@@ -757,13 +780,11 @@ static rw_status normalize_run(rw_context* ctx, const rw_csr* A, const float* w,
     unsigned long long sat = ~0ull;
     double cap = min_b;
     rw_status rc;
-    // total(s) saturated at sat; also the walk-row and invalid-weight counts
-    auto total = [&](double sv, unsigned long long* sum, unsigned long long* cnt,
-                     unsigned long long* bad) -> rw_status {
-        RW_COUNT_LAUNCH();
-        k_norm_total<<<blocks, 256, 0, s>>>(n, A->row_ptr, A->col, w, sv, min_b, cap, sat, part);
-        rw_status r2 = check_launch("budget total");
-        if (r2) return r2;
+    float* wv = alloc_n<float>(sc, n);
+    if (!wv) return RW_ERR_ALLOC;
+    // the partial results of one launch summed on the host (saturating the first)
+    auto reduce = [&](unsigned long long* sum, unsigned long long* cnt, unsigned long long* bad) -> rw_status {
+        rw_status r2;
         if ((r2 = check_cuda(cudaMemcpyAsync(hp.data(), part, sizeof(unsigned long long) * hp.size(),
                                              cudaMemcpyDeviceToHost, s),
                              "copy")) ||
@@ -775,13 +796,24 @@ static rw_status normalize_run(rw_context* ctx, const rw_csr* A, const float* w,
             c += hp[3 * i + 1];
             b += hp[3 * i + 2];
         }
-        *sum = a;
+        if (sum) *sum = a;
         if (cnt) *cnt = c;
         if (bad) *bad = b;
         return RW_OK;
     };
+    // total(s) = sum of V_k(s) over the walk rows, saturated at sat
+    auto total = [&](double sv, unsigned long long* sum) -> rw_status {
+        RW_COUNT_LAUNCH();
+        k_norm_sum<<<blocks, 256, 0, s>>>(n, wv, sv, min_b, cap, sat, part);
+        rw_status r2 = check_launch("budget total");
+        if (r2) return r2;
+        return reduce(sum, nullptr, nullptr);
+    };
     unsigned long long sum = 0, nw = 0, bad = 0;
-    if ((rc = total(0.0, &sum, &nw, &bad))) return rc;
+    RW_COUNT_LAUNCH();
+    k_norm_prep<<<blocks, 256, 0, s>>>(n, A->row_ptr, A->col, w, wv, part);
+    if ((rc = check_launch("budget weights"))) return rc;
+    if ((rc = reduce(nullptr, &nw, &bad))) return rc;
     if (bad) {
         set_error("rw_budget_normalize: %llu walk rows with a negative, infinite or NaN weight", bad);
         return RW_ERR_ARG;
@@ -798,26 +830,47 @@ static rw_status normalize_run(rw_context* ctx, const rw_csr* A, const float* w,
     }
     const uint64_t T = (uint64_t)tot;
     const unsigned long long target = (unsigned long long)T << kFracBits;
-    sat = target + 1;
+    // totals saturate far above the target (only the comparison with the
+    // target is used), so that they can be interpolated
+    sat = 1ull << 62;
     cap = std::min((double)T, 2147483648.0);
-    if ((rc = total(0.0, &sum, nullptr, nullptr))) return rc;
+    if ((rc = total(0.0, &sum))) return rc;
     double lo = 0.0;
     if (sum < target) {
         double hi = 1.0;
+        unsigned long long sum_lo = sum;
         for (;;) {  // doubling: the first hi with total(hi) > target
-            if ((rc = total(hi, &sum, nullptr, nullptr))) return rc;
+            if ((rc = total(hi, &sum))) return rc;
             if (sum > target) break;
             lo = hi;
+            sum_lo = sum;
             if (sum == target || hi > 1e300) break;
             hi *= 2.0;
         }
         if (sum > target) {
-            for (int it = 0; it < 2200; ++it) {  // bisection: total(lo) <= target < total(hi)
-                const double mid = 0.5 * (lo + hi);
+            // total(lo) <= target < total(hi): the answer is the largest double
+            // s in [lo, hi) with total(s) <= target (total does not decrease
+            // in s), the point where plain bisection stops, so the search may
+            // take any points inside the bracket.  Odd steps interpolate the
+            // totals, even steps bisect (the bracket at least halves every two
+            // steps); it stops when lo and hi are adjacent doubles.
+            unsigned long long sum_hi = sum;
+            for (int it = 0; it < 4400; ++it) {
+                double mid = 0.5 * (lo + hi);
+                if ((it & 1) && sum_hi > sum_lo) {
+                    const double f = (double)(target - sum_lo) / (double)(sum_hi - sum_lo);
+                    const double g = lo + f * (hi - lo);
+                    if (g > lo && g < hi) mid = g;
+                }
                 if (!(mid > lo && mid < hi)) break;
-                if ((rc = total(mid, &sum, nullptr, nullptr))) return rc;
-                if (sum <= target) lo = mid;
-                else hi = mid;
+                if ((rc = total(mid, &sum))) return rc;
+                if (sum <= target) {
+                    lo = mid;
+                    sum_lo = sum;
+                } else {
+                    hi = mid;
+                    sum_hi = sum;
+                }
             }
         }
     }

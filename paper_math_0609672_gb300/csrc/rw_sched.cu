@@ -315,6 +315,35 @@ __device__ __forceinline__ void load_slot(const T* p, T (&v)[NR]) {
     }
 }
 
+// warp_sums over each group of G lanes (G a power of two, NR <= G): value j
+// of a group ends in the group's lane j.  G = 32 is warp_sums.
+template <typename T, int NR, int G>
+__device__ __forceinline__ T group_sums(T (&v)[NR]) {
+    const unsigned lane = lane_id();
+    int cnt = NR;
+#pragma unroll
+    for (int o = G / 2; o >= 1; o >>= 1) {
+        if (cnt > 1) {
+            const int half = cnt / 2;
+            const bool upper = (lane & o) != 0;
+#pragma unroll
+            for (int i = 0; i < NR / 2; ++i) {
+                if (i < half) {
+                    const T send = upper ? v[i] : v[i + half];
+                    const T keep = upper ? v[i + half] : v[i];
+                    v[i] = keep + __shfl_xor_sync(kFull, send, o);
+                }
+            }
+            cnt = half;
+        } else {
+            v[0] += __shfl_xor_sync(kFull, v[0], o);
+        }
+    }
+    constexpr unsigned span = G / NR;  // value j sits in the group's lanes j * span ...
+    const unsigned src = (lane & ~(unsigned)(G - 1)) + (((lane & (G - 1)) * span) & (G - 1));
+    return __shfl_sync(kFull, v[0], src);
+}
+
 // CL: the run is solved by a thread-block cluster instead of one block.  Every
 // CTA keeps the whole run's x values in its shared memory; row q of a level
 // belongs to CTA q mod csize (warp q / csize), which writes the new value into
@@ -1072,6 +1101,24 @@ __global__ void __launch_bounds__(512, MINB) k_syncfree_vec(const FreeParams<T> 
         if (owner) st_relaxed(P.x + (size_t)cur.row * P.nrhs + jo, cur.b - sum);
     }
 }
+
+template <typename T>
+__global__ void k_inverse_diag(T* w, const T* __restrict__ d, int64_t n, int nrhs) {
+    const int64_t cnt = n * nrhs;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x)
+        w[i] = w[i] / d[i / nrhs];
+}
+
+template <typename T>
+rw_status apply_inverse_diag(rw_context* ctx, T* w, const T* d, int64_t n, int nrhs) {
+    const int64_t cnt = n * nrhs;
+    if (cnt == 0) return RW_OK;
+    RW_COUNT_LAUNCH();
+    k_inverse_diag<T><<<grid_for(cnt, 256, ctx->num_sms * 8), 256, 0, ctx->stream>>>(w, d, n, nrhs);
+    return check_launch("inverse diagonal");
+}
+template rw_status apply_inverse_diag<double>(rw_context*, double*, const double*, int64_t, int);
+template rw_status apply_inverse_diag<float>(rw_context*, float*, const float*, int64_t, int);
 
 template <typename T>
 __global__ void k_fill_pending_sched(T* x, int64_t cnt) {

@@ -416,7 +416,8 @@ static rw_status precond_t(rw_context* ctx, const FactorView& F, const T* yv, co
                                  thin_values<T>(*F.bwd_sched), r, nullptr, w, nrhs, F.bar, true);
     if (rc) return rc;
     if (tm && tm->on) cudaEventRecord(ctx->ev[6], ctx->stream);
-    rc = solve_runs<T>(ctx, *F.fwd_sched, F.y_rp, F.y_col, yv, thin_values<T>(*F.fwd_sched), w, d,
+    if ((rc = apply_inverse_diag<T>(ctx, w, d, F.n, nrhs))) return rc;
+    rc = solve_runs<T>(ctx, *F.fwd_sched, F.y_rp, F.y_col, yv, thin_values<T>(*F.fwd_sched), w, nullptr,
                        z, nrhs, F.bar);
     if (tm && tm->on) {
         cudaEventRecord(ctx->ev[7], ctx->stream);

@@ -101,7 +101,8 @@ rw_status time_precond(rw_context* ctx, const TuneTarget& X, const T* yv, const 
     auto once = [&]() -> rw_status {
         rw_status r2 = solve_runs<T>(ctx, *X.bwd, X.yt_rp, X.yt_col, ytv, tvb, r, nullptr, w, nrhs, X.bar, true);
         if (r2) return r2;
-        return solve_runs<T>(ctx, *X.fwd, X.y_rp, X.y_col, yv, tvf, w, dv, z, nrhs, X.bar);
+        if ((r2 = apply_inverse_diag<T>(ctx, w, dv, X.fwd->n, nrhs))) return r2;
+        return solve_runs<T>(ctx, *X.fwd, X.y_rp, X.y_col, yv, tvf, w, nullptr, z, nrhs, X.bar);
     };
     if ((rc = once())) return rc;
     cudaEventRecord(ctx->ev[10], s);
