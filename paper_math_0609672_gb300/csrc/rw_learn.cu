@@ -77,10 +77,11 @@ __global__ void k_features(int32_t n, const int32_t* __restrict__ rp, const int3
         const int deg = up + lo;
         double ent = 0.0, nex = 0.0, ndeg = 0.0;
         int64_t up2 = 0;
+        const double inv = 1.0 / wsum;  // one division per row (FP64 division is long on GB300)
         for (int32_t p = s; p < e; ++p) {
             const int32_t c = col[p];
             if (c == k) continue;
-            const double pr = -val[p] / wsum;
+            const double pr = -val[p] * inv;
             if (pr > 0.0) ent -= pr * log(pr);
             nex += exr[c];
             ndeg += (double)ndeg_of[c];
