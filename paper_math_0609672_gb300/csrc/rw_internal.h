@@ -91,22 +91,28 @@ inline int grid_for(int64_t work, int block, int max_blocks) {
 // ---- build path (rw_tables.cu, rw_walk.cu, rw_emit.cu, rw_levels.cu) -------
 
 // Walk tables of one matrix, in the layout read by the walk kernel.
-//  tab:   32-byte sectors of 8 uint32 words in three regions.  A node's slots
+//  tab:   32-byte sectors of 8 uint32 words in four regions.  A node's slots
 //         (slot 0 = header, slot s + 1 = successor s in ascending column
 //         order) form ng = ceil((1 + deg) / 4) groups; slot j lives in group
 //         j / 4, word j % 4 its threshold (0 for the header slot: always
 //         passed), word 4 + j % 4 its successor word (the successor's node
-//         index, bit 31 set when that node has a summary; deg for the header
-//         slot, 0 for padding).
+//         index in bits 27..0, in bits 31..28 its class: 0 without a
+//         summary, ng for 3 <= ng <= 8, 15 above; deg for the header slot,
+//         0 for padding).
 //           sectors [0, 2n): node j's groups at 2j, 2j + 1 when ng <= 2;
 //           sectors [2n, 3n): node j's summary at 2n + j when ng > 2 -- deg in
 //             word 0, in words 1..7 the last threshold of groups 0..6
 //             (0xFFFFFFFF past the last);
-//           sectors [3n, 3n + G): the groups of the nodes with a summary.
-//         The summaries (32 bytes per node, dense) and gbase stay in L2 on
-//         large matrices, so a hop to a node with a summary costs one DRAM
-//         sector (its group) besides two L2 reads issued together; a node of
-//         at most seven neighbours costs one or two sectors of group 0/1.
+//           sectors [3n, 11n): node j's groups at 3n + 8j when 2 < ng <= 8
+//             (a fixed stride, so that a group's address needs no load);
+//           sectors [11n, 11n + G): the groups of the nodes with more than
+//             eight, at gbase[j] (a prefix over those nodes).
+//         The summaries (32 bytes per node, dense) stay in L2 on large
+//         matrices, so a hop to a node with a summary costs one DRAM sector
+//         (its group) besides one L2 read (two, with gbase, above eight
+//         groups); a node of at most seven neighbours costs one or two
+//         sectors of group 0/1.  Sectors [3n, 11n) are allocated for every
+//         node but touched only by the nodes that use it.
 //  gbase: [n] the sector of each node's group 0.
 //  fthr:  per walk row a block [updeg, lowdeg, ft_0 .. ft_{updeg-1}, pad].
 // The walk works with node indices throughout (home: below the start row,
@@ -116,7 +122,7 @@ struct Tables {
     uint32_t* tab = nullptr;
     uint32_t* gbase = nullptr;    // [n] sector of each node's group 0
     uint32_t* fthr = nullptr;
-    uint32_t* toff = nullptr;     // [n+1] groups of the nodes with a summary before each node (prefix)
+    uint32_t* toff = nullptr;     // [n+1] groups of the nodes with more than eight groups before each node
     uint32_t* foff8 = nullptr;    // [n+1] first-step blocks (32-byte blocks)
     int32_t* deg = nullptr;       // [n] off-diagonal count
     int32_t* lowdeg = nullptr;    // [n] entries with column < row

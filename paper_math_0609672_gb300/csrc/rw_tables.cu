@@ -162,9 +162,10 @@ __global__ void k_row_info(int32_t n, int64_t nnz, const int32_t* __restrict__ r
         lowdeg[l] = lo;
         dpos[l] = dp;
         // groups of four slots, ceil((1 + deg) / 4); a node of more than two
-        // has a summary and its groups in the third region of the tables
+        // has a summary, a node of more than eight its groups in the fourth
+        // region of the tables (counted here for their prefix)
         const uint32_t ng = (uint32_t)(1 + d + 3) / 4u;
-        blk_full[l] = ng > 2u ? ng : 0u;
+        blk_full[l] = ng > 8u ? ng : 0u;
         blk_first[l] = up > 0 ? (uint32_t)(2 + up + 7) / 8u : 0u;
         walk_flag[l] = up > 0 ? 1u : 0u;
     }
@@ -185,7 +186,9 @@ __global__ void k_fill_tables(int32_t n, const int32_t* __restrict__ rp,
         diag[l] = dg;
         const uint64_t ng = ((uint64_t)d + 4u) / 4u;
         const bool big = ng > 2u;
-        const uint64_t g0 = big ? 3u * (uint64_t)n + toff[l] : 2u * (uint64_t)l;
+        const uint64_t g0 = !big      ? 2u * (uint64_t)l
+                            : ng <= 8u ? 3u * (uint64_t)n + 8u * (uint64_t)l
+                                       : 11u * (uint64_t)n + toff[l];
         gbase[l] = (uint32_t)g0;
         // slot j: threshold at word 8 * (g0 + j / 4) + j % 4, successor word at + 4
         auto word = [&](uint64_t j) -> uint32_t* { return tab + (g0 + j / 4u) * 8u + (j % 4u); };
@@ -200,7 +203,10 @@ __global__ void k_fill_tables(int32_t n, const int32_t* __restrict__ rp,
             w[0] = cumulative_threshold(c, dg);
             const int32_t jc = col[p];
             const uint32_t ngc = (uint32_t)(deg[jc] + 4) / 4u;
-            w[4] = (uint32_t)jc | (ngc > 2u ? 0x80000000u : 0u);  // flag: the successor has a summary
+            // bits 31..28: the successor's group class (0: no summary, 3..8:
+            // its ng, 15: more than eight groups)
+            const uint32_t cls = ngc <= 2u ? 0u : ngc <= 8u ? ngc : 15u;
+            w[4] = (uint32_t)jc | (cls << 28);
             ++j;
         }
         for (; j < ng * 4u; ++j) {
@@ -281,7 +287,11 @@ rw_status build_tables(rw_context* ctx, const rw_csr* A, Tables& T, Pool& pool) 
                          "copy")))
         return rc;
     if ((rc = read_status(ctx, "matrix validation"))) return rc;
-    T.sectors = 3u * (uint64_t)n + hs[0];
+    T.sectors = 11u * (uint64_t)n + hs[0];
+    if (n >= (1 << 28)) {
+        set_error("walk tables: n = %d exceeds the 2^28 node-index range of the successor words", n);
+        return RW_ERR_CAPACITY;
+    }
     if (T.sectors >= 0x80000000ull) {
         set_error("walk tables: %llu sectors exceed the 2^31 sector-index range", (unsigned long long)T.sectors);
         return RW_ERR_CAPACITY;

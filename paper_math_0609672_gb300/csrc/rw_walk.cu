@@ -9,10 +9,12 @@
 // them, so the next node is known when the group arrives.  A hop to a node of
 // degree <= 7 reads its group 0 (and group 1 only when the draw passes group
 // 0); a hop to a node of higher degree reads the node's summary (the last
-// threshold of each group; a dense node-indexed region that stays in L2) and
-// its group base together, then the one group that holds the drawn successor.
-// Random reads from HBM are limited per sector, not per byte, so the kernel is
-// bound by the DRAM sectors per hop: one for 27-point nodes.
+// threshold of each group; a dense node-indexed region that stays in L2), then
+// the one group that holds the drawn successor, at an address the successor
+// word gives without a load (nodes of more than 31 neighbours: a group base
+// read beside the summary).  Random reads from HBM are limited per sector,
+// not per byte, so the kernel is bound by the DRAM sectors per hop: one for
+// 27-point nodes.
 //
 // Walk w of row k (rows 0..k-1 are homes, ground absorbs):
 //   step 1: draw 0 picks an upper neighbour j > k with probability
@@ -57,8 +59,19 @@ __device__ __forceinline__ uint4 ld_nc4(const uint32_t* p) {
     return __ldg(reinterpret_cast<const uint4*>(p));
 }
 
-constexpr uint32_t kSumFlag = 0x80000000u;    // successor word: node with a summary
-constexpr uint32_t kNodeMask = 0x7FFFFFFFu;
+// Successor word: node index in bits 27..0, the node's group class in bits
+// 31..28 (0: at most two groups, no summary; 3..8: its ng, groups at the
+// fixed slot 3n + 8 * node; 15: more than eight groups, at gbase[node]).
+constexpr uint32_t kNodeMask = 0x0FFFFFFFu;
+constexpr uint32_t kHugeClass = 15u;
+// Late in a launch (every walk started, at most kSpecLanes walks left in the
+// warp) and on very long walks, a hop prefetches the node's groups to L2
+// together with the summary read: it then waits for one DRAM round trip
+// instead of an L2 read followed by a DRAM read.  The long walks set the
+// launch's length; while the memory system is busy the extra sectors would
+// cost more than they save.
+constexpr uint64_t kSpecHops = 16384u;
+constexpr int kSpecLanes = 8;
 
 // 32 bytes (eight words) in one load; p must be 32-byte aligned (sectors are).
 __device__ __forceinline__ void ld_nc8(const uint32_t* p, uint4& lo, uint4& hi) {
@@ -106,27 +119,42 @@ __device__ __forceinline__ uint32_t count_le4(const uint4 t, uint32_t u) {
     return (uint32_t)(t.x <= u) + (uint32_t)(t.y <= u) + (uint32_t)(t.z <= u) + (uint32_t)(t.w <= u);
 }
 
-// One transition from the node of successor word cw (node index, bit 31 set
-// when the node has a summary), with draw u: the least slot j whose threshold
-// exceeds u (thresholds do not decrease along the slots, the header slot
-// counts as passed), i.e. successor j - 1, ground if j > deg.  Returns that
-// successor's word; *ground is set when the walk is absorbed.  n2 = 2n, the
-// first summary sector.
+// Bulk prefetch of `bytes` (a multiple of 16) at p (16-byte aligned) into L2.
+__device__ __forceinline__ void prefetch_l2(const uint32_t* p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// One transition from the node of successor word cw with draw u: the least
+// slot j whose threshold exceeds u (thresholds do not decrease along the
+// slots, the header slot counts as passed), i.e. successor j - 1, ground if
+// j > deg.  Returns that successor's word; *ground is set when the walk is
+// absorbed.  n: the matrix's node count (the summaries start at sector 2n,
+// the fixed group slots at 3n).  spec: prefetch the node's groups to L2
+// before the summary read returns.
 __device__ __forceinline__ uint32_t hop_node(const uint32_t* __restrict__ tab, const uint32_t* __restrict__ gbase,
-                                             uint32_t n2, uint32_t cw, uint32_t u, bool* ground, uint64_t keep,
-                                             uint64_t stream) {
+                                             uint32_t n, uint32_t cw, uint32_t u, bool* ground, uint64_t keep,
+                                             uint64_t stream, bool spec) {
     const uint32_t node = cw & kNodeMask;
+    const uint32_t cls = cw >> 28;
     uint4 t, w;
     uint32_t deg, j = 0xFFFFFFFFu, nw = 0u;
-    if (cw & kSumFlag) {
-        // summary and group base together (both kept in L2)
-        ld_nc8_hint(tab + (size_t)(n2 + node) * 8u, t, w, keep);
-        const uint32_t g0 = ld_nc_hint(gbase + node, keep);
+    if (cls != 0u) {
+        const uint32_t* sum = tab + ((size_t)2u * n + node) * 8u;
+        const uint32_t* gp;
+        if (cls != kHugeClass) {
+            gp = tab + ((size_t)3u * n + (size_t)8u * node) * 8u;
+            if (spec) prefetch_l2(gp, cls * 32u);
+            ld_nc8_hint(sum, t, w, keep);  // kept in L2
+        } else {
+            // summary and group base together (both kept in L2)
+            ld_nc8_hint(sum, t, w, keep);
+            gp = tab + (size_t)ld_nc_hint(gbase + node, keep) * 8u;
+        }
         deg = t.x;
         const uint32_t ng = (deg + 4u) >> 2;
         uint32_t g = (uint32_t)(t.y <= u) + (uint32_t)(t.z <= u) + (uint32_t)(t.w <= u) + count_le4(w, u);
         for (; g < ng; ++g) {  // one iteration unless the node has more than seven groups
-            ld_nc8_hint(tab + (size_t)(g0 + g) * 8u, t, w, stream);
+            ld_nc8_hint(gp + (size_t)g * 8u, t, w, stream);
             if (g == 0u) t.x = 0u;
             const uint32_t c = count_le4(t, u);
             if (c < 4u) {
@@ -178,7 +206,7 @@ __global__ void __launch_bounds__(256) k_walk(const WalkParams P) {
     // the walking lane's matrix (fixed for a single-matrix launch)
     const uint32_t* tab = P.m0.tab;
     const uint32_t* gbase = P.m0.gbase;
-    uint32_t key0 = P.m0.key0, key1 = P.m0.key1, tag = P.m0.tag, n2 = 2u * P.m0.n;
+    uint32_t key0 = P.m0.key0, key1 = P.m0.key1, tag = P.m0.tag, nn = P.m0.n;
     uint64_t h = 0;
     Philox4 rnd{0u, 0u, 0u, 0u};
     unsigned long long my_hops = 0;
@@ -228,7 +256,7 @@ __global__ void __launch_bounds__(256) k_walk(const WalkParams P) {
                     key0 = mw.key0;
                     key1 = mw.key1;
                     tag = mw.tag;
-                    n2 = 2u * mw.n;
+                    nn = mw.n;
                 }
                 k = (uint32_t)info.x;
                 w = (uint32_t)(widx - P.wbase[r]) + (P.wofs ? P.wofs[r] : 0u);
@@ -260,7 +288,9 @@ __global__ void __launch_bounds__(256) k_walk(const WalkParams P) {
             pool_next += ntake;
             idle = __ballot_sync(kFull, !active);
         }
-        if (__ballot_sync(kFull, active) == 0u) break;
+        const unsigned live = __ballot_sync(kFull, active);
+        if (live == 0u) break;
+        const bool sparse = exhausted && __popc(live) <= kSpecLanes;
 
         // ---- one hop of every active lane ----
         bool stepping = false;
@@ -285,7 +315,8 @@ __global__ void __launch_bounds__(256) k_walk(const WalkParams P) {
             bool done = false;
             ++h;
             bool ground;
-            const uint32_t nw = hop_node(tab, gbase, n2, coff, u, &ground, keep, stream);
+            const bool spec = sparse || h >= kSpecHops;
+            const uint32_t nw = hop_node(tab, gbase, nn, coff, u, &ground, keep, stream, spec);
             const uint32_t nb = nw & kNodeMask;
             if (ground) {
                 end = -1;
@@ -413,7 +444,7 @@ __global__ void __launch_bounds__(256) k_walk_reuse(const WalkParams P, const Re
     uint32_t k = 0, w = 0, coff = 0, ret = 0;
     const uint32_t* tab = P.m0.tab;
     const uint32_t* gbase = P.m0.gbase;
-    const uint32_t key0 = P.m0.key0, key1 = P.m0.key1, tag = P.m0.tag, n2 = 2u * P.m0.n;
+    const uint32_t key0 = P.m0.key0, key1 = P.m0.key1, tag = P.m0.tag, nn = P.m0.n;
     uint64_t h = 0;
     Philox4 rnd{0u, 0u, 0u, 0u};
     unsigned long long my_hops = 0;
@@ -522,7 +553,7 @@ __global__ void __launch_bounds__(256) k_walk_reuse(const WalkParams P, const Re
                 const uint32_t u = q == 0u ? rnd.v0 : q == 1u ? rnd.v1 : q == 2u ? rnd.v2 : rnd.v3;
                 ++h;
                 bool ground;
-                to_word = hop_node(tab, gbase, n2, coff, u, &ground, keep, stream);
+                to_word = hop_node(tab, gbase, nn, coff, u, &ground, keep, stream, false);
                 const uint32_t nb = to_word & kNodeMask;
                 if (ground) {
                     outcome = 2;
