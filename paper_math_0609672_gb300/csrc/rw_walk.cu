@@ -121,7 +121,7 @@ __device__ __forceinline__ uint32_t count_le4(const uint4 t, uint32_t u) {
 
 // Bulk prefetch of `bytes` (a multiple of 16) at p (16-byte aligned) into L2.
 __device__ __forceinline__ void prefetch_l2(const uint32_t* p, uint32_t bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes));
 }
 
 // One transition from the node of successor word cw with draw u: the least

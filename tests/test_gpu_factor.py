@@ -353,6 +353,44 @@ def _reuse_cases():
         yield f"random{j}", A, int(rng.integers(1, 50)), [0.0, 1e-3, 0.1][j]
 
 
+def _degree_classes_matrix(seed):
+    """Random R-matrix whose nodes span every transition-table layout: at most
+    two groups of four slots (degree <= 7), three to eight groups (8..31) and
+    more than eight (32 and up), so every path of a hop is taken."""
+    rng = np.random.default_rng(seed)
+    n = 3000
+    perm = rng.permutation(n)
+    ei, ej = [perm[:-1]], [perm[1:]]
+    extra = rng.choice([0, 1, 4, 8, 13, 18, 24, 30, 45, 150], size=n,
+                       p=[0.45, 0.2, 0.1, 0.07, 0.06, 0.05, 0.04, 0.02, 0.008, 0.002])
+    for i in range(n):
+        nb = rng.choice(n, size=int(extra[i]), replace=False)
+        nb = nb[nb != i]
+        ei.append(np.minimum(nb, i))
+        ej.append(np.maximum(nb, i))
+    ei, ej = np.concatenate(ei), np.concatenate(ej)
+    g = np.exp(rng.uniform(np.log(0.1), np.log(10.0), ei.size))
+    ei, ej, g = W._dedup_edges(ei, ej, g)
+    rs = W.conductance_sums(n, ei, ej, g)
+    excess = np.where(rng.random(n) < 0.3, rng.uniform(0.0, 0.05, n) * rs, 0.0)
+    excess[rng.integers(n)] = 0.1 * rs.max()
+    A = W.assemble(n, ei, ej, g, excess)
+    deg = np.diff(A.rowptr) - 1
+    ng = (deg + 4) // 4
+    assert (ng <= 2).any() and ((ng > 2) & (ng <= 8)).any() and (ng > 8).any()
+    assert len(set(ng[(ng > 2) & (ng <= 8)].tolist())) == 6   # every class 3..8
+    return A
+
+
+@pytest.mark.parametrize("reuse", [False, True])
+def test_degree_classes_bit_exact(P, ctx, ctx_reuse, reuse):
+    A = _degree_classes_matrix(21)
+    c = ctx_reuse if reuse else ctx
+    t = gpu_factor(P, c, A, 40, 4242, 1e-3)
+    ref = oracle.build_factor(A, 40, 4242, 1e-3, reuse=reuse, records=True)
+    assert_factor_equal(t, ref)
+
+
 @pytest.mark.parametrize("case", list(range(8)))
 def test_reuse_bit_exact(P, ctx_reuse, case):
     name, A, walks, drop = list(_reuse_cases())[case]
