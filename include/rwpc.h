@@ -56,8 +56,10 @@ typedef enum {
     RW_ERR_CUDA = -7,           /* a CUDA runtime call failed */
     RW_ERR_TIMEOUT = -8,        /* a bounded device-side wait gave up */
     RW_ERR_CAPACITY = -9        /* a fixed-size table is too small: a row has more than 2^29 possible
-                                   end points (merge table limit), or n * nrhs exceeds the 2^20-entry
-                                   scratch array of rw_precond_apply_static */
+                                   end points (merge table limit), a matrix has 2^28 nodes or more or
+                                   needs 2^31 walk-table sectors or more (the walk tables' index
+                                   range), or n * nrhs exceeds the 2^20-entry scratch array of
+                                   rw_precond_apply_static */
 } rw_status;
 
 typedef enum { RW_FP64 = 0, RW_FP32_MIXED = 1 } rw_precision;
